@@ -1,0 +1,236 @@
+/*
+ * fcpd.h -- C ABI of the GB300 (sm_103a) Fast Coherent Point Drift EM loop.
+ *
+ * Method: X.-W. Feng, D.-Z. Feng, Y. Zhu, "Fast Coherent Point Drift",
+ * arXiv 2006.06281.  Notation is the paper's:
+ *   X  (M x D)  model points -- they move        (Sec. I, Sec. II)
+ *   Y  (N x D)  scene points -- they stay fixed
+ *   T  = X + Phi W, the transformed model points (Eq. 9-11)
+ *   Phi (M x M) Gaussian Gram matrix of X, width beta (Eq. 11)
+ *   w  outlier weight, 0 <= w < 1 (Eq. 2); lambda regulariser (Eq. 7);
+ *   sigma2 the variance of the Gaussian mixture (Eq. 1, Eq. 18).
+ *
+ * One registration = setup (Gram matrix + its eigendecomposition, Eq. 16,
+ * done once) followed by EM iterations.  Each iteration runs on the GPU only:
+ *   E-step   Eq. 4 posterior with the uniform-outlier constant c, then the
+ *            corresponding constraint Eq. 5 (each row of P rescaled to sum 1),
+ *            reduced to Ytil = P^ Y without ever storing the M x N matrix P;
+ *   M-step   Eq. 17 (full basis) or Eq. 20 (top-K basis):
+ *            T = X + U diag(l_i / (l_i + lambda sigma2)) U^T (Ytil - X);
+ *   variance Eq. 18 over the row-normalised posterior, with the new T.
+ *
+ * Conventions for every entry point
+ *   - Point arrays are row-major, point-major (D contiguous values per
+ *     point), element type double for CPD_FP64 and float for CPD_FP32.
+ *   - A point-array pointer may be HOST memory (pageable or pinned) or DEVICE
+ *     memory of the current CUDA device; the library tells them apart with
+ *     cudaPointerGetAttributes and stages host data through its own device
+ *     buffers.  The caller owns every array it passes; the library keeps no
+ *     pointer to caller memory after a call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work is enqueued on it.  A call that returns host values (sigma2_out,
+ *     iters_done, a host output array) synchronises that stream first.
+ *   - Errors: every call returns a cpd_status.  Arguments are validated
+ *     before any device work; on CPD_EINVAL nothing is enqueued and outputs
+ *     are untouched.  No C++ exception crosses this boundary.
+ *     cpd_last_error() gives a one-line description of the last failure on
+ *     the calling thread.
+ *   - A numeric failure found on the device (a row of P whose mass underflows
+ *     to 0 so Eq. 5 cannot normalise it, or a variance that is not positive
+ *     and finite) sets a device status word; later kernels of the same
+ *     context become no-ops and the next synchronising call returns
+ *     CPD_ENUMERIC.
+ *   - Only D = 3 is implemented (the paper's experiments are 3-D point sets).
+ *   - Host-side fault injection for tests: environment variable CPD_FAULT =
+ *     "alloc" (first device allocation of cpd_setup fails -> CPD_ENOMEM),
+ *     "solver" (the eigensolver reports failure -> CPD_ESOLVER) or
+ *     "nan_sigma" (the initial variance is NaN -> CPD_ENUMERIC on the first
+ *     iteration).  Nothing is faulted on the GPU.
+ */
+#ifndef FCPD_H
+#define FCPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FCPD_ABI_VERSION 1
+
+typedef enum {
+    CPD_OK = 0,
+    CPD_EINVAL = 1,    /* invalid argument                               */
+    CPD_ENOMEM = 2,    /* device allocation failed                       */
+    CPD_ECUDA = 3,     /* a CUDA runtime call failed                     */
+    CPD_ESOLVER = 4,   /* the eigensolver failed (Eq. 16)                */
+    CPD_ENUMERIC = 5,  /* row mass 0 (Eq. 5) or sigma2 not positive/finite */
+    CPD_ETIMEOUT = 6,  /* a bounded device wait gave up                  */
+    CPD_ESTATE = 7     /* call not valid in the context's current state  */
+} cpd_status;
+
+typedef enum {
+    CPD_FP64 = 0,      /* double everywhere                              */
+    CPD_FP32 = 1       /* float points/basis, FP64 scalar reductions     */
+} cpd_precision;
+
+/* Registration parameters (Sec. IV "Parameter settings": w, beta, lambda). */
+typedef struct {
+    int32_t D;            /* point dimension; must be 3                        */
+    int32_t precision;    /* cpd_precision                                     */
+    double  w;            /* outlier weight, 0 <= w < 1 (Eq. 2)                */
+    double  beta;         /* Gaussian kernel width > 0 (Eq. 10-11)             */
+    double  lambda;       /* regularisation weight > 0 (Eq. 7, Eq. 15)         */
+    double  sigma2_init;  /* initial variance; <= 0 means "from the data":
+                             sum_mn |y_n - x_m|^2 / (D M N)                    */
+    int64_t K;            /* 0 or M: full eigenbasis (Eq. 17);
+                             1..M-1: the K largest eigenpairs (Eq. 19-20);
+                             K > M is rejected with CPD_EINVAL                 */
+    int32_t max_iter;     /* iteration count used by cpd_register (> 0)        */
+    int32_t flags;        /* reserved, must be 0                               */
+    double  tol;          /* > 0: stop once RMS_m |T_k - T_(k-1)| <= tol;
+                             0: run the requested number of iterations        */
+} cpd_params;
+
+typedef struct cpd_ctx cpd_ctx;   /* opaque; owned by the library */
+
+/* ABI version of the loaded library (FCPD_ABI_VERSION). */
+int32_t cpd_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *cpd_status_string(cpd_status s);
+
+/* One-line description of the last failure on the calling thread ("" if none). */
+const char *cpd_last_error(void);
+
+/* Fill *p with defaults: D=3, FP32, w=0.1, beta=2, lambda=2, sigma2 from data,
+ * full basis, max_iter=50, tol=0. */
+void cpd_params_default(cpd_params *p);
+
+/*
+ * Setup (done once per model point set; Eq. 11, Eq. 16, Eq. 19).
+ *   X      M x D points (host or device), element type per p->precision.
+ *   M      number of model points, 1 <= M <= 46340.
+ *   stream cudaStream_t all work of this context is enqueued on.
+ *   out    receives the new context (owned by the caller; free with
+ *          cpd_destroy).
+ * Builds Phi in FP64 on the device, eigendecomposes it in FP64 (cuSOLVER,
+ * the one library call of the path, setup only), clamps the eigenvalues at 0,
+ * keeps the K largest (or all) eigenpairs in descending order, stores the
+ * basis in the working precision and frees Phi.  Synchronises `stream`.
+ * Errors: CPD_EINVAL (arguments), CPD_ENOMEM, CPD_ESOLVER, CPD_ECUDA; *out is
+ * left untouched on error.
+ */
+cpd_status cpd_setup(const void *X, int64_t M, const cpd_params *p, void *stream, cpd_ctx **out);
+
+/*
+ * Run EM iterations (Eq. 4, 5, 17/20, 18) against scene Y.
+ *   Y          N x D scene points (host or device), context precision.
+ *   N          number of scene points, >= 1.
+ *   n_iter     iterations to run (>= 0); with p->tol > 0 fewer may run.
+ *   T_out      if non-NULL, receives the current T (M x D, host or device).
+ *   sigma2_out if non-NULL, receives the current sigma2 (host double).
+ *   iters_done if non-NULL, receives the total iteration count of the
+ *              context (host int).
+ * The context keeps T, sigma2 and the iteration count between calls, so a
+ * registration can be run in pieces; the first call after cpd_setup or
+ * cpd_reset starts from W = 0 (T = X) and the initial variance.  A call with
+ * a different Y (or N) continues from the current state with the new scene.
+ * Iterations are replayed from a captured CUDA graph on `stream`; the call
+ * synchronises only if it returns host values.
+ */
+cpd_status cpd_iterate(cpd_ctx *ctx, const void *Y, int64_t N, int32_t n_iter,
+                       void *T_out, double *sigma2_out, int32_t *iters_done);
+
+/*
+ * cpd_iterate with per-kernel timing, for benchmarking: runs n_iter
+ * (1..4096) iterations from one captured CUDA graph that also holds a timing
+ * event after every kernel, synchronises `stream`, and writes 8 floats to
+ * phase_ms (host): the milliseconds summed over the n_iter iterations of
+ * [0] E pass A, [1] its reduction (+ c, Eq. 4), [2] E pass B, [3] its
+ * reduction (Eq. 5), [4] projection U^T (Ytil - X), [5] diagonal update,
+ * [6] expansion T = X + U B with the Eq. 18 epilogue; [7] the whole span
+ * from the first kernel's start to the last kernel's end.
+ */
+cpd_status cpd_iterate_profiled(cpd_ctx *ctx, const void *Y, int64_t N, int32_t n_iter,
+                                float *phase_ms);
+
+/* Restart the context's registration: T = X, iteration count 0, sigma2
+ * re-initialised on the next cpd_iterate.  The eigenbasis is kept. */
+cpd_status cpd_reset(cpd_ctx *ctx);
+
+/*
+ * Optional ground truth for Eq. 22: Yhat (M x D, host or device) is the true
+ * position of each model point.  Each following iteration records
+ * RMSE = sqrt(mean_m |t_m - yhat_m|^2); if rmse_tol > 0 the loop stops at the
+ * first iteration whose RMSE <= rmse_tol.  Yhat = NULL clears it.
+ */
+cpd_status cpd_set_ground_truth(cpd_ctx *ctx, const void *Yhat, double rmse_tol);
+
+/* Synchronise and read the context state: sigma2, iterations completed, and
+ * the device status word (a cpd_status; CPD_OK if no device failure). */
+cpd_status cpd_get_state(cpd_ctx *ctx, double *sigma2, int32_t *iters, int32_t *device_status);
+
+/*
+ * Per-iteration history of the current registration (synchronises).
+ * Entry k (0 <= k < n) describes iteration k+1: sigma2 after it (Eq. 18),
+ * the Eq. 3 log-likelihood evaluated in its E-step, and its Eq. 22 RMSE
+ * (NaN without ground truth).  Any output may be NULL.  Only the first
+ * 65536 iterations are recorded.  CPD_EINVAL if n exceeds the count run.
+ */
+cpd_status cpd_get_history(cpd_ctx *ctx, int32_t n, double *sigma2_hist, double *loglik_hist,
+                           double *rmse_hist);
+
+/* W of the last M-step (Eq. 17 / Eq. 20), M x D into W_out (host or device).
+ * CPD_ESTATE before the first iteration. */
+cpd_status cpd_get_W(cpd_ctx *ctx, void *W_out);
+
+/* The kept eigenbasis (Eq. 16 / 19): U_out (M x K row-major, context
+ * precision, host or device; may be NULL) and lam_out (K doubles, host,
+ * descending, clamped at 0; may be NULL).  K is cpd_basis_rank(ctx). */
+cpd_status cpd_get_basis(cpd_ctx *ctx, void *U_out, double *lam_out);
+int64_t cpd_basis_rank(const cpd_ctx *ctx);
+
+/*
+ * One M-step on the context's basis (Eq. 17 / 20), without touching the
+ * context's registration state: T_out = X + U diag(l/(l + lambda sigma2))
+ * U^T (Ytil - X) and, if W_out is non-NULL, W_out = U diag(1/(l + lambda
+ * sigma2)) U^T (Ytil - X).  Ytil, T_out, W_out: M x D (host or device).
+ */
+cpd_status cpd_mstep(cpd_ctx *ctx, const void *Ytil, double sigma2, void *T_out, void *W_out);
+
+/*
+ * One E-step, no context needed (Eq. 4 then Eq. 5):
+ *   T (M x D), Y (N x D): host or device, element type per `precision`.
+ *   Ytil_out (M x D, required): sum_n p^_mn y_n, the row-normalised estimate.
+ *   P1_out   (M doubles, optional, host or device): row mass sum_n p_mn
+ *            before Eq. 5.
+ *   den_out  (N doubles, optional, host or device): column denominators
+ *            sum_m e_mn + c of Eq. 4.
+ *   sums_out (2 host doubles, optional): [0] = sum_m sum_n p^_mn |y_n - t_m|^2
+ *            (the Eq. 18 numerator at T itself), [1] = Eq. 3 log-likelihood.
+ * Scratch is allocated on `stream` for the call and freed before return.
+ * Synchronises `stream`.  CPD_ENUMERIC if a row mass is 0 or not finite.
+ */
+cpd_status cpd_estep(const void *T, int64_t M, const void *Y, int64_t N, int32_t precision,
+                     double sigma2, double w, void *Ytil_out, void *P1_out, void *den_out,
+                     double *sums_out, void *stream);
+
+/*
+ * Whole registration: cpd_setup, p->max_iter iterations of cpd_iterate (fewer
+ * with p->tol > 0), outputs, cpd_destroy.
+ *   T_out (required) M x D; W_out (optional) M x D; sigma2_out, iters_done
+ *   optional host outputs.
+ */
+cpd_status cpd_register(const void *X, int64_t M, const void *Y, int64_t N, const cpd_params *p,
+                        void *stream, void *T_out, void *W_out, double *sigma2_out,
+                        int32_t *iters_done);
+
+/* Free a context (NULL is ignored).  Synchronises its stream first. */
+void cpd_destroy(cpd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCPD_H */

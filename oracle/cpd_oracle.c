@@ -23,6 +23,13 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#else
+static int omp_get_num_threads(void) { return 1; }
+static int omp_get_thread_num(void) { return 0; }
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_ENUMERIC 5
@@ -155,38 +162,53 @@ int fcpd_oracle_estep(const double *T, int64_t M, const double *Y, int64_t N, in
  * its eigendecomposition (Eq. 16): Phi U = U Lambda, hence
  *   T = X + U diag(l_i / (l_i + lambda sigma2)) U^T (Ytil - X).
  * U is M x K row-major (U[m*K + i] = i-th eigenvector, m-th entry), lam[K].
- * A (K x D, optional) receives U^T (Ytil - X); W (M x D, optional) the
+ * A (K x D, required) receives U^T (Ytil - X); W (M x D, optional) the
  * coefficients of Eq. 17 / Eq. 20.
  */
 void fcpd_oracle_mstep(const double *U, const double *lam, int64_t M, int64_t K,
                        const double *X, const double *Ytil, int32_t D,
                        double lambda, double sigma2, double *T, double *W, double *A)
 {
-    double *Acoef = A;
-    /* U^T (Ytil - X): one K x D coefficient per eigenvector */
-#pragma omp parallel for schedule(static)
+    /* the diagonal update: only (Lambda + lambda sigma2 I)^-1 changes per
+     * iteration (the paper's point after Eq. 17) */
+    double *dinv = NULL, *sdiag = NULL;
+    dinv = (double *)malloc((size_t)K * sizeof(double));
+    sdiag = (double *)malloc((size_t)K * sizeof(double));
     for (int64_t i = 0; i < K; ++i) {
-        for (int32_t d = 0; d < D; ++d) {
-            double s = 0.0;
-            for (int64_t m = 0; m < M; ++m)
-                s += U[m * K + i] * (Ytil[m * D + d] - X[m * D + d]);
-            Acoef[i * D + d] = s;
+        dinv[i] = 1.0 / (lam[i] + lambda * sigma2);
+        sdiag[i] = lam[i] * dinv[i];
+    }
+    /* A = U^T (Ytil - X): for each (i, d) a sum over m in ascending order.
+     * Threads split the columns i; each walks the rows m in order. */
+#pragma omp parallel
+    {
+        int nt = omp_get_num_threads(), t = omp_get_thread_num();
+        int64_t i0 = K * t / nt, i1 = K * (t + 1) / nt;
+        for (int64_t i = i0; i < i1; ++i)
+            for (int32_t d = 0; d < D; ++d) A[i * D + d] = 0.0;
+        for (int64_t m = 0; m < M; ++m) {
+            for (int64_t i = i0; i < i1; ++i) {
+                double u = U[m * K + i];
+                for (int32_t d = 0; d < D; ++d)
+                    A[i * D + d] += u * (Ytil[m * D + d] - X[m * D + d]);
+            }
         }
     }
-    /* the diagonal update: only (Lambda + lambda sigma2 I)^-1 changes per iteration */
+    /* T = X + U diag(l_i / (l_i + lambda sigma2)) A ; W = U diag(1/(l_i + lambda sigma2)) A */
 #pragma omp parallel for schedule(static)
     for (int64_t m = 0; m < M; ++m) {
         for (int32_t d = 0; d < D; ++d) {
             double t = 0.0, wv = 0.0;
             for (int64_t i = 0; i < K; ++i) {
-                double inv = 1.0 / (lam[i] + lambda * sigma2);
-                t += U[m * K + i] * (lam[i] * inv) * Acoef[i * D + d];
-                wv += U[m * K + i] * inv * Acoef[i * D + d];
+                t += U[m * K + i] * sdiag[i] * A[i * D + d];
+                wv += U[m * K + i] * dinv[i] * A[i * D + d];
             }
             T[m * D + d] = X[m * D + d] + t;
             if (W) W[m * D + d] = wv;
         }
     }
+    free(dinv);
+    free(sdiag);
 }
 
 /*

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the fast-CPD C ABI (include/fcpd.h).
+
+Argument marshalling only: every step of the EM loop runs in libfcpd.so's
+sm_103a kernels.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays;
+outputs follow the inputs (CUDA tensors in, CUDA tensors out; host arrays in,
+numpy arrays out).  There is no CPU fallback: if the library has not been
+built, the first call raises.
+
+Names follow the paper (Fast Coherent Point Drift, arXiv 2006.06281):
+X model points (they move), Y scene points, T = X + Phi W, w outlier
+weight, beta kernel width, lam the regularisation weight lambda.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfcpd.so")
+
+FP64, FP32 = 0, 1
+STATUS = {0: "CPD_OK", 1: "CPD_EINVAL", 2: "CPD_ENOMEM", 3: "CPD_ECUDA", 4: "CPD_ESOLVER",
+          5: "CPD_ENUMERIC", 6: "CPD_ETIMEOUT", 7: "CPD_ESTATE"}
+OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
+
+# Every symbol include/fcpd.h declares (checked by the tests).
+EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
+           "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
+           "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
+           "cpd_estep", "cpd_register", "cpd_destroy"]
+
+
+class CpdParams(C.Structure):
+    _fields_ = [("D", C.c_int32), ("precision", C.c_int32), ("w", C.c_double), ("beta", C.c_double),
+                ("lam", C.c_double), ("sigma2_init", C.c_double), ("K", C.c_int64),
+                ("max_iter", C.c_int32), ("flags", C.c_int32), ("tol", C.c_double)]
+
+
+class CpdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libfcpd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = C.CDLL(LIB_PATH)
+            vp, i64, i32, d, dp = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int32)
+            pp = C.POINTER(CpdParams)
+            sig = {
+                "cpd_abi_version": ([], i32),
+                "cpd_status_string": ([C.c_int], C.c_char_p),
+                "cpd_last_error": ([], C.c_char_p),
+                "cpd_params_default": ([pp], None),
+                "cpd_setup": ([vp, i64, pp, vp, C.POINTER(vp)], C.c_int),
+                "cpd_iterate": ([vp, vp, i64, i32, vp, dp, ip], C.c_int),
+                "cpd_iterate_profiled": ([vp, vp, i64, i32, C.POINTER(C.c_float)], C.c_int),
+                "cpd_reset": ([vp], C.c_int),
+                "cpd_set_ground_truth": ([vp, vp, d], C.c_int),
+                "cpd_get_state": ([vp, dp, ip, ip], C.c_int),
+                "cpd_get_history": ([vp, i32, vp, vp, vp], C.c_int),
+                "cpd_get_W": ([vp, vp], C.c_int),
+                "cpd_get_basis": ([vp, vp, vp], C.c_int),
+                "cpd_basis_rank": ([vp], i64),
+                "cpd_mstep": ([vp, vp, d, vp, vp], C.c_int),
+                "cpd_estep": ([vp, i64, vp, i64, i32, d, d, vp, vp, vp, dp, vp], C.c_int),
+                "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
+                "cpd_destroy": ([vp], None),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        msg = load().cpd_last_error().decode()
+        raise CpdError(status, msg)
+
+
+# ----------------------------------------------------------------- marshalling
+def _is_torch(a):
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _dtype_of(precision):
+    return np.float64 if precision == FP64 else np.float32
+
+
+def _prep(a, precision, name):
+    """Returns (object kept alive, pointer, is_cuda)."""
+    want = _dtype_of(precision)
+    if _is_torch(a):
+        import torch
+        td = torch.float64 if precision == FP64 else torch.float32
+        if a.dtype != td:
+            raise TypeError(f"{name}: expected {td}, got {a.dtype}")
+        a = a.contiguous()
+        return a, a.data_ptr(), a.is_cuda
+    arr = np.ascontiguousarray(a, dtype=want)
+    return arr, arr.ctypes.data, False
+
+
+def _out_like(n, cols, precision, cuda, device=None):
+    if cuda:
+        import torch
+        td = torch.float64 if precision == FP64 else torch.float32
+        t = torch.empty((n, cols), dtype=td, device=device)
+        return t, t.data_ptr()
+    arr = np.empty((n, cols), dtype=_dtype_of(precision))
+    return arr, arr.ctypes.data
+
+
+def _stream_handle(stream, cuda):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    if cuda:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    return 0
+
+
+def make_params(precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, max_iter=50, tol=0.0,
+                sigma2_init=0.0) -> CpdParams:
+    p = CpdParams()
+    load().cpd_params_default(C.byref(p))
+    p.precision, p.w, p.beta, p.lam, p.K = int(precision), float(w), float(beta), float(lam), int(K)
+    p.max_iter, p.tol, p.sigma2_init = int(max_iter), float(tol), float(sigma2_init)
+    return p
+
+
+class Context:
+    """A registration context: setup (Gram matrix + eigendecomposition) once,
+    then EM iterations against one or more scenes."""
+
+    def __init__(self, X, precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, tol=0.0, sigma2_init=0.0,
+                 stream=None):
+        lib = load()
+        self.precision = precision
+        self._X, px, self.cuda = _prep(X, precision, "X")
+        self.device = self._X.device if self.cuda else None
+        self.M = int(self._X.shape[0])
+        self.stream = _stream_handle(stream, self.cuda)
+        self.params = make_params(precision, w, beta, lam, K, 0, tol, sigma2_init)
+        h = C.c_void_p()
+        _check(lib.cpd_setup(px, self.M, C.byref(self.params), self.stream, C.byref(h)))
+        self._h = h
+        self.K = int(lib.cpd_basis_rank(h))
+
+    def iterate(self, Y, n_iter, want_T=True):
+        """Runs n_iter EM iterations; returns (T or None, sigma2, iterations so far)."""
+        Yk, py, ycuda = _prep(Y, self.precision, "Y")
+        T, pt = _out_like(self.M, 3, self.precision, ycuda, self.device) if want_T else (None, None)
+        s2, it = C.c_double(0), C.c_int32(0)
+        _check(load().cpd_iterate(self._h, py, int(Yk.shape[0]), int(n_iter), pt, C.byref(s2), C.byref(it)))
+        return T, s2.value, it.value
+
+    def iterate_into(self, Y, n_iter, T_out):
+        """Runs n_iter iterations writing T into the caller's buffer T_out
+        (host or device); returns (sigma2, iterations so far)."""
+        Yk, py, _ = _prep(Y, self.precision, "Y")
+        _, pt, _ = _prep(T_out, self.precision, "T_out")
+        s2, it = C.c_double(0), C.c_int32(0)
+        _check(load().cpd_iterate(self._h, py, int(Yk.shape[0]), int(n_iter), pt, C.byref(s2), C.byref(it)))
+        return s2.value, it.value
+
+    def iterate_profiled(self, Y, n_iter):
+        """n_iter iterations from a graph with timing events after every
+        kernel; returns the 8 phase times (ms) described in fcpd.h."""
+        Yk, py, _ = _prep(Y, self.precision, "Y")
+        out = (C.c_float * 8)()
+        _check(load().cpd_iterate_profiled(self._h, py, int(Yk.shape[0]), int(n_iter), out))
+        return list(out)
+
+    def iterate_async(self, Y, n_iter, T_out=None):
+        """Enqueues n_iter iterations without synchronising (device arrays only)."""
+        Yk, py, _ = _prep(Y, self.precision, "Y")
+        pt = None
+        if T_out is not None:
+            _, pt, _ = _prep(T_out, self.precision, "T_out")
+        _check(load().cpd_iterate(self._h, py, int(Yk.shape[0]), int(n_iter), pt, None, None))
+
+    def reset(self):
+        _check(load().cpd_reset(self._h))
+
+    def set_ground_truth(self, Yhat, rmse_tol=0.0):
+        if Yhat is None:
+            _check(load().cpd_set_ground_truth(self._h, None, float(rmse_tol)))
+            return
+        self._gt, p, _ = _prep(Yhat, self.precision, "Yhat")
+        _check(load().cpd_set_ground_truth(self._h, p, float(rmse_tol)))
+
+    def state(self):
+        s2, it, ds = C.c_double(0), C.c_int32(0), C.c_int32(0)
+        _check(load().cpd_get_state(self._h, C.byref(s2), C.byref(it), C.byref(ds)))
+        return s2.value, it.value, ds.value
+
+    def history(self, n):
+        a, b, c = np.empty(n), np.empty(n), np.empty(n)
+        _check(load().cpd_get_history(self._h, int(n), a.ctypes.data, b.ctypes.data, c.ctypes.data))
+        return dict(sigma2=a, loglik=b, rmse=c)
+
+    def W(self):
+        W, pw = _out_like(self.M, 3, self.precision, self.cuda, self.device)
+        _check(load().cpd_get_W(self._h, pw))
+        return W
+
+    def basis(self):
+        U = np.empty((self.M, self.K), dtype=_dtype_of(self.precision))
+        lam = np.empty(self.K)
+        _check(load().cpd_get_basis(self._h, U.ctypes.data, lam.ctypes.data))
+        return U, lam
+
+    def mstep(self, Ytil, sigma2, want_W=False):
+        Yk, py, ycuda = _prep(Ytil, self.precision, "Ytil")
+        T, pt = _out_like(self.M, 3, self.precision, ycuda, self.device)
+        W, pw = _out_like(self.M, 3, self.precision, ycuda, self.device) if want_W else (None, None)
+        _check(load().cpd_mstep(self._h, py, float(sigma2), pt, pw))
+        return (T, W) if want_W else T
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cpd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def estep(T, Y, sigma2, w, precision=FP32, stream=None):
+    """One E-step (Eq. 4 + Eq. 5).  Returns dict(Ytil, P1, den, vsum, loglik)."""
+    Tk, pt, tcuda = _prep(T, precision, "T")
+    Yk, py, _ = _prep(Y, precision, "Y")
+    M, N = int(Tk.shape[0]), int(Yk.shape[0])
+    dev = Tk.device if tcuda else None
+    Ytil, pyt = _out_like(M, 3, precision, tcuda, dev)
+    if tcuda:
+        import torch
+        P1 = torch.empty(M, dtype=torch.float64, device=dev)
+        den = torch.empty(N, dtype=torch.float64, device=dev)
+        pp1, pden = P1.data_ptr(), den.data_ptr()
+    else:
+        P1, den = np.empty(M), np.empty(N)
+        pp1, pden = P1.ctypes.data, den.ctypes.data
+    sums = (C.c_double * 2)()
+    _check(load().cpd_estep(pt, M, py, N, int(precision), float(sigma2), float(w), pyt, pp1, pden, sums,
+                            _stream_handle(stream, tcuda)))
+    return dict(Ytil=Ytil, P1=P1, den=den, vsum=sums[0], loglik=sums[1])
+
+
+def register(X, Y, precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, max_iter=50, tol=0.0,
+             sigma2_init=0.0, want_W=False, stream=None):
+    """Whole registration through cpd_register.  Returns (T, W or None, sigma2, iters)."""
+    Xk, px, xcuda = _prep(X, precision, "X")
+    Yk, py, _ = _prep(Y, precision, "Y")
+    M = int(Xk.shape[0])
+    dev = Xk.device if xcuda else None
+    T, pt = _out_like(M, 3, precision, xcuda, dev)
+    W, pw = _out_like(M, 3, precision, xcuda, dev) if want_W else (None, None)
+    p = make_params(precision, w, beta, lam, K, max_iter, tol, sigma2_init)
+    s2, it = C.c_double(0), C.c_int32(0)
+    _check(load().cpd_register(px, M, py, int(Yk.shape[0]), C.byref(p), _stream_handle(stream, xcuda),
+                               pt, pw, C.byref(s2), C.byref(it)))
+    return T, W, s2.value, it.value

@@ -1,0 +1,174 @@
+// Internal declarations of the sm_103a fast-CPD library (not part of the ABI).
+//
+// Device data layout (all buffers owned by a context, sized at setup /
+// first iterate):
+//   X4, T4    M model points as 4-vectors {x, y, z, 0}       (FP32: float4, FP64: dvec4)
+//   Y4        N scene points {x, y, z, |y|^2}
+//   Yb        N scene points prepared for E-pass B: {q y, -log2 den_n} (FP32) or
+//             {y, 1/den_n} (FP64)
+//   U         M x ldU row-major eigenbasis, ldU = K rounded up to 16 bytes;
+//             column k is the k-th largest eigenvector of Phi (Eq. 16, 19)
+//   lam       K eigenvalues (double), descending, clamped at 0
+//   Yt4       M rows {Ytil_m (3), V_m / P1_m} after the E-step (Eq. 5)
+//   R4        M rows {Ytil_m - x_m (3), 0}: the M-step right-hand side (Eq. 17)
+//   B4, C4    K rows s_k A_k and A_k / (l_k + lambda sigma2)
+//   partials  split-reduction scratch of the E-step and the M-step
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fcpd.h"
+
+namespace fcpd {
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kHistCap = 65536;
+
+struct __align__(32) dvec4 {
+  double x, y, z, w;
+};
+
+template <typename F> struct Vec;
+template <> struct Vec<float> { using t4 = float4; };
+template <> struct Vec<double> { using t4 = dvec4; };
+
+// Registration state kept on the device so that iterations need no host sync.
+struct DevState {
+  double sigma2;        // variance used by the next E-step / M-step
+  double loglik;        // Eq. 3 at the last E-step
+  double last_dT2;      // sum_m |T_k - T_(k-1)|^2 of the last iteration
+  double last_rmse;     // Eq. 22 of the last iteration (NaN without ground truth)
+  double w;             // outlier weight
+  double lambda;        // regulariser
+  double tol;           // RMS(T_k - T_(k-1)) stop threshold (0: off)
+  double gt_tol;        // RMSE stop threshold (0: off)
+  double vsum;          // sum_m V_m / P1_m of the last E-step (Eq. 18 numerator at T)
+  double* hist;         // 3 x kHistCap: sigma2, log-likelihood, RMSE per iteration
+  int iter;             // iterations completed
+  int iter_target;      // iterations run until iter == iter_target
+  int status;           // cpd_status of a device-side failure (0 = none)
+  int done;             // tolerance reached
+  int has_gt;           // ground truth present
+  int M, N, K;
+  int n_flag_cols;      // FP32: columns whose Gaussian sum needs the exact log-domain path
+  int n_flag_rows;      // FP32: rows whose mass needs the exact log-domain path
+  unsigned int ticket_a;  // last-block counters (reset by their last block)
+  unsigned int ticket_b;
+  unsigned int ticket_m;
+  unsigned int ticket_e;
+};
+
+static_assert(sizeof(DevState) == 136, "DevState layout changed: update the benchmark's transfer count");
+
+// True when the current iteration must not run (target reached, converged,
+// or a device failure recorded).  Read once per block at kernel entry.
+__device__ __forceinline__ bool iteration_gated(const DevState* st) {
+  return st->iter >= st->iter_target || st->done || st->status != 0;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Sum of a double over a block (blockDim.x multiple of 32, <= 1024).
+// Result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------- launchers
+struct EstepPlan {
+  int a_col_tiles, a_row_chunks, a_rows_per_chunk;   // pass A grid
+  int b_row_tiles, b_col_chunks, b_cols_per_chunk;   // pass B grid
+  int64_t partA_elems, partB_elems;                  // scratch sizes (elements of F)
+  int64_t redA_blocks, redB_blocks;                  // reduce grids
+  int64_t sums_elems;                                // double scratch for block sums
+  int64_t flags_elems;                               // int scratch: flagged rows + columns
+};
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms);
+
+struct MstepPlan {
+  int p_col_tiles, p_row_chunks, p_rows_per_chunk;   // projection grid
+  int e_blocks;                                      // expansion grid
+  int64_t partP_elems;                               // scratch (elements of F)
+  int64_t sums_elems;                                // double scratch for block sums
+};
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms);
+
+// Optional `ev` arrays: an event is recorded (as an external event-record
+// node when captured) after each kernel: 4 for the E-step (pass A, its
+// reduction, pass B, its reduction), 3 for the M-step (projection, diagonal
+// update, expansion).
+inline void record_after(cudaEvent_t* ev, int i, cudaStream_t s) {
+  if (ev) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+}
+
+// E-step: passes A and B with their reductions.  Reads T4, Y4 and st->sigma2;
+// writes Yt4, R4 (R4 needs X4; may be null to skip) and per-row P1 (double,
+// optional), per-column den (double, optional).  Gated by `gate` (iteration mode)
+// or always run (standalone).
+template <typename F>
+void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
+                  int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
+                  F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
+                  typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
+                  bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr);
+
+// M-step: projection A = U^T R, diagonal update, expansion T = X + U B and
+// the Eq. 18 variance in the epilogue.  With `iteration` false the state is
+// not advanced (standalone M-step: T_out receives T, no sigma2 update).
+template <typename F>
+void launch_mstep(const MstepPlan& pl, const F* U, int64_t ldU, const double* lam, int64_t M,
+                  int64_t K, const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
+                  const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
+                  const typename Vec<F>::t4* Yhat4, F* partP, double* sums,
+                  typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, DevState* st,
+                  bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr);
+
+// W = U C (C from the last M-step), written as 4-vectors.
+template <typename F>
+void launch_w(const MstepPlan& pl, const F* U, int64_t ldU, int64_t M, int64_t K,
+              const typename Vec<F>::t4* C4, typename Vec<F>::t4* W4, cudaStream_t s);
+
+// Setup helpers.
+void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double* Phi, cudaStream_t s);
+template <typename F>
+void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, const double* w,
+                          double* lam, cudaStream_t s);
+template <typename F>
+void launch_sigma2_init(const typename Vec<F>::t4* X4, int64_t M, const typename Vec<F>::t4* Y4,
+                        int64_t N, double* scratch, DevState* st, cudaStream_t s);
+
+// Packing between caller arrays (row-major n x 3, float or double) and 4-vectors.
+// `with_norm` stores |p|^2 in the 4th lane, else 0.
+template <typename F>
+void launch_pack(const F* src, int64_t n, typename Vec<F>::t4* dst, bool with_norm, cudaStream_t s);
+template <typename F>
+void launch_unpack(const typename Vec<F>::t4* src, int64_t n, F* dst, cudaStream_t s);
+void launch_begin_iterations(DevState* st, int n_iter, cudaStream_t s);
+void launch_state_init(DevState* st, double sigma2, cudaStream_t s);
+void launch_state_params(DevState* st, double w, double lambda, double tol, double gt_tol, int has_gt,
+                         double* hist, int64_t M, int64_t N, int64_t K, cudaStream_t s);
+template <typename F>
+void launch_residual(const typename Vec<F>::t4* Yt4, const typename Vec<F>::t4* X4, typename Vec<F>::t4* R4,
+                     int64_t M, cudaStream_t s);
+// Sets kernel attributes (dynamic shared memory); call before any stream capture.
+void mstep_prepare();
+
+}  // namespace fcpd

@@ -1,0 +1,617 @@
+// E-step of fast CPD on sm_103a: Eq. 4 (posterior with the uniform-outlier
+// constant c) followed by Eq. 5 (the corresponding constraint: every row of P
+// rescaled to sum to 1), reduced to Ytil = P^ Y without storing P.
+//
+// The M x N posterior is evaluated twice, n-body style, instead of being
+// materialised:
+//   pass A  each thread owns scene points y_n (columns) in registers and
+//           streams model-point tiles t_m through shared memory, accumulating
+//           den_n = sum_m e_mn (+ c in the reduction);
+//   pass B  each thread owns model points t_m (rows) and streams scene tiles
+//           {y_n, den_n} through shared memory, accumulating
+//           P1_m = sum_n e_mn/den_n, sum_n (e_mn/den_n) y_n and
+//           V_m = sum_n (e_mn/den_n) |y_n - t_m|^2.
+// Both passes split their long dimension over blocks; a reduction kernel
+// sums the split partials in a fixed order (deterministic), applies Eq. 5
+// (Ytil_m = PY_m / P1_m) and checks the row mass.
+//
+// FP32 form: coordinates are pre-scaled by q = sqrt(log2(e) / (2 sigma2)), so
+// e_mn = 2^(-|q y_n - q t_m|^2) is one MUFU ex2 per pair, and pass B folds
+// 1/den_n into the exponent: e_mn / den_n = 2^(-log2 den_n - |q y - q t|^2).
+// FP32 flushes Gaussians below 2^-126 (about 13 sigma away).  A column whose
+// denominator or a row whose mass falls below 2^-88 / 2^-90 (where flushed
+// terms could matter) is listed and recomputed exactly by one warp in the log
+// domain (max exponent first, then the shifted sum), so FP32 results stay
+// valid wherever the FP64 definition is; the status becomes CPD_ENUMERIC only
+// if the mass is 0 even in double precision.
+// FP64 form: exp(-|y - t|^2 / (2 sigma2)) in double, times 1/den_n.
+#include "common.cuh"
+
+#include <math.h>
+
+#include <algorithm>
+
+namespace fcpd {
+
+namespace {
+
+constexpr int kThreadsA = 128;   // pass A block
+constexpr int kColsA32 = 8;      // scene points per thread, FP32
+constexpr int kColsA64 = 4;      // scene points per thread, FP64
+constexpr int kTileA = 128;      // model points per shared-memory tile
+constexpr int kThreadsB = 128;   // pass B block
+constexpr int kRowsB32 = 4;      // model points per thread, FP32
+constexpr int kRowsB64 = 2;      // model points per thread, FP64
+constexpr int kTileB = 128;      // scene points per shared-memory tile
+constexpr int kThreadsR = 256;   // reduction kernels
+constexpr int kThreadsF = 256;   // log-domain fix-up kernels (one warp per item)
+constexpr float kFar = 1e18f;    // padding coordinate: its Gaussian weight is exactly 0
+constexpr double kColFloor = 0x1p-88;   // FP32 column sums below this take the exact path
+constexpr double kRowFloor = 0x1p-90;   // FP32 row masses below this take the exact path
+
+__device__ __forceinline__ float scale_q(double sigma2) {
+  return (float)sqrt(kLog2e / (2.0 * sigma2));
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------------------ pass A
+__global__ void __launch_bounds__(kThreadsA)
+passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
+          int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_cols = 0;
+  __shared__ float4 sT[kTileA];
+  const float q = scale_q(st->sigma2);
+  const int nbase = blockIdx.x * (kThreadsA * kColsA32) + threadIdx.x;
+  float yx[kColsA32], yy[kColsA32], yz[kColsA32], acc[kColsA32];
+#pragma unroll
+  for (int j = 0; j < kColsA32; ++j) {
+    const int n = nbase + j * kThreadsA;
+    if (n < N) {
+      const float4 y = Y4[n];
+      yx[j] = q * y.x; yy[j] = q * y.y; yz[j] = q * y.z;
+    } else {
+      yx[j] = -kFar; yy[j] = -kFar; yz[j] = -kFar;
+    }
+    acc[j] = 0.f;
+  }
+  const int r0 = blockIdx.y * rows_per_chunk;
+  const int r1 = min(M, r0 + rows_per_chunk);
+  for (int base = r0; base < r1; base += kTileA) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileA; i += kThreadsA) {
+      const int m = base + i;
+      float4 t = make_float4(kFar, kFar, kFar, 0.f);
+      if (m < r1) {
+        t = T4[m];
+        t.x *= q; t.y *= q; t.z *= q;
+      }
+      sT[i] = t;
+    }
+    __syncthreads();
+    const int cnt = min(kTileA, r1 - base);
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i) {
+      const float4 t = sT[i];
+#pragma unroll
+      for (int j = 0; j < kColsA32; ++j) {
+        const float dx = yx[j] - t.x, dy = yy[j] - t.y, dz = yz[j] - t.z;
+        float d2 = dx * dx;
+        d2 = fmaf(dy, dy, d2);
+        d2 = fmaf(dz, dz, d2);
+        acc[j] += ex2_approx(-d2);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kColsA32; ++j) {
+    const int n = nbase + j * kThreadsA;
+    if (n < N) partA[(size_t)blockIdx.y * N + n] = acc[j];
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsA)
+passA_f64(const dvec4* __restrict__ T4, int M, int rows_per_chunk, const dvec4* __restrict__ Y4,
+          int N, double* __restrict__ partA, const DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  __shared__ dvec4 sT[kTileA];
+  const double inv2s2 = 1.0 / (2.0 * st->sigma2);
+  const int nbase = blockIdx.x * (kThreadsA * kColsA64) + threadIdx.x;
+  double yx[kColsA64], yy[kColsA64], yz[kColsA64], acc[kColsA64];
+#pragma unroll
+  for (int j = 0; j < kColsA64; ++j) {
+    const int n = nbase + j * kThreadsA;
+    const dvec4 y = n < N ? Y4[n] : dvec4{0, 0, 0, 0};
+    yx[j] = y.x; yy[j] = y.y; yz[j] = y.z;
+    acc[j] = 0.0;
+  }
+  const int r0 = blockIdx.y * rows_per_chunk;
+  const int r1 = min(M, r0 + rows_per_chunk);
+  for (int base = r0; base < r1; base += kTileA) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileA; i += kThreadsA) {
+      const int m = base + i;
+      sT[i] = m < r1 ? T4[m] : dvec4{0, 0, 0, 0};
+    }
+    __syncthreads();
+    const int cnt = min(kTileA, r1 - base);
+    for (int i = 0; i < cnt; ++i) {
+      const dvec4 t = sT[i];
+#pragma unroll
+      for (int j = 0; j < kColsA64; ++j) {
+        const double dx = yx[j] - t.x, dy = yy[j] - t.y, dz = yz[j] - t.z;
+        acc[j] += exp(-(dx * dx + dy * dy + dz * dz) * inv2s2);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kColsA64; ++j) {
+    const int n = nbase + j * kThreadsA;
+    if (n < N) partA[(size_t)blockIdx.y * N + n] = acc[j];
+  }
+}
+
+__device__ __forceinline__ double outlier_c(const DevState* st, int M, int N) {
+  const double w = st->w;
+  return pow(2.0 * kPi * st->sigma2, 1.5) * (w / (1.0 - w)) * ((double)M / (double)N);
+}
+
+// ------------------------------------------------- pass A reduction (+ c)
+// den_n = sum of the split partials + c (Eq. 4).  Prepares pass B's scene
+// records and reduces the Eq. 3 log-likelihood sum_n ln den_n (+ constants).
+template <typename F>
+__global__ void __launch_bounds__(kThreadsR)
+reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t4* __restrict__ Y4,
+        int N, typename Vec<F>::t4* __restrict__ Yb, double* __restrict__ den_out,
+        double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const double s2 = st->sigma2;
+  const double w = st->w;
+  const double c = outlier_c(st, M, N);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double lnden = 0.0;
+  int bad = 0;
+  if (n < N) {
+    double s = 0.0;
+    for (int k = 0; k < chunks; ++k) s += (double)partA[(size_t)k * N + n];
+    const double den = s + c;
+    const typename Vec<F>::t4 y = Y4[n];
+    if constexpr (sizeof(F) == 4) {
+      const float q = scale_q(s2);
+      if (!(den >= kColFloor) || !isfinite(den)) {
+        // Gaussians flushed by FP32 may dominate: exact log-domain path
+        flag_cols[atomicAdd(&st->n_flag_cols, 1)] = n;
+        Yb[n] = make_float4(q * y.x, q * y.y, q * y.z, 0.f);
+      } else {
+        Yb[n] = make_float4(q * y.x, q * y.y, q * y.z, (float)(-log2(den)));
+        if (den_out) den_out[n] = den;
+        lnden = log(den);
+      }
+    } else {
+      // the column of Eq. 4 is 0/0 in double precision: the definition fails
+      bad = !(den > 0.0) || !isfinite(den);
+      Yb[n] = dvec4{y.x, y.y, y.z, bad ? 0.0 : 1.0 / den};
+      if (den_out) den_out[n] = den;
+      lnden = bad ? 0.0 : log(den);
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ENUMERIC);
+  const double bs = block_sum(lnden, sh);
+  if (threadIdx.x == 0) {
+    sums[blockIdx.x] = bs;
+    __threadfence();
+    last = atomicAdd(&st->ticket_a, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sums)[i];
+    const double tot = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+      st->loglik = tot + (double)N * log((1.0 - w) / (double)M) - 1.5 * (double)N * log(2.0 * kPi * s2);
+      st->ticket_a = 0;
+    }
+  }
+}
+
+// Exact FP32 column denominators in the log domain for the listed columns:
+// den_n = 2^a (sum_m 2^(-d'^2_mn - a)) + c with a = max_m (-d'^2_mn).
+__global__ void __launch_bounds__(kThreadsF)
+fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, int N,
+         float4* __restrict__ Yb, double* __restrict__ den_out, const int* __restrict__ flag_cols,
+         DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  const int count = st->n_flag_cols;
+  if (count == 0) return;
+  const float q = scale_q(st->sigma2);
+  const double c = outlier_c(st, M, N);
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (kThreadsF / 32);
+  for (int j = blockIdx.x * (kThreadsF / 32) + (threadIdx.x >> 5); j < count; j += nwarps) {
+    const int n = flag_cols[j];
+    const float4 y = Y4[n];
+    const float yx = q * y.x, yy = q * y.y, yz = q * y.z;
+    float amax = -INFINITY;
+    for (int m = lane; m < M; m += 32) {
+      const float4 t = T4[m];
+      const float dx = yx - q * t.x, dy = yy - q * t.y, dz = yz - q * t.z;
+      float d2 = dx * dx;
+      d2 = fmaf(dy, dy, d2);
+      d2 = fmaf(dz, dz, d2);
+      amax = fmaxf(amax, -d2);
+    }
+    amax = warp_max(amax);
+    float sum = 0.f;
+    for (int m = lane; m < M; m += 32) {
+      const float4 t = T4[m];
+      const float dx = yx - q * t.x, dy = yy - q * t.y, dz = yz - q * t.z;
+      float d2 = dx * dx;
+      d2 = fmaf(dy, dy, d2);
+      d2 = fmaf(dz, dz, d2);
+      sum += ex2_approx(-d2 - amax);
+    }
+    sum = warp_sumf(sum);
+    if (lane == 0) {
+      const double den = (double)sum * exp2((double)amax) + c;
+      if (!(den > 0.0) || !isfinite(den)) {
+        atomicExch(&st->status, (int)CPD_ENUMERIC);
+      } else {
+        Yb[n].w = (float)(-log2(den));
+        if (den_out) den_out[n] = den;
+        atomicAdd(&st->loglik, log(den));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+__global__ void __launch_bounds__(kThreadsB)
+passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
+          int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
+  __shared__ float4 sY[kTileB];
+  const float q = scale_q(st->sigma2);
+  const int mbase = blockIdx.x * (kThreadsB * kRowsB32) + threadIdx.x;
+  float tx[kRowsB32], ty[kRowsB32], tz[kRowsB32];
+  float p1[kRowsB32], px[kRowsB32], py[kRowsB32], pz[kRowsB32], v[kRowsB32];
+#pragma unroll
+  for (int j = 0; j < kRowsB32; ++j) {
+    const int m = mbase + j * kThreadsB;
+    if (m < M) {
+      const float4 t = T4[m];
+      tx[j] = q * t.x; ty[j] = q * t.y; tz[j] = q * t.z;
+    } else {
+      tx[j] = kFar; ty[j] = kFar; tz[j] = kFar;
+    }
+    p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.f;
+  }
+  const int c0 = blockIdx.y * cols_per_chunk;
+  const int c1 = min(N, c0 + cols_per_chunk);
+  for (int base = c0; base < c1; base += kTileB) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileB; i += kThreadsB) {
+      const int n = base + i;
+      sY[i] = n < c1 ? Yb[n] : make_float4(-kFar, -kFar, -kFar, 0.f);
+    }
+    __syncthreads();
+    const int cnt = min(kTileB, c1 - base);
+#pragma unroll 2
+    for (int i = 0; i < cnt; ++i) {
+      const float4 y = sY[i];
+#pragma unroll
+      for (int j = 0; j < kRowsB32; ++j) {
+        const float dx = tx[j] - y.x, dy = ty[j] - y.y, dz = tz[j] - y.z;
+        float d2 = dx * dx;
+        d2 = fmaf(dy, dy, d2);
+        d2 = fmaf(dz, dz, d2);
+        const float wv = ex2_approx(y.w - d2);   // e_mn / den_n
+        p1[j] += wv;
+        px[j] = fmaf(wv, y.x, px[j]);
+        py[j] = fmaf(wv, y.y, py[j]);
+        pz[j] = fmaf(wv, y.z, pz[j]);
+        v[j] = fmaf(wv, d2, v[j]);
+      }
+    }
+  }
+  const size_t plane = (size_t)gridDim.y * M;
+#pragma unroll
+  for (int j = 0; j < kRowsB32; ++j) {
+    const int m = mbase + j * kThreadsB;
+    if (m < M) {
+      const size_t o = (size_t)blockIdx.y * M + m;
+      partB[o] = p1[j];
+      partB[o + plane] = px[j];
+      partB[o + 2 * plane] = py[j];
+      partB[o + 3 * plane] = pz[j];
+      partB[o + 4 * plane] = v[j];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsB)
+passB_f64(const dvec4* __restrict__ T4, int M, const dvec4* __restrict__ Yb, int N,
+          int cols_per_chunk, double* __restrict__ partB, const DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  __shared__ dvec4 sY[kTileB];
+  const double inv2s2 = 1.0 / (2.0 * st->sigma2);
+  const int mbase = blockIdx.x * (kThreadsB * kRowsB64) + threadIdx.x;
+  double tx[kRowsB64], ty[kRowsB64], tz[kRowsB64];
+  double p1[kRowsB64], px[kRowsB64], py[kRowsB64], pz[kRowsB64], v[kRowsB64];
+#pragma unroll
+  for (int j = 0; j < kRowsB64; ++j) {
+    const int m = mbase + j * kThreadsB;
+    const dvec4 t = m < M ? T4[m] : dvec4{0, 0, 0, 0};
+    tx[j] = t.x; ty[j] = t.y; tz[j] = t.z;
+    p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.0;
+  }
+  const int c0 = blockIdx.y * cols_per_chunk;
+  const int c1 = min(N, c0 + cols_per_chunk);
+  for (int base = c0; base < c1; base += kTileB) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileB; i += kThreadsB) {
+      const int n = base + i;
+      sY[i] = n < c1 ? Yb[n] : dvec4{0, 0, 0, 0};
+    }
+    __syncthreads();
+    const int cnt = min(kTileB, c1 - base);
+    for (int i = 0; i < cnt; ++i) {
+      const dvec4 y = sY[i];
+#pragma unroll
+      for (int j = 0; j < kRowsB64; ++j) {
+        const double dx = tx[j] - y.x, dy = ty[j] - y.y, dz = tz[j] - y.z;
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        const double wv = exp(-d2 * inv2s2) * y.w;      // e_mn / den_n
+        p1[j] += wv;
+        px[j] += wv * y.x;
+        py[j] += wv * y.y;
+        pz[j] += wv * y.z;
+        v[j] += wv * d2;
+      }
+    }
+  }
+  const size_t plane = (size_t)gridDim.y * M;
+#pragma unroll
+  for (int j = 0; j < kRowsB64; ++j) {
+    const int m = mbase + j * kThreadsB;
+    if (m < M) {
+      const size_t o = (size_t)blockIdx.y * M + m;
+      partB[o] = p1[j];
+      partB[o + plane] = px[j];
+      partB[o + 2 * plane] = py[j];
+      partB[o + 3 * plane] = pz[j];
+      partB[o + 4 * plane] = v[j];
+    }
+  }
+}
+
+// Writes the Eq. 5 outputs of row m from its (possibly rescaled) sums.
+template <typename F>
+__device__ __forceinline__ void write_row(int m, double p1s, double px, double py, double pz, double v,
+                                          double unscale, double unscale2,
+                                          const typename Vec<F>::t4* __restrict__ X4,
+                                          typename Vec<F>::t4* __restrict__ Yt4,
+                                          typename Vec<F>::t4* __restrict__ R4, double* vrow_out) {
+  const double yx = px / p1s * unscale, yy = py / p1s * unscale, yz = pz / p1s * unscale;
+  const double vrow = v / p1s * unscale2;
+  using V4 = typename Vec<F>::t4;
+  V4 yt;
+  yt.x = (F)yx; yt.y = (F)yy; yt.z = (F)yz; yt.w = (F)vrow;
+  Yt4[m] = yt;
+  if (R4) {
+    const V4 x = X4[m];
+    V4 r;
+    r.x = (F)(yx - (double)x.x); r.y = (F)(yy - (double)x.y); r.z = (F)(yz - (double)x.z); r.w = (F)0;
+    R4[m] = r;
+  }
+  *vrow_out = vrow;
+}
+
+// --------------------------------------------- pass B reduction + Eq. 5
+// Ytil_m = PY_m / P1_m (the corresponding constraint), V_m / P1_m =
+// sum_n p^_mn |y_n - t_m|^2, R_m = Ytil_m - x_m.  FP64: a row whose mass is
+// 0 or not finite cannot be normalised -> CPD_ENUMERIC.  FP32: rows whose
+// mass is below 2^-90 are listed for the exact log-domain path.
+template <typename F>
+__global__ void __launch_bounds__(kThreadsR)
+reduceB(const F* __restrict__ partB, int chunks, int M, const typename Vec<F>::t4* __restrict__ X4,
+        typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
+        double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
+        DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double vrow = 0.0;
+  int bad = 0;
+  if (m < M) {
+    const size_t plane = (size_t)chunks * M;
+    double p1 = 0, px = 0, py = 0, pz = 0, v = 0;
+    for (int k = 0; k < chunks; ++k) {
+      const size_t o = (size_t)k * M + m;
+      p1 += (double)partB[o];
+      px += (double)partB[o + plane];
+      py += (double)partB[o + 2 * plane];
+      pz += (double)partB[o + 3 * plane];
+      v += (double)partB[o + 4 * plane];
+    }
+    if constexpr (sizeof(F) == 4) {
+      if (!(p1 >= kRowFloor) || !isfinite(p1)) {
+        flag_rows[atomicAdd(&st->n_flag_rows, 1)] = m;
+      } else {
+        const double q = (double)scale_q(st->sigma2);
+        write_row<F>(m, p1, px, py, pz, v, 1.0 / q, 1.0 / (q * q), X4, Yt4, R4, &vrow);
+        if (P1_out) P1_out[m] = p1;
+      }
+    } else {
+      if (!(p1 > 0.0) || !isfinite(p1)) {
+        bad = 1;
+        p1 = 1.0;   // keep outputs finite; the status word reports the failure
+      }
+      write_row<F>(m, p1, px, py, pz, v, 1.0, 1.0, X4, Yt4, R4, &vrow);
+      if (P1_out) P1_out[m] = bad ? 0.0 : p1;
+    }
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ENUMERIC);
+  const double bs = block_sum(vrow, sh);
+  if (threadIdx.x == 0) {
+    sums[blockIdx.x] = bs;
+    __threadfence();
+    last = atomicAdd(&st->ticket_b, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double vv = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) vv += ((volatile double*)sums)[i];
+    const double tot = block_sum(vv, sh);
+    if (threadIdx.x == 0) {
+      st->vsum = tot;
+      st->ticket_b = 0;
+    }
+  }
+}
+
+// Exact FP32 rows in the log domain for the listed rows: with
+// a = max_n (lid_n - d'^2_mn), every sum is taken over 2^(lid_n - d'^2 - a);
+// the Eq. 5 ratios do not depend on the shift, and P1_m = 2^a * sum.
+__global__ void __launch_bounds__(kThreadsF)
+fixB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
+         const float4* __restrict__ X4, float4* __restrict__ Yt4, float4* __restrict__ R4,
+         double* __restrict__ P1_out, const int* __restrict__ flag_rows, DevState* __restrict__ st, int gate) {
+  if (gate && iteration_gated(st)) return;
+  const int count = st->n_flag_rows;
+  if (count == 0) return;
+  const float q = scale_q(st->sigma2);
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (kThreadsF / 32);
+  for (int j = blockIdx.x * (kThreadsF / 32) + (threadIdx.x >> 5); j < count; j += nwarps) {
+    const int m = flag_rows[j];
+    const float4 t = T4[m];
+    const float tx = q * t.x, ty = q * t.y, tz = q * t.z;
+    float amax = -INFINITY;
+    for (int n = lane; n < N; n += 32) {
+      const float4 y = Yb[n];
+      const float dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
+      float d2 = dx * dx;
+      d2 = fmaf(dy, dy, d2);
+      d2 = fmaf(dz, dz, d2);
+      amax = fmaxf(amax, y.w - d2);
+    }
+    amax = warp_max(amax);
+    float p1 = 0.f, px = 0.f, py = 0.f, pz = 0.f, v = 0.f;
+    for (int n = lane; n < N; n += 32) {
+      const float4 y = Yb[n];
+      const float dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
+      float d2 = dx * dx;
+      d2 = fmaf(dy, dy, d2);
+      d2 = fmaf(dz, dz, d2);
+      const float wv = ex2_approx(y.w - d2 - amax);
+      p1 += wv;
+      px = fmaf(wv, y.x, px);
+      py = fmaf(wv, y.y, py);
+      pz = fmaf(wv, y.z, pz);
+      v = fmaf(wv, d2, v);
+    }
+    p1 = warp_sumf(p1); px = warp_sumf(px); py = warp_sumf(py); pz = warp_sumf(pz); v = warp_sumf(v);
+    if (lane == 0) {
+      const double mass = (double)p1 * exp2((double)amax);
+      if (!(mass > 0.0) || !isfinite(mass)) {
+        atomicExch(&st->status, (int)CPD_ENUMERIC);    // zero even in double precision
+      } else {
+        const double qd = (double)q;
+        double vrow = 0.0;
+        write_row<float>(m, (double)p1, px, py, pz, v, 1.0 / qd, 1.0 / (qd * qd), X4, Yt4, R4, &vrow);
+        if (P1_out) P1_out[m] = mass;
+        atomicAdd(&st->vsum, vrow);
+      }
+    }
+  }
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms) {
+  EstepPlan p{};
+  const int64_t target = (int64_t)sms * 8;
+  const int64_t colsA = kThreadsA * (fp64 ? kColsA64 : kColsA32);
+  p.a_col_tiles = (int)cdiv(N, colsA);
+  int64_t want = std::max<int64_t>(1, cdiv(target, p.a_col_tiles));
+  int64_t rpc = cdiv(cdiv(M, want), kTileA) * kTileA;
+  p.a_rows_per_chunk = (int)rpc;
+  p.a_row_chunks = (int)cdiv(M, rpc);
+  const int64_t rowsB = kThreadsB * (fp64 ? kRowsB64 : kRowsB32);
+  p.b_row_tiles = (int)cdiv(M, rowsB);
+  want = std::max<int64_t>(1, cdiv(target, p.b_row_tiles));
+  int64_t cpc = cdiv(cdiv(N, want), kTileB) * kTileB;
+  p.b_cols_per_chunk = (int)cpc;
+  p.b_col_chunks = (int)cdiv(N, cpc);
+  p.partA_elems = (int64_t)p.a_row_chunks * N;
+  p.partB_elems = (int64_t)5 * p.b_col_chunks * M;
+  p.redA_blocks = cdiv(N, kThreadsR);
+  p.redB_blocks = cdiv(M, kThreadsR);
+  p.sums_elems = std::max(p.redA_blocks, p.redB_blocks);
+  p.flags_elems = M + N;
+  return p;
+}
+
+template <typename F>
+void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
+                  int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
+                  F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
+                  typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
+                  bool gate, cudaStream_t s, cudaEvent_t* ev) {
+  const int g = gate ? 1 : 0;
+  dim3 ga(pl.a_col_tiles, pl.a_row_chunks);
+  dim3 gb(pl.b_row_tiles, pl.b_col_chunks);
+  int* flag_rows = flags;
+  int* flag_cols = flags + M;
+  if constexpr (sizeof(F) == 4) {
+    passA_f32<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
+  } else {
+    passA_f64<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
+  }
+  record_after(ev, 0, s);
+  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, (int)M, Y4, (int)N, Yb,
+                                                            den_out, sums, flag_cols, st, g);
+  if constexpr (sizeof(F) == 4) {
+    fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
+  }
+  record_after(ev, 1, s);
+  if constexpr (sizeof(F) == 4) {
+    passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+  } else {
+    passB_f64<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+  }
+  record_after(ev, 2, s);
+  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, (int)M, X4, Yt4, R4,
+                                                            P1_out, sums, flag_rows, st, g);
+  if constexpr (sizeof(F) == 4) {
+    fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
+  }
+  record_after(ev, 3, s);
+}
+
+template void launch_estep<float>(const EstepPlan&, const float4*, const float4*, int64_t, const float4*,
+                                  float4*, int64_t, float*, float*, double*, int*, float4*, float4*, double*,
+                                  double*, DevState*, bool, cudaStream_t, cudaEvent_t*);
+template void launch_estep<double>(const EstepPlan&, const dvec4*, const dvec4*, int64_t, const dvec4*,
+                                   dvec4*, int64_t, double*, double*, double*, int*, dvec4*, dvec4*, double*,
+                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*);
+
+}  // namespace fcpd

@@ -1,0 +1,706 @@
+// C ABI of the GB300 fast-CPD EM loop (declared in include/fcpd.h).
+//
+// Host side only: argument validation, device buffers of a context, staging of
+// host arrays, the one-time eigendecomposition (cuSOLVER, FP64), and the
+// replay of captured per-iteration CUDA graphs.  Every arithmetic step of the
+// EM loop runs in the kernels of estep.cu / mstep.cu / setup.cu.
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace fcpd;
+
+namespace {
+
+thread_local std::string g_err;
+
+cpd_status fail(cpd_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+bool fault_enabled(const char* what) {
+  const char* f = std::getenv("CPD_FAULT");
+  return f && std::strcmp(f, what) == 0;
+}
+
+#define CUDA_TRY(call)                                                                                   \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) {                                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? CPD_ENOMEM : CPD_ECUDA,                              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                   \
+    }                                                                                                    \
+  } while (0)
+
+#define STATUS_TRY(call)              \
+  do {                                \
+    cpd_status s_ = (call);           \
+    if (s_ != CPD_OK) return s_;      \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Device buffer that grows on demand.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cpd_status ensure(size_t want) {
+    if (want <= bytes) return CPD_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return fail(CPD_ENOMEM, std::string("cudaMalloc(") + std::to_string(want) + "): " + cudaGetErrorString(e));
+    }
+    bytes = want;
+    return CPD_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+cpd_status validate_params(const cpd_params* p) {
+  if (!p) return fail(CPD_EINVAL, "params is NULL");
+  if (p->D != 3) return fail(CPD_EINVAL, "only D = 3 is implemented");
+  if (p->precision != CPD_FP64 && p->precision != CPD_FP32) return fail(CPD_EINVAL, "unknown precision");
+  if (!(p->w >= 0.0 && p->w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
+  if (!(p->beta > 0.0) || !std::isfinite(p->beta)) return fail(CPD_EINVAL, "beta must be > 0");
+  if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return fail(CPD_EINVAL, "lambda must be > 0");
+  if (std::isnan(p->sigma2_init) || std::isinf(p->sigma2_init)) return fail(CPD_EINVAL, "sigma2_init not finite");
+  if (p->K < 0) return fail(CPD_EINVAL, "K must be >= 0");
+  if (p->max_iter < 0) return fail(CPD_EINVAL, "max_iter must be >= 0");
+  if (p->flags != 0) return fail(CPD_EINVAL, "flags must be 0");
+  if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return fail(CPD_EINVAL, "tol must be >= 0");
+  return CPD_OK;
+}
+
+constexpr int64_t kMaxM = 46340;          // M*M doubles indexable by the 32-bit eigensolver API
+constexpr int64_t kMaxN = 1LL << 30;
+
+}  // namespace
+
+struct cpd_ctx {
+  cpd_params p{};
+  int dev = 0;
+  int sms = 0;
+  bool fp64 = false;
+  size_t es = 4;                 // element size of the working precision
+  size_t v4 = 16;                // bytes of one 4-vector
+  int64_t M = 0, K = 0, ldU = 0, N = 0;
+  cudaStream_t stream = nullptr; // caller's stream
+  cudaStream_t cap = nullptr;    // internal stream used only for graph capture
+  Buf X4, T4, U, lam, Yt4, R4, B4, C4, Yhat4, W4, hist;
+  Buf st, st_aux;
+  Buf Y4, Yb, partA, partB, partP, sums, flags, stage;
+  Buf auxT4, auxR4, auxB4, auxC4;
+  EstepPlan ep{};
+  MstepPlan mp{};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
+  cudaGraphExec_t prof_graph = nullptr;             // n iterations with timing events
+  int prof_iters = 0;
+  std::vector<cudaEvent_t> prof_ev;                 // 8 per iteration
+  bool started = false;
+  bool has_gt = false;
+  double gt_tol = 0.0;
+  static constexpr int kBatch = 8;
+
+  ~cpd_ctx() {
+    drop_graphs();
+    for (Buf* b : {&X4, &T4, &U, &lam, &Yt4, &R4, &B4, &C4, &Yhat4, &W4, &hist, &st, &st_aux, &Y4, &Yb,
+                   &partA, &partB, &partP, &sums, &flags, &stage, &auxT4, &auxR4, &auxB4, &auxC4})
+      b->release();
+    if (cap) cudaStreamDestroy(cap);
+  }
+  void drop_graphs() {
+    for (auto& g : graph)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+    if (prof_graph) cudaGraphExecDestroy(prof_graph);
+    prof_graph = nullptr;
+    prof_iters = 0;
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    prof_ev.clear();
+  }
+  DevState* dst() const { return st.as<DevState>(); }
+};
+
+namespace {
+
+// Copies a caller point array (n x 3 of the context precision, host or device)
+// into 4-vectors `dst` (4th lane |p|^2 if with_norm).
+cpd_status upload_points(cpd_ctx* c, const void* src, int64_t n, void* dst, bool with_norm, Buf& stage,
+                         bool fp64, cudaStream_t s) {
+  const size_t es = fp64 ? 8 : 4;
+  const void* dev = src;
+  if (!is_device_ptr(src)) {
+    STATUS_TRY(stage.ensure((size_t)n * 3 * es));
+    CUDA_TRY(cudaMemcpyAsync(stage.p, src, (size_t)n * 3 * es, cudaMemcpyHostToDevice, s));
+    dev = stage.p;
+  }
+  (void)c;
+  if (fp64) launch_pack<double>((const double*)dev, n, (dvec4*)dst, with_norm, s);
+  else launch_pack<float>((const float*)dev, n, (float4*)dst, with_norm, s);
+  CUDA_TRY(cudaGetLastError());
+  return CPD_OK;
+}
+
+// Writes 4-vectors `src` to a caller array (n x 3, host or device).  Host
+// destinations synchronise `s`.
+cpd_status download_points(const void* src, int64_t n, void* dst, Buf& stage, bool fp64, cudaStream_t s) {
+  const size_t es = fp64 ? 8 : 4;
+  const bool dev = is_device_ptr(dst);
+  void* out = dst;
+  if (!dev) {
+    STATUS_TRY(stage.ensure((size_t)n * 3 * es));
+    out = stage.p;
+  }
+  if (fp64) launch_unpack<double>((const dvec4*)src, n, (double*)out, s);
+  else launch_unpack<float>((const float4*)src, n, (float*)out, s);
+  CUDA_TRY(cudaGetLastError());
+  if (!dev) {
+    CUDA_TRY(cudaMemcpyAsync(dst, stage.p, (size_t)n * 3 * es, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return CPD_OK;
+}
+
+cpd_status read_state(cpd_ctx* c, DevState* h) {
+  CUDA_TRY(cudaMemcpyAsync(h, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return CPD_OK;
+}
+
+// The kernels of one EM iteration, enqueued on `s` (used only under capture).
+// With `ev` (8 events) the iteration is bracketed by timing events: ev[0]
+// before pass A, ev[1..4] after the E-step kernels, ev[5..7] after the M-step
+// kernels.
+void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  cudaEvent_t* ee = ev ? ev + 1 : nullptr;
+  cudaEvent_t* em = ev ? ev + 5 : nullptr;
+  DevState* st = c->dst();
+  if (c->fp64) {
+    launch_estep<double>(c->ep, c->T4.as<dvec4>(), c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), c->Yb.as<dvec4>(),
+                         c->N, c->partA.as<double>(), c->partB.as<double>(), c->sums.as<double>(), c->flags.as<int>(),
+                         c->Yt4.as<dvec4>(), c->R4.as<dvec4>(), nullptr, nullptr, st, true, s, ee);
+    launch_mstep<double>(c->mp, c->U.as<double>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<dvec4>(),
+                         c->R4.as<dvec4>(), c->Yt4.as<dvec4>(), c->T4.as<dvec4>(),
+                         c->has_gt ? c->Yhat4.as<dvec4>() : nullptr, c->partP.as<double>(), c->sums.as<double>(),
+                         c->B4.as<dvec4>(), c->C4.as<dvec4>(), st, true, s, em);
+  } else {
+    launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
+                        c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
+                        c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, ee);
+    launch_mstep<float>(c->mp, c->U.as<float>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<float4>(),
+                        c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
+                        c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->partP.as<float>(), c->sums.as<double>(),
+                        c->B4.as<float4>(), c->C4.as<float4>(), st, true, s, em);
+  }
+}
+
+cpd_status capture_graph(cpd_ctx* c, int which) {
+  const int iters = which == 0 ? 1 : cpd_ctx::kBatch;
+  CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+  for (int i = 0; i < iters; ++i) enqueue_iteration(c, c->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph[which], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return CPD_OK;
+}
+
+// Sizes the scene-dependent buffers for N scene points.
+cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
+  if (N == c->N) return CPD_OK;
+  c->drop_graphs();
+  c->ep = plan_estep(c->M, N, c->fp64, c->sms);
+  STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
+  STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
+  STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
+  STATUS_TRY(c->partB.ensure((size_t)c->ep.partB_elems * c->es));
+  STATUS_TRY(c->sums.ensure((size_t)std::max(c->ep.sums_elems, c->mp.sums_elems) * sizeof(double)));
+  STATUS_TRY(c->flags.ensure((size_t)c->ep.flags_elems * sizeof(int)));
+  c->N = N;
+  launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, c->gt_tol, c->has_gt ? 1 : 0,
+                      c->hist.as<double>(), c->M, N, c->K, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  return CPD_OK;
+}
+
+
+// Scene upload and, for a fresh registration, T = X and the initial variance.
+cpd_status prepare_iterate(cpd_ctx* c, const void* Y, int64_t N) {
+  STATUS_TRY(ensure_scene(c, N));
+  STATUS_TRY(upload_points(c, Y, N, c->Y4.p, true, c->stage, c->fp64, c->stream));
+  if (!c->started) {
+    CUDA_TRY(cudaMemcpyAsync(c->T4.p, c->X4.p, (size_t)c->M * c->v4, cudaMemcpyDeviceToDevice, c->stream));
+    if (fault_enabled("nan_sigma")) {
+      launch_state_init(c->dst(), std::nan(""), c->stream);
+    } else if (c->p.sigma2_init > 0.0) {
+      launch_state_init(c->dst(), c->p.sigma2_init, c->stream);
+    } else {
+      launch_state_init(c->dst(), 0.0, c->stream);
+      if (c->fp64) launch_sigma2_init<double>(c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), N, nullptr, c->dst(), c->stream);
+      else launch_sigma2_init<float>(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), N, nullptr, c->dst(), c->stream);
+    }
+    CUDA_TRY(cudaGetLastError());
+    c->started = true;
+  }
+  return CPD_OK;
+}
+
+cpd_status capture_profiled(cpd_ctx* c, int n_iter) {
+  if (c->prof_graph) cudaGraphExecDestroy(c->prof_graph);
+  c->prof_graph = nullptr;
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  c->prof_ev.assign((size_t)8 * n_iter, nullptr);
+  for (auto& e : c->prof_ev) CUDA_TRY(cudaEventCreate(&e));
+  CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+  for (int i = 0; i < n_iter; ++i) enqueue_iteration(c, c->cap, &c->prof_ev[(size_t)8 * i]);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->prof_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  c->prof_iters = n_iter;
+  return CPD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int32_t cpd_abi_version(void) { return FCPD_ABI_VERSION; }
+
+const char* cpd_status_string(cpd_status s) {
+  switch (s) {
+    case CPD_OK: return "CPD_OK";
+    case CPD_EINVAL: return "CPD_EINVAL";
+    case CPD_ENOMEM: return "CPD_ENOMEM";
+    case CPD_ECUDA: return "CPD_ECUDA";
+    case CPD_ESOLVER: return "CPD_ESOLVER";
+    case CPD_ENUMERIC: return "CPD_ENUMERIC";
+    case CPD_ETIMEOUT: return "CPD_ETIMEOUT";
+    case CPD_ESTATE: return "CPD_ESTATE";
+  }
+  return "CPD_UNKNOWN";
+}
+
+const char* cpd_last_error(void) { return g_err.c_str(); }
+
+void cpd_params_default(cpd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->D = 3;
+  p->precision = CPD_FP32;
+  p->w = 0.1;
+  p->beta = 2.0;
+  p->lambda = 2.0;
+  p->sigma2_init = 0.0;
+  p->K = 0;
+  p->max_iter = 50;
+  p->flags = 0;
+  p->tol = 0.0;
+}
+
+int64_t cpd_basis_rank(const cpd_ctx* ctx) { return ctx ? ctx->K : 0; }
+
+cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream, cpd_ctx** out) {
+  g_err.clear();
+  STATUS_TRY(validate_params(p));
+  if (!X) return fail(CPD_EINVAL, "X is NULL");
+  if (!out) return fail(CPD_EINVAL, "out is NULL");
+  if (M < 1 || M > kMaxM) return fail(CPD_EINVAL, "M must be in [1, 46340]");
+  if (p->K > M) return fail(CPD_EINVAL, "K must not exceed M");
+  if (fault_enabled("alloc")) return fail(CPD_ENOMEM, "injected allocation failure (CPD_FAULT=alloc)");
+
+  cpd_ctx* c = new (std::nothrow) cpd_ctx();
+  if (!c) return fail(CPD_ENOMEM, "host allocation failed");
+  auto bail = [&](cpd_status s) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    delete c;
+    return s;
+  };
+  c->p = *p;
+  c->fp64 = p->precision == CPD_FP64;
+  c->es = c->fp64 ? 8 : 4;
+  c->v4 = c->fp64 ? sizeof(dvec4) : sizeof(float4);
+  c->M = M;
+  c->K = (p->K == 0 || p->K >= M) ? M : p->K;
+  c->ldU = round_up(c->K, 16 / (int64_t)c->es);
+  c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(fail(CPD_ECUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "cannot query the SM count"));
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "cannot create the capture stream"));
+  mstep_prepare();
+
+  cpd_status s;
+  if ((s = c->X4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->T4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->st.ensure(sizeof(DevState))) != CPD_OK) return bail(s);
+  if ((s = c->st_aux.ensure(sizeof(DevState))) != CPD_OK) return bail(s);
+  if ((s = c->hist.ensure((size_t)3 * kHistCap * sizeof(double))) != CPD_OK) return bail(s);
+  if ((s = upload_points(c, X, M, c->X4.p, false, c->stage, c->fp64, c->stream)) != CPD_OK) return bail(s);
+
+  // Eq. 11 in FP64, then Eq. 16 by the FP64 symmetric eigensolver.
+  Buf phi, wv, info, work;
+  auto free_setup = [&]() { phi.release(); wv.release(); info.release(); work.release(); };
+  if ((s = phi.ensure((size_t)M * M * sizeof(double))) != CPD_OK) return bail(s);
+  if ((s = wv.ensure((size_t)M * sizeof(double))) != CPD_OK) { free_setup(); return bail(s); }
+  if ((s = info.ensure(sizeof(int))) != CPD_OK) { free_setup(); return bail(s); }
+  launch_gram_f64(c->X4.p, c->fp64, M, p->beta, phi.as<double>(), c->stream);
+  cusolverDnHandle_t h = nullptr;
+  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) { free_setup(); return bail(fail(CPD_ESOLVER, "cusolverDnCreate failed")); }
+  cusolverDnSetStream(h, c->stream);
+  int lwork = 0;
+  cusolverStatus_t cs = cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M,
+                                                    phi.as<double>(), (int)M, wv.as<double>(), &lwork);
+  if (cs == CUSOLVER_STATUS_SUCCESS) {
+    if ((s = work.ensure((size_t)std::max(lwork, 1) * sizeof(double))) != CPD_OK) {
+      cusolverDnDestroy(h); free_setup(); return bail(s);
+    }
+    cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M, phi.as<double>(), (int)M,
+                          wv.as<double>(), work.as<double>(), lwork, info.as<int>());
+  }
+  int hinfo = 0;
+  if (cs == CUSOLVER_STATUS_SUCCESS) {
+    cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+  }
+  cusolverDnDestroy(h);
+  work.release();
+  if (cs != CUSOLVER_STATUS_SUCCESS || hinfo != 0 || fault_enabled("solver")) {
+    free_setup();
+    return bail(fail(CPD_ESOLVER, "eigensolver failed (status " + std::to_string((int)cs) + ", info " +
+                                      std::to_string(hinfo) + (fault_enabled("solver") ? ", injected" : "") + ")"));
+  }
+  if ((s = c->U.ensure((size_t)M * c->ldU * c->es)) != CPD_OK) { free_setup(); return bail(s); }
+  if ((s = c->lam.ensure((size_t)c->K * sizeof(double))) != CPD_OK) { free_setup(); return bail(s); }
+  if (c->fp64) launch_extract_basis<double>(phi.as<double>(), M, c->K, c->U.as<double>(), c->ldU, wv.as<double>(),
+                                            c->lam.as<double>(), c->stream);
+  else launch_extract_basis<float>(phi.as<double>(), M, c->K, c->U.as<float>(), c->ldU, wv.as<double>(),
+                                   c->lam.as<double>(), c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
+  free_setup();
+
+  c->mp = plan_mstep(M, c->K, c->fp64, c->sms);
+  if ((s = c->Yt4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->R4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->B4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->C4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
+  if ((s = c->partP.ensure((size_t)c->mp.partP_elems * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->sums.ensure((size_t)c->mp.sums_elems * sizeof(double))) != CPD_OK) return bail(s);
+  launch_state_init(c->dst(), 0.0, c->stream);
+  launch_state_params(c->dst(), p->w, p->lambda, p->tol, 0.0, 0, c->hist.as<double>(), M, 0, c->K, c->stream);
+  launch_state_init(c->st_aux.as<DevState>(), 0.0, c->stream);
+  launch_state_params(c->st_aux.as<DevState>(), p->w, p->lambda, 0.0, 0.0, 0, nullptr, M, 0, c->K, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "setup failed"));
+  *out = c;
+  return CPD_OK;
+}
+
+cpd_status cpd_reset(cpd_ctx* c) {
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  c->started = false;
+  return CPD_OK;
+}
+
+cpd_status cpd_iterate(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, void* T_out, double* sigma2_out,
+                       int32_t* iters_done) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (!Y) return fail(CPD_EINVAL, "Y is NULL");
+  if (N < 1 || N > kMaxN) return fail(CPD_EINVAL, "N must be in [1, 2^30]");
+  if (n_iter < 0) return fail(CPD_EINVAL, "n_iter must be >= 0");
+  DeviceGuard guard(c->dev);
+  STATUS_TRY(prepare_iterate(c, Y, N));
+  if (n_iter > 0) {
+    launch_begin_iterations(c->dst(), n_iter, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    const int nb = n_iter / cpd_ctx::kBatch, n1 = n_iter % cpd_ctx::kBatch;
+    if (nb > 0 && !c->graph[1]) STATUS_TRY(capture_graph(c, 1));
+    if (n1 > 0 && !c->graph[0]) STATUS_TRY(capture_graph(c, 0));
+    for (int i = 0; i < nb; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[1], c->stream));
+    for (int i = 0; i < n1; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[0], c->stream));
+  }
+  if (T_out) STATUS_TRY(download_points(c->T4.p, c->M, T_out, c->stage, c->fp64, c->stream));
+  if (sigma2_out || iters_done || (T_out && !is_device_ptr(T_out))) {
+    DevState h;
+    STATUS_TRY(read_state(c, &h));
+    if (sigma2_out) *sigma2_out = h.sigma2;
+    if (iters_done) *iters_done = h.iter;
+    if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+  }
+  return CPD_OK;
+}
+
+cpd_status cpd_iterate_profiled(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, float* phase_ms) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (!Y || !phase_ms) return fail(CPD_EINVAL, "Y and phase_ms are required");
+  if (N < 1 || N > kMaxN) return fail(CPD_EINVAL, "N must be in [1, 2^30]");
+  if (n_iter < 1 || n_iter > 4096) return fail(CPD_EINVAL, "n_iter must be in [1, 4096]");
+  DeviceGuard guard(c->dev);
+  STATUS_TRY(prepare_iterate(c, Y, N));
+  launch_begin_iterations(c->dst(), n_iter, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (!c->prof_graph || c->prof_iters != n_iter) STATUS_TRY(capture_profiled(c, n_iter));
+  CUDA_TRY(cudaGraphLaunch(c->prof_graph, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int p = 0; p < 8; ++p) phase_ms[p] = 0.f;
+  for (int i = 0; i < n_iter; ++i) {
+    const cudaEvent_t* ev = &c->prof_ev[(size_t)8 * i];
+    for (int p = 0; p < 7; ++p) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]));
+      phase_ms[p] += ms;
+    }
+  }
+  float total = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&total, c->prof_ev[0], c->prof_ev[(size_t)8 * n_iter - 1]));
+  phase_ms[7] = total;
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+  return CPD_OK;
+}
+
+cpd_status cpd_set_ground_truth(cpd_ctx* c, const void* Yhat, double rmse_tol) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (!(rmse_tol >= 0.0) || !std::isfinite(rmse_tol)) return fail(CPD_EINVAL, "rmse_tol must be >= 0");
+  DeviceGuard guard(c->dev);
+  c->drop_graphs();
+  if (Yhat) {
+    STATUS_TRY(c->Yhat4.ensure((size_t)c->M * c->v4));
+    STATUS_TRY(upload_points(c, Yhat, c->M, c->Yhat4.p, false, c->stage, c->fp64, c->stream));
+    c->has_gt = true;
+    c->gt_tol = rmse_tol;
+  } else {
+    c->has_gt = false;
+    c->gt_tol = 0.0;
+  }
+  launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, c->gt_tol, c->has_gt ? 1 : 0, c->hist.as<double>(),
+                      c->M, c->N, c->K, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  return CPD_OK;
+}
+
+cpd_status cpd_get_state(cpd_ctx* c, double* sigma2, int32_t* iters, int32_t* device_status) {
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  DeviceGuard guard(c->dev);
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  if (sigma2) *sigma2 = h.sigma2;
+  if (iters) *iters = h.iter;
+  if (device_status) *device_status = h.status;
+  return CPD_OK;
+}
+
+cpd_status cpd_get_history(cpd_ctx* c, int32_t n, double* s2h, double* llh, double* rmh) {
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  DeviceGuard guard(c->dev);
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  if (n < 0 || n > h.iter || n > kHistCap) return fail(CPD_EINVAL, "n exceeds the recorded iterations");
+  if (n == 0) return CPD_OK;
+  const double* base = c->hist.as<double>();
+  if (s2h) CUDA_TRY(cudaMemcpy(s2h, base, n * sizeof(double), cudaMemcpyDefault));
+  if (llh) CUDA_TRY(cudaMemcpy(llh, base + kHistCap, n * sizeof(double), cudaMemcpyDefault));
+  if (rmh) CUDA_TRY(cudaMemcpy(rmh, base + 2 * kHistCap, n * sizeof(double), cudaMemcpyDefault));
+  return CPD_OK;
+}
+
+cpd_status cpd_get_W(cpd_ctx* c, void* W_out) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (!W_out) return fail(CPD_EINVAL, "W_out is NULL");
+  DeviceGuard guard(c->dev);
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  if (!c->started || h.iter == 0) return fail(CPD_ESTATE, "no M-step has run yet");
+  STATUS_TRY(c->W4.ensure((size_t)c->M * c->v4));
+  if (c->fp64) launch_w<double>(c->mp, c->U.as<double>(), c->ldU, c->M, c->K, c->C4.as<dvec4>(), c->W4.as<dvec4>(), c->stream);
+  else launch_w<float>(c->mp, c->U.as<float>(), c->ldU, c->M, c->K, c->C4.as<float4>(), c->W4.as<float4>(), c->stream);
+  CUDA_TRY(cudaGetLastError());
+  return download_points(c->W4.p, c->M, W_out, c->stage, c->fp64, c->stream);
+}
+
+cpd_status cpd_get_basis(cpd_ctx* c, void* U_out, double* lam_out) {
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  DeviceGuard guard(c->dev);
+  if (U_out)
+    CUDA_TRY(cudaMemcpy2DAsync(U_out, (size_t)c->K * c->es, c->U.p, (size_t)c->ldU * c->es, (size_t)c->K * c->es,
+                               (size_t)c->M, cudaMemcpyDefault, c->stream));
+  if (lam_out)
+    CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam.p, (size_t)c->K * sizeof(double), cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return CPD_OK;
+}
+
+cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, void* W_out) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (!Ytil || !T_out) return fail(CPD_EINVAL, "Ytil and T_out are required");
+  if (!(sigma2 > 0.0) || !std::isfinite(sigma2)) return fail(CPD_EINVAL, "sigma2 must be > 0");
+  DeviceGuard guard(c->dev);
+  STATUS_TRY(c->auxT4.ensure((size_t)c->M * c->v4));
+  STATUS_TRY(c->auxR4.ensure((size_t)c->M * c->v4));
+  STATUS_TRY(c->auxB4.ensure((size_t)c->K * c->v4));
+  STATUS_TRY(c->auxC4.ensure((size_t)c->K * c->v4));
+  STATUS_TRY(upload_points(c, Ytil, c->M, c->auxT4.p, false, c->stage, c->fp64, c->stream));
+  DevState* sa = c->st_aux.as<DevState>();
+  launch_state_init(sa, sigma2, c->stream);
+  if (c->fp64) {
+    launch_residual<double>(c->auxT4.as<dvec4>(), c->X4.as<dvec4>(), c->auxR4.as<dvec4>(), c->M, c->stream);
+    launch_mstep<double>(c->mp, c->U.as<double>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<dvec4>(),
+                         c->auxR4.as<dvec4>(), nullptr, c->auxT4.as<dvec4>(), nullptr, c->partP.as<double>(),
+                         c->sums.as<double>(), c->auxB4.as<dvec4>(), c->auxC4.as<dvec4>(), sa, false, c->stream);
+  } else {
+    launch_residual<float>(c->auxT4.as<float4>(), c->X4.as<float4>(), c->auxR4.as<float4>(), c->M, c->stream);
+    launch_mstep<float>(c->mp, c->U.as<float>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<float4>(),
+                        c->auxR4.as<float4>(), nullptr, c->auxT4.as<float4>(), nullptr, c->partP.as<float>(),
+                        c->sums.as<double>(), c->auxB4.as<float4>(), c->auxC4.as<float4>(), sa, false, c->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  STATUS_TRY(download_points(c->auxT4.p, c->M, T_out, c->stage, c->fp64, c->stream));
+  if (W_out) {
+    if (c->fp64) launch_w<double>(c->mp, c->U.as<double>(), c->ldU, c->M, c->K, c->auxC4.as<dvec4>(), c->auxR4.as<dvec4>(), c->stream);
+    else launch_w<float>(c->mp, c->U.as<float>(), c->ldU, c->M, c->K, c->auxC4.as<float4>(), c->auxR4.as<float4>(), c->stream);
+    CUDA_TRY(cudaGetLastError());
+    STATUS_TRY(download_points(c->auxR4.p, c->M, W_out, c->stage, c->fp64, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return CPD_OK;
+}
+
+cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t precision, double sigma2, double w,
+                     void* Ytil_out, void* P1_out, void* den_out, double* sums_out, void* stream) {
+  g_err.clear();
+  if (!T || !Y || !Ytil_out) return fail(CPD_EINVAL, "T, Y and Ytil_out are required");
+  if (M < 1 || M > kMaxN || N < 1 || N > kMaxN) return fail(CPD_EINVAL, "M and N must be in [1, 2^30]");
+  if (precision != CPD_FP64 && precision != CPD_FP32) return fail(CPD_EINVAL, "unknown precision");
+  if (!(sigma2 > 0.0) || !std::isfinite(sigma2)) return fail(CPD_EINVAL, "sigma2 must be > 0");
+  if (!(w >= 0.0 && w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool fp64 = precision == CPD_FP64;
+  const size_t es = fp64 ? 8 : 4, v4 = fp64 ? sizeof(dvec4) : sizeof(float4);
+  int dev = 0, sms = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const EstepPlan ep = plan_estep(M, N, fp64, sms);
+  Buf T4, Y4, Yb, Yt4, pA, pB, sums, flags, P1, den, st, stage;
+  auto release = [&]() {
+    for (Buf* b : {&T4, &Y4, &Yb, &Yt4, &pA, &pB, &sums, &flags, &P1, &den, &st, &stage}) b->release();
+  };
+  auto run = [&]() -> cpd_status {
+    STATUS_TRY(T4.ensure((size_t)M * v4));
+    STATUS_TRY(Y4.ensure((size_t)N * v4));
+    STATUS_TRY(Yb.ensure((size_t)N * v4));
+    STATUS_TRY(Yt4.ensure((size_t)M * v4));
+    STATUS_TRY(pA.ensure((size_t)ep.partA_elems * es));
+    STATUS_TRY(pB.ensure((size_t)ep.partB_elems * es));
+    STATUS_TRY(sums.ensure((size_t)ep.sums_elems * sizeof(double)));
+    STATUS_TRY(flags.ensure((size_t)ep.flags_elems * sizeof(int)));
+    STATUS_TRY(P1.ensure((size_t)M * sizeof(double)));
+    STATUS_TRY(den.ensure((size_t)N * sizeof(double)));
+    STATUS_TRY(st.ensure(sizeof(DevState)));
+    STATUS_TRY(upload_points(nullptr, T, M, T4.p, false, stage, fp64, s));
+    STATUS_TRY(upload_points(nullptr, Y, N, Y4.p, true, stage, fp64, s));
+    launch_state_init(st.as<DevState>(), sigma2, s);
+    launch_state_params(st.as<DevState>(), w, 1.0, 0.0, 0.0, 0, nullptr, M, N, 0, s);
+    if (fp64)
+      launch_estep<double>(ep, T4.as<dvec4>(), nullptr, M, Y4.as<dvec4>(), Yb.as<dvec4>(), N, pA.as<double>(),
+                           pB.as<double>(), sums.as<double>(), flags.as<int>(), Yt4.as<dvec4>(), nullptr, P1.as<double>(),
+                           den.as<double>(), st.as<DevState>(), false, s);
+    else
+      launch_estep<float>(ep, T4.as<float4>(), nullptr, M, Y4.as<float4>(), Yb.as<float4>(), N, pA.as<float>(),
+                          pB.as<float>(), sums.as<double>(), flags.as<int>(), Yt4.as<float4>(), nullptr, P1.as<double>(),
+                          den.as<double>(), st.as<DevState>(), false, s);
+    CUDA_TRY(cudaGetLastError());
+    STATUS_TRY(download_points(Yt4.p, M, Ytil_out, stage, fp64, s));
+    if (P1_out) CUDA_TRY(cudaMemcpyAsync(P1_out, P1.p, (size_t)M * sizeof(double), cudaMemcpyDefault, s));
+    if (den_out) CUDA_TRY(cudaMemcpyAsync(den_out, den.p, (size_t)N * sizeof(double), cudaMemcpyDefault, s));
+    DevState h;
+    CUDA_TRY(cudaMemcpyAsync(&h, st.p, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (sums_out) {
+      sums_out[0] = h.vsum;
+      sums_out[1] = h.loglik;
+    }
+    if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+    return CPD_OK;
+  };
+  const cpd_status r = run();
+  cudaStreamSynchronize(s);
+  release();
+  return r;
+}
+
+cpd_status cpd_register(const void* X, int64_t M, const void* Y, int64_t N, const cpd_params* p, void* stream,
+                        void* T_out, void* W_out, double* sigma2_out, int32_t* iters_done) {
+  g_err.clear();
+  if (!T_out) return fail(CPD_EINVAL, "T_out is NULL");
+  if (!Y) return fail(CPD_EINVAL, "Y is NULL");
+  if (N < 1 || N > kMaxN) return fail(CPD_EINVAL, "N must be in [1, 2^30]");
+  cpd_ctx* c = nullptr;
+  STATUS_TRY(cpd_setup(X, M, p, stream, &c));
+  cpd_status s = cpd_iterate(c, Y, N, p->max_iter, T_out, sigma2_out, iters_done);
+  if (s == CPD_OK && W_out) s = cpd_get_W(c, W_out);
+  const std::string keep = g_err;
+  cpd_destroy(c);
+  g_err = keep;
+  return s;
+}
+
+void cpd_destroy(cpd_ctx* c) {
+  if (!c) return;
+  DeviceGuard guard(c->dev);
+  cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,404 @@
+"""CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: the FP64 path within 1e-10 relative (Frobenius) on T and sigma2,
+the FP32 path within 1e-4; E-step intermediates as stated per test.  Inputs
+are the seeded generator's point sets (uniform model points, Gaussian-RBF
+deformation, noise, optional uniform outliers)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_06281_gb300 import cpd, datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_06281_gb300 import build
+    build.build()
+    cpd.load()
+
+
+def dev(a, prec):
+    return torch.tensor(np.asarray(a), dtype=torch.float64 if prec == cpd.FP64 else torch.float32,
+                        device="cuda")
+
+
+def host(t):
+    return t.double().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t, dtype=np.float64)
+
+
+def sigma2_tol(tol_T, T, sigma2):
+    """sigma2 tolerance implied by a relative tolerance tol_T on T: sigma2 is a
+    mean of |y - t|^2 / D over pairs at distance ~ sqrt(D sigma2), so an
+    error dt in T moves it by about 2 sqrt(D sigma2) dt / D, i.e. a relative
+    error of 2 |T|_rms tol_T / sqrt(D sigma2)."""
+    t_rms = float(np.sqrt((np.asarray(T) ** 2).sum(1).mean()))
+    return tol_T * max(1.0, 2.0 * t_rms / math.sqrt(3.0 * sigma2))
+
+
+def rel(a, b):
+    return float(np.linalg.norm(host(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def pointsets(M, n_out=0, n_in=None, seed=0, amp=0.15):
+    return datagen.gen(M, n_out=n_out, amp=amp, noise=0.01, seed=seed, n_in=n_in)
+
+
+# --------------------------------------------------------------- E-step
+ESTEP_SIZES = [(1, 1), (3, 7), (33, 129), (300, 517), (1100, 2100), (2100, 1030)]
+
+
+@pytest.mark.parametrize("M,N", ESTEP_SIZES)
+@pytest.mark.parametrize("sigma2", [0.05, 1e-4])
+def test_estep_fp64(M, N, sigma2):
+    ps = pointsets(M, n_out=max(N - M, 0), n_in=min(M, N), seed=M + N)
+    T, Y = ps.Yhat, ps.Y
+    o = oracle.estep(T, Y, sigma2, 0.1)
+    assert o["status"] == oracle.OK
+    g = cpd.estep(dev(T, cpd.FP64), dev(Y, cpd.FP64), sigma2, 0.1, cpd.FP64)
+    np.testing.assert_allclose(host(g["den"]), o["den"], rtol=1e-12)
+    np.testing.assert_allclose(host(g["P1"]), o["P1"], rtol=1e-11)
+    assert rel(g["Ytil"], o["Ytil"]) <= 1e-12
+    vs = float((o["S"] / o["P1"] - 2 * (o["Ytil"] * T).sum(1) + (T * T).sum(1)).sum())
+    assert g["vsum"] == pytest.approx(vs, rel=1e-8, abs=1e-12)
+    assert g["loglik"] == pytest.approx(o["loglik"], rel=1e-12)
+
+
+def fp32_den_rtol(sigma2):
+    """Bound on the relative error of an FP32 column denominator.
+
+    The FP32 path evaluates 2^(-|q y - q t|^2) with q = sqrt(log2(e)/(2 sigma2))
+    applied to the coordinates first.  Each scaled coordinate carries an
+    absolute rounding error of at most 2^-24 q |c| (|c| <= 1.5 for these
+    point sets), so the exponent d'^2 is off by at most
+    2 d' sqrt(3) * 2 * 2^-24 * 1.5 q, and the Gaussian by ln 2 times that.
+    Terms that matter for den have d'^2 <= 25 (d' <= 5); ex2.approx and the
+    FP32 accumulation add ~1e-6.  Hence rtol = 3e-6 q + 2e-6."""
+    q = math.sqrt(1.4426950408889634 / (2 * sigma2))
+    return 3e-6 * q + 2e-6
+
+
+@pytest.mark.parametrize("M,N", ESTEP_SIZES)
+@pytest.mark.parametrize("sigma2", [0.05, 1e-3, 1e-4])
+def test_estep_fp32(M, N, sigma2):
+    ps = pointsets(M, n_out=max(N - M, 0), n_in=min(M, N), seed=M + 2 * N)
+    T = ps.Yhat.astype(np.float32).astype(np.float64)
+    Y = ps.Y.astype(np.float32).astype(np.float64)
+    o = oracle.estep(T, Y, sigma2, 0.1)
+    assert o["status"] == oracle.OK
+    g = cpd.estep(dev(T, cpd.FP32), dev(Y, cpd.FP32), sigma2, 0.1, cpd.FP32)
+    np.testing.assert_allclose(host(g["den"]), o["den"], rtol=fp32_den_rtol(sigma2))
+    # rows with almost no mass have larger relative error; weight by mass
+    p1 = host(g["P1"])
+    assert np.abs(p1 - o["P1"]).max() <= 2e-5 * max(o["P1"].max(), 1.0)
+    assert rel(g["Ytil"], o["Ytil"]) <= 1e-5
+    assert g["loglik"] == pytest.approx(o["loglik"], rel=1e-5, abs=1e-3)
+
+
+def test_estep_host_arrays_match_device_arrays():
+    ps = pointsets(700, n_out=50, seed=3)
+    a = cpd.estep(ps.Yhat.astype(np.float32), ps.Y.astype(np.float32), 1e-3, 0.2, cpd.FP32)
+    b = cpd.estep(dev(ps.Yhat, cpd.FP32), dev(ps.Y, cpd.FP32), 1e-3, 0.2, cpd.FP32)
+    assert np.array_equal(a["Ytil"], host(b["Ytil"]).astype(np.float32))
+    assert np.array_equal(a["P1"], host(b["P1"]))
+
+
+def test_estep_row_underflow_reports_enumeric():
+    X = np.array([[0.0, 0, 0], [0.01, 0, 0], [50.0, 50.0, 50.0]])
+    Y = np.array([[0.0, 0.001, 0], [0.012, 0, 0]])
+    for prec in (cpd.FP32, cpd.FP64):
+        with pytest.raises(cpd.CpdError) as ei:
+            cpd.estep(dev(X, prec), dev(Y, prec), 1e-3, 0.1, prec)
+        assert ei.value.status == cpd.ENUMERIC
+
+
+# -------------------------------------------------------- registration
+def run_gpu(X, Y, prec, n_iter, K=0, w=0.1, lam=2.0, beta=2.0, gt=None):
+    with cpd.Context(dev(X, prec), precision=prec, w=w, beta=beta, lam=lam, K=K) as ctx:
+        if gt is not None:
+            ctx.set_ground_truth(dev(gt, prec), 0.0)
+        T, s2, it = ctx.iterate(dev(Y, prec), n_iter)
+        hist = ctx.history(it)
+    return host(T), s2, it, hist
+
+
+def test_register_fp64_m500():
+    cfg = datagen.WORKLOADS["fp64_m500"]
+    ps = pointsets(cfg["M"], amp=cfg["amp"], seed=cfg["seed"])
+    ref = oracle.register(ps.X, ps.Y, w=cfg["omega"], beta=cfg["beta"], lam_reg=cfg["lam"], n_iter=cfg["iters"])
+    T, s2, it, hist = run_gpu(ps.X, ps.Y, cpd.FP64, cfg["iters"], w=cfg["omega"], lam=cfg["lam"],
+                              beta=cfg["beta"], gt=ps.Yhat)
+    assert it == cfg["iters"]
+    assert rel(T, ref["T"]) <= FP64_TOL
+    stol = sigma2_tol(FP64_TOL, ref["T"], ref["sigma2"])
+    assert s2 == pytest.approx(ref["sigma2"], rel=stol)
+    np.testing.assert_allclose(hist["sigma2"], ref["sigma2_hist"], rtol=stol)
+    np.testing.assert_allclose(hist["loglik"], ref["loglik_hist"], rtol=1e-10)
+    assert hist["rmse"][-1] == pytest.approx(oracle.rmse(ref["T"], ps.Yhat), rel=1e-9)
+
+
+def test_register_fp32_m5000():
+    cfg = datagen.WORKLOADS["fp32_m5000"]
+    ps = pointsets(cfg["M"], amp=cfg["amp"], seed=cfg["seed"])
+    X, Y = ps.X.astype(np.float32), ps.Y.astype(np.float32)
+    ref = oracle.register(X, Y, w=cfg["omega"], beta=cfg["beta"], lam_reg=cfg["lam"], n_iter=cfg["iters"])
+    T, s2, it, hist = run_gpu(X, Y, cpd.FP32, cfg["iters"], w=cfg["omega"], lam=cfg["lam"], beta=cfg["beta"])
+    assert it == cfg["iters"]
+    assert rel(T, ref["T"]) <= FP32_TOL
+    stol = sigma2_tol(FP32_TOL, ref["T"], ref["sigma2"])
+    assert s2 == pytest.approx(ref["sigma2"], rel=stol)
+    np.testing.assert_allclose(hist["sigma2"], ref["sigma2_hist"], rtol=stol)
+
+
+# (M = N = 1 collapses sigma2 to the rounding floor within a few iterations;
+# its closed form is checked separately on a far-apart pair.)
+RAGGED = [(1, 2), (2, 3), (31, 33), (127, 129), (513, 1025), (700, 450)]
+
+
+@pytest.mark.parametrize("M,N", RAGGED)
+@pytest.mark.parametrize("prec", [cpd.FP64, cpd.FP32])
+def test_register_ragged_sizes(M, N, prec):
+    ps = pointsets(M, n_out=max(N - M, 0), n_in=min(M, N), seed=11 * M + N)
+    X, Y = ps.X, ps.Y
+    if prec == cpd.FP32:
+        X, Y = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    ref = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=12)
+    assert ref["status"] == oracle.OK
+    T, s2, it, _ = run_gpu(X, Y, prec, 12)
+    tol = FP64_TOL if prec == cpd.FP64 else FP32_TOL
+    assert it == 12
+    assert rel(T, ref["T"]) <= tol
+    assert s2 == pytest.approx(ref["sigma2"], rel=sigma2_tol(tol, ref["T"], ref["sigma2"]))
+
+
+def test_single_point_closed_form_on_gpu():
+    x = np.array([[0.1, -0.2, 0.3]])
+    y = np.array([[2.1, 1.8, -1.7]])
+    r2 = float(((y - x) ** 2).sum())
+    T, s2, it, hist = run_gpu(x, y, cpd.FP64, 6, lam=2.0)
+    s = r2 / 3
+    for k in range(6):
+        f = 2.0 * s / (1 + 2.0 * s)
+        s = f * f * r2 / 3
+        assert hist["sigma2"][k] == pytest.approx(s, rel=1e-11)
+
+
+@pytest.mark.parametrize("prec,M,K,iters", [(cpd.FP64, 300, 17, 20), (cpd.FP32, 2000, 200, 40)])
+def test_lowrank_basis(prec, M, K, iters):
+    ps = pointsets(M, seed=5)
+    X, Y = ps.X, ps.Y
+    if prec == cpd.FP32:
+        X, Y = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
+    ref = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=iters, K=K)
+    T, s2, it, _ = run_gpu(X, Y, prec, iters, K=K)
+    tol = FP64_TOL if prec == cpd.FP64 else FP32_TOL
+    assert rel(T, ref["T"]) <= tol
+    assert s2 == pytest.approx(ref["sigma2"], rel=sigma2_tol(tol, ref["T"], ref["sigma2"]))
+
+
+def test_outlier_weight_zero_and_large():
+    ps = pointsets(200, n_out=40, seed=21)
+    for w in (0.0, 0.7):
+        ref = oracle.register(ps.X, ps.Y, w=w, beta=2.0, lam_reg=10.0, n_iter=15)
+        T, s2, _, _ = run_gpu(ps.X, ps.Y, cpd.FP64, 15, w=w, lam=10.0)
+        assert rel(T, ref["T"]) <= FP64_TOL
+
+
+# ------------------------------------------------------------- setup / M-step
+def test_eigenbasis_fp64():
+    ps = pointsets(400, seed=8)
+    U0, l0 = oracle.eig(ps.X, 2.0)
+    Phi = oracle.gram(ps.X, 2.0)
+    with cpd.Context(dev(ps.X, cpd.FP64), precision=cpd.FP64) as ctx:
+        U, lam = ctx.basis()
+    assert np.all(np.diff(lam) <= 0) and np.all(lam >= 0)
+    np.testing.assert_allclose(lam, l0, rtol=0, atol=1e-11 * l0[0])
+    k = 60
+    res = np.abs(Phi @ U[:, :k] - U[:, :k] * lam[:k]).max()
+    assert res <= 1e-11 * lam[0]
+    assert np.abs(U.T @ U - np.eye(400)).max() <= 1e-11
+
+
+def test_standalone_mstep_matches_oracle():
+    ps = pointsets(250, seed=9)
+    s = datagen.Stream(99)
+    Ytil = ps.X + 0.05 * s.normal(750).reshape(250, 3)
+    U0, l0 = oracle.eig(ps.X, 2.0)
+    To, Wo, _ = oracle.mstep(U0, l0, ps.X, Ytil, 2.0, 0.25)
+    with cpd.Context(dev(ps.X, cpd.FP64), precision=cpd.FP64, lam=2.0) as ctx:
+        T, W = ctx.mstep(dev(Ytil, cpd.FP64), 0.25, want_W=True)
+    assert rel(T, To) <= 1e-12
+    assert rel(W, Wo) <= 1e-9       # (Phi + 0.5 I)^-1 is well conditioned here
+
+
+def test_W_after_registration_fp64():
+    ps = pointsets(120, seed=12)
+    ref = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=3)
+    with cpd.Context(dev(ps.X, cpd.FP64), precision=cpd.FP64) as ctx:
+        with pytest.raises(cpd.CpdError) as ei:
+            ctx.W()
+        assert ei.value.status == cpd.ESTATE
+        ctx.iterate(dev(ps.Y, cpd.FP64), 3)
+        W = ctx.W()
+    # W itself is ill-conditioned in the full basis: compare Phi W (= T - X)
+    Phi = oracle.gram(ps.X, 2.0)
+    assert rel(Phi @ host(W), ref["T"] - ps.X) <= 1e-9
+
+
+# --------------------------------------------------------- API behaviour
+def test_host_and_device_inputs_give_identical_results():
+    ps = pointsets(700, n_out=100, seed=13)
+    X, Y = ps.X.astype(np.float32), ps.Y.astype(np.float32)
+    with cpd.Context(X, precision=cpd.FP32) as a:
+        Ta, sa, _ = a.iterate(Y, 10)
+    with cpd.Context(dev(X, cpd.FP32), precision=cpd.FP32) as b:
+        Tb, sb, _ = b.iterate(dev(Y, cpd.FP32), 10)
+    assert isinstance(Ta, np.ndarray)
+    assert np.array_equal(Ta, Tb.cpu().numpy()) and sa == sb
+
+
+def test_iterations_in_pieces_equal_one_call():
+    ps = pointsets(600, seed=14)
+    X, Y = dev(ps.X, cpd.FP32), dev(ps.Y, cpd.FP32)
+    with cpd.Context(X) as a:
+        Ta, sa, ia = a.iterate(Y, 19)
+    with cpd.Context(X) as b:
+        b.iterate(Y, 3, want_T=False)
+        b.iterate(Y, 8, want_T=False)
+        Tb, sb, ib = b.iterate(Y, 8)
+        b.reset()
+        Tc, sc, ic = b.iterate(Y, 19)
+    assert ia == ib == ic == 19
+    assert torch.equal(Ta, Tb) and torch.equal(Ta, Tc) and sa == sb == sc
+
+
+def test_tolerance_stops_early():
+    ps = pointsets(500, seed=15)
+    with cpd.Context(dev(ps.X, cpd.FP64), precision=cpd.FP64, tol=1e-4) as ctx:
+        _, _, it = ctx.iterate(dev(ps.Y, cpd.FP64), 400)
+    assert 5 < it < 400
+    ref = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=it)
+    prev = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=it - 1)
+    step = np.sqrt(((ref["T"] - prev["T"]) ** 2).sum(1).mean())
+    assert step <= 1e-4
+
+
+def test_ground_truth_tolerance_gives_time_to_tolerance():
+    cfg = datagen.WORKLOADS["fp64_m500"]
+    ps = pointsets(cfg["M"], amp=cfg["amp"], seed=cfg["seed"])
+    with cpd.Context(dev(ps.X, cpd.FP64), precision=cpd.FP64) as ctx:
+        ctx.set_ground_truth(dev(ps.Yhat, cpd.FP64), 5e-3)
+        _, _, it = ctx.iterate(dev(ps.Y, cpd.FP64), 200)
+        h = ctx.history(it)
+    assert it < 200 and h["rmse"][-1] <= 5e-3 and np.all(h["rmse"][:-1] > 5e-3)
+    ref = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=it)
+    assert oracle.rmse(ref["T"], ps.Yhat) == pytest.approx(h["rmse"][-1], rel=1e-9)
+
+
+def test_register_entry_point():
+    ps = pointsets(300, seed=16)
+    ref = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=25)
+    T, W, s2, it = cpd.register(dev(ps.X, cpd.FP64), dev(ps.Y, cpd.FP64), precision=cpd.FP64, max_iter=25,
+                                want_W=True)
+    assert it == 25 and rel(T, ref["T"]) <= FP64_TOL
+    Phi = oracle.gram(ps.X, 2.0)
+    assert rel(Phi @ host(W), ref["T"] - ps.X) <= 1e-9
+
+
+def test_injected_solver_failure(monkeypatch):
+    monkeypatch.setenv("CPD_FAULT", "solver")
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.Context(dev(np.random.default_rng(0).random((20, 3)), cpd.FP64), precision=cpd.FP64)
+    assert ei.value.status == cpd.ESOLVER
+
+
+def test_injected_nan_variance_reports_enumeric(monkeypatch):
+    ps = pointsets(50, seed=17)
+    with cpd.Context(dev(ps.X, cpd.FP32)) as ctx:
+        monkeypatch.setenv("CPD_FAULT", "nan_sigma")
+        with pytest.raises(cpd.CpdError) as ei:
+            ctx.iterate(dev(ps.Y, cpd.FP32), 3)
+        assert ei.value.status == cpd.ENUMERIC
+        monkeypatch.delenv("CPD_FAULT")
+        _, _, ds = ctx.state()
+        assert ds == cpd.ENUMERIC
+        ctx.reset()
+        _, s2, it = ctx.iterate(dev(ps.Y, cpd.FP32), 3)
+        assert it == 3 and math.isfinite(s2)
+
+
+def test_model_point_far_from_scene_reports_enumeric():
+    ps = pointsets(100, seed=18)
+    X = np.vstack([ps.X, [[40.0, 40.0, 40.0]]])
+    with cpd.Context(dev(X, cpd.FP32), sigma2_init=1e-3) as ctx:
+        with pytest.raises(cpd.CpdError) as ei:
+            ctx.iterate(dev(ps.Y, cpd.FP32), 2)
+    assert ei.value.status == cpd.ENUMERIC
+
+
+def test_history_bounds():
+    ps = pointsets(64, seed=19)
+    with cpd.Context(dev(ps.X, cpd.FP32)) as ctx:
+        ctx.iterate(dev(ps.Y, cpd.FP32), 4)
+        with pytest.raises(cpd.CpdError):
+            ctx.history(5)
+        assert len(ctx.history(4)["sigma2"]) == 4
+
+
+# ------------------------------------------------- full size (20000 x 20000)
+@pytest.fixture(scope="module")
+def big():
+    cfg = datagen.WORKLOADS["fp32_m20000_full"]
+    ps = pointsets(cfg["M"], amp=cfg["amp"], seed=cfg["seed"])
+    X = ps.X.astype(np.float32).astype(np.float64)
+    Y = ps.Y.astype(np.float32).astype(np.float64)
+    return ps, X, Y
+
+
+def test_full_size_estep_elementwise(big):
+    ps, X, Y = big
+    T = ps.Yhat.astype(np.float32).astype(np.float64)
+    o = oracle.estep(T, Y, 1e-3, 0.1)
+    g = cpd.estep(dev(T, cpd.FP32), dev(Y, cpd.FP32), 1e-3, 0.1, cpd.FP32)
+    np.testing.assert_allclose(host(g["den"]), o["den"], rtol=fp32_den_rtol(1e-3))
+    assert rel(g["Ytil"], o["Ytil"]) <= 1e-5
+    assert g["vsum"] == pytest.approx(
+        float((o["S"] / o["P1"] - 2 * (o["Ytil"] * T).sum(1) + (T * T).sum(1)).sum()), rel=1e-3)
+
+
+@pytest.mark.parametrize("K", [0, 200])
+def test_full_size_first_iteration_properties(big, K):
+    """At M = N = 20000 (the benchmark's launch configuration) one iteration
+    from T = X: the M-step output satisfies Eq. 15 (full basis) and
+    T - X = Phi W (Eq. 9-11) on sampled rows; sigma2 equals Eq. 18 at the
+    returned T; the E-step input is the oracle's (T = X is known)."""
+    ps, X, Y = big
+    M = X.shape[0]
+    s0 = oracle.sigma2_init(X, Y)
+    o = oracle.estep(X, Y, s0, 0.1)
+    with cpd.Context(dev(X, cpd.FP32), precision=cpd.FP32, K=K) as ctx:
+        T, s1, it = ctx.iterate(dev(Y, cpd.FP32), 1)
+        W = host(ctx.W())
+    T = host(T)
+    R = o["Ytil"] - X
+    rows = np.random.default_rng(0).choice(M, 200, replace=False)
+    d2 = ((X[rows, None, :] - X[None, :, :]) ** 2).sum(-1)
+    Phi_rows = np.exp(-d2 / 8.0)                      # beta = 2: rows of Eq. 11
+    lhs = Phi_rows @ W
+    assert np.linalg.norm(T[rows] - X[rows] - lhs) <= 1e-4 * np.linalg.norm(T[rows] - X[rows])
+    if K == 0:
+        res = lhs + 2.0 * s0 * W[rows] - R[rows]
+        assert np.linalg.norm(res) <= 1e-4 * np.linalg.norm(R[rows])
+    s1_ref = oracle.sigma2_update(o["S"], o["P1"], o["Ytil"], T)
+    assert s1 == pytest.approx(s1_ref, rel=1e-4)

@@ -20,10 +20,10 @@ MUTANTS = {
     "no_row_normalisation": ("Ytil[m * D + d] = py[d] / p1;", "Ytil[m * D + d] = py[d];"),
     "outlier_ratio_inverted": ("((double)M / (double)N)", "((double)N / (double)M)"),
     "gram_width_wrong": ("exp(-d2 / (2.0 * beta * beta))", "exp(-d2 / (beta * beta))"),
-    "mstep_missing_eigenvalue_factor": ("t += U[m * K + i] * (lam[i] * inv) * Acoef[i * D + d];",
-                                        "t += U[m * K + i] * inv * Acoef[i * D + d];"),
+    "mstep_missing_eigenvalue_factor": ("sdiag[i] = lam[i] * dinv[i];", "sdiag[i] = dinv[i];"),
     "mstep_drops_X": ("T[m * D + d] = X[m * D + d] + t;", "T[m * D + d] = t;"),
-    "mstep_residual_sign": ("(Ytil[m * D + d] - X[m * D + d])", "(X[m * D + d] - Ytil[m * D + d])"),
+    "mstep_residual_sign": ("A[i * D + d] += u * (Ytil[m * D + d] - X[m * D + d]);",
+                            "A[i * D + d] += u * (X[m * D + d] - Ytil[m * D + d]);"),
     "sigma2_cross_term_sign": ("(t1 - 2.0 * t2 + t3)", "(t1 + 2.0 * t2 + t3)"),
     "sigma2_normaliser": ("return (t1 - 2.0 * t2 + t3) / ((double)D * (double)M);",
                           "return (t1 - 2.0 * t2 + t3) / ((double)M);"),
