@@ -116,13 +116,14 @@ KERNELS = ["e_pass_a", "e_reduce_a", "e_pass_b", "e_reduce_b", "m_project", "m_d
 OPS_PER_PAIR = {"e_pass_a": 7, "e_pass_b": 12}      # FP32 pipe ops per Gaussian pair (kernel mix)
 
 
-def roofline_entries(phase_ms, launches, M, N, K, peaks, es=4):
-    """Algorithmic work per launch / measured average launch duration."""
+def roofline_entries(phase_ms, M, N, K, peaks, es=4):
+    """Algorithmic work per launch / measured average launch duration
+    (phase_ms: milliseconds per launch of each kernel)."""
     clk = peaks["sm_max_mhz"] * 1e6
     sms = 152
     out = {}
     for i, name in enumerate(KERNELS):
-        t = phase_ms[i] / launches / 1e3            # s per launch
+        t = phase_ms[i] / 1e3                       # s per launch
         if t <= 0:
             continue
         if name in OPS_PER_PAIR:
@@ -311,7 +312,7 @@ def main():
     ev0.record()
     for _ in range(R):
         ctx.reset()
-        phases += np.array(ctx.iterate_profiled(Y, I))
+        phases += np.array(ctx.iterate_profiled(Y, I)) / R     # per-launch averages
     ev1.record()
     torch.cuda.synchronize()
     barrier()
@@ -320,15 +321,15 @@ def main():
     value = world * steps / (t_ms / 1e3)
 
     # per-kernel roofline from the events inside the timed region
-    roof = roofline_entries(phases, steps, M, N, K, peaks)
+    roof = roofline_entries(phases, M, N, K, peaks)
     dominant = max((k for k in roof if "frac" in roof[k]), key=lambda k: roof[k]["ms"])
     rd = dict(roof[dominant])
     tr = traffic_for(dominant)
     roofline = dict(kernel=dominant, bound=rd["bound"], achieved=rd["achieved"], peak=rd["peak"], unit=rd["unit"],
                     frac=rd["frac"], traffic=tr, peak_source=peaks["source"])
-    e_ms = sum(phases[:4]) / steps
-    m_ms = sum(phases[4:7]) / steps
-    estep = dict(pairs_per_s=M * N / (e_ms / 1e3), ms_per_iter=e_ms,
+    e_ms = sum(phases[:4])
+    m_ms = sum(phases[4:7])
+    estep = dict(pairs_per_s=M * N / (e_ms / 1e3), ms_per_iter=e_ms, m_step_ms_per_iter=m_ms,
                  pass_a=roof.get("e_pass_a"), pass_b=roof.get("e_pass_b"))
 
     # time to tolerance (RMSE of Eq. 22 against the noise-free ground truth)
@@ -381,11 +382,11 @@ def main():
         nl = max(1, min(R, 10))
         for _ in range(nl):
             ctxl.reset()
-            ph += np.array(ctxl.iterate_profiled(Y, I))
+            ph += np.array(ctxl.iterate_profiled(Y, I)) / nl
         b.record()
         torch.cuda.synchronize()
         lms = a.elapsed_time(b)
-        lroof = roofline_entries(ph, nl * I, M, N, 200, peaks)
+        lroof = roofline_entries(ph, M, N, 200, peaks)
         lowrank = dict(K=200, iters_per_s=nl * I / (lms / 1e3), setup_s=lsetup,
                        kernel_ms={k: v["ms"] for k, v in lroof.items()})
         ctxl.close()

@@ -104,9 +104,11 @@ struct EstepPlan {
 EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms);
 
 struct MstepPlan {
-  int p_col_tiles, p_row_chunks, p_rows_per_chunk;   // projection grid
-  int e_blocks;                                      // expansion grid
-  int64_t partP_elems;                               // scratch (elements of F)
+  int64_t ldU, ldM;                                  // row strides of U (M x ldU) and U^T (K x ldM)
+  int p_col_tiles, p_row_chunks, p_rows_per_chunk;   // projection U^T R grid
+  int e_col_tiles, e_row_chunks, e_rows_per_chunk;   // expansion U B grid
+  int e_blocks;                                      // expansion reduction grid
+  int64_t part_elems;                                // scratch (elements of F), shared by both
   int64_t sums_elems;                                // double scratch for block sums
 };
 MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms);
@@ -130,27 +132,28 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
                   bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr);
 
-// M-step: projection A = U^T R, diagonal update, expansion T = X + U B and
-// the Eq. 18 variance in the epilogue.  With `iteration` false the state is
-// not advanced (standalone M-step: T_out receives T, no sigma2 update).
+// M-step: projection a = U^T R, diagonal update, expansion T = X + U B and
+// the Eq. 18 variance in the epilogue.  U is M x ldU, Ut = U^T is K x ldM.
+// With `iteration` false the state is not advanced (standalone M-step:
+// T4 receives T, no sigma2 update, st supplies sigma2 and lambda).
 template <typename F>
-void launch_mstep(const MstepPlan& pl, const F* U, int64_t ldU, const double* lam, int64_t M,
-                  int64_t K, const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
+void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* lam, int64_t M, int64_t K,
+                  const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
-                  const typename Vec<F>::t4* Yhat4, F* partP, double* sums,
+                  const typename Vec<F>::t4* Yhat4, F* part, double* sums,
                   typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, DevState* st,
                   bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr);
 
 // W = U C (C from the last M-step), written as 4-vectors.
 template <typename F>
-void launch_w(const MstepPlan& pl, const F* U, int64_t ldU, int64_t M, int64_t K,
-              const typename Vec<F>::t4* C4, typename Vec<F>::t4* W4, cudaStream_t s);
+void launch_w(const MstepPlan& pl, const F* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
+              typename Vec<F>::t4* W4, DevState* st, cudaStream_t s);
 
 // Setup helpers.
 void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double* Phi, cudaStream_t s);
 template <typename F>
-void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, const double* w,
-                          double* lam, cudaStream_t s);
+void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
+                          const double* w, double* lam, cudaStream_t s);
 template <typename F>
 void launch_sigma2_init(const typename Vec<F>::t4* X4, int64_t M, const typename Vec<F>::t4* Y4,
                         int64_t N, double* scratch, DevState* st, cudaStream_t s);
@@ -168,7 +171,6 @@ void launch_state_params(DevState* st, double w, double lambda, double tol, doub
 template <typename F>
 void launch_residual(const typename Vec<F>::t4* Yt4, const typename Vec<F>::t4* X4, typename Vec<F>::t4* R4,
                      int64_t M, cudaStream_t s);
-// Sets kernel attributes (dynamic shared memory); call before any stream capture.
-void mstep_prepare();
+
 
 }  // namespace fcpd

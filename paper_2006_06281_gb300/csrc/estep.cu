@@ -49,8 +49,11 @@ constexpr float kFar = 1e18f;    // padding coordinate: its Gaussian weight is e
 constexpr double kColFloor = 0x1p-88;   // FP32 column sums below this take the exact path
 constexpr double kRowFloor = 0x1p-90;   // FP32 row masses below this take the exact path
 
+// q = sqrt(log2(e) / (2 sigma2)) in FP32 (GB300's FP64 rate is a small
+// fraction of FP32; every kernel derives q with this same function, so the
+// scaled coordinates agree bitwise between passes).
 __device__ __forceinline__ float scale_q(double sigma2) {
-  return (float)sqrt(kLog2e / (2.0 * sigma2));
+  return sqrtf(1.44269504f / (2.0f * (float)sigma2));
 }
 
 __device__ __forceinline__ float warp_max(float v) {
@@ -64,26 +67,64 @@ __device__ __forceinline__ float warp_sumf(float v) {
   return v;
 }
 
+// Packed FP32 pairs (two lanes of one 64-bit register) for the f32x2
+// arithmetic of sm_100-class GPUs: one instruction issues two FP32 ops,
+// leaving issue slots for the MUFU ex2 and shared-memory loads.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b) {
+  f2_t r;
+  asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t r, float& a, float& b) {
+  asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+  f2_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // ------------------------------------------------------------------ pass A
+// FP32 pass A: each thread owns kColsA32 scene points as kColsA32/2 packed
+// pairs; a model point is broadcast from shared memory as duplicated pairs
+// {(x,x),(y,y)},{(z,z),-}.  Per pair of Gaussians: 3 sub + 1 mul + 2 fma on
+// f32x2, two MUFU ex2 and two scalar adds.
 __global__ void __launch_bounds__(kThreadsA)
 passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
           int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_cols = 0;
-  __shared__ float4 sT[kTileA];
+  constexpr int P = kColsA32 / 2;
+  __shared__ ulonglong2 sT[kTileA][2];
   const float q = scale_q(st->sigma2);
   const int nbase = blockIdx.x * (kThreadsA * kColsA32) + threadIdx.x;
-  float yx[kColsA32], yy[kColsA32], yz[kColsA32], acc[kColsA32];
+  f2_t yx[P], yy[P], yz[P];
+  float acc[2 * P];
 #pragma unroll
-  for (int j = 0; j < kColsA32; ++j) {
-    const int n = nbase + j * kThreadsA;
-    if (n < N) {
-      const float4 y = Y4[n];
-      yx[j] = q * y.x; yy[j] = q * y.y; yz[j] = q * y.z;
-    } else {
-      yx[j] = -kFar; yy[j] = -kFar; yz[j] = -kFar;
-    }
-    acc[j] = 0.f;
+  for (int p = 0; p < P; ++p) {
+    const int n0 = nbase + (2 * p) * kThreadsA, n1 = n0 + kThreadsA;
+    const float4 far4 = make_float4(-kFar / q, -kFar / q, -kFar / q, 0.f);
+    const float4 y0 = n0 < N ? Y4[n0] : far4;
+    const float4 y1 = n1 < N ? Y4[n1] : far4;
+    yx[p] = f2_pack(q * y0.x, q * y1.x);
+    yy[p] = f2_pack(q * y0.y, q * y1.y);
+    yz[p] = f2_pack(q * y0.z, q * y1.z);
+    acc[2 * p] = acc[2 * p + 1] = 0.f;
   }
   const int r0 = blockIdx.y * rows_per_chunk;
   const int r1 = min(M, r0 + rows_per_chunk);
@@ -91,32 +132,39 @@ passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4
     __syncthreads();
     for (int i = threadIdx.x; i < kTileA; i += kThreadsA) {
       const int m = base + i;
-      float4 t = make_float4(kFar, kFar, kFar, 0.f);
+      float tx = kFar, ty = kFar, tz = kFar;
       if (m < r1) {
-        t = T4[m];
-        t.x *= q; t.y *= q; t.z *= q;
+        const float4 t = T4[m];
+        tx = q * t.x; ty = q * t.y; tz = q * t.z;
       }
-      sT[i] = t;
+      sT[i][0] = make_ulonglong2(f2_pack(tx, tx), f2_pack(ty, ty));
+      sT[i][1] = make_ulonglong2(f2_pack(tz, tz), 0ull);
     }
     __syncthreads();
     const int cnt = min(kTileA, r1 - base);
 #pragma unroll 2
     for (int i = 0; i < cnt; ++i) {
-      const float4 t = sT[i];
+      const ulonglong2 a = sT[i][0];
+      const f2_t tz2 = sT[i][1].x;
 #pragma unroll
-      for (int j = 0; j < kColsA32; ++j) {
-        const float dx = yx[j] - t.x, dy = yy[j] - t.y, dz = yz[j] - t.z;
-        float d2 = dx * dx;
-        d2 = fmaf(dy, dy, d2);
-        d2 = fmaf(dz, dz, d2);
-        acc[j] += ex2_approx(-d2);
+      for (int p = 0; p < P; ++p) {
+        const f2_t dx = f2_sub(yx[p], a.x), dy = f2_sub(yy[p], a.y), dz = f2_sub(yz[p], tz2);
+        f2_t d2 = f2_mul(dx, dx);
+        d2 = f2_fma(dy, dy, d2);
+        d2 = f2_fma(dz, dz, d2);
+        float d0, d1;
+        f2_unpack(d2, d0, d1);                  // register halves: no move
+        acc[2 * p] += ex2_approx(-d0);          // scalar adds: no repacking of
+        acc[2 * p + 1] += ex2_approx(-d1);      // the MUFU results
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < kColsA32; ++j) {
-    const int n = nbase + j * kThreadsA;
-    if (n < N) partA[(size_t)blockIdx.y * N + n] = acc[j];
+  for (int p = 0; p < P; ++p) {
+    const float a0 = acc[2 * p], a1 = acc[2 * p + 1];
+    const int n0 = nbase + (2 * p) * kThreadsA, n1 = n0 + kThreadsA;
+    if (n0 < N) partA[(size_t)blockIdx.y * N + n0] = a0;
+    if (n1 < N) partA[(size_t)blockIdx.y * N + n1] = a1;
   }
 }
 
@@ -169,6 +217,12 @@ __device__ __forceinline__ double outlier_c(const DevState* st, int M, int N) {
 // ------------------------------------------------- pass A reduction (+ c)
 // den_n = sum of the split partials + c (Eq. 4).  Prepares pass B's scene
 // records and reduces the Eq. 3 log-likelihood sum_n ln den_n (+ constants).
+// A block owns kRedCols columns; kRedSub threads per column each sum a strided
+// subset of the chunks (coalesced across columns), then the subsets are added
+// in a fixed order -- deterministic.
+constexpr int kRedCols = 64;
+constexpr int kRedSub = kThreadsR / kRedCols;
+
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
 reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t4* __restrict__ Y4,
@@ -176,17 +230,29 @@ reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t
         double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
   __shared__ double sh[32];
+  __shared__ F part[kRedSub][kRedCols];
   __shared__ bool last;
+  __shared__ double c_sh;
   const double s2 = st->sigma2;
   const double w = st->w;
-  const double c = outlier_c(st, M, N);
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x == 0) c_sh = outlier_c(st, M, N);   // FP64 pow once per block
+  const int col = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
+  const int n = blockIdx.x * kRedCols + col;
+  F s = (F)0;   // FP32 partials summed in FP32 (fixed order), FP64 in FP64
+  if (n < N) {
+#pragma unroll 8
+    for (int k = sub; k < chunks; k += kRedSub) s += partA[(size_t)k * N + n];
+  }
+  part[sub][col] = s;
+  __syncthreads();
+  const double c = c_sh;
   double lnden = 0.0;
   int bad = 0;
-  if (n < N) {
-    double s = 0.0;
-    for (int k = 0; k < chunks; ++k) s += (double)partA[(size_t)k * N + n];
-    const double den = s + c;
+  if (sub == 0 && n < N) {
+    F tot = (F)0;
+#pragma unroll
+    for (int j = 0; j < kRedSub; ++j) tot += part[j][col];
+    const double den = (double)tot + c;
     const typename Vec<F>::t4 y = Y4[n];
     if constexpr (sizeof(F) == 4) {
       const float q = scale_q(s2);
@@ -195,9 +261,10 @@ reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t
         flag_cols[atomicAdd(&st->n_flag_cols, 1)] = n;
         Yb[n] = make_float4(q * y.x, q * y.y, q * y.z, 0.f);
       } else {
-        Yb[n] = make_float4(q * y.x, q * y.y, q * y.z, (float)(-log2(den)));
+        const float lid = -log2f((float)den);          // exponent offset of pass B
+        Yb[n] = make_float4(q * y.x, q * y.y, q * y.z, lid);
         if (den_out) den_out[n] = den;
-        lnden = log(den);
+        lnden = -0.69314718055994531 * (double)lid;    // ln den from the same log2
       }
     } else {
       // the column of Eq. 4 is 0/0 in double precision: the definition fails
@@ -218,7 +285,7 @@ reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t
   if (last) {
     __threadfence();
     double v = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sums)[i];
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(sums + i);
     const double tot = block_sum(v, sh);
     if (threadIdx.x == 0) {
       st->loglik = tot + (double)N * log((1.0 - w) / (double)M) - 1.5 * (double)N * log(2.0 * kPi * s2);
@@ -269,67 +336,95 @@ fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, in
       if (!(den > 0.0) || !isfinite(den)) {
         atomicExch(&st->status, (int)CPD_ENUMERIC);
       } else {
-        Yb[n].w = (float)(-log2(den));
+        const float lid = (float)(-log2(den));
+        Yb[n].w = lid;
         if (den_out) den_out[n] = den;
-        atomicAdd(&st->loglik, log(den));
+        atomicAdd(&st->loglik, -0.69314718055994531 * (double)lid);
       }
     }
   }
 }
 
 // ------------------------------------------------------------------ pass B
+// FP32 pass B: each thread owns kRowsB32 model points as packed pairs; scene
+// records are broadcast from shared memory as {(x,x),(y,y)},{(z,z),(l,l)}
+// with l = -log2 den_n.  Per pair of Gaussians: 3 sub + 1 mul + 2 fma for the
+// distance and 1 sub for the exponent on f32x2, two MUFU ex2, then scalar
+// 1 add + 4 fma per Gaussian to accumulate P1, PY (3) and V.
 __global__ void __launch_bounds__(kThreadsB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
           int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
-  __shared__ float4 sY[kTileB];
+  // the column list was consumed by fixA (the previous kernel) and the row
+  // list is filled only after this kernel: both can be cleared here
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->n_flag_cols = 0;
+    st->n_flag_rows = 0;
+  }
+  constexpr int P = kRowsB32 / 2;
+  __shared__ ulonglong2 sY[kTileB][2];
   const float q = scale_q(st->sigma2);
   const int mbase = blockIdx.x * (kThreadsB * kRowsB32) + threadIdx.x;
-  float tx[kRowsB32], ty[kRowsB32], tz[kRowsB32];
-  float p1[kRowsB32], px[kRowsB32], py[kRowsB32], pz[kRowsB32], v[kRowsB32];
+  f2_t tx[P], ty[P], tz[P];
+  float p1[2 * P], px[2 * P], py[2 * P], pz[2 * P], v[2 * P];
 #pragma unroll
-  for (int j = 0; j < kRowsB32; ++j) {
-    const int m = mbase + j * kThreadsB;
-    if (m < M) {
-      const float4 t = T4[m];
-      tx[j] = q * t.x; ty[j] = q * t.y; tz[j] = q * t.z;
-    } else {
-      tx[j] = kFar; ty[j] = kFar; tz[j] = kFar;
+  for (int p = 0; p < P; ++p) {
+    float c[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = mbase + (2 * p + h) * kThreadsB;
+      if (m < M) {
+        const float4 t = T4[m];
+        c[h][0] = q * t.x; c[h][1] = q * t.y; c[h][2] = q * t.z;
+      } else {
+        c[h][0] = c[h][1] = c[h][2] = kFar;
+      }
     }
-    p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.f;
+    tx[p] = f2_pack(c[0][0], c[1][0]);
+    ty[p] = f2_pack(c[0][1], c[1][1]);
+    tz[p] = f2_pack(c[0][2], c[1][2]);
   }
+#pragma unroll
+  for (int j = 0; j < 2 * P; ++j) p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.f;
   const int c0 = blockIdx.y * cols_per_chunk;
   const int c1 = min(N, c0 + cols_per_chunk);
   for (int base = c0; base < c1; base += kTileB) {
     __syncthreads();
     for (int i = threadIdx.x; i < kTileB; i += kThreadsB) {
       const int n = base + i;
-      sY[i] = n < c1 ? Yb[n] : make_float4(-kFar, -kFar, -kFar, 0.f);
+      const float4 y = n < c1 ? Yb[n] : make_float4(-kFar, -kFar, -kFar, 0.f);
+      sY[i][0] = make_ulonglong2(f2_pack(y.x, y.x), f2_pack(y.y, y.y));
+      sY[i][1] = make_ulonglong2(f2_pack(y.z, y.z), f2_pack(y.w, y.w));
     }
     __syncthreads();
     const int cnt = min(kTileB, c1 - base);
 #pragma unroll 2
     for (int i = 0; i < cnt; ++i) {
-      const float4 y = sY[i];
+      const ulonglong2 a = sY[i][0], b = sY[i][1];
 #pragma unroll
-      for (int j = 0; j < kRowsB32; ++j) {
-        const float dx = tx[j] - y.x, dy = ty[j] - y.y, dz = tz[j] - y.z;
-        float d2 = dx * dx;
-        d2 = fmaf(dy, dy, d2);
-        d2 = fmaf(dz, dz, d2);
-        const float wv = ex2_approx(y.w - d2);   // e_mn / den_n
-        p1[j] += wv;
-        px[j] = fmaf(wv, y.x, px[j]);
-        py[j] = fmaf(wv, y.y, py[j]);
-        pz[j] = fmaf(wv, y.z, pz[j]);
-        v[j] = fmaf(wv, d2, v[j]);
+      for (int p = 0; p < P; ++p) {
+        const f2_t dx = f2_sub(tx[p], a.x), dy = f2_sub(ty[p], a.y), dz = f2_sub(tz[p], b.x);
+        f2_t d2 = f2_mul(dx, dx);
+        d2 = f2_fma(dy, dy, d2);
+        d2 = f2_fma(dz, dz, d2);
+        float e0, e1, q0, q1, yx, yy, yz, lid;
+        f2_unpack(f2_sub(b.y, d2), e0, e1);     // register halves: no move
+        f2_unpack(d2, q0, q1);
+        f2_unpack(a.x, yx, lid);
+        f2_unpack(a.y, yy, lid);
+        f2_unpack(b.x, yz, lid);
+        const float w0 = ex2_approx(e0), w1 = ex2_approx(e1);   // e_mn / den_n
+        p1[2 * p] += w0;                         p1[2 * p + 1] += w1;
+        px[2 * p] = fmaf(w0, yx, px[2 * p]);     px[2 * p + 1] = fmaf(w1, yx, px[2 * p + 1]);
+        py[2 * p] = fmaf(w0, yy, py[2 * p]);     py[2 * p + 1] = fmaf(w1, yy, py[2 * p + 1]);
+        pz[2 * p] = fmaf(w0, yz, pz[2 * p]);     pz[2 * p + 1] = fmaf(w1, yz, pz[2 * p + 1]);
+        v[2 * p] = fmaf(w0, q0, v[2 * p]);       v[2 * p + 1] = fmaf(w1, q1, v[2 * p + 1]);
       }
     }
   }
   const size_t plane = (size_t)gridDim.y * M;
 #pragma unroll
-  for (int j = 0; j < kRowsB32; ++j) {
+  for (int j = 0; j < 2 * P; ++j) {
     const int m = mbase + j * kThreadsB;
     if (m < M) {
       const size_t o = (size_t)blockIdx.y * M + m;
@@ -405,8 +500,9 @@ __device__ __forceinline__ void write_row(int m, double p1s, double px, double p
                                           const typename Vec<F>::t4* __restrict__ X4,
                                           typename Vec<F>::t4* __restrict__ Yt4,
                                           typename Vec<F>::t4* __restrict__ R4, double* vrow_out) {
-  const double yx = px / p1s * unscale, yy = py / p1s * unscale, yz = pz / p1s * unscale;
-  const double vrow = v / p1s * unscale2;
+  const double inv = 1.0 / p1s;                       // one FP64 division per row
+  const double yx = px * inv * unscale, yy = py * inv * unscale, yz = pz * inv * unscale;
+  const double vrow = v * inv * unscale2;
   using V4 = typename Vec<F>::t4;
   V4 yt;
   yt.x = (F)yx; yt.y = (F)yy; yt.z = (F)yz; yt.w = (F)vrow;
@@ -425,6 +521,11 @@ __device__ __forceinline__ void write_row(int m, double p1s, double px, double p
 // sum_n p^_mn |y_n - t_m|^2, R_m = Ytil_m - x_m.  FP64: a row whose mass is
 // 0 or not finite cannot be normalised -> CPD_ENUMERIC.  FP32: rows whose
 // mass is below 2^-90 are listed for the exact log-domain path.
+// A block owns 32 rows; each warp sums a strided subset of the chunks for
+// the five quantities of those rows, and warp 0 adds the subsets in order.
+constexpr int kRedRows = 32;
+constexpr int kRedWarps = kThreadsR / 32;
+
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
 reduceB(const F* __restrict__ partB, int chunks, int M, const typename Vec<F>::t4* __restrict__ X4,
@@ -433,27 +534,39 @@ reduceB(const F* __restrict__ partB, int chunks, int M, const typename Vec<F>::t
         DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
   __shared__ double sh[32];
+  __shared__ F part[kRedWarps][5][kRedRows];
   __shared__ bool last;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int m = blockIdx.x * kRedRows + lane;
+  const size_t plane = (size_t)chunks * M;
+  F a[5] = {(F)0, (F)0, (F)0, (F)0, (F)0};   // summed in F, fixed order
+  if (m < M) {
+#pragma unroll 4
+    for (int k = wid; k < chunks; k += kRedWarps) {
+      const size_t o = (size_t)k * M + m;
+#pragma unroll
+      for (int qn = 0; qn < 5; ++qn) a[qn] += partB[o + qn * plane];
+    }
+  }
+#pragma unroll
+  for (int qn = 0; qn < 5; ++qn) part[wid][qn][lane] = a[qn];
+  __syncthreads();
   double vrow = 0.0;
   int bad = 0;
-  if (m < M) {
-    const size_t plane = (size_t)chunks * M;
-    double p1 = 0, px = 0, py = 0, pz = 0, v = 0;
-    for (int k = 0; k < chunks; ++k) {
-      const size_t o = (size_t)k * M + m;
-      p1 += (double)partB[o];
-      px += (double)partB[o + plane];
-      py += (double)partB[o + 2 * plane];
-      pz += (double)partB[o + 3 * plane];
-      v += (double)partB[o + 4 * plane];
+  if (wid == 0 && m < M) {
+    F f1 = 0, fx = 0, fy = 0, fz = 0, fv = 0;
+#pragma unroll
+    for (int j = 0; j < kRedWarps; ++j) {
+      f1 += part[j][0][lane]; fx += part[j][1][lane]; fy += part[j][2][lane];
+      fz += part[j][3][lane]; fv += part[j][4][lane];
     }
+    double p1 = f1, px = fx, py = fy, pz = fz, v = fv;
     if constexpr (sizeof(F) == 4) {
       if (!(p1 >= kRowFloor) || !isfinite(p1)) {
         flag_rows[atomicAdd(&st->n_flag_rows, 1)] = m;
       } else {
-        const double q = (double)scale_q(st->sigma2);
-        write_row<F>(m, p1, px, py, pz, v, 1.0 / q, 1.0 / (q * q), X4, Yt4, R4, &vrow);
+        const float qi = 1.0f / scale_q(st->sigma2);
+        write_row<F>(m, p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, X4, Yt4, R4, &vrow);
         if (P1_out) P1_out[m] = p1;
       }
     } else {
@@ -476,7 +589,7 @@ reduceB(const F* __restrict__ partB, int chunks, int M, const typename Vec<F>::t
   if (last) {
     __threadfence();
     double vv = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) vv += ((volatile double*)sums)[i];
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) vv += __ldcg(sums + i);
     const double tot = block_sum(vv, sh);
     if (threadIdx.x == 0) {
       st->vsum = tot;
@@ -532,9 +645,9 @@ fixB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, in
       if (!(mass > 0.0) || !isfinite(mass)) {
         atomicExch(&st->status, (int)CPD_ENUMERIC);    // zero even in double precision
       } else {
-        const double qd = (double)q;
+        const float qi = 1.0f / q;
         double vrow = 0.0;
-        write_row<float>(m, (double)p1, px, py, pz, v, 1.0 / qd, 1.0 / (qd * qd), X4, Yt4, R4, &vrow);
+        write_row<float>(m, (double)p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, X4, Yt4, R4, &vrow);
         if (P1_out) P1_out[m] = mass;
         atomicAdd(&st->vsum, vrow);
       }
@@ -546,25 +659,37 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 }  // namespace
 
+// Grids for passes A and B: all blocks resident in one wave (blocks <= SMs x
+// resident blocks per SM from the occupancy calculator), with the split of
+// the long dimension chosen so every block gets the same amount of work.
 EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms) {
   EstepPlan p{};
-  const int64_t target = (int64_t)sms * 8;
+  int occA = 0, occB = 0;
+  if (fp64) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, passA_f64, kThreadsA, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, passB_f64, kThreadsB, 0);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, passA_f32, kThreadsA, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, passB_f32, kThreadsB, 0);
+  }
+  const int64_t slotsA = (int64_t)sms * std::max(occA, 1);
+  const int64_t slotsB = (int64_t)sms * std::max(occB, 1);
   const int64_t colsA = kThreadsA * (fp64 ? kColsA64 : kColsA32);
   p.a_col_tiles = (int)cdiv(N, colsA);
-  int64_t want = std::max<int64_t>(1, cdiv(target, p.a_col_tiles));
-  int64_t rpc = cdiv(cdiv(M, want), kTileA) * kTileA;
+  int64_t want = std::max<int64_t>(1, slotsA / p.a_col_tiles);
+  int64_t rpc = std::max<int64_t>(32, cdiv(M, want));
   p.a_rows_per_chunk = (int)rpc;
   p.a_row_chunks = (int)cdiv(M, rpc);
   const int64_t rowsB = kThreadsB * (fp64 ? kRowsB64 : kRowsB32);
   p.b_row_tiles = (int)cdiv(M, rowsB);
-  want = std::max<int64_t>(1, cdiv(target, p.b_row_tiles));
-  int64_t cpc = cdiv(cdiv(N, want), kTileB) * kTileB;
+  want = std::max<int64_t>(1, slotsB / p.b_row_tiles);
+  int64_t cpc = std::max<int64_t>(32, cdiv(N, want));
   p.b_cols_per_chunk = (int)cpc;
   p.b_col_chunks = (int)cdiv(N, cpc);
   p.partA_elems = (int64_t)p.a_row_chunks * N;
   p.partB_elems = (int64_t)5 * p.b_col_chunks * M;
-  p.redA_blocks = cdiv(N, kThreadsR);
-  p.redB_blocks = cdiv(M, kThreadsR);
+  p.redA_blocks = cdiv(N, kRedCols);
+  p.redB_blocks = cdiv(M, kRedRows);
   p.sums_elems = std::max(p.redA_blocks, p.redB_blocks);
   p.flags_elems = M + N;
   return p;

@@ -125,7 +125,7 @@ struct cpd_ctx {
   int64_t M = 0, K = 0, ldU = 0, N = 0;
   cudaStream_t stream = nullptr; // caller's stream
   cudaStream_t cap = nullptr;    // internal stream used only for graph capture
-  Buf X4, T4, U, lam, Yt4, R4, B4, C4, Yhat4, W4, hist;
+  Buf X4, T4, U, Ut, lam, Yt4, R4, B4, C4, Yhat4, W4, hist;
   Buf st, st_aux;
   Buf Y4, Yb, partA, partB, partP, sums, flags, stage;
   Buf auxT4, auxR4, auxB4, auxC4;
@@ -142,7 +142,7 @@ struct cpd_ctx {
 
   ~cpd_ctx() {
     drop_graphs();
-    for (Buf* b : {&X4, &T4, &U, &lam, &Yt4, &R4, &B4, &C4, &Yhat4, &W4, &hist, &st, &st_aux, &Y4, &Yb,
+    for (Buf* b : {&X4, &T4, &U, &Ut, &lam, &Yt4, &R4, &B4, &C4, &Yhat4, &W4, &hist, &st, &st_aux, &Y4, &Yb,
                    &partA, &partB, &partP, &sums, &flags, &stage, &auxT4, &auxR4, &auxB4, &auxC4})
       b->release();
     if (cap) cudaStreamDestroy(cap);
@@ -221,16 +221,16 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
     launch_estep<double>(c->ep, c->T4.as<dvec4>(), c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), c->Yb.as<dvec4>(),
                          c->N, c->partA.as<double>(), c->partB.as<double>(), c->sums.as<double>(), c->flags.as<int>(),
                          c->Yt4.as<dvec4>(), c->R4.as<dvec4>(), nullptr, nullptr, st, true, s, ee);
-    launch_mstep<double>(c->mp, c->U.as<double>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<dvec4>(),
-                         c->R4.as<dvec4>(), c->Yt4.as<dvec4>(), c->T4.as<dvec4>(),
+    launch_mstep<double>(c->mp, c->U.as<double>(), c->Ut.as<double>(), c->lam.as<double>(), c->M, c->K,
+                         c->X4.as<dvec4>(), c->R4.as<dvec4>(), c->Yt4.as<dvec4>(), c->T4.as<dvec4>(),
                          c->has_gt ? c->Yhat4.as<dvec4>() : nullptr, c->partP.as<double>(), c->sums.as<double>(),
                          c->B4.as<dvec4>(), c->C4.as<dvec4>(), st, true, s, em);
   } else {
     launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
                         c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
                         c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, ee);
-    launch_mstep<float>(c->mp, c->U.as<float>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<float4>(),
-                        c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
+    launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
+                        c->X4.as<float4>(), c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
                         c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->partP.as<float>(), c->sums.as<double>(),
                         c->B4.as<float4>(), c->C4.as<float4>(), st, true, s, em);
   }
@@ -289,14 +289,23 @@ cpd_status prepare_iterate(cpd_ctx* c, const void* Y, int64_t N) {
   return CPD_OK;
 }
 
+// Iterations that carry timing events: every kProfEvery-th and the last.
+constexpr int kProfEvery = 10;
+bool profiled_iteration(int i, int n_iter) { return i % kProfEvery == 0 || i == n_iter - 1; }
+
 cpd_status capture_profiled(cpd_ctx* c, int n_iter) {
   if (c->prof_graph) cudaGraphExecDestroy(c->prof_graph);
   c->prof_graph = nullptr;
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
-  c->prof_ev.assign((size_t)8 * n_iter, nullptr);
+  int sampled = 0;
+  for (int i = 0; i < n_iter; ++i) sampled += profiled_iteration(i, n_iter) ? 1 : 0;
+  c->prof_ev.assign((size_t)8 * sampled, nullptr);
   for (auto& e : c->prof_ev) CUDA_TRY(cudaEventCreate(&e));
   CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
-  for (int i = 0; i < n_iter; ++i) enqueue_iteration(c, c->cap, &c->prof_ev[(size_t)8 * i]);
+  for (int i = 0, j = 0; i < n_iter; ++i) {
+    if (profiled_iteration(i, n_iter)) enqueue_iteration(c, c->cap, &c->prof_ev[(size_t)8 * j++]);
+    else enqueue_iteration(c, c->cap, nullptr);
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap, &g);
   if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -367,14 +376,12 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   c->v4 = c->fp64 ? sizeof(dvec4) : sizeof(float4);
   c->M = M;
   c->K = (p->K == 0 || p->K >= M) ? M : p->K;
-  c->ldU = round_up(c->K, 16 / (int64_t)c->es);
   c->stream = (cudaStream_t)stream;
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(fail(CPD_ECUDA, "no CUDA device"));
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
     return bail(fail(CPD_ECUDA, "cannot query the SM count"));
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(CPD_ECUDA, "cannot create the capture stream"));
-  mstep_prepare();
 
   cpd_status s;
   if ((s = c->X4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
@@ -383,6 +390,13 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   if ((s = c->st_aux.ensure(sizeof(DevState))) != CPD_OK) return bail(s);
   if ((s = c->hist.ensure((size_t)3 * kHistCap * sizeof(double))) != CPD_OK) return bail(s);
   if ((s = upload_points(c, X, M, c->X4.p, false, c->stage, c->fp64, c->stream)) != CPD_OK) return bail(s);
+
+  // The long-lived basis is allocated before the setup temporaries.
+  c->mp = plan_mstep(M, c->K, c->fp64, c->sms);
+  c->ldU = c->mp.ldU;
+  if ((s = c->U.ensure((size_t)M * c->ldU * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->Ut.ensure((size_t)c->K * c->mp.ldM * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->lam.ensure((size_t)c->K * sizeof(double))) != CPD_OK) return bail(s);
 
   // Eq. 11 in FP64, then Eq. 16 by the FP64 symmetric eigensolver.
   Buf phi, wv, info, work;
@@ -416,21 +430,18 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
     return bail(fail(CPD_ESOLVER, "eigensolver failed (status " + std::to_string((int)cs) + ", info " +
                                       std::to_string(hinfo) + (fault_enabled("solver") ? ", injected" : "") + ")"));
   }
-  if ((s = c->U.ensure((size_t)M * c->ldU * c->es)) != CPD_OK) { free_setup(); return bail(s); }
-  if ((s = c->lam.ensure((size_t)c->K * sizeof(double))) != CPD_OK) { free_setup(); return bail(s); }
-  if (c->fp64) launch_extract_basis<double>(phi.as<double>(), M, c->K, c->U.as<double>(), c->ldU, wv.as<double>(),
-                                            c->lam.as<double>(), c->stream);
-  else launch_extract_basis<float>(phi.as<double>(), M, c->K, c->U.as<float>(), c->ldU, wv.as<double>(),
-                                   c->lam.as<double>(), c->stream);
+  if (c->fp64) launch_extract_basis<double>(phi.as<double>(), M, c->K, c->U.as<double>(), c->ldU, c->Ut.as<double>(),
+                                            c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
+  else launch_extract_basis<float>(phi.as<double>(), M, c->K, c->U.as<float>(), c->ldU, c->Ut.as<float>(),
+                                   c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
   free_setup();
 
-  c->mp = plan_mstep(M, c->K, c->fp64, c->sms);
   if ((s = c->Yt4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->R4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->B4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->C4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
-  if ((s = c->partP.ensure((size_t)c->mp.partP_elems * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->partP.ensure((size_t)c->mp.part_elems * c->es)) != CPD_OK) return bail(s);
   if ((s = c->sums.ensure((size_t)c->mp.sums_elems * sizeof(double))) != CPD_OK) return bail(s);
   launch_state_init(c->dst(), 0.0, c->stream);
   launch_state_params(c->dst(), p->w, p->lambda, p->tol, 0.0, 0, c->hist.as<double>(), M, 0, c->K, c->stream);
@@ -491,16 +502,17 @@ cpd_status cpd_iterate_profiled(cpd_ctx* c, const void* Y, int64_t N, int32_t n_
   CUDA_TRY(cudaGraphLaunch(c->prof_graph, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   for (int p = 0; p < 8; ++p) phase_ms[p] = 0.f;
-  for (int i = 0; i < n_iter; ++i) {
-    const cudaEvent_t* ev = &c->prof_ev[(size_t)8 * i];
+  const int sampled = (int)(c->prof_ev.size() / 8);
+  for (int j = 0; j < sampled; ++j) {
+    const cudaEvent_t* ev = &c->prof_ev[(size_t)8 * j];
     for (int p = 0; p < 7; ++p) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]));
-      phase_ms[p] += ms;
+      phase_ms[p] += ms / (float)sampled;
     }
   }
   float total = 0.f;
-  CUDA_TRY(cudaEventElapsedTime(&total, c->prof_ev[0], c->prof_ev[(size_t)8 * n_iter - 1]));
+  CUDA_TRY(cudaEventElapsedTime(&total, c->prof_ev[0], c->prof_ev.back()));
   phase_ms[7] = total;
   DevState h;
   STATUS_TRY(read_state(c, &h));
@@ -563,8 +575,10 @@ cpd_status cpd_get_W(cpd_ctx* c, void* W_out) {
   STATUS_TRY(read_state(c, &h));
   if (!c->started || h.iter == 0) return fail(CPD_ESTATE, "no M-step has run yet");
   STATUS_TRY(c->W4.ensure((size_t)c->M * c->v4));
-  if (c->fp64) launch_w<double>(c->mp, c->U.as<double>(), c->ldU, c->M, c->K, c->C4.as<dvec4>(), c->W4.as<dvec4>(), c->stream);
-  else launch_w<float>(c->mp, c->U.as<float>(), c->ldU, c->M, c->K, c->C4.as<float4>(), c->W4.as<float4>(), c->stream);
+  if (c->fp64) launch_w<double>(c->mp, c->Ut.as<double>(), c->M, c->K, c->C4.as<dvec4>(), c->partP.as<double>(),
+                                c->W4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
+  else launch_w<float>(c->mp, c->Ut.as<float>(), c->M, c->K, c->C4.as<float4>(), c->partP.as<float>(),
+                       c->W4.as<float4>(), c->st_aux.as<DevState>(), c->stream);
   CUDA_TRY(cudaGetLastError());
   return download_points(c->W4.p, c->M, W_out, c->stage, c->fp64, c->stream);
 }
@@ -596,20 +610,22 @@ cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, v
   launch_state_init(sa, sigma2, c->stream);
   if (c->fp64) {
     launch_residual<double>(c->auxT4.as<dvec4>(), c->X4.as<dvec4>(), c->auxR4.as<dvec4>(), c->M, c->stream);
-    launch_mstep<double>(c->mp, c->U.as<double>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<dvec4>(),
-                         c->auxR4.as<dvec4>(), nullptr, c->auxT4.as<dvec4>(), nullptr, c->partP.as<double>(),
+    launch_mstep<double>(c->mp, c->U.as<double>(), c->Ut.as<double>(), c->lam.as<double>(), c->M, c->K,
+                         c->X4.as<dvec4>(), c->auxR4.as<dvec4>(), nullptr, c->auxT4.as<dvec4>(), nullptr, c->partP.as<double>(),
                          c->sums.as<double>(), c->auxB4.as<dvec4>(), c->auxC4.as<dvec4>(), sa, false, c->stream);
   } else {
     launch_residual<float>(c->auxT4.as<float4>(), c->X4.as<float4>(), c->auxR4.as<float4>(), c->M, c->stream);
-    launch_mstep<float>(c->mp, c->U.as<float>(), c->ldU, c->lam.as<double>(), c->M, c->K, c->X4.as<float4>(),
-                        c->auxR4.as<float4>(), nullptr, c->auxT4.as<float4>(), nullptr, c->partP.as<float>(),
+    launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
+                        c->X4.as<float4>(), c->auxR4.as<float4>(), nullptr, c->auxT4.as<float4>(), nullptr, c->partP.as<float>(),
                         c->sums.as<double>(), c->auxB4.as<float4>(), c->auxC4.as<float4>(), sa, false, c->stream);
   }
   CUDA_TRY(cudaGetLastError());
   STATUS_TRY(download_points(c->auxT4.p, c->M, T_out, c->stage, c->fp64, c->stream));
   if (W_out) {
-    if (c->fp64) launch_w<double>(c->mp, c->U.as<double>(), c->ldU, c->M, c->K, c->auxC4.as<dvec4>(), c->auxR4.as<dvec4>(), c->stream);
-    else launch_w<float>(c->mp, c->U.as<float>(), c->ldU, c->M, c->K, c->auxC4.as<float4>(), c->auxR4.as<float4>(), c->stream);
+    if (c->fp64) launch_w<double>(c->mp, c->Ut.as<double>(), c->M, c->K, c->auxC4.as<dvec4>(), c->partP.as<double>(),
+                                  c->auxR4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
+    else launch_w<float>(c->mp, c->Ut.as<float>(), c->M, c->K, c->auxC4.as<float4>(), c->partP.as<float>(),
+                         c->auxR4.as<float4>(), c->st_aux.as<DevState>(), c->stream);
     CUDA_TRY(cudaGetLastError());
     STATUS_TRY(download_points(c->auxR4.p, c->M, W_out, c->stage, c->fp64, c->stream));
   }

@@ -1,21 +1,26 @@
 // M-step of fast CPD on sm_103a (Eq. 17 full basis, Eq. 20 top-K basis) and
-// the variance update (Eq. 18), fused.
+// the variance update (Eq. 18), fused into the last kernel.
 //
-//   project  A = U^T R with R = Ytil - X (K x 3).  U is M x ldU row-major;
-//            each thread streams 16-byte vectors of W consecutive columns down
-//            a chunk of rows (coalesced HBM reads), rows of R are broadcast
-//            from shared memory; the row chunks are split over blocks and
-//            summed by `project_reduce` in a fixed order.
-//   diag     s_k = l_k / (l_k + lambda sigma2) -- "only a diagonal is
-//            updated" per iteration; B_k = s_k A_k, C_k = A_k/(l_k + lambda sigma2).
-//   expand   T = X + U B.  Each warp owns kRows rows and sweeps them with
-//            16-byte loads while B tiles are shared through shared memory.
-//            Epilogue (per row, FP64): the Eq. 18 term with the new T,
-//              sum_n p^_mn |y_n - t_new|^2
-//                = V_m/P1_m + 2 (t_old - t_new).(Ytil_m - t_old) + |t_old - t_new|^2,
-//            which is Eq. 18's trace form shifted to t_old (no cancellation of
-//            O(1) terms); the last block sums the block partials in a fixed
-//            order and advances the device state (sigma2, history, stop test).
+// Both dense products of the M-step are skinny (3 right-hand sides) and
+// HBM-bound, so both run through one streaming kernel, `colsum`:
+//     out[c][d] = sum_r A[r][c] * V[r][d]     (A row-major, d = 0..2)
+// Each thread owns W consecutive columns (two 16-byte vectors = 32 bytes per
+// row; 32-byte segments measured steadier across physical placements than
+// 16-byte ones), walks a chunk of rows with loads in flight, and takes V[r]
+// from shared memory;
+// the row chunks are split over blocks and summed in a fixed order.
+//   projection  A = U  (M x K), V = R = Ytil - X  ->  a_k = (U^T R)_k
+//   expansion   A = U^T (K x M, stored once at setup), V = B  ->  (U B)_m
+// with the diagonal update in between: s_k = l_k / (l_k + lambda sigma2),
+// B_k = s_k a_k ("only a diagonal changes per iteration", Sec. III) and
+// C_k = a_k / (l_k + lambda sigma2) for W.
+// The expansion's reduction kernel writes T = X + U B and evaluates, per row
+// in FP64, the Eq. 18 term with the new T, shifted to the old T (no
+// cancellation of O(1) terms):
+//   sum_n p^_mn |y_n - t_new|^2
+//     = V_m/P1_m + 2 (t_old - t_new).(Ytil_m - t_old) + |t_old - t_new|^2;
+// its last block sums the block partials in a fixed order and advances the
+// device state (sigma2, history, stop test).
 #include "common.cuh"
 
 #include <math.h>
@@ -41,44 +46,47 @@ __device__ __forceinline__ float lane_of(const float4& v, int i) {
 }
 __device__ __forceinline__ double lane_of(const double2& v, int i) { return i == 0 ? v.x : v.y; }
 
-constexpr int kThreadsP = 128;   // projection block
-constexpr int kRTile = 256;      // rows of R staged per shared-memory tile
-constexpr int kThreadsE = 256;   // expansion block (8 warps)
-constexpr int kRows = 4;         // rows per warp in the expansion
-constexpr int kThreadsD = 256;   // diagonal-update block
+constexpr int kThreadsP = 128;   // streaming kernel block
+constexpr int kRTile = 256;      // rows of V staged per shared-memory tile
+constexpr int kThreadsD = 256;   // reduction kernels
+constexpr int kRedCols = 64;     // columns per reduction block
+constexpr int kRedSub = kThreadsD / kRedCols;
 
-template <typename F> __host__ __device__ constexpr int ktile_e() { return sizeof(F) == 4 ? 2048 : 1024; }
-
-// ---------------------------------------------------------------- project
+// ---------------------------------------------------------------- colsum
 template <typename F>
 __global__ void __launch_bounds__(kThreadsP)
-project(const F* __restrict__ U, int64_t ldU, int M, int K, const typename Vec<F>::t4* __restrict__ R4,
-        int rows_per_chunk, F* __restrict__ partP, const DevState* __restrict__ st, int gate) {
+colsum(const F* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
+       int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
+       int clear_row_flags) {
   if (gate && iteration_gated(st)) return;
+  // the E-step's row list was consumed by fixB before this kernel
+  if (clear_row_flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
   using V4 = typename Vec<F>::t4;
   using LT = typename L16<F>::t;
-  constexpr int W = L16<F>::W;
-  __shared__ V4 sR[kRTile];
-  const int k0 = (blockIdx.x * kThreadsP + threadIdx.x) * W;
+  constexpr int L = L16<F>::W;           // elements per 16-byte vector
+  constexpr int W = 2 * L;               // columns per thread
+  __shared__ V4 sV[kRTile];
+  const int c0 = (blockIdx.x * kThreadsP + threadIdx.x) * W;
   const int r0 = blockIdx.y * rows_per_chunk;
-  const int r1 = min(M, r0 + rows_per_chunk);
+  const int r1 = min(rows, r0 + rows_per_chunk);
   F acc[W][3];
 #pragma unroll
   for (int w = 0; w < W; ++w) acc[w][0] = acc[w][1] = acc[w][2] = (F)0;
   for (int base = r0; base < r1; base += kRTile) {
     const int cnt = min(kRTile, r1 - base);
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kThreadsP) sR[i] = R4[base + i];
+    for (int i = threadIdx.x; i < cnt; i += kThreadsP) sV[i] = V[base + i];
     __syncthreads();
-    if (k0 < K) {
-      const F* up = U + (size_t)base * ldU + k0;
-#pragma unroll 8
+    if (c0 < cols) {
+      const F* ap = A + (size_t)base * ldA + c0;
+#pragma unroll 4
       for (int i = 0; i < cnt; ++i) {
-        const LT u = __ldg(reinterpret_cast<const LT*>(up + (size_t)i * ldU));
-        const V4 r = sR[i];
+        const LT* row = reinterpret_cast<const LT*>(ap + (size_t)i * ldA);
+        const LT u0 = __ldg(row), u1 = __ldg(row + 1);
+        const V4 r = sV[i];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-          const F uw = lane_of(u, w);
+          const F uw = w < L ? lane_of(u0, w) : lane_of(u1, w - L);
           acc[w][0] = fma(uw, r.x, acc[w][0]);
           acc[w][1] = fma(uw, r.y, acc[w][1]);
           acc[w][2] = fma(uw, r.z, acc[w][2]);
@@ -86,130 +94,109 @@ project(const F* __restrict__ U, int64_t ldU, int M, int K, const typename Vec<F
       }
     }
   }
-  if (k0 < K) {
+  if (c0 < cols) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      F* out = partP + ((size_t)blockIdx.y * 3 + d) * ldU + k0;
-      if constexpr (W == 4) {
-        *reinterpret_cast<float4*>(out) = make_float4(acc[0][d], acc[1][d], acc[2][d], acc[3][d]);
+      F* out = part + ((size_t)blockIdx.y * 3 + d) * ldP + c0;
+      if constexpr (L == 4) {
+        reinterpret_cast<float4*>(out)[0] = make_float4(acc[0][d], acc[1][d], acc[2][d], acc[3][d]);
+        reinterpret_cast<float4*>(out)[1] = make_float4(acc[4][d], acc[5][d], acc[6][d], acc[7][d]);
       } else {
-        *reinterpret_cast<double2*>(out) = make_double2(acc[0][d], acc[1][d]);
+        reinterpret_cast<double2*>(out)[0] = make_double2(acc[0][d], acc[1][d]);
+        reinterpret_cast<double2*>(out)[1] = make_double2(acc[2][d], acc[3][d]);
       }
     }
   }
 }
 
-// Sums the projection partials (FP64, fixed order) and applies the diagonal
-// update with the sigma2 of this iteration's E-step.
+// Sum of the chunk partials of column `col` (accumulated in F: FP32 partials
+// are summed in FP32 -- GB300's FP64 rate is a small fraction of FP32 -- in a
+// fixed order; the FP64 path sums in FP64).  kRedSub threads per column each
+// take a strided subset; the subsets are added in order through `part`.
+template <typename F>
+__device__ __forceinline__ void chunk_sums(const F* __restrict__ partials, int chunks, int64_t ldP, int col,
+                                           int ncols, F (&a)[3], F (*part)[3][kRedCols]) {
+  const int c = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
+  F s[3] = {(F)0, (F)0, (F)0};
+  if (col < ncols) {
+#pragma unroll 4
+    for (int k = sub; k < chunks; k += kRedSub)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) s[d] += partials[((size_t)k * 3 + d) * ldP + col];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) part[sub][d][c] = s[d];
+  __syncthreads();
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F t = (F)0;
+#pragma unroll
+    for (int j = 0; j < kRedSub; ++j) t += part[j][d][c];
+    a[d] = t;
+  }
+}
+
+// Diagonal update (once per column k) with the sigma2 of this iteration's
+// E-step: B_k = s_k a_k, C_k = a_k / (l_k + lambda sigma2).
 template <typename F>
 __global__ void __launch_bounds__(kThreadsD)
-project_reduce(const F* __restrict__ partP, int chunks, int64_t ldU, int K, const double* __restrict__ lam,
-               typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
-               const DevState* __restrict__ st, int gate) {
+diag_update(const F* __restrict__ partP, int chunks, int64_t ldU, int K, const double* __restrict__ lam,
+            typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
+            const DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
-  double a[3] = {0.0, 0.0, 0.0};
-  for (int c = 0; c < chunks; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) a[d] += (double)partP[((size_t)c * 3 + d) * ldU + k];
-  const double den = lam[k] + st->lambda * st->sigma2;
-  const double s = lam[k] / den;
+  __shared__ F part[kRedSub][3][kRedCols];
+  __shared__ double lamsig;
+  if (threadIdx.x == 0) lamsig = st->lambda * st->sigma2;
+  const int k = blockIdx.x * kRedCols + threadIdx.x % kRedCols;
+  F a[3];
+  chunk_sums<F>(partP, chunks, ldU, k, K, a, part);
+  if (threadIdx.x >= kRedCols || k >= K) return;
+  const double inv = 1.0 / (lam[k] + lamsig);          // one FP64 division per column
+  const double s = lam[k] * inv;
   using V4 = typename Vec<F>::t4;
   V4 b, cw;
   b.x = (F)(s * a[0]); b.y = (F)(s * a[1]); b.z = (F)(s * a[2]); b.w = (F)0;
-  cw.x = (F)(a[0] / den); cw.y = (F)(a[1] / den); cw.z = (F)(a[2] / den); cw.w = (F)0;
+  cw.x = (F)(a[0] * inv); cw.y = (F)(a[1] * inv); cw.z = (F)(a[2] * inv); cw.w = (F)0;
   B4[k] = b;
   C4[k] = cw;
 }
 
-// ----------------------------------------------------------------- expand
+// T = X + U B (X may be null: W = U C) from the expansion partials; with EPI
+// the Eq. 18 epilogue and the device-state update of the iteration.
 template <typename F, bool EPI>
-__global__ void __launch_bounds__(kThreadsE)
-expand(const F* __restrict__ U, int64_t ldU, int M, int K, const typename Vec<F>::t4* __restrict__ B4,
-       const typename Vec<F>::t4* __restrict__ X4, const typename Vec<F>::t4* __restrict__ Yt4,
-       typename Vec<F>::t4* __restrict__ Tout, const typename Vec<F>::t4* __restrict__ Yhat4,
-       double* __restrict__ sums, DevState* __restrict__ st, int gate) {
+__global__ void __launch_bounds__(kThreadsD)
+expand_finish(const F* __restrict__ partE, int chunks, int64_t ldM, int M,
+              const typename Vec<F>::t4* __restrict__ X4, const typename Vec<F>::t4* __restrict__ Yt4,
+              typename Vec<F>::t4* __restrict__ Tout, const typename Vec<F>::t4* __restrict__ Yhat4,
+              double* __restrict__ sums, DevState* __restrict__ st, int gate) {
   if (gate && iteration_gated(st)) return;
   using V4 = typename Vec<F>::t4;
-  using LT = typename L16<F>::t;
-  constexpr int W = L16<F>::W;
-  constexpr int KT = ktile_e<F>();
-  extern __shared__ __align__(32) unsigned char smem_raw[];
-  V4* sB = reinterpret_cast<V4*>(smem_raw);
+  __shared__ F part[kRedSub][3][kRedCols];
   __shared__ double sh[32];
   __shared__ bool last;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row0 = (blockIdx.x * (kThreadsE / 32) + warp) * kRows;
-  F acc[kRows][3];
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) acc[r][0] = acc[r][1] = acc[r][2] = (F)0;
-  for (int kb = 0; kb < K; kb += KT) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < KT; i += kThreadsE) {
-      const int k = kb + i;
-      V4 z;
-      z.x = z.y = z.z = z.w = (F)0;
-      sB[i] = k < K ? B4[k] : z;
-    }
-    __syncthreads();
-    const int kcnt = min(KT, K - kb);
-    for (int kk = lane * W; kk < kcnt; kk += 32 * W) {
-      V4 b[W];
-#pragma unroll
-      for (int w = 0; w < W; ++w) b[w] = sB[kk + w];
-#pragma unroll
-      for (int r = 0; r < kRows; ++r) {
-        const int m = row0 + r;
-        if (m < M) {
-          const LT u = __ldg(reinterpret_cast<const LT*>(U + (size_t)m * ldU + kb + kk));
-#pragma unroll
-          for (int w = 0; w < W; ++w) {
-            const F uw = lane_of(u, w);
-            acc[r][0] = fma(uw, b[w].x, acc[r][0]);
-            acc[r][1] = fma(uw, b[w].y, acc[r][1]);
-            acc[r][2] = fma(uw, b[w].z, acc[r][2]);
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kRows; ++r)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      F v = acc[r][d];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[r][d] = v;
-    }
+  const int m = blockIdx.x * kRedCols + threadIdx.x % kRedCols;
+  F a[3];
+  chunk_sums<F>(partE, chunks, ldM, m, M, a, part);
   double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
-  if (lane < kRows) {
-    F s0 = 0, s1 = 0, s2 = 0;
-#pragma unroll
-    for (int r = 0; r < kRows; ++r)
-      if (lane == r) { s0 = acc[r][0]; s1 = acc[r][1]; s2 = acc[r][2]; }
-    const int m = row0 + lane;
-    if (m < M) {
-      double x0 = 0, x1 = 0, x2 = 0;
-      if (X4) { const V4 x = X4[m]; x0 = x.x; x1 = x.y; x2 = x.z; }
-      V4 tn;
-      tn.x = (F)(x0 + (double)s0); tn.y = (F)(x1 + (double)s1); tn.z = (F)(x2 + (double)s2); tn.w = (F)0;
-      if constexpr (EPI) {
-        const V4 to = Tout[m];
-        const V4 yt = Yt4[m];
-        const double dx = (double)to.x - tn.x, dy = (double)to.y - tn.y, dz = (double)to.z - tn.z;
-        const double gx = (double)yt.x - to.x, gy = (double)yt.y - to.y, gz = (double)yt.z - to.z;
-        dT2 = dx * dx + dy * dy + dz * dz;
-        contrib = (double)yt.w + 2.0 * (dx * gx + dy * gy + dz * gz) + dT2;
-        if (Yhat4) {
-          const V4 h = Yhat4[m];
-          const double ex = (double)tn.x - h.x, ey = (double)tn.y - h.y, ez = (double)tn.z - h.z;
-          gt2 = ex * ex + ey * ey + ez * ez;
-        }
+  if (threadIdx.x < kRedCols && m < M) {
+    double x0 = 0, x1 = 0, x2 = 0;
+    if (X4) { const V4 x = X4[m]; x0 = x.x; x1 = x.y; x2 = x.z; }
+    V4 tn;
+    tn.x = (F)(x0 + (double)a[0]); tn.y = (F)(x1 + (double)a[1]); tn.z = (F)(x2 + (double)a[2]); tn.w = (F)0;
+    if constexpr (EPI) {
+      const V4 to = Tout[m];
+      const V4 yt = Yt4[m];
+      const double dx = (double)to.x - tn.x, dy = (double)to.y - tn.y, dz = (double)to.z - tn.z;
+      const double gx = (double)yt.x - to.x, gy = (double)yt.y - to.y, gz = (double)yt.z - to.z;
+      dT2 = dx * dx + dy * dy + dz * dz;
+      contrib = (double)yt.w + 2.0 * (dx * gx + dy * gy + dz * gz) + dT2;
+      if (Yhat4) {
+        const V4 h = Yhat4[m];
+        const double ex = (double)tn.x - h.x, ey = (double)tn.y - h.y, ez = (double)tn.z - h.z;
+        gt2 = ex * ex + ey * ey + ez * ez;
       }
-      Tout[m] = tn;
     }
+    Tout[m] = tn;
   }
   if constexpr (EPI) {
     const double b0 = block_sum(contrib, sh);
@@ -225,12 +212,11 @@ expand(const F* __restrict__ U, int64_t ldU, int M, int K, const typename Vec<F>
     __syncthreads();
     if (last) {
       __threadfence();
-      const volatile double* vs = sums;
       double a0 = 0, a1 = 0, a2 = 0;
       for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        a0 += vs[(size_t)i * 3];
-        a1 += vs[(size_t)i * 3 + 1];
-        a2 += vs[(size_t)i * 3 + 2];
+        a0 += __ldcg(sums + (size_t)i * 3);
+        a1 += __ldcg(sums + (size_t)i * 3 + 1);
+        a2 += __ldcg(sums + (size_t)i * 3 + 2);
       }
       const double t0 = block_sum(a0, sh);
       const double t1 = block_sum(a1, sh);
@@ -259,75 +245,80 @@ expand(const F* __restrict__ U, int64_t ldU, int M, int K, const typename Vec<F>
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-template <typename F>
-size_t expand_smem() { return sizeof(typename Vec<F>::t4) * ktile_e<F>(); }
+// Row chunks for a colsum over a rows x ld matrix: enough blocks to fill the
+// GPU, but at least ~256 KB of the matrix per block (a small matrix needs few
+// chunks, which keeps the partial sums short).
+void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int& col_tiles, int& chunks, int& rpc) {
+  col_tiles = (int)cdiv(ld, (int64_t)kThreadsP * W);
+  const int64_t target = (int64_t)sms * 8;
+  int64_t ch = std::max<int64_t>(1, cdiv(target, col_tiles));
+  ch = std::min<int64_t>(ch, std::max<int64_t>(1, rows * ld * es / (256 * 1024)));
+  const int64_t r = std::max<int64_t>(32, cdiv(rows, ch));
+  rpc = (int)r;
+  chunks = (int)cdiv(rows, r);
+}
 
 }  // namespace
 
-// The expansion uses 32 KB of dynamic shared memory, within the default
-// 48 KB limit; the attribute is set explicitly so a larger tile stays legal.
-void mstep_prepare() {
-  cudaFuncSetAttribute(expand<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expand_smem<float>());
-  cudaFuncSetAttribute(expand<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expand_smem<float>());
-  cudaFuncSetAttribute(expand<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expand_smem<double>());
-  cudaFuncSetAttribute(expand<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)expand_smem<double>());
-}
-
 MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms) {
   MstepPlan p{};
-  const int W = fp64 ? 2 : 4;
-  const int64_t ldU = cdiv(K, W) * W;
-  p.p_col_tiles = (int)cdiv(ldU, (int64_t)kThreadsP * W);
-  const int64_t target = (int64_t)sms * 8;
-  int64_t chunks = std::max<int64_t>(1, cdiv(target, p.p_col_tiles));
-  int64_t rpc = std::max<int64_t>(16, cdiv(M, chunks));
-  p.p_rows_per_chunk = (int)rpc;
-  p.p_row_chunks = (int)cdiv(M, rpc);
-  p.partP_elems = (int64_t)p.p_row_chunks * 3 * ldU;
-  p.e_blocks = (int)cdiv(M, (kThreadsE / 32) * kRows);
+  const int W = fp64 ? 4 : 8;          // columns per colsum thread (32 bytes); row strides padded to it
+  const int64_t es = fp64 ? 8 : 4;
+  p.ldU = cdiv(K, W) * W;
+  p.ldM = cdiv(M, W) * W;
+  plan_colsum(M, p.ldU, es, sms, W, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+  plan_colsum(K, p.ldM, es, sms, W, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+  p.part_elems = std::max((int64_t)p.p_row_chunks * 3 * p.ldU, (int64_t)p.e_row_chunks * 3 * p.ldM);
+  p.e_blocks = (int)cdiv(M, kRedCols);
   p.sums_elems = (int64_t)p.e_blocks * 3;
   return p;
 }
 
 template <typename F>
-void launch_mstep(const MstepPlan& pl, const F* U, int64_t ldU, const double* lam, int64_t M, int64_t K,
+void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
-                  const typename Vec<F>::t4* Yhat4, F* partP, double* sums, typename Vec<F>::t4* B4,
+                  const typename Vec<F>::t4* Yhat4, F* part, double* sums, typename Vec<F>::t4* B4,
                   typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev) {
   const int g = iteration ? 1 : 0;
-  project<F><<<dim3(pl.p_col_tiles, pl.p_row_chunks), kThreadsP, 0, s>>>(U, ldU, (int)M, (int)K, R4,
-                                                                       pl.p_rows_per_chunk, partP, st, g);
+  colsum<F><<<dim3(pl.p_col_tiles, pl.p_row_chunks), kThreadsP, 0, s>>>(U, pl.ldU, (int)M, (int)K, R4,
+                                                                      pl.p_rows_per_chunk, part, pl.ldU, st, g,
+                                                                      g);
   record_after(ev, 0, s);
-  project_reduce<F><<<(unsigned)cdiv(K, kThreadsD), kThreadsD, 0, s>>>(partP, pl.p_row_chunks, ldU, (int)K,
-                                                                       lam, B4, C4, st, g);
+  diag_update<F><<<(unsigned)cdiv(K, kRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
+                                                                   B4, C4, st, g);
   record_after(ev, 1, s);
+  colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,
+                                                                      pl.e_rows_per_chunk, part, pl.ldM, st, g,
+                                                                      0);
   if (iteration) {
-    expand<F, true><<<pl.e_blocks, kThreadsE, expand_smem<F>(), s>>>(U, ldU, (int)M, (int)K, B4, X4, Yt4,
-                                                                      T4, Yhat4, sums, st, g);
+    expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
+                                                             Yhat4, sums, st, g);
   } else {
-    expand<F, false><<<pl.e_blocks, kThreadsE, expand_smem<F>(), s>>>(U, ldU, (int)M, (int)K, B4, X4, Yt4,
-                                                                       T4, nullptr, sums, st, 0);
+    expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
+                                                              T4, nullptr, sums, st, 0);
   }
   record_after(ev, 2, s);
 }
 
 template <typename F>
-void launch_w(const MstepPlan& pl, const F* U, int64_t ldU, int64_t M, int64_t K,
-              const typename Vec<F>::t4* C4, typename Vec<F>::t4* W4, cudaStream_t s) {
-  expand<F, false><<<pl.e_blocks, kThreadsE, expand_smem<F>(), s>>>(U, ldU, (int)M, (int)K, C4, nullptr,
-                                                                     nullptr, W4, nullptr, nullptr, nullptr, 0);
+void launch_w(const MstepPlan& pl, const F* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
+              typename Vec<F>::t4* W4, DevState* st, cudaStream_t s) {
+  colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, C4,
+                                                                      pl.e_rows_per_chunk, part, pl.ldM, st, 0, 0);
+  expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
+                                                            nullptr, W4, nullptr, nullptr, st, 0);
 }
 
-template void launch_mstep<float>(const MstepPlan&, const float*, int64_t, const double*, int64_t, int64_t,
-                                  const float4*, const float4*, const float4*, float4*, const float4*,
-                                  float*, double*, float4*, float4*, DevState*, bool, cudaStream_t, cudaEvent_t*);
-template void launch_mstep<double>(const MstepPlan&, const double*, int64_t, const double*, int64_t, int64_t,
+template void launch_mstep<float>(const MstepPlan&, const float*, const float*, const double*, int64_t, int64_t,
+                                  const float4*, const float4*, const float4*, float4*, const float4*, float*,
+                                  double*, float4*, float4*, DevState*, bool, cudaStream_t, cudaEvent_t*);
+template void launch_mstep<double>(const MstepPlan&, const double*, const double*, const double*, int64_t, int64_t,
                                    const dvec4*, const dvec4*, const dvec4*, dvec4*, const dvec4*, double*,
                                    double*, dvec4*, dvec4*, DevState*, bool, cudaStream_t, cudaEvent_t*);
-template void launch_w<float>(const MstepPlan&, const float*, int64_t, int64_t, int64_t, const float4*,
-                              float4*, cudaStream_t);
-template void launch_w<double>(const MstepPlan&, const double*, int64_t, int64_t, int64_t, const dvec4*,
-                               dvec4*, cudaStream_t);
+template void launch_w<float>(const MstepPlan&, const float*, int64_t, int64_t, const float4*, float*, float4*,
+                              DevState*, cudaStream_t);
+template void launch_w<double>(const MstepPlan&, const double*, int64_t, int64_t, const dvec4*, double*, dvec4*,
+                               DevState*, cudaStream_t);
 
 }  // namespace fcpd

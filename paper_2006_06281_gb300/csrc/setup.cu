@@ -69,6 +69,16 @@ __global__ void extract_basis(const double* __restrict__ V, int M, int K, F* __r
   }
 }
 
+// U^T row k is eigenvector M-1-k: a contiguous column of V, cast to F, with
+// zero padding for M <= m < ldM.
+template <typename F>
+__global__ void extract_basis_t(const double* __restrict__ V, int M, int K, F* __restrict__ Ut, int64_t ldM) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)K * ldM) return;
+  const int k = (int)(i / ldM), m = (int)(i % ldM);
+  Ut[i] = m < M ? (F)V[(size_t)(M - 1 - k) * M + m] : (F)0;
+}
+
 __global__ void extract_lambda(const double* __restrict__ w, int M, int K, double* __restrict__ lam) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < K) lam[k] = fmax(w[M - 1 - k], 0.0);   // clamp: Phi is PSD, LAPACK-level noise can be < 0
@@ -170,10 +180,11 @@ void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double
 }
 
 template <typename F>
-void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, const double* w,
-                          double* lam, cudaStream_t s) {
+void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
+                          const double* w, double* lam, cudaStream_t s) {
   dim3 grid((unsigned)cdiv(ldU, 32), (unsigned)cdiv(M, 32));
   extract_basis<F><<<grid, dim3(32, 8), 0, s>>>(V, (int)M, (int)K, U, ldU);
+  extract_basis_t<F><<<(unsigned)cdiv(K * ldM, kThreads), kThreads, 0, s>>>(V, (int)M, (int)K, Ut, ldM);
   extract_lambda<<<(unsigned)cdiv(K, kThreads), kThreads, 0, s>>>(w, (int)M, (int)K, lam);
 }
 
@@ -201,10 +212,10 @@ template void launch_pack<float>(const float*, int64_t, float4*, bool, cudaStrea
 template void launch_pack<double>(const double*, int64_t, dvec4*, bool, cudaStream_t);
 template void launch_unpack<float>(const float4*, int64_t, float*, cudaStream_t);
 template void launch_unpack<double>(const dvec4*, int64_t, double*, cudaStream_t);
-template void launch_extract_basis<float>(const double*, int64_t, int64_t, float*, int64_t, const double*,
-                                          double*, cudaStream_t);
-template void launch_extract_basis<double>(const double*, int64_t, int64_t, double*, int64_t, const double*,
-                                           double*, cudaStream_t);
+template void launch_extract_basis<float>(const double*, int64_t, int64_t, float*, int64_t, float*, int64_t,
+                                          const double*, double*, cudaStream_t);
+template void launch_extract_basis<double>(const double*, int64_t, int64_t, double*, int64_t, double*, int64_t,
+                                           const double*, double*, cudaStream_t);
 template void launch_sigma2_init<float>(const float4*, int64_t, const float4*, int64_t, double*, DevState*,
                                         cudaStream_t);
 template void launch_sigma2_init<double>(const dvec4*, int64_t, const dvec4*, int64_t, double*, DevState*,

@@ -144,7 +144,9 @@ def test_register_fp64_m500():
     stol = sigma2_tol(FP64_TOL, ref["T"], ref["sigma2"])
     assert s2 == pytest.approx(ref["sigma2"], rel=stol)
     np.testing.assert_allclose(hist["sigma2"], ref["sigma2_hist"], rtol=stol)
-    np.testing.assert_allclose(hist["loglik"], ref["loglik_hist"], rtol=1e-10)
+    # Eq. 3 carries -(N D / 2) ln sigma2: its absolute error follows sigma2's
+    np.testing.assert_allclose(hist["loglik"], ref["loglik_hist"], rtol=1e-10,
+                               atol=ps.Y.shape[0] * 1.5 * stol)
     assert hist["rmse"][-1] == pytest.approx(oracle.rmse(ref["T"], ps.Yhat), rel=1e-9)
 
 
@@ -171,6 +173,10 @@ RAGGED = [(1, 2), (2, 3), (31, 33), (127, 129), (513, 1025), (700, 450)]
 def test_register_ragged_sizes(M, N, prec):
     ps = pointsets(M, n_out=max(N - M, 0), n_in=min(M, N), seed=11 * M + N)
     X, Y = ps.X, ps.Y
+    if M < 4:
+        # outliers drawn in the bounding box of fewer than 4 inliers would
+        # collapse onto them; use an independent, non-degenerate scene
+        Y = pointsets(max(N, 4), seed=7 * N + 1).Y[:N]
     if prec == cpd.FP32:
         X, Y = X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64)
     ref = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=12)
