@@ -218,6 +218,32 @@ cpd_status cpd_estep(const void *T, int64_t M, const void *Y, int64_t N, int32_t
                      double *sums_out, void *stream);
 
 /*
+ * cpd_estep without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need an E-step -- code running while another framework captures
+ * a CUDA graph (allocation cannot be captured), loops that must not stall on
+ * the device synchronisation cudaMalloc/cudaFree may cause, and programs
+ * that reserve all device memory up front.  It computes exactly what
+ * cpd_estep computes for precision CPD_FP32, with the same kernels, but takes
+ * all scratch from one 24 MiB array that the library holds (as a static
+ * device variable) for its lifetime on every GPU that loads it.
+ *   T (M x 3 floats), Y (N x 3 floats), Ytil_out (M x 3 floats), and the
+ *   optional P1_out (M doubles) and den_out (N doubles) must be DEVICE
+ *   arrays; sums_out (2 host doubles) is optional, as in cpd_estep.
+ *   Limits: 1 <= M, N <= 32768; larger sizes, host arrays or a plan that
+ *   does not fit the array return CPD_EINVAL with a message.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * Every call uses the same array, so calls that may overlap on the GPU (on
+ * different streams, or from different threads) race and must be
+ * serialised by the caller.  The array keeps the last call's contents; the
+ * call re-initialises everything that must start from zero.  Synchronises
+ * `stream`.
+ */
+cpd_status cpd_estep_noalloc(const void *T, int64_t M, const void *Y, int64_t N, double sigma2, double w,
+                             void *Ytil_out, void *P1_out, void *den_out, double *sums_out, void *stream);
+
+/*
  * Whole registration: cpd_setup, p->max_iter iterations of cpd_iterate (fewer
  * with p->tol > 0), outputs, cpd_destroy.
  *   T_out (required) M x D; W_out (optional) M x D; sigma2_out, iters_done

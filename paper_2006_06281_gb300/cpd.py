@@ -30,7 +30,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
-           "cpd_estep", "cpd_register", "cpd_destroy"]
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_destroy"]
 
 
 class CpdParams(C.Structure):
@@ -78,6 +78,7 @@ def load():
                 "cpd_basis_rank": ([vp], i64),
                 "cpd_mstep": ([vp, vp, d, vp, vp], C.c_int),
                 "cpd_estep": ([vp, i64, vp, i64, i32, d, d, vp, vp, vp, dp, vp], C.c_int),
+                "cpd_estep_noalloc": ([vp, i64, vp, i64, d, d, vp, vp, vp, dp, vp], C.c_int),
                 "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
                 "cpd_destroy": ([vp], None),
             }
@@ -275,6 +276,24 @@ def estep(T, Y, sigma2, w, precision=FP32, stream=None):
     sums = (C.c_double * 2)()
     _check(load().cpd_estep(pt, M, py, N, int(precision), float(sigma2), float(w), pyt, pp1, pden, sums,
                             _stream_handle(stream, tcuda)))
+    return dict(Ytil=Ytil, P1=P1, den=den, vsum=sums[0], loglik=sums[1])
+
+
+def estep_noalloc(T, Y, sigma2, w, stream=None):
+    """cpd_estep_noalloc: the FP32 E-step with no device allocation (CUDA
+    tensors only).  Returns dict(Ytil, P1, den, vsum, loglik) like estep()."""
+    import torch
+    Tk, pt, tcuda = _prep(T, FP32, "T")
+    Yk, py, ycuda = _prep(Y, FP32, "Y")
+    if not (tcuda and ycuda):
+        raise TypeError("estep_noalloc takes CUDA tensors")
+    M, N = int(Tk.shape[0]), int(Yk.shape[0])
+    Ytil = torch.empty((M, 3), dtype=torch.float32, device=Tk.device)
+    P1 = torch.empty(M, dtype=torch.float64, device=Tk.device)
+    den = torch.empty(N, dtype=torch.float64, device=Tk.device)
+    sums = (C.c_double * 2)()
+    _check(load().cpd_estep_noalloc(pt, M, py, N, float(sigma2), float(w), Ytil.data_ptr(), P1.data_ptr(),
+                                    den.data_ptr(), sums, _stream_handle(stream, True)))
     return dict(Ytil=Ytil, P1=P1, den=den, vsum=sums[0], loglik=sums[1])
 
 

@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/fcpd.h"
 
 namespace fcpd {
@@ -91,6 +93,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   }
   return r;
 }
+
+// Message returned by cpd_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------- launchers
 struct EstepPlan {

@@ -115,6 +115,8 @@ constexpr int64_t kMaxN = 1LL << 30;
 
 }  // namespace
 
+void fcpd::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct cpd_ctx {
   cpd_params p{};
   int dev = 0;
