@@ -112,7 +112,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- roofline
-KERNELS = ["e_pass_a", "e_reduce_a", "e_pass_b", "e_reduce_b", "m_project", "m_diag", "m_expand"]
+KERNELS = ["e_pass_a", "e_reduce_a", "e_pass_b", "e_reduce_b", "m_project", "m_diag", "m_expand", "m_finish"]
 OPS_PER_PAIR = {"e_pass_a": 7, "e_pass_b": 12}      # FP32 pipe ops per Gaussian pair (kernel mix)
 
 
@@ -134,7 +134,7 @@ def roofline_entries(phase_ms, M, N, K, peaks, es=4):
                              basis=f"{OPS_PER_PAIR[name]} FP32 ops + 1 ex2 per pair; 152 SMs x 128 FP32 lanes "
                                    f"x {peaks['sm_max_mhz']:.0f} MHz")
         elif name in ("m_project", "m_expand"):
-            byts = M * K * es + (M * 16 * 4 if name == "m_expand" else M * 16)
+            byts = M * K * es + (K * 16 if name == "m_expand" else M * 16)   # basis once + the staged 3-vectors
             out[name] = dict(bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
                              frac=byts / t / 1e9 / peaks["hbm_gbs"], ms=t * 1e3, bytes=byts)
         else:
@@ -143,15 +143,13 @@ def roofline_entries(phase_ms, M, N, K, peaks, es=4):
 
 
 def traffic_for(kernel):
-    """dram bytes per launch recorded by ncu in profiles/, if the kernel source
-    is unchanged since (sha256 of its .cu file recorded beside the figure)."""
+    """dram bytes per launch recorded by ncu in profiles/, if the kernel's
+    source file is unchanged since (its sha256 is recorded beside the figure)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
+    src = {"e_pass_a": "estep.cu", "e_pass_b": "estep.cu", "colsum": "mstep.cu"}.get(kernel)
+    if src is None or not os.path.exists(path):
         return None
-    src = {"e_pass_a": "estep.cu", "e_pass_b": "estep.cu", "m_project": "mstep.cu", "m_expand": "mstep.cu"}
-    if kernel not in src:
-        return None
-    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2006_06281_gb300", "csrc", src[kernel]), "rb").read()).hexdigest()
+    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2006_06281_gb300", "csrc", src), "rb").read()).hexdigest()
     for line in open(path):
         if line.startswith("#"):
             continue
@@ -159,6 +157,24 @@ def traffic_for(kernel):
         if kv.get("kernel") == kernel and kv.get("source_sha256") == sha:
             return float(kv["dram_bytes_per_launch"])
     return None
+
+
+def dominant_kernel(roof):
+    """The kernel with the largest time per iteration.  The two M-step
+    products are launches of one kernel (colsum): they count together, and
+    its per-launch figures are their average."""
+    cands = {}
+    for k in ("e_pass_a", "e_pass_b"):
+        if k in roof:
+            cands[k] = (roof[k]["ms"], dict(roof[k]))
+    if "m_project" in roof and "m_expand" in roof:
+        a, b = roof["m_project"], roof["m_expand"]
+        t = (a["ms"] + b["ms"]) / 2
+        byts = (a["bytes"] + b["bytes"]) / 2
+        cands["colsum"] = (2 * t, dict(bound="hbm", achieved=byts / (t / 1e3) / 1e9, peak=a["peak"], unit="GB/s",
+                                       frac=byts / (t / 1e3) / 1e9 / a["peak"], ms=t, launches_per_iter=2))
+    name = max(cands, key=lambda k: cands[k][0])
+    return name, cands[name][1]
 
 
 # ---------------------------------------------------------- CPU baseline
@@ -245,6 +261,37 @@ def workload_config(cfg, M, N, K):
                 l2="inputs larger than L2: the eigenbasis U is M*K*4 bytes, read twice per step")
 
 
+# ----------------------------------------------------------- N > 1 ranks
+def timing_helpers(world, device):
+    """Barrier and max-over-ranks for the timed region.  Ranks exchange
+    nothing else: each registers its own independent pair (weak scaling)."""
+    import torch
+    import torch.distributed as dist
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def allmax(x):
+        if world == 1:
+            return x
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, allmax
+
+
+def rank_seed(cfg, rank):
+    """Each rank registers its own pair: the workload's seed offset by the rank."""
+    return cfg["seed"] + rank
+
+
+def job_rate(steps_per_rank, world, max_ms):
+    """Whole-job iterations per second: all ranks' steps over the slowest rank's time."""
+    return world * steps_per_rank / (max_ms / 1e3)
+
+
 # ------------------------------------------------------------------ ours
 def main():
     args = parse()
@@ -262,24 +309,14 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def allmax(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier, allmax = timing_helpers(world, torch.device("cuda", local))
 
     from paper_2006_06281_gb300 import build, cpd
     build.build()
     peaks = load_peaks()
 
     M = cfg["M"]
-    ps = datagen.gen(M, cfg["n_out"], cfg["amp"], cfg["noise"], cfg["seed"] + rank)
+    ps = datagen.gen(M, cfg["n_out"], cfg["amp"], cfg["noise"], rank_seed(cfg, rank))
     N = ps.Y.shape[0]
     K = cfg["K"] or M
     X = torch.tensor(ps.X, dtype=torch.float32, device="cuda")
@@ -308,7 +345,7 @@ def main():
     sampler = ClockSampler(gpu_index)
     time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    phases = np.zeros(8)
+    phases = np.zeros(9)
     ev0.record()
     for _ in range(R):
         ctx.reset()
@@ -318,17 +355,16 @@ def main():
     barrier()
     clocks = sampler.stop()
     t_ms = allmax(ev0.elapsed_time(ev1))
-    value = world * steps / (t_ms / 1e3)
+    value = job_rate(steps, world, t_ms)
 
     # per-kernel roofline from the events inside the timed region
     roof = roofline_entries(phases, M, N, K, peaks)
-    dominant = max((k for k in roof if "frac" in roof[k]), key=lambda k: roof[k]["ms"])
-    rd = dict(roof[dominant])
+    dominant, rd = dominant_kernel(roof)
     tr = traffic_for(dominant)
     roofline = dict(kernel=dominant, bound=rd["bound"], achieved=rd["achieved"], peak=rd["peak"], unit=rd["unit"],
-                    frac=rd["frac"], traffic=tr, peak_source=peaks["source"])
+                    frac=rd["frac"], traffic=tr, ms_per_launch=rd["ms"], peak_source=peaks["source"])
     e_ms = sum(phases[:4])
-    m_ms = sum(phases[4:7])
+    m_ms = sum(phases[4:8])
     estep = dict(pairs_per_s=M * N / (e_ms / 1e3), ms_per_iter=e_ms, m_step_ms_per_iter=m_ms,
                  pass_a=roof.get("e_pass_a"), pass_b=roof.get("e_pass_b"))
 
@@ -364,7 +400,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = allmax(e0.elapsed_time(e1))
-    e2e = dict(value=world * ne / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=N * 3 * 4,
+    e2e = dict(value=job_rate(ne, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * 3 * 4,
                d2h_bytes_per_step=M * 3 * 4 + STATE_BYTES, steps=ne)
 
     # low-rank variant (fast-CPD-L, Eq. 20), K = 200, same pair
@@ -377,7 +413,7 @@ def main():
         ctxl.reset()
         ctxl.iterate_profiled(Y, I)
         torch.cuda.synchronize()
-        ph = np.zeros(8)
+        ph = np.zeros(9)
         a.record()
         nl = max(1, min(R, 10))
         for _ in range(nl):

@@ -146,12 +146,13 @@ cpd_status cpd_iterate(cpd_ctx *ctx, const void *Y, int64_t N, int32_t n_iter,
  * cpd_iterate with per-kernel timing, for benchmarking: runs n_iter
  * (1..4096) iterations from one captured CUDA graph in which every 10th
  * iteration (and the last) also records a timing event after each kernel,
- * synchronises `stream`, and writes 8 floats to phase_ms (host): the
+ * synchronises `stream`, and writes 9 floats to phase_ms (host): the
  * milliseconds per launch, averaged over those sampled iterations, of
  * [0] E pass A, [1] its reduction (+ c, Eq. 4), [2] E pass B, [3] its
  * reduction (Eq. 5), [4] projection U^T (Ytil - X), [5] diagonal update,
- * [6] expansion T = X + U B with the Eq. 18 epilogue; [7] the whole span
- * from the first iteration's start to the last iteration's end.
+ * [6] expansion U B, [7] its reduction with T = X + U B and Eq. 18;
+ * [8] the whole span from the first iteration's start to the last
+ * iteration's end.
  */
 cpd_status cpd_iterate_profiled(cpd_ctx *ctx, const void *Y, int64_t N, int32_t n_iter,
                                 float *phase_ms);

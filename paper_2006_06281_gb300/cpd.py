@@ -188,9 +188,9 @@ class Context:
 
     def iterate_profiled(self, Y, n_iter):
         """n_iter iterations from a graph with timing events after every
-        kernel; returns the 8 phase times (ms) described in fcpd.h."""
+        kernel; returns the 9 phase times (ms) described in fcpd.h."""
         Yk, py, _ = _prep(Y, self.precision, "Y")
-        out = (C.c_float * 8)()
+        out = (C.c_float * 9)()
         _check(load().cpd_iterate_profiled(self._h, py, int(Yk.shape[0]), int(n_iter), out))
         return list(out)
 

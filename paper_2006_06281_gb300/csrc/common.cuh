@@ -120,10 +120,14 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms);
 
 // Optional `ev` arrays: an event is recorded (as an external event-record
 // node when captured) after each kernel: 4 for the E-step (pass A, its
-// reduction, pass B, its reduction), 3 for the M-step (projection, diagonal
-// update, expansion).
+// reduction, pass B, its reduction), 4 for the M-step (projection, diagonal
+// update, expansion, its reduction + Eq. 18).
 inline void record_after(cudaEvent_t* ev, int i, cudaStream_t s) {
-  if (ev) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+  if (!ev) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+  else cudaEventRecord(ev[i], s);
 }
 
 // E-step: passes A and B with their reductions.  Reads T4, Y4 and st->sigma2;

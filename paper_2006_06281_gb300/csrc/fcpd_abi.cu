@@ -136,7 +136,7 @@ struct cpd_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
   cudaGraphExec_t prof_graph = nullptr;             // n iterations with timing events
   int prof_iters = 0;
-  std::vector<cudaEvent_t> prof_ev;                 // 8 per iteration
+  std::vector<cudaEvent_t> prof_ev;                 // 9 per sampled iteration
   bool started = false;
   bool has_gt = false;
   double gt_tol = 0.0;
@@ -211,9 +211,9 @@ cpd_status read_state(cpd_ctx* c, DevState* h) {
 }
 
 // The kernels of one EM iteration, enqueued on `s` (used only under capture).
-// With `ev` (8 events) the iteration is bracketed by timing events: ev[0]
-// before pass A, ev[1..4] after the E-step kernels, ev[5..7] after the M-step
-// kernels.
+// With `ev` (kEvPerIter = 9 events) the iteration is bracketed by timing
+// events: ev[0] before pass A, ev[1..4] after the E-step kernels, ev[5..8]
+// after the M-step kernels.
 void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
   cudaEvent_t* ee = ev ? ev + 1 : nullptr;
@@ -293,6 +293,8 @@ cpd_status prepare_iterate(cpd_ctx* c, const void* Y, int64_t N) {
 
 // Iterations that carry timing events: every kProfEvery-th and the last.
 constexpr int kProfEvery = 10;
+constexpr int kEvPerIter = 9;
+constexpr int kPhases = kEvPerIter - 1;
 bool profiled_iteration(int i, int n_iter) { return i % kProfEvery == 0 || i == n_iter - 1; }
 
 cpd_status capture_profiled(cpd_ctx* c, int n_iter) {
@@ -301,11 +303,11 @@ cpd_status capture_profiled(cpd_ctx* c, int n_iter) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   int sampled = 0;
   for (int i = 0; i < n_iter; ++i) sampled += profiled_iteration(i, n_iter) ? 1 : 0;
-  c->prof_ev.assign((size_t)8 * sampled, nullptr);
+  c->prof_ev.assign((size_t)kEvPerIter * sampled, nullptr);
   for (auto& e : c->prof_ev) CUDA_TRY(cudaEventCreate(&e));
   CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
   for (int i = 0, j = 0; i < n_iter; ++i) {
-    if (profiled_iteration(i, n_iter)) enqueue_iteration(c, c->cap, &c->prof_ev[(size_t)8 * j++]);
+    if (profiled_iteration(i, n_iter)) enqueue_iteration(c, c->cap, &c->prof_ev[(size_t)kEvPerIter * j++]);
     else enqueue_iteration(c, c->cap, nullptr);
   }
   cudaGraph_t g = nullptr;
@@ -503,11 +505,11 @@ cpd_status cpd_iterate_profiled(cpd_ctx* c, const void* Y, int64_t N, int32_t n_
   if (!c->prof_graph || c->prof_iters != n_iter) STATUS_TRY(capture_profiled(c, n_iter));
   CUDA_TRY(cudaGraphLaunch(c->prof_graph, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
-  for (int p = 0; p < 8; ++p) phase_ms[p] = 0.f;
-  const int sampled = (int)(c->prof_ev.size() / 8);
+  for (int p = 0; p <= kPhases; ++p) phase_ms[p] = 0.f;
+  const int sampled = (int)(c->prof_ev.size() / kEvPerIter);
   for (int j = 0; j < sampled; ++j) {
-    const cudaEvent_t* ev = &c->prof_ev[(size_t)8 * j];
-    for (int p = 0; p < 7; ++p) {
+    const cudaEvent_t* ev = &c->prof_ev[(size_t)kEvPerIter * j];
+    for (int p = 0; p < kPhases; ++p) {
       float ms = 0.f;
       CUDA_TRY(cudaEventElapsedTime(&ms, ev[p], ev[p + 1]));
       phase_ms[p] += ms / (float)sampled;
@@ -515,7 +517,7 @@ cpd_status cpd_iterate_profiled(cpd_ctx* c, const void* Y, int64_t N, int32_t n_
   }
   float total = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&total, c->prof_ev[0], c->prof_ev.back()));
-  phase_ms[7] = total;
+  phase_ms[kPhases] = total;
   DevState h;
   STATUS_TRY(read_state(c, &h));
   if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");

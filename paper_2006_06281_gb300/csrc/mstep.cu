@@ -291,6 +291,7 @@ void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* la
   colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,
                                                                       pl.e_rows_per_chunk, part, pl.ldM, st, g,
                                                                       0);
+  record_after(ev, 2, s);
   if (iteration) {
     expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
                                                              Yhat4, sums, st, g);
@@ -298,7 +299,7 @@ void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* la
     expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
                                                               T4, nullptr, sums, st, 0);
   }
-  record_after(ev, 2, s);
+  record_after(ev, 3, s);
 }
 
 template <typename F>

@@ -118,6 +118,10 @@ WORKLOADS = {
     # FP32 case: M = N = 5000, full eigenbasis, 100 EM iterations
     "fp32_m5000": dict(M=5000, n_out=0, amp=0.15, noise=0.01, seed=0,
                        omega=0.1, lam=2.0, beta=2.0, iters=100, K=0),
+    # M = N = 8000, full eigenbasis: the basis (256 MB) exceeds L2 but the
+    # whole case fits a few GB -- the size used for detailed profiler captures
+    "fp32_m8000_full": dict(M=8000, n_out=0, amp=0.15, noise=0.01, seed=0,
+                            omega=0.1, lam=2.0, beta=2.0, iters=50, K=0),
     # bunny-scale case: M = N = 20000, full eigenbasis (Table IV's largest
     # reported size with both methods)
     "fp32_m20000_full": dict(M=20000, n_out=0, amp=0.15, noise=0.01, seed=0,
