@@ -257,6 +257,76 @@ cpd_status cpd_register(const void *X, int64_t M, const void *Y, int64_t N, cons
 /* Free a context (NULL is ignored).  Synchronises its stream first. */
 void cpd_destroy(cpd_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched registrations.  The paper registers one pair at a time; these
+ * entry points run many independent registrations (X_i, Y_i), i < n_pairs,
+ * of uneven sizes together: every call advances all of them by the same
+ * number of EM iterations (Eq. 4, 5, 17/20, 18, exactly as cpd_iterate) in
+ * ONE persistent cooperative kernel launch, replayed from a CUDA graph.  The
+ * launch's blocks take the work items of all pairs (tiles of the E-step
+ * passes, row chunks of the basis products, reduction blocks) from a shared
+ * queue, largest pairs first, and meet at a grid-wide barrier between the
+ * phases of an iteration.
+ * ---------------------------------------------------------------------- */
+typedef struct cpd_batch cpd_batch;   /* opaque; owned by the library */
+
+/*
+ * Create a batch: setup of every pair (Eq. 11, Eq. 16, Eq. 19, as cpd_setup,
+ * several pairs at a time on internal streams), scene upload, and the start
+ * of every registration (T_i = X_i, initial variance).
+ *   n_pairs            1..65536.
+ *   X[i], M[i]         model points of pair i: M[i] x 3 floats (host or
+ *                      device), 1 <= M[i] <= 46340.
+ *   Y[i], N[i]         scene points of pair i: N[i] x 3 floats (host or
+ *                      device), N[i] >= 1.
+ *   p                  shared parameters; precision must be CPD_FP32.  The
+ *                      basis of pair i keeps min(p->K, M[i]) eigenpairs (all
+ *                      with p->K = 0).  p->tol > 0 stops each pair on its own.
+ *   barrier_timeout_s  wall-time limit of one wait at a grid barrier inside
+ *                      the kernel, in (0, 60]; 0 selects 5 s.  A wait that
+ *                      exceeds it ends the launch with CPD_ETIMEOUT.
+ *   stream             cudaStream_t all later work of the batch runs on.
+ * The caller's arrays are only read during the call.  Synchronises.
+ * Errors: CPD_EINVAL (arguments, with the pair index), CPD_ENOMEM,
+ * CPD_ESOLVER, CPD_ECUDA (including a device without cooperative launch);
+ * *out is left untouched on error.
+ */
+cpd_status cpd_batch_create(int32_t n_pairs, const void *const *X, const int64_t *M, const void *const *Y,
+                            const int64_t *N, const cpd_params *p, double barrier_timeout_s, void *stream,
+                            cpd_batch **out);
+
+/*
+ * Run n_iter (0..2^20) EM iterations of every pair that has not stopped (by
+ * p->tol or a device failure) in one launch, then synchronise.  CPD_ETIMEOUT
+ * if a grid barrier's wait ran out (the registrations' state is then
+ * undefined until cpd_batch_reset); per-pair failures are reported by
+ * cpd_batch_state, not here.
+ */
+cpd_status cpd_batch_iterate(cpd_batch *b, int32_t n_iter);
+
+/* Per-pair state, n_pairs entries in each (host) array, any of which may be
+ * NULL: sigma2 (Eq. 18), iterations completed, device status (a cpd_status).
+ * Synchronises. */
+cpd_status cpd_batch_state(cpd_batch *b, double *sigma2, int32_t *iters, int32_t *device_status);
+
+/* Current T of pair i: M[i] x 3 floats into T_out (host or device).
+ * Synchronises if T_out is host memory. */
+cpd_status cpd_batch_get_T(cpd_batch *b, int32_t i, void *T_out);
+
+/* Sizes of pair i: model points, scene points, kept eigenpairs. */
+cpd_status cpd_batch_info(const cpd_batch *b, int32_t i, int64_t *M, int64_t *N, int64_t *K);
+
+/* Launch shape of the persistent kernel: pairs, resident blocks (the grid),
+ * and work items per iteration over all phases. */
+cpd_status cpd_batch_launch_shape(const cpd_batch *b, int32_t *n_pairs, int32_t *grid, int32_t *n_items);
+
+/* Restart every registration: T_i = X_i, iteration count 0, initial variance
+ * re-computed from the stored scene.  Synchronises. */
+cpd_status cpd_batch_reset(cpd_batch *b);
+
+/* Free a batch and all its pairs (NULL is ignored).  Synchronises first. */
+void cpd_batch_destroy(cpd_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,9 @@ OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
-           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_destroy"]
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_destroy",
+           "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
+           "cpd_batch_launch_shape", "cpd_batch_reset", "cpd_batch_destroy"]
 
 
 class CpdParams(C.Structure):
@@ -81,6 +83,15 @@ def load():
                 "cpd_estep_noalloc": ([vp, i64, vp, i64, d, d, vp, vp, vp, dp, vp], C.c_int),
                 "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
                 "cpd_destroy": ([vp], None),
+                "cpd_batch_create": ([i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64), pp, d, vp,
+                                      C.POINTER(vp)], C.c_int),
+                "cpd_batch_iterate": ([vp, i32], C.c_int),
+                "cpd_batch_state": ([vp, dp, ip, ip], C.c_int),
+                "cpd_batch_get_T": ([vp, i32, vp], C.c_int),
+                "cpd_batch_info": ([vp, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
+                "cpd_batch_launch_shape": ([vp, ip, ip, ip], C.c_int),
+                "cpd_batch_reset": ([vp], C.c_int),
+                "cpd_batch_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -243,6 +254,93 @@ class Context:
     def close(self):
         if getattr(self, "_h", None):
             load().cpd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent FP32 registrations (X_i, Y_i) advanced together by one
+    persistent kernel launch per `iterate` call (cpd_batch_*)."""
+
+    def __init__(self, Xs, Ys, w=0.1, beta=2.0, lam=2.0, K=0, tol=0.0, sigma2_init=0.0,
+                 barrier_timeout_s=0.0, stream=None):
+        lib = load()
+        if len(Xs) != len(Ys) or not Xs:
+            raise ValueError("Xs and Ys must be non-empty lists of equal length")
+        n = len(Xs)
+        self._keep = []
+        px, py = (C.c_void_p * n)(), (C.c_void_p * n)()
+        M, N = (C.c_int64 * n)(), (C.c_int64 * n)()
+        cuda = False
+        for i, (X, Y) in enumerate(zip(Xs, Ys)):
+            xk, xp, xc = _prep(X, FP32, f"X[{i}]")
+            yk, yp, _ = _prep(Y, FP32, f"Y[{i}]")
+            self._keep += [xk, yk]
+            px[i], py[i], M[i], N[i] = xp, yp, int(xk.shape[0]), int(yk.shape[0])
+            cuda = cuda or xc
+        self.n = n
+        self.M, self.N = list(M), list(N)
+        self.stream = _stream_handle(stream, True)
+        self.params = make_params(FP32, w, beta, lam, K, 0, tol, sigma2_init)
+        h = C.c_void_p()
+        _check(lib.cpd_batch_create(n, px, M, py, N, C.byref(self.params), float(barrier_timeout_s), self.stream,
+                                    C.byref(h)))
+        self._h = h
+        self._keep = []                  # the library holds its own copies
+        self.K = []
+        for i in range(n):
+            k = C.c_int64()
+            _check(lib.cpd_batch_info(h, i, None, None, C.byref(k)))
+            self.K.append(k.value)
+
+    def iterate(self, n_iter):
+        _check(load().cpd_batch_iterate(self._h, int(n_iter)))
+
+    def state(self):
+        """(sigma2 array, iterations array, device status array) of all pairs."""
+        s2 = np.empty(self.n)
+        it = np.empty(self.n, dtype=np.int32)
+        stt = np.empty(self.n, dtype=np.int32)
+        _check(load().cpd_batch_state(self._h, s2.ctypes.data_as(C.POINTER(C.c_double)),
+                                      it.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      stt.ctypes.data_as(C.POINTER(C.c_int32))))
+        return s2, it, stt
+
+    def T(self, i, device=None):
+        """T of pair i (numpy, or a CUDA tensor on `device`)."""
+        if device is not None:
+            import torch
+            out = torch.empty((self.M[i], 3), dtype=torch.float32, device=device)
+            _check(load().cpd_batch_get_T(self._h, int(i), out.data_ptr()))
+            torch.cuda.synchronize(device)
+            return out
+        out = np.empty((self.M[i], 3), dtype=np.float32)
+        _check(load().cpd_batch_get_T(self._h, int(i), out.ctypes.data))
+        return out
+
+    def launch_shape(self):
+        """(pairs, grid blocks, work items per iteration)."""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().cpd_batch_launch_shape(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def reset(self):
+        _check(load().cpd_batch_reset(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cpd_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

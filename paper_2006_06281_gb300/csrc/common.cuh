@@ -19,6 +19,15 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
+
+// Pointer qualifier of the device bodies' arguments.  A translation unit whose
+// kernel writes and later reads the same buffers within one launch (the
+// batched persistent kernel) defines it empty before including this header,
+// so the compiler never turns those loads into non-coherent cache loads.
+#ifndef FCPD_RESTRICT
+#define FCPD_RESTRICT __restrict__
+#endif
 
 #include "../../include/fcpd.h"
 
@@ -116,7 +125,65 @@ struct MstepPlan {
   int64_t part_elems;                                // scratch (elements of F), shared by both
   int64_t sums_elems;                                // double scratch for block sums
 };
-MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms);
+// `colsum_threads`: block size of the streaming kernel the plan is for (128
+// for the per-pair launches, 256 inside the batched persistent kernel).
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads = 128);
+
+// ------------------------------------------------------------ batched mode
+// One registration inside the batched persistent kernel: its sizes, plans
+// and buffers (all device pointers).
+struct BatchPair {
+  int M, N, K;
+  EstepPlan ep;
+  MstepPlan mp;
+  const float4* X4;
+  float4* T4;
+  const float* U;
+  const float* Ut;
+  const double* lam;
+  float4* Yt4;
+  float4* R4;
+  float4* B4;
+  float4* C4;
+  const float4* Y4;
+  float4* Yb;
+  const float4* Yhat4;
+  float* partA;
+  float* partB;
+  float* partP;
+  double* sums;
+  int* flags;
+  DevState* st;
+  int narrow;                 // projection by the row-split body (K <= 128)
+};
+struct BatchItem {
+  int pair, bx, by;
+};
+// Control block of one persistent launch (zeroed before each launch).
+struct BatchCtl {
+  unsigned int barrier_count;
+  unsigned int barrier_gen;
+  unsigned int next_item[16];
+  int status;                 // CPD_ETIMEOUT if a grid barrier gave up
+};
+constexpr int kFixItems = 4;  // work items per pair for the log-domain fix-ups
+// Resident blocks of the persistent kernel on `sms` SMs (0 on failure).
+int batch_resident_blocks(int sms);
+// Fills ep, mp and narrow of every pair from its M, N, K.
+void plan_batch(BatchPair* pairs_host, int n_pairs, int resident);
+// Work items of every phase (phase ph owns items [phase_off[ph], phase_off[ph+1])).
+void batch_items(const BatchPair* pairs_host, int n_pairs, int resident, std::vector<BatchItem>& items,
+                 std::vector<int>& phase_off);
+// Zeroes ctl, then runs n_iter iterations of every pair in one cooperative
+// launch of `grid` blocks.  barrier_extra > 0 makes every grid barrier wait
+// for blocks that do not exist (host-side fault injection for the timeout
+// path).
+cudaError_t launch_batch(const BatchPair* pairs_dev, int n_pairs, const BatchItem* items, const int* phase_off,
+                         BatchCtl* ctl, int grid, int n_iter, double wait_limit_s, int barrier_extra,
+                         cudaStream_t s);
+// Copies every pair's device state into out[0..n_pairs).
+void launch_batch_states(const BatchPair* pairs_dev, int n_pairs, DevState* out, cudaStream_t s);
+
 
 // Optional `ev` arrays: an event is recorded (as an external event-record
 // node when captured) after each kernel: 4 for the E-step (pass A, its

@@ -10,7 +10,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -55,7 +58,6 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 struct DeviceGuard {
   int prev = -1;
@@ -270,24 +272,30 @@ cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
 }
 
 
+// A fresh registration against the uploaded scene: T = X, iteration count 0
+// and the initial variance (given, or the mean squared distance over all
+// model/scene pairs, evaluated on the device).
+cpd_status start_registration(cpd_ctx* c) {
+  CUDA_TRY(cudaMemcpyAsync(c->T4.p, c->X4.p, (size_t)c->M * c->v4, cudaMemcpyDeviceToDevice, c->stream));
+  if (fault_enabled("nan_sigma")) {
+    launch_state_init(c->dst(), std::nan(""), c->stream);
+  } else if (c->p.sigma2_init > 0.0) {
+    launch_state_init(c->dst(), c->p.sigma2_init, c->stream);
+  } else {
+    launch_state_init(c->dst(), 0.0, c->stream);
+    if (c->fp64) launch_sigma2_init<double>(c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), c->N, nullptr, c->dst(), c->stream);
+    else launch_sigma2_init<float>(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, nullptr, c->dst(), c->stream);
+  }
+  CUDA_TRY(cudaGetLastError());
+  c->started = true;
+  return CPD_OK;
+}
+
 // Scene upload and, for a fresh registration, T = X and the initial variance.
 cpd_status prepare_iterate(cpd_ctx* c, const void* Y, int64_t N) {
   STATUS_TRY(ensure_scene(c, N));
   STATUS_TRY(upload_points(c, Y, N, c->Y4.p, true, c->stage, c->fp64, c->stream));
-  if (!c->started) {
-    CUDA_TRY(cudaMemcpyAsync(c->T4.p, c->X4.p, (size_t)c->M * c->v4, cudaMemcpyDeviceToDevice, c->stream));
-    if (fault_enabled("nan_sigma")) {
-      launch_state_init(c->dst(), std::nan(""), c->stream);
-    } else if (c->p.sigma2_init > 0.0) {
-      launch_state_init(c->dst(), c->p.sigma2_init, c->stream);
-    } else {
-      launch_state_init(c->dst(), 0.0, c->stream);
-      if (c->fp64) launch_sigma2_init<double>(c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), N, nullptr, c->dst(), c->stream);
-      else launch_sigma2_init<float>(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), N, nullptr, c->dst(), c->stream);
-    }
-    CUDA_TRY(cudaGetLastError());
-    c->started = true;
-  }
+  if (!c->started) STATUS_TRY(start_registration(c));
   return CPD_OK;
 }
 
@@ -721,6 +729,308 @@ void cpd_destroy(cpd_ctx* c) {
   DeviceGuard guard(c->dev);
   cudaStreamSynchronize(c->stream);
   delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched registrations
+// Many independent registrations (X_i, Y_i) advanced together by one
+// persistent kernel launch per call (batch.cu).  Each pair keeps a full
+// context (its own eigenbasis and state); the batch adds the work-item lists
+// of the persistent kernel, its control block and a CUDA graph of the launch.
+struct cpd_batch {
+  int dev = 0;
+  int sms = 0;
+  int n = 0;
+  int grid = 0;
+  double wait_s = 5.0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cpd_ctx*> ctx;
+  std::vector<BatchPair> pairs;
+  std::vector<int> phase_off_host;
+  Buf pairs_dev, items, phase_off, ctl, states;
+  int n_items = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = -1;
+  int graph_extra = -1;
+
+  ~cpd_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (cpd_ctx* c : ctx) delete c;
+    for (Buf* b : {&pairs_dev, &items, &phase_off, &ctl, &states}) b->release();
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace {
+
+constexpr int kMaxBatch = 1 << 16;
+
+// Per-pair buffers sized for the batched plan, scene upload and the start of
+// the registration.
+cpd_status batch_load_pair(cpd_ctx* c, const BatchPair& bp, const void* Y) {
+  if (bp.mp.ldU != c->mp.ldU || bp.mp.ldM != c->mp.ldM)
+    return fail(CPD_ECUDA, "internal: batched basis layout differs from the context's");
+  c->drop_graphs();
+  c->ep = bp.ep;
+  c->mp = bp.mp;
+  const int64_t N = bp.N;
+  STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
+  STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
+  STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
+  STATUS_TRY(c->partB.ensure((size_t)c->ep.partB_elems * c->es));
+  STATUS_TRY(c->partP.ensure((size_t)c->mp.part_elems * c->es));
+  STATUS_TRY(c->sums.ensure((size_t)std::max(c->ep.sums_elems, c->mp.sums_elems) * sizeof(double)));
+  STATUS_TRY(c->flags.ensure((size_t)c->ep.flags_elems * sizeof(int)));
+  c->N = N;
+  launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, 0.0, 0, c->hist.as<double>(), c->M, N, c->K,
+                      c->stream);
+  STATUS_TRY(upload_points(c, Y, N, c->Y4.p, true, c->stage, false, c->stream));
+  return start_registration(c);
+}
+
+BatchPair batch_pointers(cpd_ctx* c, const BatchPair& plan) {
+  BatchPair b = plan;
+  b.X4 = c->X4.as<float4>();
+  b.T4 = c->T4.as<float4>();
+  b.U = c->U.as<float>();
+  b.Ut = c->Ut.as<float>();
+  b.lam = c->lam.as<double>();
+  b.Yt4 = c->Yt4.as<float4>();
+  b.R4 = c->R4.as<float4>();
+  b.B4 = c->B4.as<float4>();
+  b.C4 = c->C4.as<float4>();
+  b.Y4 = c->Y4.as<float4>();
+  b.Yb = c->Yb.as<float4>();
+  b.Yhat4 = nullptr;
+  b.partA = c->partA.as<float>();
+  b.partB = c->partB.as<float>();
+  b.partP = c->partP.as<float>();
+  b.sums = c->sums.as<double>();
+  b.flags = c->flags.as<int>();
+  b.st = c->dst();
+  return b;
+}
+
+cpd_status batch_capture(cpd_batch* b, int n_iter, int extra) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_iters = -1;
+  CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  cudaError_t le = launch_batch(b->pairs_dev.as<BatchPair>(), b->n, b->items.as<BatchItem>(), b->phase_off.as<int>(),
+                                b->ctl.as<BatchCtl>(), b->grid, n_iter, b->wait_s, extra, b->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(CPD_ECUDA, std::string("capture of the batched launch: ") +
+                               cudaGetErrorString(le != cudaSuccess ? le : e));
+  }
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  b->graph_iters = n_iter;
+  b->graph_extra = extra;
+  return CPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpd_status cpd_batch_create(int32_t n_pairs, const void* const* X, const int64_t* M, const void* const* Y,
+                            const int64_t* N, const cpd_params* p, double barrier_timeout_s, void* stream,
+                            cpd_batch** out) {
+  g_err.clear();
+  STATUS_TRY(validate_params(p));
+  if (!out) return fail(CPD_EINVAL, "out is NULL");
+  if (n_pairs < 1 || n_pairs > kMaxBatch) return fail(CPD_EINVAL, "n_pairs must be in [1, 65536]");
+  if (!X || !M || !Y || !N) return fail(CPD_EINVAL, "X, M, Y and N are required");
+  if (p->precision != CPD_FP32) return fail(CPD_EINVAL, "batched registrations run in FP32 only");
+  if (barrier_timeout_s == 0.0) barrier_timeout_s = 5.0;
+  if (!(barrier_timeout_s > 0.0 && barrier_timeout_s <= 60.0))
+    return fail(CPD_EINVAL, "barrier_timeout_s must be in (0, 60] (0 selects 5 s)");
+  for (int i = 0; i < n_pairs; ++i) {
+    if (!X[i] || !Y[i]) return fail(CPD_EINVAL, "pair " + std::to_string(i) + ": X or Y is NULL");
+    if (M[i] < 1 || M[i] > kMaxM) return fail(CPD_EINVAL, "pair " + std::to_string(i) + ": M must be in [1, 46340]");
+    if (N[i] < 1 || N[i] > kMaxN) return fail(CPD_EINVAL, "pair " + std::to_string(i) + ": N must be in [1, 2^30]");
+  }
+  if (fault_enabled("alloc")) return fail(CPD_ENOMEM, "injected allocation failure (CPD_FAULT=alloc)");
+
+  cpd_batch* b = new (std::nothrow) cpd_batch();
+  if (!b) return fail(CPD_ENOMEM, "host allocation failed");
+  auto bail = [&](cpd_status s) {
+    const std::string keep = g_err;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    delete b;
+    g_err = keep;
+    return s;
+  };
+  b->n = n_pairs;
+  b->wait_s = barrier_timeout_s;
+  b->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&b->dev) != cudaSuccess) return bail(fail(CPD_ECUDA, "no CUDA device"));
+  if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "cannot query the SM count"));
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->dev);
+  if (!coop) return bail(fail(CPD_ECUDA, "the device does not support cooperative launches"));
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "cannot create the capture stream"));
+  b->grid = batch_resident_blocks(b->sms);
+  if (b->grid < 1) return bail(fail(CPD_ECUDA, "the persistent kernel cannot be made resident"));
+
+  // Setup of every pair (Eq. 11, Eq. 16, Eq. 19): several host threads, each
+  // on its own stream, so the eigensolves of small pairs overlap.
+  b->ctx.assign((size_t)n_pairs, nullptr);
+  std::vector<cpd_status> st((size_t)n_pairs, CPD_OK);
+  std::vector<std::string> msg((size_t)n_pairs);
+  std::atomic<int> next{0};
+  std::atomic<bool> stop{false};
+  const int nthreads = std::min(n_pairs, 8);
+  auto worker = [&]() {
+    cudaSetDevice(b->dev);
+    cudaStream_t ws = nullptr;
+    if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+      stop = true;
+      return;
+    }
+    for (int i; !stop && (i = next.fetch_add(1)) < n_pairs;) {
+      cpd_params pi = *p;
+      pi.K = (p->K == 0 || p->K > M[i]) ? 0 : p->K;
+      cpd_ctx* c = nullptr;
+      st[i] = cpd_setup(X[i], M[i], &pi, ws, &c);
+      if (st[i] != CPD_OK) {
+        msg[i] = cpd_last_error();
+        stop = true;
+        break;
+      }
+      cudaStreamSynchronize(ws);
+      c->stream = b->stream;
+      b->ctx[i] = c;
+    }
+    cudaStreamSynchronize(ws);
+    cudaStreamDestroy(ws);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n_pairs; ++i)
+    if (st[i] != CPD_OK) return bail(fail(st[i], "pair " + std::to_string(i) + ": " + msg[i]));
+  for (int i = 0; i < n_pairs; ++i)
+    if (!b->ctx[i]) return bail(fail(CPD_ECUDA, "pair setup did not run (stream creation failed)"));
+
+  // Work-item plan of the persistent kernel and the per-pair buffers it implies.
+  b->pairs.assign((size_t)n_pairs, BatchPair{});
+  for (int i = 0; i < n_pairs; ++i) {
+    b->pairs[i].M = (int)M[i];
+    b->pairs[i].N = (int)N[i];
+    b->pairs[i].K = (int)b->ctx[i]->K;
+  }
+  plan_batch(b->pairs.data(), n_pairs, b->grid);
+  cpd_status s;
+  for (int i = 0; i < n_pairs; ++i) {
+    if ((s = batch_load_pair(b->ctx[i], b->pairs[i], Y[i])) != CPD_OK) return bail(s);
+    b->pairs[i] = batch_pointers(b->ctx[i], b->pairs[i]);
+  }
+  std::vector<BatchItem> items;
+  batch_items(b->pairs.data(), n_pairs, b->grid, items, b->phase_off_host);
+  b->n_items = (int)items.size();
+  if ((s = b->pairs_dev.ensure(sizeof(BatchPair) * (size_t)n_pairs)) != CPD_OK) return bail(s);
+  if ((s = b->items.ensure(sizeof(BatchItem) * items.size())) != CPD_OK) return bail(s);
+  if ((s = b->phase_off.ensure(sizeof(int) * b->phase_off_host.size())) != CPD_OK) return bail(s);
+  if ((s = b->ctl.ensure(sizeof(BatchCtl))) != CPD_OK) return bail(s);
+  if ((s = b->states.ensure(sizeof(DevState) * (size_t)n_pairs)) != CPD_OK) return bail(s);
+  if (cudaMemcpyAsync(b->pairs_dev.p, b->pairs.data(), sizeof(BatchPair) * (size_t)n_pairs, cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->items.p, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->phase_off.p, b->phase_off_host.data(), sizeof(int) * b->phase_off_host.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "upload of the batch plan failed"));
+  *out = b;
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_iterate(cpd_batch* b, int32_t n_iter) {
+  g_err.clear();
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  if (n_iter < 0 || n_iter > (1 << 20)) return fail(CPD_EINVAL, "n_iter must be in [0, 2^20]");
+  if (n_iter == 0) return CPD_OK;
+  DeviceGuard guard(b->dev);
+  const int extra = fault_enabled("barrier") ? 1 : 0;
+  if (!b->graph || b->graph_iters != n_iter || b->graph_extra != extra) STATUS_TRY(batch_capture(b, n_iter, extra));
+  CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+  BatchCtl h;
+  CUDA_TRY(cudaMemcpyAsync(&h, b->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (h.status != 0)
+    return fail((cpd_status)h.status, "a grid barrier of the batched kernel timed out (" +
+                                          std::to_string(b->wait_s) + " s); the pairs' state is undefined until "
+                                          "cpd_batch_reset" + (extra ? " (injected: CPD_FAULT=barrier)" : ""));
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_state(cpd_batch* b, double* sigma2, int32_t* iters, int32_t* device_status) {
+  g_err.clear();
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  DeviceGuard guard(b->dev);
+  std::vector<DevState> h((size_t)b->n);
+  launch_batch_states(b->pairs_dev.as<BatchPair>(), b->n, b->states.as<DevState>(), b->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(h.data(), b->states.p, sizeof(DevState) * h.size(), cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < b->n; ++i) {
+    if (sigma2) sigma2[i] = h[i].sigma2;
+    if (iters) iters[i] = h[i].iter;
+    if (device_status) device_status[i] = h[i].status;
+  }
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_get_T(cpd_batch* b, int32_t i, void* T_out) {
+  g_err.clear();
+  if (!b || !T_out) return fail(CPD_EINVAL, "batch and T_out are required");
+  if (i < 0 || i >= b->n) return fail(CPD_EINVAL, "pair index out of range");
+  DeviceGuard guard(b->dev);
+  cpd_ctx* c = b->ctx[i];
+  return download_points(c->T4.p, c->M, T_out, c->stage, false, b->stream);
+}
+
+cpd_status cpd_batch_info(const cpd_batch* b, int32_t i, int64_t* M, int64_t* N, int64_t* K) {
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  if (i < 0 || i >= b->n) return fail(CPD_EINVAL, "pair index out of range");
+  if (M) *M = b->ctx[i]->M;
+  if (N) *N = b->ctx[i]->N;
+  if (K) *K = b->ctx[i]->K;
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_launch_shape(const cpd_batch* b, int32_t* n_pairs, int32_t* grid, int32_t* n_items) {
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  if (n_pairs) *n_pairs = b->n;
+  if (grid) *grid = b->grid;
+  if (n_items) *n_items = b->n_items;
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_reset(cpd_batch* b) {
+  g_err.clear();
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  DeviceGuard guard(b->dev);
+  for (cpd_ctx* c : b->ctx) STATUS_TRY(start_registration(c));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  return CPD_OK;
+}
+
+void cpd_batch_destroy(cpd_batch* b) {
+  if (!b) return;
+  DeviceGuard guard(b->dev);
+  cudaStreamSynchronize(b->stream);
+  delete b;
 }
 
 }  // extern "C"

@@ -1,29 +1,7 @@
-// M-step of fast CPD on sm_103a (Eq. 17 full basis, Eq. 20 top-K basis) and
-// the variance update (Eq. 18), fused into the last kernel.
-//
-// Both dense products of the M-step are skinny (3 right-hand sides) and
-// HBM-bound, so both run through one streaming kernel, `colsum`:
-//     out[c][d] = sum_r A[r][c] * V[r][d]     (A row-major, d = 0..2)
-// Each thread owns W consecutive columns (two 16-byte vectors = 32 bytes per
-// row; 32-byte segments measured steadier across physical placements than
-// 16-byte ones), walks a chunk of rows with loads in flight, and takes V[r]
-// from shared memory;
-// the row chunks are split over blocks and summed in a fixed order.
-//   projection  A = U  (M x K), V = R = Ytil - X  ->  a_k = (U^T R)_k
-//   expansion   A = U^T (K x M, stored once at setup), V = B  ->  (U B)_m
-// with the diagonal update in between: s_k = l_k / (l_k + lambda sigma2),
-// B_k = s_k a_k ("only a diagonal changes per iteration", Sec. III) and
-// C_k = a_k / (l_k + lambda sigma2) for W.
-// The expansion's reduction kernel writes T = X + U B and evaluates, per row
-// in FP64, the Eq. 18 term with the new T, shifted to the old T (no
-// cancellation of O(1) terms):
-//   sum_n p^_mn |y_n - t_new|^2
-//     = V_m/P1_m + 2 (t_old - t_new).(Ytil_m - t_old) + |t_old - t_new|^2;
-// its last block sums the block partials in a fixed order and advances the
-// device state (sigma2, history, stop test).
-#include "common.cuh"
-
-#include <math.h>
+// M-step of fast CPD on sm_103a: the per-registration kernels (thin wrappers
+// over the device bodies in mstep_dev.cuh), their launch plan and launcher.
+// See mstep_dev.cuh for the method (Eq. 17, Eq. 20, Eq. 18) and the design.
+#include "mstep_dev.cuh"
 
 #include <algorithm>
 
@@ -31,216 +9,31 @@ namespace fcpd {
 
 namespace {
 
-template <typename F> struct L16;
-template <> struct L16<float> {
-  using t = float4;
-  static constexpr int W = 4;
-};
-template <> struct L16<double> {
-  using t = double2;
-  static constexpr int W = 2;
-};
+using namespace dev;
 
-__device__ __forceinline__ float lane_of(const float4& v, int i) {
-  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ double lane_of(const double2& v, int i) { return i == 0 ? v.x : v.y; }
-
-constexpr int kThreadsP = 128;   // streaming kernel block
-constexpr int kRTile = 256;      // rows of V staged per shared-memory tile
-constexpr int kThreadsD = 256;   // reduction kernels
-constexpr int kRedCols = 64;     // columns per reduction block
-constexpr int kRedSub = kThreadsD / kRedCols;
-
-// ---------------------------------------------------------------- colsum
 template <typename F>
 __global__ void __launch_bounds__(kThreadsP)
 colsum(const F* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
        int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
        int clear_row_flags) {
-  if (gate && iteration_gated(st)) return;
-  // the E-step's row list was consumed by fixB before this kernel
-  if (clear_row_flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
-  using V4 = typename Vec<F>::t4;
-  using LT = typename L16<F>::t;
-  constexpr int L = L16<F>::W;           // elements per 16-byte vector
-  constexpr int W = 2 * L;               // columns per thread
-  __shared__ V4 sV[kRTile];
-  const int c0 = (blockIdx.x * kThreadsP + threadIdx.x) * W;
-  const int r0 = blockIdx.y * rows_per_chunk;
-  const int r1 = min(rows, r0 + rows_per_chunk);
-  F acc[W][3];
-#pragma unroll
-  for (int w = 0; w < W; ++w) acc[w][0] = acc[w][1] = acc[w][2] = (F)0;
-  for (int base = r0; base < r1; base += kRTile) {
-    const int cnt = min(kRTile, r1 - base);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kThreadsP) sV[i] = V[base + i];
-    __syncthreads();
-    if (c0 < cols) {
-      const F* ap = A + (size_t)base * ldA + c0;
-#pragma unroll 4
-      for (int i = 0; i < cnt; ++i) {
-        const LT* row = reinterpret_cast<const LT*>(ap + (size_t)i * ldA);
-        const LT u0 = __ldg(row), u1 = __ldg(row + 1);
-        const V4 r = sV[i];
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          const F uw = w < L ? lane_of(u0, w) : lane_of(u1, w - L);
-          acc[w][0] = fma(uw, r.x, acc[w][0]);
-          acc[w][1] = fma(uw, r.y, acc[w][1]);
-          acc[w][2] = fma(uw, r.z, acc[w][2]);
-        }
-      }
-    }
-  }
-  if (c0 < cols) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      F* out = part + ((size_t)blockIdx.y * 3 + d) * ldP + c0;
-      if constexpr (L == 4) {
-        reinterpret_cast<float4*>(out)[0] = make_float4(acc[0][d], acc[1][d], acc[2][d], acc[3][d]);
-        reinterpret_cast<float4*>(out)[1] = make_float4(acc[4][d], acc[5][d], acc[6][d], acc[7][d]);
-      } else {
-        reinterpret_cast<double2*>(out)[0] = make_double2(acc[0][d], acc[1][d]);
-        reinterpret_cast<double2*>(out)[1] = make_double2(acc[2][d], acc[3][d]);
-      }
-    }
-  }
+  dev::colsum_body<F, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
-// Sum of the chunk partials of column `col` (accumulated in F: FP32 partials
-// are summed in FP32 -- GB300's FP64 rate is a small fraction of FP32 -- in a
-// fixed order; the FP64 path sums in FP64).  kRedSub threads per column each
-// take a strided subset; the subsets are added in order through `part`.
-template <typename F>
-__device__ __forceinline__ void chunk_sums(const F* __restrict__ partials, int chunks, int64_t ldP, int col,
-                                           int ncols, F (&a)[3], F (*part)[3][kRedCols]) {
-  const int c = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
-  F s[3] = {(F)0, (F)0, (F)0};
-  if (col < ncols) {
-#pragma unroll 4
-    for (int k = sub; k < chunks; k += kRedSub)
-#pragma unroll
-      for (int d = 0; d < 3; ++d) s[d] += partials[((size_t)k * 3 + d) * ldP + col];
-  }
-#pragma unroll
-  for (int d = 0; d < 3; ++d) part[sub][d][c] = s[d];
-  __syncthreads();
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    F t = (F)0;
-#pragma unroll
-    for (int j = 0; j < kRedSub; ++j) t += part[j][d][c];
-    a[d] = t;
-  }
-}
-
-// Diagonal update (once per column k) with the sigma2 of this iteration's
-// E-step: B_k = s_k a_k, C_k = a_k / (l_k + lambda sigma2).
 template <typename F>
 __global__ void __launch_bounds__(kThreadsD)
 diag_update(const F* __restrict__ partP, int chunks, int64_t ldU, int K, const double* __restrict__ lam,
             typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
             const DevState* __restrict__ st, int gate) {
-  if (gate && iteration_gated(st)) return;
-  __shared__ F part[kRedSub][3][kRedCols];
-  __shared__ double lamsig;
-  if (threadIdx.x == 0) lamsig = st->lambda * st->sigma2;
-  const int k = blockIdx.x * kRedCols + threadIdx.x % kRedCols;
-  F a[3];
-  chunk_sums<F>(partP, chunks, ldU, k, K, a, part);
-  if (threadIdx.x >= kRedCols || k >= K) return;
-  const double inv = 1.0 / (lam[k] + lamsig);          // one FP64 division per column
-  const double s = lam[k] * inv;
-  using V4 = typename Vec<F>::t4;
-  V4 b, cw;
-  b.x = (F)(s * a[0]); b.y = (F)(s * a[1]); b.z = (F)(s * a[2]); b.w = (F)0;
-  cw.x = (F)(a[0] * inv); cw.y = (F)(a[1] * inv); cw.z = (F)(a[2] * inv); cw.w = (F)0;
-  B4[k] = b;
-  C4[k] = cw;
+  dev::diag_update_body<F>(partP, chunks, ldU, K, lam, B4, C4, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
-// T = X + U B (X may be null: W = U C) from the expansion partials; with EPI
-// the Eq. 18 epilogue and the device-state update of the iteration.
 template <typename F, bool EPI>
 __global__ void __launch_bounds__(kThreadsD)
 expand_finish(const F* __restrict__ partE, int chunks, int64_t ldM, int M,
               const typename Vec<F>::t4* __restrict__ X4, const typename Vec<F>::t4* __restrict__ Yt4,
               typename Vec<F>::t4* __restrict__ Tout, const typename Vec<F>::t4* __restrict__ Yhat4,
               double* __restrict__ sums, DevState* __restrict__ st, int gate) {
-  if (gate && iteration_gated(st)) return;
-  using V4 = typename Vec<F>::t4;
-  __shared__ F part[kRedSub][3][kRedCols];
-  __shared__ double sh[32];
-  __shared__ bool last;
-  const int m = blockIdx.x * kRedCols + threadIdx.x % kRedCols;
-  F a[3];
-  chunk_sums<F>(partE, chunks, ldM, m, M, a, part);
-  double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
-  if (threadIdx.x < kRedCols && m < M) {
-    double x0 = 0, x1 = 0, x2 = 0;
-    if (X4) { const V4 x = X4[m]; x0 = x.x; x1 = x.y; x2 = x.z; }
-    V4 tn;
-    tn.x = (F)(x0 + (double)a[0]); tn.y = (F)(x1 + (double)a[1]); tn.z = (F)(x2 + (double)a[2]); tn.w = (F)0;
-    if constexpr (EPI) {
-      const V4 to = Tout[m];
-      const V4 yt = Yt4[m];
-      const double dx = (double)to.x - tn.x, dy = (double)to.y - tn.y, dz = (double)to.z - tn.z;
-      const double gx = (double)yt.x - to.x, gy = (double)yt.y - to.y, gz = (double)yt.z - to.z;
-      dT2 = dx * dx + dy * dy + dz * dz;
-      contrib = (double)yt.w + 2.0 * (dx * gx + dy * gy + dz * gz) + dT2;
-      if (Yhat4) {
-        const V4 h = Yhat4[m];
-        const double ex = (double)tn.x - h.x, ey = (double)tn.y - h.y, ez = (double)tn.z - h.z;
-        gt2 = ex * ex + ey * ey + ez * ez;
-      }
-    }
-    Tout[m] = tn;
-  }
-  if constexpr (EPI) {
-    const double b0 = block_sum(contrib, sh);
-    const double b1 = block_sum(dT2, sh);
-    const double b2 = block_sum(gt2, sh);
-    if (threadIdx.x == 0) {
-      sums[(size_t)blockIdx.x * 3] = b0;
-      sums[(size_t)blockIdx.x * 3 + 1] = b1;
-      sums[(size_t)blockIdx.x * 3 + 2] = b2;
-      __threadfence();
-      last = atomicAdd(&st->ticket_e, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      double a0 = 0, a1 = 0, a2 = 0;
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        a0 += __ldcg(sums + (size_t)i * 3);
-        a1 += __ldcg(sums + (size_t)i * 3 + 1);
-        a2 += __ldcg(sums + (size_t)i * 3 + 2);
-      }
-      const double t0 = block_sum(a0, sh);
-      const double t1 = block_sum(a1, sh);
-      const double t2 = block_sum(a2, sh);
-      if (threadIdx.x == 0) {
-        const int it = st->iter;
-        const double s2new = t0 / (3.0 * (double)M);
-        const double rm = st->has_gt ? sqrt(t2 / (double)M) : nan("");
-        if (st->hist && it < kHistCap) {
-          st->hist[it] = s2new;
-          st->hist[kHistCap + it] = st->loglik;
-          st->hist[2 * kHistCap + it] = rm;
-        }
-        st->last_dT2 = t1;
-        st->last_rmse = rm;
-        if (!(s2new > 0.0) || !isfinite(s2new)) st->status = (int)CPD_ENUMERIC;
-        else st->sigma2 = s2new;
-        st->iter = it + 1;
-        if (st->tol > 0.0 && sqrt(t1 / (double)M) <= st->tol) st->done = 1;
-        if (st->gt_tol > 0.0 && st->has_gt && rm <= st->gt_tol) st->done = 1;
-        st->ticket_e = 0;
-      }
-    }
-  }
+  dev::expand_finish_body<F, EPI>(partE, chunks, ldM, M, X4, Yt4, Tout, Yhat4, sums, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -248,8 +41,9 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Row chunks for a colsum over a rows x ld matrix: enough blocks to fill the
 // GPU, but at least ~256 KB of the matrix per block (a small matrix needs few
 // chunks, which keeps the partial sums short).
-void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int& col_tiles, int& chunks, int& rpc) {
-  col_tiles = (int)cdiv(ld, (int64_t)kThreadsP * W);
+void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int threads, int& col_tiles, int& chunks,
+                 int& rpc) {
+  col_tiles = (int)cdiv(ld, (int64_t)threads * W);
   const int64_t target = (int64_t)sms * 8;
   int64_t ch = std::max<int64_t>(1, cdiv(target, col_tiles));
   ch = std::min<int64_t>(ch, std::max<int64_t>(1, rows * ld * es / (256 * 1024)));
@@ -260,16 +54,16 @@ void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int& col_
 
 }  // namespace
 
-MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms) {
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads) {
   MstepPlan p{};
   const int W = fp64 ? 4 : 8;          // columns per colsum thread (32 bytes); row strides padded to it
   const int64_t es = fp64 ? 8 : 4;
   p.ldU = cdiv(K, W) * W;
   p.ldM = cdiv(M, W) * W;
-  plan_colsum(M, p.ldU, es, sms, W, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
-  plan_colsum(K, p.ldM, es, sms, W, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+  plan_colsum(M, p.ldU, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+  plan_colsum(K, p.ldM, es, sms, W, colsum_threads, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
   p.part_elems = std::max((int64_t)p.p_row_chunks * 3 * p.ldU, (int64_t)p.e_row_chunks * 3 * p.ldM);
-  p.e_blocks = (int)cdiv(M, kRedCols);
+  p.e_blocks = (int)cdiv(M, kMRedCols);
   p.sums_elems = (int64_t)p.e_blocks * 3;
   return p;
 }
@@ -285,7 +79,7 @@ void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* la
                                                                       pl.p_rows_per_chunk, part, pl.ldU, st, g,
                                                                       g);
   record_after(ev, 0, s);
-  diag_update<F><<<(unsigned)cdiv(K, kRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
+  diag_update<F><<<(unsigned)cdiv(K, kMRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
                                                                    B4, C4, st, g);
   record_after(ev, 1, s);
   colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,

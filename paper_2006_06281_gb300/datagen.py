@@ -109,6 +109,29 @@ def gen(M: int, n_out: int = 0, amp: float = 0.15, noise: float = 0.01,
     return PointSets(X=X, Y=allY[perm].copy(), Yhat=Yhat, n_inliers=noisy.shape[0], perm=perm)
 
 
+def pair_sizes(n_pairs: int, lo: int, hi: int, seed: int) -> list[tuple[int, int]]:
+    """(M_i, N_i) for a batch of registrations: both drawn independently and
+    uniformly from the integers lo..hi (one SplitMix64 stream)."""
+    u = Stream(seed).uniform(2 * n_pairs)
+    v = lo + np.floor(u * (hi - lo + 1)).astype(np.int64)
+    v = np.minimum(v, hi)
+    return [(int(v[2 * i]), int(v[2 * i + 1])) for i in range(n_pairs)]
+
+
+def gen_pair(M: int, N: int, seed: int, amp: float = 0.15, noise: float = 0.01) -> PointSets:
+    """One registration of uneven sizes: with N >= M the scene holds the M
+    deformed, noisy model points plus N - M uniform outliers; with N < M it
+    holds the deformed, noisy images of a seeded random N-subset of X
+    (scene-side missing points)."""
+    return gen(M, n_out=max(N - M, 0), amp=amp, noise=noise, seed=seed, n_in=min(M, N))
+
+
+def gen_batch(n_pairs: int, lo: int, hi: int, seed0: int) -> list[PointSets]:
+    """Pairs i < n_pairs with sizes from pair_sizes(n_pairs, lo, hi, seed0)
+    and point sets gen_pair(M_i, N_i, seed0 + i)."""
+    return [gen_pair(M, N, seed0 + i) for i, (M, N) in enumerate(pair_sizes(n_pairs, lo, hi, seed0))]
+
+
 # Named workloads (sizes and parameters of the paper-scale runs; Sec. IV).
 # omega, lam, beta: outlier weight, regularisation weight, kernel width.
 WORKLOADS = {
@@ -132,4 +155,16 @@ WORKLOADS = {
     # outlier case: M = 20000, N = 25000 (20% extra uniform outliers), K = 200
     "fp32_m20000_n25000_k200": dict(M=20000, n_out=5000, amp=0.15, noise=0.01, seed=0,
                                     omega=0.2, lam=3.0, beta=2.0, iters=150, K=200),
+}
+
+# Batches of independent registrations (gen_batch): n_pairs pairs with M_i,
+# N_i uniform in lo..hi, pair i seeded seed0 + i, basis K = min(M_i, 128).
+BATCH_WORKLOADS = {
+    # 256 uneven pairs, sizes 500..8000 (the sizes of the paper's single scans)
+    "fp32_batch256_m500_8000_k128": dict(n_pairs=256, lo=500, hi=8000, seed0=1000, K=128,
+                                         omega=0.1, lam=2.0, beta=2.0, iters=100),
+    # same with sizes 500..3000: a batch whose 256 eigendecompositions take
+    # seconds rather than minutes
+    "fp32_batch256_m500_3000_k128": dict(n_pairs=256, lo=500, hi=3000, seed0=1000, K=128,
+                                         omega=0.1, lam=2.0, beta=2.0, iters=100),
 }

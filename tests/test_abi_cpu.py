@@ -127,3 +127,42 @@ def test_binding_raises_typed_errors(lib):
     with pytest.raises(cpd.CpdError) as ei:
         cpd.Context(np.zeros((4, 3), dtype=np.float32), K=9)
     assert ei.value.status == cpd.EINVAL
+
+
+def test_batch_entry_points_reject_bad_arguments(lib):
+    X = np.zeros((10, 3), dtype=np.float32)
+    arr = (C.c_void_p * 2)(X.ctypes.data, X.ctypes.data)
+    null = (C.c_void_p * 2)(X.ctypes.data, None)
+    n = (C.c_int64 * 2)(10, 10)
+    bad_n = (C.c_int64 * 2)(10, 0)
+    h = C.c_void_p()
+    p32, p64 = cpd.make_params(cpd.FP32), cpd.make_params(cpd.FP64)
+    create = lib.cpd_batch_create
+    assert create(0, arr, n, arr, n, C.byref(p32), 0.0, None, C.byref(h)) == cpd.EINVAL
+    assert create(2, arr, n, arr, n, C.byref(p64), 0.0, None, C.byref(h)) == cpd.EINVAL
+    assert b"FP32" in lib.cpd_last_error()
+    assert create(2, arr, n, arr, n, C.byref(p32), 100.0, None, C.byref(h)) == cpd.EINVAL
+    assert create(2, arr, n, arr, n, C.byref(p32), -1.0, None, C.byref(h)) == cpd.EINVAL
+    assert create(2, null, n, arr, n, C.byref(p32), 0.0, None, C.byref(h)) == cpd.EINVAL
+    assert b"pair 1" in lib.cpd_last_error()
+    assert create(2, arr, n, arr, bad_n, C.byref(p32), 0.0, None, C.byref(h)) == cpd.EINVAL
+    assert create(2, arr, n, arr, n, C.byref(p32), 0.0, None, None) == cpd.EINVAL
+    assert h.value is None
+    i = C.c_int32()
+    assert lib.cpd_batch_iterate(None, 1) == cpd.EINVAL
+    assert lib.cpd_batch_state(None, None, None, None) == cpd.EINVAL
+    assert lib.cpd_batch_get_T(None, 0, X.ctypes.data) == cpd.EINVAL
+    assert lib.cpd_batch_info(None, 0, None, None, None) == cpd.EINVAL
+    assert lib.cpd_batch_launch_shape(None, C.byref(i), None, None) == cpd.EINVAL
+    assert lib.cpd_batch_reset(None) == cpd.EINVAL
+    lib.cpd_batch_destroy(None)   # ignored
+
+
+def test_batch_injected_allocation_failure(lib, monkeypatch):
+    monkeypatch.setenv("CPD_FAULT", "alloc")
+    X = np.zeros((10, 3), dtype=np.float32)
+    arr = (C.c_void_p * 1)(X.ctypes.data)
+    n = (C.c_int64 * 1)(10)
+    h = C.c_void_p()
+    assert lib.cpd_batch_create(1, arr, n, arr, n, C.byref(cpd.make_params()), 0.0, None, C.byref(h)) == cpd.ENOMEM
+    assert h.value is None

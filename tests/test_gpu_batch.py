@@ -1,0 +1,179 @@
+"""Batched registrations (cpd_batch_*) against the oracle and the per-pair path (GPU).
+
+Many independent registrations of uneven sizes run together in one
+persistent kernel launch per call; each pair must follow the same EM
+iteration (Eq. 4, 5, 17/20, 18) as a registration on its own.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2006_06281_gb300 import cpd, datagen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4     # relative Frobenius error of T after the run (as for the per-pair FP32 path)
+
+# uneven pairs: outliers (N > M), missing scene points (N < M), ragged tile
+# edges (1025 = one 1024-point tile + 1), a pair smaller than one warp, and a
+# full basis (M <= 128 keeps all eigenpairs with K = 128)
+PAIRS = [(700, 900), (1500, 1100), (300, 800), (2100, 1700), (20, 45), (1025, 1030), (129, 127)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_06281_gb300 import build
+    build.build()
+    cpd.load()
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def sigma2_tol(tol_T, T, sigma2):
+    """sigma2 tolerance implied by a relative tolerance tol_T on T (sigma2 is
+    a mean of |y - t|^2 / D over pairs at distance ~ sqrt(D sigma2))."""
+    t_rms = float(np.sqrt((np.asarray(T) ** 2).sum(1).mean()))
+    return tol_T * max(1.0, 2.0 * t_rms / np.sqrt(3.0 * sigma2))
+
+
+@pytest.fixture(scope="module")
+def scenes():
+    return [datagen.gen_pair(M, N, seed=500 + i) for i, (M, N) in enumerate(PAIRS)]
+
+
+def test_batch_matches_oracle(scenes):
+    Xs = [f32(ps.X) for ps in scenes]
+    Ys = [f32(ps.Y) for ps in scenes]
+    iters, K = 25, 128
+    with cpd.Batch([torch.tensor(x, device="cuda") for x in Xs], Ys, w=0.1, beta=2.0, lam=2.0, K=K) as b:
+        assert b.K == [min(K, x.shape[0]) for x in Xs]
+        b.iterate(iters)
+        s2, it, st = b.state()
+        assert list(it) == [iters] * len(Xs) and not st.any()
+        for i, (x, y) in enumerate(zip(Xs, Ys)):
+            Kr = min(K, x.shape[0])
+            ref = oracle.register(x.astype(np.float64), y.astype(np.float64), w=0.1, beta=2.0, lam_reg=2.0,
+                                  n_iter=iters, K=0 if Kr == x.shape[0] else Kr)
+            T = b.T(i)
+            assert rel(T, ref["T"]) <= FP32_TOL, (i, PAIRS[i], rel(T, ref["T"]))
+            assert s2[i] == pytest.approx(ref["sigma2"], rel=sigma2_tol(FP32_TOL, ref["T"], ref["sigma2"])), i
+
+
+def test_batch_matches_per_pair_contexts(scenes):
+    Xs = [f32(ps.X) for ps in scenes]
+    Ys = [f32(ps.Y) for ps in scenes]
+    with cpd.Batch(Xs, Ys, K=128) as b:
+        b.iterate(15)
+        s2, _, _ = b.state()
+        for i, (x, y) in enumerate(zip(Xs, Ys)):
+            with cpd.Context(x, precision=cpd.FP32, K=min(128, x.shape[0])) as c:
+                T1, s21, _ = c.iterate(y, 15)
+            # same arithmetic, different tiling and summation order
+            assert rel(b.T(i), T1.astype(np.float64)) <= 5e-5
+            assert s2[i] == pytest.approx(s21, rel=1e-4)
+
+
+def test_batch_in_pieces_equals_one_call(scenes):
+    Xs = [f32(ps.X) for ps in scenes[:4]]
+    Ys = [f32(ps.Y) for ps in scenes[:4]]
+    with cpd.Batch(Xs, Ys, K=128) as b:
+        b.iterate(7)
+        b.iterate(5)
+        Ta = [b.T(i) for i in range(4)]
+        sa = b.state()[0]
+        b.reset()
+        assert not b.state()[1].any()
+        b.iterate(12)
+        for i in range(4):
+            np.testing.assert_array_equal(b.T(i), Ta[i])
+        np.testing.assert_array_equal(b.state()[0], sa)
+
+
+def test_batch_tolerance_stops_each_pair_on_its_own(scenes):
+    Xs = [f32(ps.X) for ps in scenes[:5]]
+    Ys = [f32(ps.Y) for ps in scenes[:5]]
+    tol = 2e-3
+    with cpd.Batch(Xs, Ys, K=128, tol=tol) as b:
+        b.iterate(200)
+        _, it, st = b.state()
+        assert not st.any()
+        for i, (x, y) in enumerate(zip(Xs, Ys)):
+            with cpd.Context(x, precision=cpd.FP32, K=min(128, x.shape[0]), tol=tol) as c:
+                _, _, it1 = c.iterate(y, 200)
+            # the stop test sqrt(mean |dT|^2) <= tol may flip by one iteration
+            # between the two summation orders when it crosses tol closely
+            assert abs(int(it[i]) - it1) <= 1, (i, it[i], it1)
+        assert len(set(it.tolist())) > 1, "the pairs should stop at different iterations"
+
+
+def test_batch_barrier_timeout_is_reported_and_recoverable(scenes, monkeypatch):
+    Xs = [f32(ps.X) for ps in scenes[:3]]
+    Ys = [f32(ps.Y) for ps in scenes[:3]]
+    with cpd.Batch(Xs, Ys, K=128, barrier_timeout_s=0.2) as b:
+        # every grid barrier waits for one block that does not exist: each wait
+        # ends after 0.2 s and the launch returns with CPD_ETIMEOUT
+        monkeypatch.setenv("CPD_FAULT", "barrier")
+        with pytest.raises(cpd.CpdError) as ei:
+            b.iterate(2)
+        assert ei.value.status == cpd.ETIMEOUT
+        monkeypatch.delenv("CPD_FAULT")
+        b.reset()
+        b.iterate(6)
+        got = [b.T(i) for i in range(3)]
+    with cpd.Batch(Xs, Ys, K=128) as fresh:
+        fresh.iterate(6)
+        for i in range(3):
+            np.testing.assert_array_equal(got[i], fresh.T(i))
+
+
+def test_batch_rejects_bad_arguments():
+    x = np.zeros((10, 3), np.float32)
+    lib = cpd.load()
+    with pytest.raises(cpd.CpdError) as ei:
+        cpd.Batch([x], [x], barrier_timeout_s=100.0)
+    assert ei.value.status == cpd.EINVAL
+    with pytest.raises(ValueError):
+        cpd.Batch([x], [])
+    p = cpd.make_params(cpd.FP64)
+    import ctypes as C
+    h = C.c_void_p()
+    arr = (C.c_void_p * 1)(x.ctypes.data)
+    n = (C.c_int64 * 1)(10)
+    assert lib.cpd_batch_create(1, arr, n, arr, n, C.byref(p), 0.0, None, C.byref(h)) == cpd.EINVAL
+    assert b"FP32" in lib.cpd_last_error()
+
+
+def test_batch256_sampled_pairs_against_oracle():
+    """256 uneven pairs of 500..3000 points in one launch: every pair runs,
+    and sampled pairs (largest, smallest, one with N < M, one with N > M)
+    match the oracle."""
+    cfg = datagen.BATCH_WORKLOADS["fp32_batch256_m500_3000_k128"]
+    sets = datagen.gen_batch(cfg["n_pairs"], cfg["lo"], cfg["hi"], cfg["seed0"])
+    Xs = [torch.tensor(f32(ps.X), device="cuda") for ps in sets]
+    Ys = [torch.tensor(f32(ps.Y), device="cuda") for ps in sets]
+    iters = 10
+    with cpd.Batch(Xs, Ys, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=cfg["K"]) as b:
+        n, grid, items = b.launch_shape()
+        assert n == 256 and grid > 0 and items > 256
+        b.iterate(iters)
+        s2, it, st = b.state()
+        assert (it == iters).all() and not st.any() and np.isfinite(s2).all()
+        sizes = np.array([(ps.X.shape[0], ps.Y.shape[0]) for ps in sets])
+        work = sizes[:, 0] * sizes[:, 1]
+        picks = {int(np.argmax(work)), int(np.argmin(work)),
+                 int(np.argmax(sizes[:, 0] - sizes[:, 1])), int(np.argmax(sizes[:, 1] - sizes[:, 0]))}
+        for i in sorted(picks):
+            ps = sets[i]
+            ref = oracle.register(f32(ps.X).astype(np.float64), f32(ps.Y).astype(np.float64), w=cfg["omega"],
+                                  beta=cfg["beta"], lam_reg=cfg["lam"], n_iter=iters, K=cfg["K"])
+            assert rel(b.T(i, device="cuda").cpu().numpy(), ref["T"]) <= FP32_TOL, (i, sizes[i])
