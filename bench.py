@@ -56,6 +56,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowrank", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--batch", default="fp32_batch256_m500_3000_k128",
+                    help="batched-registration workload to time as well ('none' skips it)")
+    ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--no-batch-baseline", action="store_true",
+                    help="skip timing the same pairs through per-pair contexts")
     return ap.parse_args()
 
 
@@ -142,14 +147,26 @@ def roofline_entries(phase_ms, M, N, K, peaks, es=4):
     return out
 
 
+TRAFFIC_SOURCES = {"e_pass_a": ["estep.cu", "estep_dev.cuh"], "e_pass_b": ["estep.cu", "estep_dev.cuh"],
+                   "colsum": ["mstep.cu", "mstep_dev.cuh"]}
+
+
+def source_digest(kernel):
+    """sha256 over the files that hold a kernel's code (wrapper + device body)."""
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2006_06281_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_for(kernel):
     """dram bytes per launch recorded by ncu in profiles/, if the kernel's
-    source file is unchanged since (its sha256 is recorded beside the figure)."""
+    source files are unchanged since (their sha256 is recorded beside the
+    figure)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    src = {"e_pass_a": "estep.cu", "e_pass_b": "estep.cu", "colsum": "mstep.cu"}.get(kernel)
-    if src is None or not os.path.exists(path):
+    if kernel not in TRAFFIC_SOURCES or not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2006_06281_gb300", "csrc", src), "rb").read()).hexdigest()
+    sha = source_digest(kernel)
     for line in open(path):
         if line.startswith("#"):
             continue
@@ -250,6 +267,79 @@ def run_reference(args, cfg):
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batch(args, peaks, torch):
+    """Many uneven registrations in one persistent launch per call
+    (cpd_batch_*): pair-iterations/s and Gaussian pairs/s over the batch,
+    setup reported separately, and the same pairs run one after another
+    through per-pair contexts for comparison."""
+    from paper_2006_06281_gb300 import cpd, datagen
+    bc = datagen.BATCH_WORKLOADS[args.batch]
+    sets = datagen.gen_batch(bc["n_pairs"], bc["lo"], bc["hi"], bc["seed0"])
+    Xs = [torch.tensor(ps.X, dtype=torch.float32, device="cuda") for ps in sets]
+    Ys = [torch.tensor(ps.Y, dtype=torch.float32, device="cuda") for ps in sets]
+    MN = np.array([(x.shape[0], y.shape[0]) for x, y in zip(Xs, Ys)], dtype=np.float64)
+    I = bc["iters"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = cpd.Batch(Xs, Ys, w=bc["omega"], beta=bc["beta"], lam=bc["lam"], K=bc["K"])
+    setup_s = time.perf_counter() - t0
+    n, grid, items = b.launch_shape()
+    for _ in range(2):                      # graph capture + warm-up, untimed
+        b.reset()
+        b.iterate(I)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(max(1, args.batch_reps)):
+        b.reset()
+        torch.cuda.synchronize()
+        ev0.record()
+        b.iterate(I)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    s2, it, st = b.state()
+    phase, busy = b.phase_profile()
+    b.close()
+    t = statistics.median(ms) / 1e3
+    gauss = float((MN[:, 0] * MN[:, 1]).sum()) * I
+    # E-step ALU floor over the batch: passes A and B at their kernel mixes
+    clk = peaks["sm_max_mhz"] * 1e6
+    floor = sum(float((MN[:, 0] * MN[:, 1]).sum()) * I / (152 * clk * min(128.0 / OPS_PER_PAIR[k], 32.0))
+                for k in ("e_pass_a", "e_pass_b"))
+    out = dict(workload=args.batch, pairs=n, M_range=[int(MN[:, 0].min()), int(MN[:, 0].max())],
+               N_range=[int(MN[:, 1].min()), int(MN[:, 1].max())], K=bc["K"], iters=I,
+               grid_blocks=grid, work_items_per_iter=items, launches_per_call=2,
+               ms_per_call=t * 1e3, pair_iters_per_s=float(it.sum()) / t, gaussian_pairs_per_s=gauss / t,
+               estep_alu_floor_frac=floor / t, all_ok=bool((it == I).all() and not st.any()),
+               phase_ms_per_iter=dict(zip(["estep_a_with_column_reduction", "estep_b_with_row_reduction",
+                                           "projection_with_diag_update", "expansion_with_sigma2"], phase)),
+               phase_busy_fraction=busy,
+               setup_s=setup_s, timed_calls=len(ms))
+    if not args.no_batch_baseline:
+        # the same registrations one after another, each from its own graph
+        ctxs = []
+        t0 = time.perf_counter()
+        for x in Xs:
+            ctxs.append(cpd.Context(x, precision=cpd.FP32, w=bc["omega"], beta=bc["beta"], lam=bc["lam"],
+                                    K=min(bc["K"], x.shape[0])))
+        seq_setup = time.perf_counter() - t0
+        for c, y in zip(ctxs, Ys):
+            c.iterate(y, I, want_T=False)     # graph capture, untimed
+            c.reset()
+        torch.cuda.synchronize()
+        ev0.record()
+        for c, y in zip(ctxs, Ys):
+            c.iterate(y, I, want_T=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        ts = ev0.elapsed_time(ev1) / 1e3
+        for c in ctxs:
+            c.close()
+        out["per_pair_sequential"] = dict(ms=ts * 1e3, pair_iters_per_s=n * I / ts, setup_s=seq_setup)
+        out["speedup_vs_per_pair"] = ts / t
+    return out
 
 
 def workload_config(cfg, M, N, K):
@@ -429,6 +519,10 @@ def main():
     else:
         ctx.close()
 
+    batch = None
+    if world == 1 and args.batch != "none":
+        batch = run_batch(args, peaks, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(ps, cfg, M, N, K)
@@ -445,7 +539,7 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, setup_s=setup_s,
+                    lowrank_k200=lowrank, setup_s=setup_s, batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "
                                   "(Table IV, MATLAB on an i7-8750H CPU): context, not a like-for-like target")
         print(json.dumps(line), flush=True)

@@ -320,6 +320,20 @@ cpd_status cpd_batch_info(const cpd_batch *b, int32_t i, int64_t *M, int64_t *N,
  * and work items per iteration over all phases. */
 cpd_status cpd_batch_launch_shape(const cpd_batch *b, int32_t *n_pairs, int32_t *grid, int32_t *n_items);
 
+/*
+ * Where the last cpd_batch_iterate call spent its time: 8 floats (host).
+ * [0..3]: milliseconds per iteration of each phase, averaged over the
+ * call's iterations, as seen by the launch's first block (from the end of
+ * the previous grid barrier to the end of the phase's own barrier, so each
+ * includes its barrier): [0] E pass A with the column reduction (Eq. 4) and
+ * its fix-up, [1] E pass B with the row reduction (Eq. 5) and its fix-up,
+ * [2] projection U^T (Ytil - X) with the diagonal update, [3] expansion
+ * with T and Eq. 18.  [4..7]: for the same phases, the fraction of the
+ * blocks' time spent inside work items (1 = no block ever waited at the
+ * barrier).  CPD_ESTATE before the first completed call.
+ */
+cpd_status cpd_batch_phase_ms(const cpd_batch *b, float *phase_ms);
+
 /* Restart every registration: T_i = X_i, iteration count 0, initial variance
  * re-computed from the stored scene.  Synchronises. */
 cpd_status cpd_batch_reset(cpd_batch *b);

@@ -32,7 +32,7 @@ EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
-           "cpd_batch_launch_shape", "cpd_batch_reset", "cpd_batch_destroy"]
+           "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_destroy"]
 
 
 class CpdParams(C.Structure):
@@ -90,6 +90,7 @@ def load():
                 "cpd_batch_get_T": ([vp, i32, vp], C.c_int),
                 "cpd_batch_info": ([vp, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)], C.c_int),
                 "cpd_batch_launch_shape": ([vp, ip, ip, ip], C.c_int),
+                "cpd_batch_phase_ms": ([vp, C.POINTER(C.c_float)], C.c_int),
                 "cpd_batch_reset": ([vp], C.c_int),
                 "cpd_batch_destroy": ([vp], None),
             }
@@ -334,6 +335,19 @@ class Batch:
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
         _check(load().cpd_batch_launch_shape(self._h, C.byref(a), C.byref(b), C.byref(c)))
         return a.value, b.value, c.value
+
+    def phase_ms(self):
+        """Milliseconds per iteration of the 4 phases in the last call: pass A
+        (+ column reduction), pass B (+ row reduction), projection (+ diagonal
+        update), expansion (+ T and Eq. 18)."""
+        return self.phase_profile()[0]
+
+    def phase_profile(self):
+        """(ms per iteration of the 4 phases, fraction of block time spent in
+        work items per phase) for the last call."""
+        out = (C.c_float * 8)()
+        _check(load().cpd_batch_phase_ms(self._h, out))
+        return list(out[:4]), list(out[4:])
 
     def reset(self):
         _check(load().cpd_batch_reset(self._h))

@@ -1,17 +1,27 @@
 // Batched registrations: many independent (X_i, Y_i) pairs of uneven sizes
 // run their EM iterations in ONE persistent cooperative kernel launch.
 //
-// Every iteration of every pair is the same sequence of phases as the
-// per-pair path (estep_dev.cuh / mstep_dev.cuh): pass A, its reduction, the
-// FP32 log-domain fix-up of columns, pass B, its reduction, the row fix-up,
-// projection U^T R, diagonal update, expansion with U^T, and the expansion's
-// reduction with Eq. 18.  For each phase the host lists the work items of all
-// pairs -- (pair, block coordinates), largest pairs first -- and the resident
-// blocks take items from an atomic counter, so small and large pairs share
-// the GPU without per-pair launches.  Phases are separated by a grid-wide
-// barrier.  The barrier's wait is bounded in wall time: if it does not
-// complete within the limit the kernel records CPD_ETIMEOUT in the control
-// block and every block returns (no GPU hang); the host reports the status.
+// Every iteration of every pair runs the same arithmetic as the per-pair
+// path (estep_dev.cuh / mstep_dev.cuh) in four phases, each closed by a
+// grid-wide barrier:
+//   A  E pass A tiles; the last row chunk of a column tile to finish reduces
+//      that tile's columns (den, Eq. 4), and the block completing a pair's
+//      columns runs the FP32 log-domain fix-up of its flagged columns;
+//   B  E pass B tiles; likewise the row reduction (Eq. 5) per row tile and
+//      the row fix-up per pair;
+//   P  projection U^T (Ytil - X) by row chunks; the last chunk of a pair
+//      runs the diagonal update;
+//   E  expansion with U^T by (column tile, row chunk); the last row chunk of
+//      a column tile forms T for those columns, and the block completing a
+//      pair's columns updates sigma2 (Eq. 18).
+// "Last" is decided by per-tile completion tickets (an atomic counter per
+// tile, reset by the block that completes it).  For each phase the host
+// lists the work items of all pairs -- (pair, block coordinates), largest
+// pairs first -- and the resident blocks take items from an atomic counter,
+// so small and large pairs share the GPU without per-pair launches.  The
+// barrier's wait is bounded in wall time: if it does not complete within the
+// limit the kernel records CPD_ETIMEOUT in the control block and every block
+// returns (no GPU hang); the host reports the status.
 //
 // Buffers such as T, Yb and the partial sums are written in one phase and
 // read in a later one of the same launch, so no argument of the device bodies
@@ -19,10 +29,22 @@
 // the read-only path).  The E-step bodies are compiled with 4 scene points
 // (pass A) and 4 model points (pass B) per thread: tiles of 1024 points keep
 // the padding of small pairs (a few hundred points) low, where the per-pair
-// launches use 16 and 8 for scenes of tens of thousands of points.
+// launches use 16 and 8 for scenes of tens of thousands of points
+// (FCPD_BATCH_PTS sets the count for full tiles; partial last tiles use
+// fewer).  The
+// reduction bodies give each thread a whole column (row) of chunk partials:
+// a pair has only a few chunks here, and a reduction block's fixed latency
+// (dependent loads, block sums, the completion ticket) is paid per 256
+// columns instead of per 32 or 64.
 #define FCPD_RESTRICT
-#define FCPD_EA_COLS 4
-#define FCPD_EB_ROWS 4
+#ifndef FCPD_BATCH_PTS
+#define FCPD_BATCH_PTS 4
+#endif
+#define FCPD_EA_COLS FCPD_BATCH_PTS
+#define FCPD_EB_ROWS FCPD_BATCH_PTS
+#define FCPD_RED_COLS 256
+#define FCPD_RED_ROWS 256
+#define FCPD_MRED_COLS 256
 #include "estep_dev.cuh"
 #include "mstep_dev.cuh"
 
@@ -38,7 +60,14 @@ constexpr int kNarrowGroups = 16;                               // 8-column grou
 constexpr int kNarrowLanes = kThreadsBatch / kNarrowGroups;     // row lanes
 constexpr int kNarrowMaxK = kNarrowGroups * 8;                  // widest basis of the narrow projection
 
-enum Phase { PH_PASSA = 0, PH_REDA, PH_FIXA, PH_PASSB, PH_REDB, PH_FIXB, PH_PROJ, PH_DIAG, PH_EXPD, PH_FIN, kPhases };
+enum Phase { PH_A = 0, PH_B, PH_P, PH_E, kPhases };
+
+constexpr int kTileColsA = dev::kThreadsA * dev::kColsA32;   // scene points per pass-A tile
+constexpr int kTileRowsB = dev::kThreadsB * dev::kRowsB32;   // model points per pass-B tile
+constexpr int kTileColsE = kThreadsBatch * 8;                // columns of U^T per expansion tile
+static_assert(kTileColsA % dev::kRedCols == 0 && kTileRowsB % dev::kRedRows == 0 &&
+                  kTileColsE % dev::kMRedCols == 0,
+              "a tile holds whole reduction blocks");
 
 static_assert(dev::kThreadsA == kThreadsBatch && dev::kThreadsB == kThreadsBatch && dev::kThreadsR == kThreadsBatch &&
                   dev::kThreadsF == kThreadsBatch && dev::kThreadsD == kThreadsBatch,
@@ -134,64 +163,221 @@ __device__ __forceinline__ void proj_narrow_body(const float* U, int64_t ldU, in
   }
 }
 
-// One work item.  For the reduction phases (REDA, REDB, DIAG, FIN) an item is
-// `by` consecutive reduction blocks starting at `bx`.
+// Expansion for a basis of at most 128 columns, fused with the T update and
+// Eq. 18: one item is a tile of kTileColsE model points over all K rows of
+// U^T (8 points per thread, B staged in shared memory), so T comes out of
+// registers; a per-pair ticket over the tiles lets the block that completes
+// the pair finish the iteration.
+__device__ __forceinline__ void expand_narrow_body(const float* Ut, int64_t ldM, int K, int M, const float4* B4,
+                                                   const float4* X4, const float4* Yt4, float4* T4,
+                                                   const float4* Yhat4, double* sums, DevState* st, int bx, int gx) {
+  if (iteration_gated(st)) return;
+  __shared__ float4 sB[kNarrowMaxK];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  for (int i = threadIdx.x; i < K; i += kThreadsBatch) sB[i] = B4[i];
+  __syncthreads();
+  const int c0 = (bx * kThreadsBatch + threadIdx.x) * 8;
+  float acc[8][3];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) acc[w][0] = acc[w][1] = acc[w][2] = 0.f;
+  if (c0 < M) {
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const float4* row = reinterpret_cast<const float4*>(Ut + (size_t)k * ldM + c0);
+      const float4 u0 = __ldg(row), u1 = __ldg(row + 1);
+      const float4 b = sB[k];
+      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        acc[w][0] = fmaf(u[w], b.x, acc[w][0]);
+        acc[w][1] = fmaf(u[w], b.y, acc[w][1]);
+        acc[w][2] = fmaf(u[w], b.z, acc[w][2]);
+      }
+    }
+  }
+  double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const int m = c0 + w;
+    if (m < M) {
+      const float4 x = X4[m];
+      float4 tn;
+      tn.x = (float)((double)x.x + (double)acc[w][0]);
+      tn.y = (float)((double)x.y + (double)acc[w][1]);
+      tn.z = (float)((double)x.z + (double)acc[w][2]);
+      tn.w = 0.f;
+      double c, d, g;
+      dev::point_terms<float4>(T4[m], tn, Yt4[m], Yhat4, m, c, d, g);
+      contrib += c;
+      dT2 += d;
+      gt2 += g;
+      T4[m] = tn;
+    }
+  }
+  const double b0 = block_sum(contrib, sh);
+  const double b1 = block_sum(dT2, sh);
+  const double b2 = block_sum(gt2, sh);
+  if (threadIdx.x == 0) {
+    sums[(size_t)bx * 3] = b0;
+    sums[(size_t)bx * 3 + 1] = b1;
+    sums[(size_t)bx * 3 + 2] = b2;
+    __threadfence();
+    last = atomicAdd(&st->ticket_e, 1u) == (unsigned)gx - 1;
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double a0 = 0, a1 = 0, a2 = 0;
+    for (int i = threadIdx.x; i < gx; i += kThreadsBatch) {
+      a0 += __ldcg(sums + (size_t)i * 3);
+      a1 += __ldcg(sums + (size_t)i * 3 + 1);
+      a2 += __ldcg(sums + (size_t)i * 3 + 2);
+    }
+    const double t0 = block_sum(a0, sh);
+    const double t1 = block_sum(a1, sh);
+    const double t2 = block_sum(a2, sh);
+    if (threadIdx.x == 0) {
+      dev::finish_iteration(st, t0, t1, t2, M);
+      st->ticket_e = 0;
+    }
+  }
+}
+
+// Pass A (B) of one tile with the fewest points per thread that cover the
+// points left in it: a partial last tile runs with 2 or 4 per thread.
+__device__ __forceinline__ void passA_tile(const BatchPair& P, int bx, int by) {
+  using namespace dev;
+  const EstepPlan& e = P.ep;
+  const int rem = P.N - bx * kTileColsA;
+  if (rem <= kThreadsA * 2) {
+    passA_f32_body<2>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
+                      e.a_row_chunks);
+    return;
+  }
+  if constexpr (kColsA32 > 4) {
+    if (rem <= kThreadsA * 4) {
+      passA_f32_body<4>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
+                        e.a_row_chunks);
+      return;
+    }
+  }
+  passA_f32_body(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles, e.a_row_chunks);
+}
+
+// The row list is cleared in phase P: rows of tiles finished during this
+// phase are listed while other tiles still run, so pass B leaves it alone.
+__device__ __forceinline__ void passB_tile(const BatchPair& P, int bx, int by) {
+  using namespace dev;
+  const EstepPlan& e = P.ep;
+  const int rem = P.M - bx * kTileRowsB;
+  if (rem <= kThreadsB * 2) {
+    passB_f32_body<2>(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles,
+                      e.b_col_chunks, 0);
+    return;
+  }
+  if constexpr (kRowsB32 > 4) {
+    if (rem <= kThreadsB * 4) {
+      passB_f32_body<4>(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles,
+                        e.b_col_chunks, 0);
+      return;
+    }
+  }
+  passB_f32_body(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles, e.b_col_chunks,
+                 0);
+}
+
+// Completion ticket of a tile of n work items: true in the block that
+// finished the tile's last item (after which the tile's results written by
+// the other blocks are visible to it).  Called by every thread of the block.
+__device__ __forceinline__ bool tile_done(unsigned int* ticket, unsigned int n) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const bool last = atomicAdd(ticket, 1u) == n - 1;
+    if (last) *ticket = 0;         // every item has arrived: rewind for the next iteration
+    s_last = last;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// One work item of phase ph for pair P: block coordinates (bx, by) of the
+// per-pair kernel it stands for.
 __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
   using namespace dev;
   const EstepPlan& e = P.ep;
   const MstepPlan& m = P.mp;
+  unsigned int* tA = P.tix;
+  unsigned int* tB = tA + e.a_col_tiles;
+  unsigned int* tP = tB + e.b_row_tiles;
+  unsigned int* tE = tP + 1;
   switch (ph) {
-    case PH_PASSA:
-      passA_f32_body(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles, e.a_row_chunks);
-      break;
-    case PH_REDA:
-      for (int u = bx; u < bx + by; ++u) {
-        reduceA_body<float>(P.partA, e.a_row_chunks, P.M, P.Y4, P.N, P.Yb, nullptr, P.sums, P.flags + P.M, P.st, 1, u,
-                            0, (int)e.redA_blocks, 1);
+    case PH_A: {
+      passA_tile(P, bx, by);
+      if (!tile_done(tA + bx, (unsigned)e.a_row_chunks)) break;
+      const int u1 = min((bx + 1) * (kTileColsA / kRedCols), (int)e.redA_blocks);
+      for (int u = bx * (kTileColsA / kRedCols); u < u1; ++u) {
+        const bool pair_done = reduceA_body<float>(P.partA, e.a_row_chunks, P.M, P.Y4, P.N, P.Yb, nullptr, P.sums,
+                                                   P.flags + P.M, P.st, 1, u, 0, (int)e.redA_blocks, 1);
         __syncthreads();
+        if (pair_done) {
+          __threadfence();
+          fixA_f32_body(P.T4, P.M, P.Y4, P.N, P.Yb, nullptr, P.flags + P.M, P.st, 1, 0, 0, 1, 1);
+          __syncthreads();
+        }
       }
       break;
-    case PH_FIXA:
-      fixA_f32_body(P.T4, P.M, P.Y4, P.N, P.Yb, nullptr, P.flags + P.M, P.st, 1, bx, 0, kFixItems, 1);
-      break;
-    case PH_PASSB:
-      passB_f32_body(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles, e.b_col_chunks);
-      break;
-    case PH_REDB:
-      for (int u = bx; u < bx + by; ++u) {
-        reduceB_body<float>(P.partB, e.b_col_chunks, P.M, P.X4, P.Yt4, P.R4, nullptr, P.sums, P.flags, P.st, 1, u, 0,
-                            (int)e.redB_blocks, 1);
+    }
+    case PH_B: {
+      passB_tile(P, bx, by);
+      if (!tile_done(tB + bx, (unsigned)e.b_col_chunks)) break;
+      const int u1 = min((bx + 1) * (kTileRowsB / kRedRows), (int)e.redB_blocks);
+      for (int u = bx * (kTileRowsB / kRedRows); u < u1; ++u) {
+        const bool pair_done = reduceB_body<float>(P.partB, e.b_col_chunks, P.M, P.X4, P.Yt4, P.R4, nullptr, P.sums,
+                                                   P.flags, P.st, 1, u, 0, (int)e.redB_blocks, 1);
         __syncthreads();
+        if (pair_done) {
+          __threadfence();
+          fixB_f32_body(P.T4, P.M, P.Yb, P.N, P.X4, P.Yt4, P.R4, nullptr, P.flags, P.st, 1, 0, 0, 1, 1);
+          __syncthreads();
+        }
       }
       break;
-    case PH_FIXB:
-      fixB_f32_body(P.T4, P.M, P.Yb, P.N, P.X4, P.Yt4, P.R4, nullptr, P.flags, P.st, 1, bx, 0, kFixItems, 1);
-      break;
-    case PH_PROJ:
+    }
+    case PH_P: {
       if (P.narrow)
         proj_narrow_body(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, by);
       else
         colsum_body<float, kThreadsBatch>(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1,
                                           bx, by, m.p_col_tiles, m.p_row_chunks);
-      break;
-    case PH_DIAG:
-      for (int u = bx; u < bx + by; ++u) {
-        diag_update_body<float>(P.partP, m.p_row_chunks, m.ldU, P.K, P.lam, P.B4, P.C4, P.st, 1, u, 0,
-                                (P.K + kMRedCols - 1) / kMRedCols, 1);
+      if (!tile_done(tP, (unsigned)(m.p_col_tiles * m.p_row_chunks))) break;
+      const int nu = (P.K + kMRedCols - 1) / kMRedCols;
+      for (int u = 0; u < nu; ++u) {
+        diag_update_body<float>(P.partP, m.p_row_chunks, m.ldU, P.K, P.lam, P.B4, P.C4, P.st, 1, u, 0, nu, 1);
         __syncthreads();
       }
       break;
-    case PH_EXPD:
+    }
+    case PH_E: {
+      if (P.narrow) {
+        expand_narrow_body(P.Ut, m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4, P.sums, P.st, bx, m.e_col_tiles);
+        break;
+      }
       colsum_body<float, kThreadsBatch>(P.Ut, m.ldM, P.K, P.M, P.B4, m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx,
                                         by, m.e_col_tiles, m.e_row_chunks);
-      break;
-    case PH_FIN:
-      for (int u = bx; u < bx + by; ++u) {
+      if (!tile_done(tE + bx, (unsigned)m.e_row_chunks)) break;
+      const int u1 = min((bx + 1) * (kTileColsE / kMRedCols), m.e_blocks);
+      for (int u = bx * (kTileColsE / kMRedCols); u < u1; ++u) {
         expand_finish_body<float, true>(P.partP, m.e_row_chunks, m.ldM, P.M, P.X4, P.Yt4, P.T4, P.Yhat4, P.sums, P.st,
                                         1, u, 0, m.e_blocks, 1);
         __syncthreads();
       }
       break;
+    }
   }
 }
 
@@ -200,21 +386,32 @@ batch_iterations(const BatchPair* __restrict__ pairs, const BatchItem* __restric
                  const int* __restrict__ phase_off, BatchCtl* __restrict__ ctl, int n_iter,
                  unsigned long long limit_ns, int barrier_extra) {
   __shared__ int s_idx;
+  unsigned long long t_prev = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = t_prev = global_ns();
   for (int it = 0; it < n_iter; ++it) {
     for (int ph = 0; ph < kPhases; ++ph) {
       const int lo = phase_off[ph], hi = phase_off[ph + 1];
+      unsigned long long busy = 0;
       for (;;) {
         if (threadIdx.x == 0) s_idx = lo + (int)atomicAdd(&ctl->next_item[ph], 1u);
         __syncthreads();
         const int idx = s_idx;
         if (idx >= hi) break;
+        const unsigned long long t0 = threadIdx.x == 0 ? global_ns() : 0ull;
         const BatchItem itm = items[idx];
         run_item(ph, pairs[itm.pair], itm.bx, itm.by);
         __syncthreads();
+        if (threadIdx.x == 0) busy += global_ns() - t0;
       }
+      if (threadIdx.x == 0 && busy) atomicAdd(&ctl->busy_ns[ph], busy);
       if (!grid_barrier(ctl, gridDim.x + (unsigned int)barrier_extra, limit_ns)) return;
       // every block has left phase ph: its item counter can be rewound
-      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->next_item[ph] = 0;
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->next_item[ph] = 0;
+        const unsigned long long t = global_ns();
+        ctl->phase_ns[ph] += t - t_prev;
+        t_prev = t;
+      }
     }
   }
 }
@@ -277,7 +474,7 @@ void plan_batch(BatchPair* P, int n_pairs, int resident) {
     const int64_t colsC = (int64_t)kThreadsBatch * 8;     // columns of one colsum tile
     if (p.narrow) {
       m.p_col_tiles = 1;
-      const int64_t rows = std::max<int64_t>(64, (128 * 1024) / (m.ldU * 4));
+      const int64_t rows = std::max<int64_t>(256, (512 * 1024) / (m.ldU * 4));
       m.p_row_chunks = (int)cdiv(M, rows);
     } else {
       m.p_col_tiles = (int)cdiv(m.ldU, colsC);
@@ -286,9 +483,14 @@ void plan_batch(BatchPair* P, int n_pairs, int resident) {
     }
     m.p_rows_per_chunk = (int)cdiv(M, m.p_row_chunks);
     m.e_col_tiles = (int)cdiv(m.ldM, colsC);
-    const int64_t erows = std::max<int64_t>(32, (256 * 1024) / (std::min(m.ldM, colsC) * 4));
-    m.e_row_chunks = (int)cdiv(K, erows);
-    m.e_rows_per_chunk = (int)cdiv(K, m.e_row_chunks);
+    if (p.narrow) {
+      m.e_row_chunks = 1;                // the fused expansion takes all K rows per tile
+      m.e_rows_per_chunk = (int)K;
+    } else {
+      const int64_t erows = std::max<int64_t>(32, (256 * 1024) / (std::min(m.ldM, colsC) * 4));
+      m.e_row_chunks = (int)cdiv(K, erows);
+      m.e_rows_per_chunk = (int)cdiv(K, m.e_row_chunks);
+    }
     m.part_elems = std::max((int64_t)m.p_row_chunks * 3 * m.ldU, (int64_t)m.e_row_chunks * 3 * m.ldM);
     m.e_blocks = (int)cdiv(M, dev::kMRedCols);
     m.sums_elems = (int64_t)m.e_blocks * 3;
@@ -296,51 +498,25 @@ void plan_batch(BatchPair* P, int n_pairs, int resident) {
   }
 }
 
-void batch_items(const BatchPair* pairs_host, int n_pairs, int resident, std::vector<BatchItem>& items,
-                 std::vector<int>& phase_off) {
+void batch_items(const BatchPair* pairs_host, int n_pairs, std::vector<BatchItem>& items, std::vector<int>& phase_off) {
   // pairs in decreasing work order within every phase (largest items first)
   std::vector<int> order(n_pairs);
   for (int i = 0; i < n_pairs; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return (double)pairs_host[a].M * pairs_host[a].N > (double)pairs_host[b].M * pairs_host[b].N;
   });
-  auto units = [&](const BatchPair& P, int ph) -> int64_t {
-    switch (ph) {
-      case PH_REDA: return P.ep.redA_blocks;
-      case PH_REDB: return P.ep.redB_blocks;
-      case PH_DIAG: return cdiv(P.K, dev::kMRedCols);
-      case PH_FIN: return P.mp.e_blocks;
-      default: return 0;
-    }
-  };
   items.clear();
   phase_off.assign(kPhases + 1, 0);
   for (int ph = 0; ph < kPhases; ++ph) {
     phase_off[ph] = (int)items.size();
-    const bool grouped = ph == PH_REDA || ph == PH_REDB || ph == PH_DIAG || ph == PH_FIN;
-    int64_t group = 1;
-    if (grouped) {
-      // about two items per resident block over the batch
-      int64_t tot = 0;
-      for (int i = 0; i < n_pairs; ++i) tot += units(pairs_host[i], ph);
-      group = std::max<int64_t>(1, cdiv(tot, 2 * (int64_t)std::max(resident, 1)));
-    }
     for (int i : order) {
       const BatchPair& P = pairs_host[i];
-      if (grouped) {
-        const int64_t u = units(P, ph);
-        for (int64_t b = 0; b < u; b += group)
-          items.push_back(BatchItem{i, (int)b, (int)std::min(group, u - b)});
-        continue;
-      }
       int gx = 1, gy = 1;
       switch (ph) {
-        case PH_PASSA: gx = P.ep.a_col_tiles; gy = P.ep.a_row_chunks; break;
-        case PH_FIXA: gx = kFixItems; break;
-        case PH_PASSB: gx = P.ep.b_row_tiles; gy = P.ep.b_col_chunks; break;
-        case PH_FIXB: gx = kFixItems; break;
-        case PH_PROJ: gx = P.mp.p_col_tiles; gy = P.mp.p_row_chunks; break;
-        case PH_EXPD: gx = P.mp.e_col_tiles; gy = P.mp.e_row_chunks; break;
+        case PH_A: gx = P.ep.a_col_tiles; gy = P.ep.a_row_chunks; break;
+        case PH_B: gx = P.ep.b_row_tiles; gy = P.ep.b_col_chunks; break;
+        case PH_P: gx = P.mp.p_col_tiles; gy = P.mp.p_row_chunks; break;
+        case PH_E: gx = P.mp.e_col_tiles; gy = P.mp.e_row_chunks; break;
       }
       for (int by = 0; by < gy; ++by)
         for (int bx = 0; bx < gx; ++bx) items.push_back(BatchItem{i, bx, by});
@@ -348,6 +524,10 @@ void batch_items(const BatchPair* pairs_host, int n_pairs, int resident, std::ve
   }
   phase_off[kPhases] = (int)items.size();
 }
+
+int batch_tickets(const BatchPair& p) { return p.ep.a_col_tiles + p.ep.b_row_tiles + 1 + p.mp.e_col_tiles; }
+
+int batch_phases() { return kPhases; }
 
 cudaError_t launch_batch(const BatchPair* pairs_dev, int n_pairs, const BatchItem* items, const int* phase_off,
                          BatchCtl* ctl, int grid, int n_iter, double wait_limit_s, int barrier_extra,

@@ -154,6 +154,7 @@ struct BatchPair {
   double* sums;
   int* flags;
   DevState* st;
+  unsigned int* tix;          // completion tickets of the pair's tiles (batch_tickets entries, zeroed)
   int narrow;                 // projection by the row-split body (K <= 128)
 };
 struct BatchItem {
@@ -165,15 +166,20 @@ struct BatchCtl {
   unsigned int barrier_gen;
   unsigned int next_item[16];
   int status;                 // CPD_ETIMEOUT if a grid barrier gave up
+  int pad;
+  unsigned long long t_start;        // block 0's clock at the start of the launch
+  unsigned long long phase_ns[16];   // per phase: block 0's time from the previous barrier to the end of this one
+  unsigned long long busy_ns[16];    // per phase: time all blocks spent inside work items
 };
-constexpr int kFixItems = 4;  // work items per pair for the log-domain fix-ups
 // Resident blocks of the persistent kernel on `sms` SMs (0 on failure).
 int batch_resident_blocks(int sms);
 // Fills ep, mp and narrow of every pair from its M, N, K.
 void plan_batch(BatchPair* pairs_host, int n_pairs, int resident);
 // Work items of every phase (phase ph owns items [phase_off[ph], phase_off[ph+1])).
-void batch_items(const BatchPair* pairs_host, int n_pairs, int resident, std::vector<BatchItem>& items,
-                 std::vector<int>& phase_off);
+void batch_items(const BatchPair* pairs_host, int n_pairs, std::vector<BatchItem>& items, std::vector<int>& phase_off);
+// Completion tickets a pair needs (after plan_batch), and the phases per iteration.
+int batch_tickets(const BatchPair& p);
+int batch_phases();
 // Zeroes ctl, then runs n_iter iterations of every pair in one cooperative
 // launch of `grid` blocks.  barrier_extra > 0 makes every grid barrier wait
 // for blocks that do not exist (host-side fault injection for the timeout

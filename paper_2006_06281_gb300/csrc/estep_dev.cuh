@@ -124,16 +124,27 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
   return d;
 }
 
+// Shared-memory tile of the FP32 passes (kTileA = kTileB records of two
+// 16-byte halves).  Declared once at namespace scope so that every kernel
+// -- and every instantiation of the pass bodies inside one kernel -- holds a
+// single copy.
+static_assert(kTileA == kTileB, "passes A and B share one tile buffer");
+__shared__ ulonglong2 s_pass_tile[kTileA][2];
+
 // ------------------------------------------------------------------ pass A
 // FP32 pass A: each thread owns kColsA32 scene points as kColsA32/2 packed
 // pairs; a model point is broadcast from shared memory as duplicated pairs
 // {(x,x),(y,y)},{(z,z),-}.  Per pair of Gaussians: 3 sub + 1 mul + 2 fma on
 // f32x2, two MUFU ex2 and two scalar adds.
+// COLS < kColsA32 serves a partial last tile: the tile still starts at
+// bx * kThreadsA * kColsA32 but each thread covers only COLS scene points.
+template <int COLS = kColsA32>
 __device__ __forceinline__ void passA_f32_body(const float4* FCPD_RESTRICT T4, int M, int rows_per_chunk, const float4* FCPD_RESTRICT Y4,
           int N, float* FCPD_RESTRICT partA, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
   if (gate && iteration_gated(st)) return;
-  constexpr int P = kColsA32 / 2;
-  __shared__ ulonglong2 sT[kTileA][2];
+  static_assert(COLS % 2 == 0 && COLS <= kColsA32, "scene points per thread: even, at most kColsA32");
+  constexpr int P = COLS / 2;
+  ulonglong2 (*sT)[2] = s_pass_tile;
   const float q = scale_q(st->sigma2);
   const int nbase = bx * (kThreadsA * kColsA32) + threadIdx.x;
   f2_t yx[P], yy[P], yz[P];
@@ -242,14 +253,20 @@ __device__ __forceinline__ double outlier_c(const DevState* st, int M, int N) {
 // A block owns kRedCols columns; kRedSub threads per column each sum a strided
 // subset of the chunks (coalesced across columns), then the subsets are added
 // in a fixed order -- deterministic.
-constexpr int kRedCols = 64;
+#ifndef FCPD_RED_COLS
+#define FCPD_RED_COLS 64
+#endif
+constexpr int kRedCols = FCPD_RED_COLS;
 constexpr int kRedSub = kThreadsR / kRedCols;
+static_assert(kRedCols * kRedSub == kThreadsR, "columns per block must divide the block");
 
 template <typename F>
-__device__ __forceinline__ void reduceA_body(const F* FCPD_RESTRICT partA, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT Y4,
+// Returns true in the block that completed the reduction over all gx blocks
+// (the one that wrote the log-likelihood).
+__device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT Y4,
         int N, typename Vec<F>::t4* FCPD_RESTRICT Yb, double* FCPD_RESTRICT den_out,
         double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_cols, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
-  if (gate && iteration_gated(st)) return;
+  if (gate && iteration_gated(st)) return false;
   __shared__ double sh[32];
   __shared__ F part[kRedSub][kRedCols];
   __shared__ bool last;
@@ -262,7 +279,7 @@ __device__ __forceinline__ void reduceA_body(const F* FCPD_RESTRICT partA, int c
   F s = (F)0;   // FP32 partials summed in FP32 (fixed order), FP64 in FP64
   if (n < N) {
 #pragma unroll 8
-    for (int k = sub; k < chunks; k += kRedSub) s += partA[(size_t)k * N + n];
+    for (int k = sub; k < chunks; k += kRedSub) s += __ldcg(partA + (size_t)k * N + n);
   }
   part[sub][col] = s;
   __syncthreads();
@@ -313,6 +330,7 @@ __device__ __forceinline__ void reduceA_body(const F* FCPD_RESTRICT partA, int c
       st->ticket_a = 0;
     }
   }
+  return last;
 }
 
 // Exact FP32 column denominators in the log domain for the listed columns:
@@ -371,17 +389,23 @@ __device__ __forceinline__ void fixA_f32_body(const float4* FCPD_RESTRICT T4, in
 // with l = -log2 den_n.  Per pair of Gaussians: 3 sub + 1 mul + 2 fma for the
 // distance and 1 sub for the exponent on f32x2, two MUFU ex2, then scalar
 // 1 add + 4 fma per Gaussian to accumulate P1, PY (3) and V.
+// ROWS < kRowsB32 serves a partial last tile (as COLS in pass A).
+// clear_rows = 0 leaves the row list alone, for callers that reduce rows in
+// the same pass (and clear the list elsewhere).
+template <int ROWS = kRowsB32>
 __device__ __forceinline__ void passB_f32_body(const float4* FCPD_RESTRICT T4, int M, const float4* FCPD_RESTRICT Yb, int N,
-          int cols_per_chunk, float* FCPD_RESTRICT partB, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+          int cols_per_chunk, float* FCPD_RESTRICT partB, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy,
+          int clear_rows = 1) {
   if (gate && iteration_gated(st)) return;
+  static_assert(ROWS % 2 == 0 && ROWS <= kRowsB32, "model points per thread: even, at most kRowsB32");
   // the column list was consumed by fixA (the previous kernel) and the row
   // list is filled only after this kernel: both can be cleared here
   if (bx == 0 && by == 0 && threadIdx.x == 0) {
     st->n_flag_cols = 0;
-    st->n_flag_rows = 0;
+    if (clear_rows) st->n_flag_rows = 0;
   }
-  constexpr int P = kRowsB32 / 2;
-  __shared__ ulonglong2 sY[kTileB][2];
+  constexpr int P = ROWS / 2;
+  ulonglong2 (*sY)[2] = s_pass_tile;
   const float q = scale_q(st->sigma2);
   const int mbase = bx * (kThreadsB * kRowsB32) + threadIdx.x;
   f2_t tx[P], ty[P], tz[P];
@@ -407,15 +431,20 @@ __device__ __forceinline__ void passB_f32_body(const float4* FCPD_RESTRICT T4, i
   for (int j = 0; j < 2 * P; ++j) p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.f;
   const int c0 = by * cols_per_chunk;
   const int c1 = min(N, c0 + cols_per_chunk);
+  // next tile's scene records prefetched into registers (as in pass A)
+  static_assert(kTileB <= kThreadsB, "one scene point per thread per tile");
+  const float4 far4 = make_float4(-kFar, -kFar, -kFar, 0.f);
+  float4 nxt = far4;
+  if (threadIdx.x < kTileB && c0 + (int)threadIdx.x < c1) nxt = Yb[c0 + threadIdx.x];
   for (int base = c0; base < c1; base += kTileB) {
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileB; i += kThreadsB) {
-      const int n = base + i;
-      const float4 y = n < c1 ? Yb[n] : make_float4(-kFar, -kFar, -kFar, 0.f);
-      sY[i][0] = make_ulonglong2(f2_pack(y.x, y.x), f2_pack(y.y, y.y));
-      sY[i][1] = make_ulonglong2(f2_pack(y.z, y.z), f2_pack(y.w, y.w));
+    if (threadIdx.x < kTileB) {
+      const float4 y = base + (int)threadIdx.x < c1 ? nxt : far4;
+      sY[threadIdx.x][0] = make_ulonglong2(f2_pack(y.x, y.x), f2_pack(y.y, y.y));
+      sY[threadIdx.x][1] = make_ulonglong2(f2_pack(y.z, y.z), f2_pack(y.w, y.w));
     }
     __syncthreads();
+    if (threadIdx.x < kTileB && base + kTileB + (int)threadIdx.x < c1) nxt = Yb[base + kTileB + threadIdx.x];
     const int cnt = min(kTileB, c1 - base);
 #pragma unroll kUnrollB
     for (int i = 0; i < cnt; ++i) {
@@ -539,43 +568,49 @@ __device__ __forceinline__ void write_row(int m, double p1s, double px, double p
 // sum_n p^_mn |y_n - t_m|^2, R_m = Ytil_m - x_m.  FP64: a row whose mass is
 // 0 or not finite cannot be normalised -> CPD_ENUMERIC.  FP32: rows whose
 // mass is below 2^-90 are listed for the exact log-domain path.
-// A block owns 32 rows; each warp sums a strided subset of the chunks for
-// the five quantities of those rows, and warp 0 adds the subsets in order.
-constexpr int kRedRows = 32;
-constexpr int kRedWarps = kThreadsR / 32;
+// A block owns kRedRows rows; kRedRowSub threads per row each sum a strided
+// subset of the chunks for the five quantities of that row (coalesced across
+// rows), and the first thread of each row adds the subsets in order.
+#ifndef FCPD_RED_ROWS
+#define FCPD_RED_ROWS 32
+#endif
+constexpr int kRedRows = FCPD_RED_ROWS;
+constexpr int kRedRowSub = kThreadsR / kRedRows;
+static_assert(kRedRows * kRedRowSub == kThreadsR && kRedRows % 32 == 0, "rows per block: a multiple of 32 dividing the block");
 
 template <typename F>
-__device__ __forceinline__ void reduceB_body(const F* FCPD_RESTRICT partB, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT X4,
+// Returns true in the block that completed the reduction over all gx blocks.
+__device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT X4,
         typename Vec<F>::t4* FCPD_RESTRICT Yt4, typename Vec<F>::t4* FCPD_RESTRICT R4,
         double* FCPD_RESTRICT P1_out, double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_rows,
         DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
-  if (gate && iteration_gated(st)) return;
+  if (gate && iteration_gated(st)) return false;
   __shared__ double sh[32];
-  __shared__ F part[kRedWarps][5][kRedRows];
+  __shared__ F part[kRedRowSub][5][kRedRows];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int m = bx * kRedRows + lane;
+  const int row = threadIdx.x % kRedRows, sub = threadIdx.x / kRedRows;
+  const int m = bx * kRedRows + row;
   const size_t plane = (size_t)chunks * M;
   F a[5] = {(F)0, (F)0, (F)0, (F)0, (F)0};   // summed in F, fixed order
   if (m < M) {
 #pragma unroll 4
-    for (int k = wid; k < chunks; k += kRedWarps) {
+    for (int k = sub; k < chunks; k += kRedRowSub) {
       const size_t o = (size_t)k * M + m;
 #pragma unroll
-      for (int qn = 0; qn < 5; ++qn) a[qn] += partB[o + qn * plane];
+      for (int qn = 0; qn < 5; ++qn) a[qn] += __ldcg(partB + o + qn * plane);
     }
   }
 #pragma unroll
-  for (int qn = 0; qn < 5; ++qn) part[wid][qn][lane] = a[qn];
+  for (int qn = 0; qn < 5; ++qn) part[sub][qn][row] = a[qn];
   __syncthreads();
   double vrow = 0.0;
   int bad = 0;
-  if (wid == 0 && m < M) {
+  if (sub == 0 && m < M) {
     F f1 = 0, fx = 0, fy = 0, fz = 0, fv = 0;
 #pragma unroll
-    for (int j = 0; j < kRedWarps; ++j) {
-      f1 += part[j][0][lane]; fx += part[j][1][lane]; fy += part[j][2][lane];
-      fz += part[j][3][lane]; fv += part[j][4][lane];
+    for (int j = 0; j < kRedRowSub; ++j) {
+      f1 += part[j][0][row]; fx += part[j][1][row]; fy += part[j][2][row];
+      fz += part[j][3][row]; fv += part[j][4][row];
     }
     double p1 = f1, px = fx, py = fy, pz = fz, v = fv;
     if constexpr (sizeof(F) == 4) {
@@ -613,6 +648,7 @@ __device__ __forceinline__ void reduceB_body(const F* FCPD_RESTRICT partB, int c
       st->ticket_b = 0;
     }
   }
+  return last;
 }
 
 // Exact FP32 rows in the log domain for the listed rows: with

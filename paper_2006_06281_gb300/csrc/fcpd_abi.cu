@@ -749,16 +749,19 @@ struct cpd_batch {
   std::vector<cpd_ctx*> ctx;
   std::vector<BatchPair> pairs;
   std::vector<int> phase_off_host;
-  Buf pairs_dev, items, phase_off, ctl, states;
+  Buf pairs_dev, items, phase_off, ctl, states, tickets;
   int n_items = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = -1;
   int graph_extra = -1;
+  BatchCtl last{};            // control block after the last call
+  int last_iters = 0;
+  size_t n_tickets = 0;
 
   ~cpd_batch() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cpd_ctx* c : ctx) delete c;
-    for (Buf* b : {&pairs_dev, &items, &phase_off, &ctl, &states}) b->release();
+    for (Buf* b : {&pairs_dev, &items, &phase_off, &ctl, &states, &tickets}) b->release();
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -931,12 +934,21 @@ cpd_status cpd_batch_create(int32_t n_pairs, const void* const* X, const int64_t
   }
   plan_batch(b->pairs.data(), n_pairs, b->grid);
   cpd_status s;
-  for (int i = 0; i < n_pairs; ++i) {
+  size_t n_tickets = 0;
+  for (int i = 0; i < n_pairs; ++i) n_tickets += (size_t)batch_tickets(b->pairs[i]);
+  if ((s = b->tickets.ensure(n_tickets * sizeof(unsigned int))) != CPD_OK) return bail(s);
+  b->n_tickets = n_tickets;
+  if (cudaMemsetAsync(b->tickets.p, 0, n_tickets * sizeof(unsigned int), b->stream) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "clearing the completion tickets failed"));
+  for (int i = 0, off = 0; i < n_pairs; ++i) {
     if ((s = batch_load_pair(b->ctx[i], b->pairs[i], Y[i])) != CPD_OK) return bail(s);
+    const int nt = batch_tickets(b->pairs[i]);
     b->pairs[i] = batch_pointers(b->ctx[i], b->pairs[i]);
+    b->pairs[i].tix = b->tickets.as<unsigned int>() + off;
+    off += nt;
   }
   std::vector<BatchItem> items;
-  batch_items(b->pairs.data(), n_pairs, b->grid, items, b->phase_off_host);
+  batch_items(b->pairs.data(), n_pairs, items, b->phase_off_host);
   b->n_items = (int)items.size();
   if ((s = b->pairs_dev.ensure(sizeof(BatchPair) * (size_t)n_pairs)) != CPD_OK) return bail(s);
   if ((s = b->items.ensure(sizeof(BatchItem) * items.size())) != CPD_OK) return bail(s);
@@ -964,9 +976,10 @@ cpd_status cpd_batch_iterate(cpd_batch* b, int32_t n_iter) {
   const int extra = fault_enabled("barrier") ? 1 : 0;
   if (!b->graph || b->graph_iters != n_iter || b->graph_extra != extra) STATUS_TRY(batch_capture(b, n_iter, extra));
   CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
-  BatchCtl h;
+  BatchCtl& h = b->last;
   CUDA_TRY(cudaMemcpyAsync(&h, b->ctl.p, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
+  b->last_iters = n_iter;
   if (h.status != 0)
     return fail((cpd_status)h.status, "a grid barrier of the batched kernel timed out (" +
                                           std::to_string(b->wait_s) + " s); the pairs' state is undefined until "
@@ -1017,11 +1030,25 @@ cpd_status cpd_batch_launch_shape(const cpd_batch* b, int32_t* n_pairs, int32_t*
   return CPD_OK;
 }
 
+cpd_status cpd_batch_phase_ms(const cpd_batch* b, float* phase_ms) {
+  if (!b || !phase_ms) return fail(CPD_EINVAL, "batch and phase_ms are required");
+  if (b->last_iters < 1) return fail(CPD_ESTATE, "no batched call has completed yet");
+  const int np = batch_phases();
+  for (int ph = 0; ph < np; ++ph) {
+    const double span = (double)b->last.phase_ns[ph];
+    phase_ms[ph] = (float)(span / 1e6 / b->last_iters);
+    phase_ms[np + ph] = span > 0 ? (float)((double)b->last.busy_ns[ph] / ((double)b->grid * span)) : 0.f;
+  }
+  return CPD_OK;
+}
+
 cpd_status cpd_batch_reset(cpd_batch* b) {
   g_err.clear();
   if (!b) return fail(CPD_EINVAL, "batch is NULL");
   DeviceGuard guard(b->dev);
   for (cpd_ctx* c : b->ctx) STATUS_TRY(start_registration(c));
+  // a launch that ended early (a barrier timeout) may have left tickets set
+  CUDA_TRY(cudaMemsetAsync(b->tickets.p, 0, b->n_tickets * sizeof(unsigned int), b->stream));
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   return CPD_OK;
 }

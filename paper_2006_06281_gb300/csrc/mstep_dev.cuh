@@ -49,8 +49,12 @@ __device__ __forceinline__ double lane_of(const double2& v, int i) { return i ==
 constexpr int kThreadsP = 128;   // streaming kernel block
 constexpr int kRTile = 256;      // rows of V staged per shared-memory tile
 constexpr int kThreadsD = 256;   // reduction kernels
-constexpr int kMRedCols = 64;     // columns per reduction block
+#ifndef FCPD_MRED_COLS
+#define FCPD_MRED_COLS 64
+#endif
+constexpr int kMRedCols = FCPD_MRED_COLS;   // columns per reduction block
 constexpr int kMRedSub = kThreadsD / kMRedCols;
+static_assert(kMRedCols * kMRedSub == kThreadsD, "columns per block must divide the block");
 
 // ---------------------------------------------------------------- colsum
 template <typename F, int THREADS>
@@ -121,7 +125,7 @@ __device__ __forceinline__ void chunk_sums(const F* FCPD_RESTRICT partials, int 
 #pragma unroll 4
     for (int k = sub; k < chunks; k += kMRedSub)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) s[d] += partials[((size_t)k * 3 + d) * ldP + col];
+      for (int d = 0; d < 3; ++d) s[d] += __ldcg(partials + ((size_t)k * 3 + d) * ldP + col);
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) part[sub][d][c] = s[d];
@@ -161,12 +165,55 @@ __device__ __forceinline__ void diag_update_body(const F* FCPD_RESTRICT partP, i
 
 // T = X + U B (X may be null: W = U C) from the expansion partials; with EPI
 // the Eq. 18 epilogue and the device-state update of the iteration.
+// Eq. 18 terms of model point m after its update from `to` to `tn` (yt:
+// Ytil_m with sum_n p^_mn |y_n - t_m|^2 in w): the shifted-form contribution,
+// the squared change of t_m, and the squared ground-truth error.
+template <typename V4>
+__device__ __forceinline__ void point_terms(const V4& to, const V4& tn, const V4& yt,
+                                            const V4* FCPD_RESTRICT Yhat4, int m, double& contrib, double& dT2,
+                                            double& gt2) {
+  const double dx = (double)to.x - tn.x, dy = (double)to.y - tn.y, dz = (double)to.z - tn.z;
+  const double gx = (double)yt.x - to.x, gy = (double)yt.y - to.y, gz = (double)yt.z - to.z;
+  dT2 = dx * dx + dy * dy + dz * dz;
+  contrib = (double)yt.w + 2.0 * (dx * gx + dy * gy + dz * gz) + dT2;
+  gt2 = 0.0;
+  if (Yhat4) {
+    const V4 h = Yhat4[m];
+    const double ex = (double)tn.x - h.x, ey = (double)tn.y - h.y, ez = (double)tn.z - h.z;
+    gt2 = ex * ex + ey * ey + ez * ez;
+  }
+}
+
+// End of an iteration from the totals over all model points (t0: Eq. 18
+// numerator, t1: sum |dT|^2, t2: sum of squared ground-truth errors):
+// sigma2, the history entry, the iteration count and the stop tests.  One
+// thread.
+__device__ __forceinline__ void finish_iteration(DevState* FCPD_RESTRICT st, double t0, double t1, double t2, int M) {
+  const int it = st->iter;
+  const double s2new = t0 / (3.0 * (double)M);
+  const double rm = st->has_gt ? sqrt(t2 / (double)M) : nan("");
+  if (st->hist && it < kHistCap) {
+    st->hist[it] = s2new;
+    st->hist[kHistCap + it] = st->loglik;
+    st->hist[2 * kHistCap + it] = rm;
+  }
+  st->last_dT2 = t1;
+  st->last_rmse = rm;
+  if (!(s2new > 0.0) || !isfinite(s2new)) st->status = (int)CPD_ENUMERIC;
+  else st->sigma2 = s2new;
+  st->iter = it + 1;
+  if (st->tol > 0.0 && sqrt(t1 / (double)M) <= st->tol) st->done = 1;
+  if (st->gt_tol > 0.0 && st->has_gt && rm <= st->gt_tol) st->done = 1;
+}
+
+// With EPI, returns true in the block that completed the iteration (wrote
+// sigma2 and the history); false otherwise.
 template <typename F, bool EPI>
-__device__ __forceinline__ void expand_finish_body(const F* FCPD_RESTRICT partE, int chunks, int64_t ldM, int M,
+__device__ __forceinline__ bool expand_finish_body(const F* FCPD_RESTRICT partE, int chunks, int64_t ldM, int M,
               const typename Vec<F>::t4* FCPD_RESTRICT X4, const typename Vec<F>::t4* FCPD_RESTRICT Yt4,
               typename Vec<F>::t4* FCPD_RESTRICT Tout, const typename Vec<F>::t4* FCPD_RESTRICT Yhat4,
               double* FCPD_RESTRICT sums, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
-  if (gate && iteration_gated(st)) return;
+  if (gate && iteration_gated(st)) return false;
   using V4 = typename Vec<F>::t4;
   __shared__ F part[kMRedSub][3][kMRedCols];
   __shared__ double sh[32];
@@ -180,19 +227,7 @@ __device__ __forceinline__ void expand_finish_body(const F* FCPD_RESTRICT partE,
     if (X4) { const V4 x = X4[m]; x0 = x.x; x1 = x.y; x2 = x.z; }
     V4 tn;
     tn.x = (F)(x0 + (double)a[0]); tn.y = (F)(x1 + (double)a[1]); tn.z = (F)(x2 + (double)a[2]); tn.w = (F)0;
-    if constexpr (EPI) {
-      const V4 to = Tout[m];
-      const V4 yt = Yt4[m];
-      const double dx = (double)to.x - tn.x, dy = (double)to.y - tn.y, dz = (double)to.z - tn.z;
-      const double gx = (double)yt.x - to.x, gy = (double)yt.y - to.y, gz = (double)yt.z - to.z;
-      dT2 = dx * dx + dy * dy + dz * dz;
-      contrib = (double)yt.w + 2.0 * (dx * gx + dy * gy + dz * gz) + dT2;
-      if (Yhat4) {
-        const V4 h = Yhat4[m];
-        const double ex = (double)tn.x - h.x, ey = (double)tn.y - h.y, ez = (double)tn.z - h.z;
-        gt2 = ex * ex + ey * ey + ez * ez;
-      }
-    }
+    if constexpr (EPI) point_terms<V4>(Tout[m], tn, Yt4[m], Yhat4, m, contrib, dT2, gt2);
     Tout[m] = tn;
   }
   if constexpr (EPI) {
@@ -219,25 +254,13 @@ __device__ __forceinline__ void expand_finish_body(const F* FCPD_RESTRICT partE,
       const double t1 = block_sum(a1, sh);
       const double t2 = block_sum(a2, sh);
       if (threadIdx.x == 0) {
-        const int it = st->iter;
-        const double s2new = t0 / (3.0 * (double)M);
-        const double rm = st->has_gt ? sqrt(t2 / (double)M) : nan("");
-        if (st->hist && it < kHistCap) {
-          st->hist[it] = s2new;
-          st->hist[kHistCap + it] = st->loglik;
-          st->hist[2 * kHistCap + it] = rm;
-        }
-        st->last_dT2 = t1;
-        st->last_rmse = rm;
-        if (!(s2new > 0.0) || !isfinite(s2new)) st->status = (int)CPD_ENUMERIC;
-        else st->sigma2 = s2new;
-        st->iter = it + 1;
-        if (st->tol > 0.0 && sqrt(t1 / (double)M) <= st->tol) st->done = 1;
-        if (st->gt_tol > 0.0 && st->has_gt && rm <= st->gt_tol) st->done = 1;
+        finish_iteration(st, t0, t1, t2, M);
         st->ticket_e = 0;
       }
     }
+    return last;
   }
+  return false;
 }
 
 }  // namespace dev
