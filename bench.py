@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--no-batch-baseline", action="store_true",
                     help="skip timing the same pairs through per-pair contexts")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched-registration section (prints its object as the JSON line)")
     return ap.parse_args()
 
 
@@ -404,6 +406,10 @@ def main():
     from paper_2006_06281_gb300 import build, cpd
     build.build()
     peaks = load_peaks()
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps(dict(impl="ours", batch=run_batch(args, peaks, torch))), flush=True)
+        return 0
 
     M = cfg["M"]
     ps = datagen.gen(M, cfg["n_out"], cfg["amp"], cfg["noise"], rank_seed(cfg, rank))

@@ -167,4 +167,7 @@ BATCH_WORKLOADS = {
     # seconds rather than minutes
     "fp32_batch256_m500_3000_k128": dict(n_pairs=256, lo=500, hi=3000, seed0=1000, K=128,
                                          omega=0.1, lam=2.0, beta=2.0, iters=100),
+    # 64 pairs, 5 iterations per launch: the small case for profiler captures
+    "fp32_batch64_m500_3000_k128": dict(n_pairs=64, lo=500, hi=3000, seed0=1000, K=128,
+                                        omega=0.1, lam=2.0, beta=2.0, iters=5),
 }
