@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--workload", default="fp32_m20000_full")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowrank", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-basis (CPD_MIXED) section")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--batch", default="fp32_batch256_m500_3000_k128",
                     help="batched-registration workload to time as well ('none' skips it)")
@@ -499,6 +500,11 @@ def main():
     e2e = dict(value=job_rate(ne, world, e2e_ms), unit=UNIT, h2d_bytes_per_step=N * 3 * 4,
                d2h_bytes_per_step=M * 3 * 4 + STATE_BYTES, steps=ne)
 
+    # the FP32 path's T after one registration, for the mixed-precision comparison
+    ctx.reset()
+    T32, s232, _ = ctx.iterate(Y, I)
+    torch.cuda.synchronize()
+
     # low-rank variant (fast-CPD-L, Eq. 20), K = 200, same pair
     lowrank = None
     if not args.no_lowrank and cfg["K"] == 0:
@@ -525,6 +531,40 @@ def main():
     else:
         ctx.close()
 
+    # mixed precision (CPD_MIXED: FP16 eigenbasis, FP32 E-step and sums),
+    # same pair and registration; its T is compared with the FP32 path's
+    mixed = None
+    if not args.no_mixed and cfg["K"] == 0:
+        t0 = time.perf_counter()
+        cm = cpd.Context(X, precision=cpd.MIXED, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0)
+        msetup = time.perf_counter() - t0
+        cm.reset()
+        cm.iterate_profiled(Y, I)
+        torch.cuda.synchronize()
+        ph = np.zeros(9)
+        nm = max(1, min(R, 10))
+        a.record()
+        for _ in range(nm):
+            cm.reset()
+            ph += np.array(cm.iterate_profiled(Y, I)) / nm
+        b.record()
+        torch.cuda.synchronize()
+        mms = a.elapsed_time(b)
+        cm.reset()
+        Tm, s2m, _ = cm.iterate(Y, I)
+        torch.cuda.synchronize()
+        cm.close()
+        mroof = roofline_entries(ph, M, N, K, peaks, es=2)
+        d32 = (T32.double() - Tm.double()).norm().item() / T32.double().norm().item()
+        mixed = dict(precision="CPD_MIXED (FP16 eigenbasis, FP32 E-step and accumulation)",
+                     iters_per_s=nm * I / (mms / 1e3), setup_s=msetup,
+                     kernel_ms={k: v["ms"] for k, v in mroof.items()},
+                     colsum_frac_of_hbm=[mroof[k]["frac"] for k in ("m_project", "m_expand") if k in mroof],
+                     rel_diff_T_vs_fp32_after=dict(iters=I, value=d32),
+                     sigma2_rel_diff_vs_fp32=abs(s2m - s232) / s232,
+                     note="error against the FP64 oracle is measured in tests/test_gpu_parity.py "
+                          "(test_mixed_precision_register_against_oracle, M = N = 5000)")
+
     batch = None
     if world == 1 and args.batch != "none":
         batch = run_batch(args, peaks, torch)
@@ -545,7 +585,7 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, setup_s=setup_s, batch=batch,
+                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, setup_s=setup_s, batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "
                                   "(Table IV, MATLAB on an i7-8750H CPU): context, not a like-for-like target")
         print(json.dumps(line), flush=True)

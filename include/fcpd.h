@@ -21,7 +21,8 @@
  *
  * Conventions for every entry point
  *   - Point arrays are row-major, point-major (D contiguous values per
- *     point), element type double for CPD_FP64 and float for CPD_FP32.
+ *     point), element type double for CPD_FP64 and float for CPD_FP32 and
+ *     CPD_MIXED.
  *   - A point-array pointer may be HOST memory (pageable or pinned) or DEVICE
  *     memory of the current CUDA device; the library tells them apart with
  *     cudaPointerGetAttributes and stages host data through its own device
@@ -71,7 +72,13 @@ typedef enum {
 
 typedef enum {
     CPD_FP64 = 0,      /* double everywhere                              */
-    CPD_FP32 = 1       /* float points/basis, FP64 scalar reductions     */
+    CPD_FP32 = 1,      /* float points/basis, FP64 scalar reductions     */
+    CPD_MIXED = 2      /* as CPD_FP32, but the eigenbasis U, U^T is stored
+                          in FP16 (products and sums in FP32): the M-step
+                          streams half the bytes.  Not a precision the
+                          paper uses; its error against the FP64 oracle is
+                          measured and stated, not bounded by the FP32
+                          tolerance.  Points, outputs: float.            */
 } cpd_precision;
 
 /* Registration parameters (Sec. IV "Parameter settings": w, beta, lambda). */
@@ -187,8 +194,9 @@ cpd_status cpd_get_history(cpd_ctx *ctx, int32_t n, double *sigma2_hist, double 
  * CPD_ESTATE before the first iteration. */
 cpd_status cpd_get_W(cpd_ctx *ctx, void *W_out);
 
-/* The kept eigenbasis (Eq. 16 / 19): U_out (M x K row-major, context
- * precision, host or device; may be NULL) and lam_out (K doubles, host,
+/* The kept eigenbasis (Eq. 16 / 19): U_out (M x K row-major, host or
+ * device; may be NULL; double for CPD_FP64, float otherwise -- the FP16
+ * basis of CPD_MIXED is converted) and lam_out (K doubles, host,
  * descending, clamped at 0; may be NULL).  K is cpd_basis_rank(ctx). */
 cpd_status cpd_get_basis(cpd_ctx *ctx, void *U_out, double *lam_out);
 int64_t cpd_basis_rank(const cpd_ctx *ctx);
@@ -203,7 +211,8 @@ cpd_status cpd_mstep(cpd_ctx *ctx, const void *Ytil, double sigma2, void *T_out,
 
 /*
  * One E-step, no context needed (Eq. 4 then Eq. 5):
- *   T (M x D), Y (N x D): host or device, element type per `precision`.
+ *   T (M x D), Y (N x D): host or device, element type per `precision`
+ *            (CPD_MIXED runs the FP32 E-step: float arrays).
  *   Ytil_out (M x D, required): sum_n p^_mn y_n, the row-normalised estimate.
  *   P1_out   (M doubles, optional, host or device): row mass sum_n p_mn
  *            before Eq. 5.

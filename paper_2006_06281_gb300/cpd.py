@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfcpd.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, MIXED = 0, 1, 2    # MIXED: FP32 points and E-step, FP16 eigenbasis
 STATUS = {0: "CPD_OK", 1: "CPD_EINVAL", 2: "CPD_ENOMEM", 3: "CPD_ECUDA", 4: "CPD_ESOLVER",
           5: "CPD_ENUMERIC", 6: "CPD_ETIMEOUT", 7: "CPD_ESTATE"}
 OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)

@@ -352,7 +352,7 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
       if (P.narrow)
         proj_narrow_body(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, by);
       else
-        colsum_body<float, kThreadsBatch>(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1,
+        colsum_body<float, float, kThreadsBatch>(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1,
                                           bx, by, m.p_col_tiles, m.p_row_chunks);
       if (!tile_done(tP, (unsigned)(m.p_col_tiles * m.p_row_chunks))) break;
       const int nu = (P.K + kMRedCols - 1) / kMRedCols;
@@ -367,7 +367,7 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
         expand_narrow_body(P.Ut, m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4, P.sums, P.st, bx, m.e_col_tiles);
         break;
       }
-      colsum_body<float, kThreadsBatch>(P.Ut, m.ldM, P.K, P.M, P.B4, m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx,
+      colsum_body<float, float, kThreadsBatch>(P.Ut, m.ldM, P.K, P.M, P.B4, m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx,
                                         by, m.e_col_tiles, m.e_row_chunks);
       if (!tile_done(tE + bx, (unsigned)m.e_row_chunks)) break;
       const int u1 = min((bx + 1) * (kTileColsE / kMRedCols), m.e_blocks);

@@ -15,6 +15,7 @@
 //   partials  split-reduction scratch of the E-step and the M-step
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,7 +128,9 @@ struct MstepPlan {
 };
 // `colsum_threads`: block size of the streaming kernel the plan is for (128
 // for the per-pair launches, 256 inside the batched persistent kernel).
-MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads = 128);
+// basis_bytes: element size of the stored basis (0: that of the working
+// precision; 2 for the FP16 basis of the mixed-precision mode).
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads = 128, int basis_bytes = 0);
 
 // ------------------------------------------------------------ batched mode
 // One registration inside the batched persistent kernel: its sizes, plans
@@ -218,8 +221,9 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
 // the Eq. 18 variance in the epilogue.  U is M x ldU, Ut = U^T is K x ldM.
 // With `iteration` false the state is not advanced (standalone M-step:
 // T4 receives T, no sigma2 update, st supplies sigma2 and lambda).
-template <typename F>
-void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* lam, int64_t M, int64_t K,
+// S: storage type of the basis (F, or __half in the mixed-precision mode).
+template <typename F, typename S = F>
+void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums,
@@ -227,8 +231,8 @@ void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* la
                   bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr);
 
 // W = U C (C from the last M-step), written as 4-vectors.
-template <typename F>
-void launch_w(const MstepPlan& pl, const F* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
+template <typename F, typename S = F>
+void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
               typename Vec<F>::t4* W4, DevState* st, cudaStream_t s);
 
 // Setup helpers.
@@ -236,6 +240,8 @@ void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double
 template <typename F>
 void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
                           const double* w, double* lam, cudaStream_t s);
+// FP16 basis (mixed-precision mode) -> M x K FP32, row-major, unpadded.
+void launch_basis_to_f32(const __half* U, int64_t M, int64_t K, int64_t ldU, float* out, cudaStream_t s);
 template <typename F>
 void launch_sigma2_init(const typename Vec<F>::t4* X4, int64_t M, const typename Vec<F>::t4* Y4,
                         int64_t N, double* scratch, DevState* st, cudaStream_t s);

@@ -100,7 +100,8 @@ struct Buf {
 cpd_status validate_params(const cpd_params* p) {
   if (!p) return fail(CPD_EINVAL, "params is NULL");
   if (p->D != 3) return fail(CPD_EINVAL, "only D = 3 is implemented");
-  if (p->precision != CPD_FP64 && p->precision != CPD_FP32) return fail(CPD_EINVAL, "unknown precision");
+  if (p->precision != CPD_FP64 && p->precision != CPD_FP32 && p->precision != CPD_MIXED)
+    return fail(CPD_EINVAL, "unknown precision");
   if (!(p->w >= 0.0 && p->w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
   if (!(p->beta > 0.0) || !std::isfinite(p->beta)) return fail(CPD_EINVAL, "beta must be > 0");
   if (!(p->lambda > 0.0) || !std::isfinite(p->lambda)) return fail(CPD_EINVAL, "lambda must be > 0");
@@ -124,7 +125,9 @@ struct cpd_ctx {
   int dev = 0;
   int sms = 0;
   bool fp64 = false;
+  bool half_basis = false;       // CPD_MIXED: U, U^T stored in FP16
   size_t es = 4;                 // element size of the working precision
+  size_t bes = 4;                // element size of the stored basis
   size_t v4 = 16;                // bytes of one 4-vector
   int64_t M = 0, K = 0, ldU = 0, N = 0;
   cudaStream_t stream = nullptr; // caller's stream
@@ -212,6 +215,27 @@ cpd_status read_state(cpd_ctx* c, DevState* h) {
   return CPD_OK;
 }
 
+// M-step launches of an FP32-point context, for either basis storage.
+void mstep_f32(cpd_ctx* c, const float4* R4, const float4* Yt4, float4* T4, const float4* Yhat4, float4* B4,
+               float4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  if (c->half_basis)
+    launch_mstep<float, __half>(c->mp, c->U.as<__half>(), c->Ut.as<__half>(), c->lam.as<double>(), c->M, c->K,
+                                c->X4.as<float4>(), R4, Yt4, T4, Yhat4, c->partP.as<float>(), c->sums.as<double>(),
+                                B4, C4, st, iteration, s, ev);
+  else
+    launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
+                        c->X4.as<float4>(), R4, Yt4, T4, Yhat4, c->partP.as<float>(), c->sums.as<double>(), B4, C4,
+                        st, iteration, s, ev);
+}
+
+void w_f32(cpd_ctx* c, const float4* C4, float4* W4, cudaStream_t s) {
+  if (c->half_basis)
+    launch_w<float, __half>(c->mp, c->Ut.as<__half>(), c->M, c->K, C4, c->partP.as<float>(), W4,
+                            c->st_aux.as<DevState>(), s);
+  else
+    launch_w<float>(c->mp, c->Ut.as<float>(), c->M, c->K, C4, c->partP.as<float>(), W4, c->st_aux.as<DevState>(), s);
+}
+
 // The kernels of one EM iteration, enqueued on `s` (used only under capture).
 // With `ev` (kEvPerIter = 9 events) the iteration is bracketed by timing
 // events: ev[0] before pass A, ev[1..4] after the E-step kernels, ev[5..8]
@@ -233,10 +257,8 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
     launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
                         c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
                         c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, ee);
-    launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
-                        c->X4.as<float4>(), c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
-                        c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->partP.as<float>(), c->sums.as<double>(),
-                        c->B4.as<float4>(), c->C4.as<float4>(), st, true, s, em);
+    mstep_f32(c, c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
+              c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->B4.as<float4>(), c->C4.as<float4>(), st, true, s, em);
   }
 }
 
@@ -384,7 +406,9 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   };
   c->p = *p;
   c->fp64 = p->precision == CPD_FP64;
+  c->half_basis = p->precision == CPD_MIXED;
   c->es = c->fp64 ? 8 : 4;
+  c->bes = c->fp64 ? 8 : c->half_basis ? 2 : 4;
   c->v4 = c->fp64 ? sizeof(dvec4) : sizeof(float4);
   c->M = M;
   c->K = (p->K == 0 || p->K >= M) ? M : p->K;
@@ -404,10 +428,10 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   if ((s = upload_points(c, X, M, c->X4.p, false, c->stage, c->fp64, c->stream)) != CPD_OK) return bail(s);
 
   // The long-lived basis is allocated before the setup temporaries.
-  c->mp = plan_mstep(M, c->K, c->fp64, c->sms);
+  c->mp = plan_mstep(M, c->K, c->fp64, c->sms, 128, (int)c->bes);
   c->ldU = c->mp.ldU;
-  if ((s = c->U.ensure((size_t)M * c->ldU * c->es)) != CPD_OK) return bail(s);
-  if ((s = c->Ut.ensure((size_t)c->K * c->mp.ldM * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->U.ensure((size_t)M * c->ldU * c->bes)) != CPD_OK) return bail(s);
+  if ((s = c->Ut.ensure((size_t)c->K * c->mp.ldM * c->bes)) != CPD_OK) return bail(s);
   if ((s = c->lam.ensure((size_t)c->K * sizeof(double))) != CPD_OK) return bail(s);
 
   // Eq. 11 in FP64, then Eq. 16 by the FP64 symmetric eigensolver.
@@ -444,6 +468,9 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   }
   if (c->fp64) launch_extract_basis<double>(phi.as<double>(), M, c->K, c->U.as<double>(), c->ldU, c->Ut.as<double>(),
                                             c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
+  else if (c->half_basis)
+    launch_extract_basis<__half>(phi.as<double>(), M, c->K, c->U.as<__half>(), c->ldU, c->Ut.as<__half>(),
+                                 c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
   else launch_extract_basis<float>(phi.as<double>(), M, c->K, c->U.as<float>(), c->ldU, c->Ut.as<float>(),
                                    c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
@@ -589,8 +616,7 @@ cpd_status cpd_get_W(cpd_ctx* c, void* W_out) {
   STATUS_TRY(c->W4.ensure((size_t)c->M * c->v4));
   if (c->fp64) launch_w<double>(c->mp, c->Ut.as<double>(), c->M, c->K, c->C4.as<dvec4>(), c->partP.as<double>(),
                                 c->W4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
-  else launch_w<float>(c->mp, c->Ut.as<float>(), c->M, c->K, c->C4.as<float4>(), c->partP.as<float>(),
-                       c->W4.as<float4>(), c->st_aux.as<DevState>(), c->stream);
+  else w_f32(c, c->C4.as<float4>(), c->W4.as<float4>(), c->stream);
   CUDA_TRY(cudaGetLastError());
   return download_points(c->W4.p, c->M, W_out, c->stage, c->fp64, c->stream);
 }
@@ -598,9 +624,24 @@ cpd_status cpd_get_W(cpd_ctx* c, void* W_out) {
 cpd_status cpd_get_basis(cpd_ctx* c, void* U_out, double* lam_out) {
   if (!c) return fail(CPD_EINVAL, "ctx is NULL");
   DeviceGuard guard(c->dev);
-  if (U_out)
+  if (U_out && c->half_basis) {
+    // converted to float on the device, then copied out
+    Buf tmp;
+    const bool dev_out = is_device_ptr(U_out);
+    float* dst = static_cast<float*>(U_out);
+    if (!dev_out) {
+      STATUS_TRY(tmp.ensure((size_t)c->M * c->K * sizeof(float)));
+      dst = tmp.as<float>();
+    }
+    launch_basis_to_f32(c->U.as<__half>(), c->M, c->K, c->ldU, dst, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    if (!dev_out)
+      CUDA_TRY(cudaMemcpyAsync(U_out, dst, (size_t)c->M * c->K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  } else if (U_out) {
     CUDA_TRY(cudaMemcpy2DAsync(U_out, (size_t)c->K * c->es, c->U.p, (size_t)c->ldU * c->es, (size_t)c->K * c->es,
                                (size_t)c->M, cudaMemcpyDefault, c->stream));
+  }
   if (lam_out)
     CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam.p, (size_t)c->K * sizeof(double), cudaMemcpyDefault, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -627,17 +668,15 @@ cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, v
                          c->sums.as<double>(), c->auxB4.as<dvec4>(), c->auxC4.as<dvec4>(), sa, false, c->stream);
   } else {
     launch_residual<float>(c->auxT4.as<float4>(), c->X4.as<float4>(), c->auxR4.as<float4>(), c->M, c->stream);
-    launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
-                        c->X4.as<float4>(), c->auxR4.as<float4>(), nullptr, c->auxT4.as<float4>(), nullptr, c->partP.as<float>(),
-                        c->sums.as<double>(), c->auxB4.as<float4>(), c->auxC4.as<float4>(), sa, false, c->stream);
+    mstep_f32(c, c->auxR4.as<float4>(), nullptr, c->auxT4.as<float4>(), nullptr, c->auxB4.as<float4>(),
+              c->auxC4.as<float4>(), sa, false, c->stream);
   }
   CUDA_TRY(cudaGetLastError());
   STATUS_TRY(download_points(c->auxT4.p, c->M, T_out, c->stage, c->fp64, c->stream));
   if (W_out) {
     if (c->fp64) launch_w<double>(c->mp, c->Ut.as<double>(), c->M, c->K, c->auxC4.as<dvec4>(), c->partP.as<double>(),
                                   c->auxR4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
-    else launch_w<float>(c->mp, c->Ut.as<float>(), c->M, c->K, c->auxC4.as<float4>(), c->partP.as<float>(),
-                         c->auxR4.as<float4>(), c->st_aux.as<DevState>(), c->stream);
+    else w_f32(c, c->auxC4.as<float4>(), c->auxR4.as<float4>(), c->stream);
     CUDA_TRY(cudaGetLastError());
     STATUS_TRY(download_points(c->auxR4.p, c->M, W_out, c->stage, c->fp64, c->stream));
   }
@@ -650,7 +689,9 @@ cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t
   g_err.clear();
   if (!T || !Y || !Ytil_out) return fail(CPD_EINVAL, "T, Y and Ytil_out are required");
   if (M < 1 || M > kMaxN || N < 1 || N > kMaxN) return fail(CPD_EINVAL, "M and N must be in [1, 2^30]");
-  if (precision != CPD_FP64 && precision != CPD_FP32) return fail(CPD_EINVAL, "unknown precision");
+  if (precision != CPD_FP64 && precision != CPD_FP32 && precision != CPD_MIXED)
+    return fail(CPD_EINVAL, "unknown precision");
+  if (precision == CPD_MIXED) precision = CPD_FP32;    // the mixed mode's E-step is the FP32 one
   if (!(sigma2 > 0.0) || !std::isfinite(sigma2)) return fail(CPD_EINVAL, "sigma2 must be > 0");
   if (!(w >= 0.0 && w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
   cudaStream_t s = (cudaStream_t)stream;

@@ -11,12 +11,12 @@ namespace {
 
 using namespace dev;
 
-template <typename F>
+template <typename F, typename S>
 __global__ void __launch_bounds__(kThreadsP)
-colsum(const F* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
+colsum(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
        int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
        int clear_row_flags) {
-  dev::colsum_body<F, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  dev::colsum_body<F, S, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 template <typename F>
@@ -54,10 +54,11 @@ void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int threa
 
 }  // namespace
 
-MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads) {
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads, int basis_bytes) {
   MstepPlan p{};
-  const int W = fp64 ? 4 : 8;          // columns per colsum thread (32 bytes); row strides padded to it
-  const int64_t es = fp64 ? 8 : 4;
+  const int64_t es = basis_bytes > 0 ? basis_bytes : (fp64 ? 8 : 4);
+  const int nv = es == 2 ? colsum_vectors<__half>() : 2;
+  const int W = (int)(16 * nv / es);   // columns per colsum thread; row strides padded to it
   p.ldU = cdiv(K, W) * W;
   p.ldM = cdiv(M, W) * W;
   plan_colsum(M, p.ldU, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
@@ -68,21 +69,21 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_thread
   return p;
 }
 
-template <typename F>
-void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* lam, int64_t M, int64_t K,
+template <typename F, typename S>
+void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums, typename Vec<F>::t4* B4,
                   typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev) {
   const int g = iteration ? 1 : 0;
-  colsum<F><<<dim3(pl.p_col_tiles, pl.p_row_chunks), kThreadsP, 0, s>>>(U, pl.ldU, (int)M, (int)K, R4,
+  colsum<F, S><<<dim3(pl.p_col_tiles, pl.p_row_chunks), kThreadsP, 0, s>>>(U, pl.ldU, (int)M, (int)K, R4,
                                                                       pl.p_rows_per_chunk, part, pl.ldU, st, g,
                                                                       g);
   record_after(ev, 0, s);
   diag_update<F><<<(unsigned)cdiv(K, kMRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
                                                                    B4, C4, st, g);
   record_after(ev, 1, s);
-  colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,
+  colsum<F, S><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,
                                                                       pl.e_rows_per_chunk, part, pl.ldM, st, g,
                                                                       0);
   record_after(ev, 2, s);
@@ -96,24 +97,32 @@ void launch_mstep(const MstepPlan& pl, const F* U, const F* Ut, const double* la
   record_after(ev, 3, s);
 }
 
-template <typename F>
-void launch_w(const MstepPlan& pl, const F* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
+template <typename F, typename S>
+void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
               typename Vec<F>::t4* W4, DevState* st, cudaStream_t s) {
-  colsum<F><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, C4,
+  colsum<F, S><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, C4,
                                                                       pl.e_rows_per_chunk, part, pl.ldM, st, 0, 0);
   expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
                                                             nullptr, W4, nullptr, nullptr, st, 0);
 }
 
-template void launch_mstep<float>(const MstepPlan&, const float*, const float*, const double*, int64_t, int64_t,
-                                  const float4*, const float4*, const float4*, float4*, const float4*, float*,
-                                  double*, float4*, float4*, DevState*, bool, cudaStream_t, cudaEvent_t*);
-template void launch_mstep<double>(const MstepPlan&, const double*, const double*, const double*, int64_t, int64_t,
-                                   const dvec4*, const dvec4*, const dvec4*, dvec4*, const dvec4*, double*,
-                                   double*, dvec4*, dvec4*, DevState*, bool, cudaStream_t, cudaEvent_t*);
-template void launch_w<float>(const MstepPlan&, const float*, int64_t, int64_t, const float4*, float*, float4*,
-                              DevState*, cudaStream_t);
-template void launch_w<double>(const MstepPlan&, const double*, int64_t, int64_t, const dvec4*, double*, dvec4*,
-                               DevState*, cudaStream_t);
+template void launch_mstep<float, float>(const MstepPlan&, const float*, const float*, const double*, int64_t,
+                                         int64_t, const float4*, const float4*, const float4*, float4*,
+                                         const float4*, float*, double*, float4*, float4*, DevState*, bool,
+                                         cudaStream_t, cudaEvent_t*);
+template void launch_mstep<double, double>(const MstepPlan&, const double*, const double*, const double*, int64_t,
+                                           int64_t, const dvec4*, const dvec4*, const dvec4*, dvec4*, const dvec4*,
+                                           double*, double*, dvec4*, dvec4*, DevState*, bool, cudaStream_t,
+                                           cudaEvent_t*);
+template void launch_mstep<float, __half>(const MstepPlan&, const __half*, const __half*, const double*, int64_t,
+                                          int64_t, const float4*, const float4*, const float4*, float4*,
+                                          const float4*, float*, double*, float4*, float4*, DevState*, bool,
+                                          cudaStream_t, cudaEvent_t*);
+template void launch_w<float, float>(const MstepPlan&, const float*, int64_t, int64_t, const float4*, float*,
+                                     float4*, DevState*, cudaStream_t);
+template void launch_w<double, double>(const MstepPlan&, const double*, int64_t, int64_t, const dvec4*, double*,
+                                       dvec4*, DevState*, cudaStream_t);
+template void launch_w<float, __half>(const MstepPlan&, const __half*, int64_t, int64_t, const float4*, float*,
+                                      float4*, DevState*, cudaStream_t);
 
 }  // namespace fcpd

@@ -26,6 +26,7 @@
 
 #include "common.cuh"
 
+#include <cuda_fp16.h>
 #include <math.h>
 
 namespace fcpd {
@@ -40,11 +41,39 @@ template <> struct L16<double> {
   using t = double2;
   static constexpr int W = 2;
 };
+template <> struct L16<__half> {     // FP16 basis of the mixed-precision mode
+  using t = uint4;
+  static constexpr int W = 8;
+};
 
 __device__ __forceinline__ float lane_of(const float4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 __device__ __forceinline__ double lane_of(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+// FP16 lane i of a 16-byte vector.  By default the half's exponent and
+// mantissa bits are moved to bit 13 of an FP32 word with integer operations:
+// that word holds the FP16 value times 2^-112 exactly (normal and subnormal
+// alike), and colsum_body pre-scales the other factor by 2^112, so every
+// product is the same as with a conversion instruction while the work goes
+// to the integer pipe.  FCPD_H2F_CVT selects the conversion instruction.
+__device__ __forceinline__ float lane_of(const uint4& v, int i) {
+  const unsigned int w = i < 2 ? v.x : i < 4 ? v.y : i < 6 ? v.z : v.w;
+#ifdef FCPD_H2F_CVT
+  const __half2 h = *reinterpret_cast<const __half2*>(&w);
+  return (i & 1) ? __high2float(h) : __low2float(h);
+#else
+  const unsigned int b = (i & 1) ? (((w >> 3) & 0x0FFFE000u) | (w & 0x80000000u))
+                                 : (((w << 13) & 0x0FFFE000u) | ((w << 16) & 0x80000000u));
+  return __uint_as_float(b);
+#endif
+}
+// Factor that undoes lane_of's 2^-112 inside each product (1 where lane_of
+// is exact).  The products u * (v * 2^112) then equal u * v exactly; this
+// relies on FP32 subnormals not being flushed (no -ftz / fast-math).
+template <typename S> __device__ __forceinline__ float lane_scale() { return 1.0f; }
+#ifndef FCPD_H2F_CVT
+template <> __device__ __forceinline__ float lane_scale<__half>() { return 0x1p112f; }
+#endif
 
 constexpr int kThreadsP = 128;   // streaming kernel block
 constexpr int kRTile = 256;      // rows of V staged per shared-memory tile
@@ -57,17 +86,31 @@ constexpr int kMRedSub = kThreadsD / kMRedCols;
 static_assert(kMRedCols * kMRedSub == kThreadsD, "columns per block must divide the block");
 
 // ---------------------------------------------------------------- colsum
-template <typename F, int THREADS>
-__device__ __forceinline__ void colsum_body(const F* FCPD_RESTRICT A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* FCPD_RESTRICT V,
+// 16-byte vectors of A per thread and row (the plan pads rows to this):
+// two (32 bytes) for FP32/FP64; one (8 columns) for an FP16 basis, whose
+// threads do twice the arithmetic per byte -- measured at M = N = 20000:
+// 5.0 TB/s with one vector, 3.6 TB/s with two.
+#ifndef FCPD_COLSUM_VEC_H
+#define FCPD_COLSUM_VEC_H 1
+#endif
+template <typename S> __host__ __device__ constexpr int colsum_vectors() {
+  return sizeof(S) == 2 ? FCPD_COLSUM_VEC_H : 2;
+}
+
+// S is the storage type of A (F itself, or FP16 for a basis stored in half
+// precision); products and sums are in F.
+template <typename F, typename S, int THREADS>
+__device__ __forceinline__ void colsum_body(const S* FCPD_RESTRICT A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* FCPD_RESTRICT V,
        int rows_per_chunk, F* FCPD_RESTRICT part, int64_t ldP, DevState* FCPD_RESTRICT st, int gate,
        int clear_row_flags, int bx, int by, int gx, int gy) {
   if (gate && iteration_gated(st)) return;
   // the E-step's row list was consumed by fixB before this kernel
   if (clear_row_flags && bx == 0 && by == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
   using V4 = typename Vec<F>::t4;
-  using LT = typename L16<F>::t;
-  constexpr int L = L16<F>::W;           // elements per 16-byte vector
-  constexpr int W = 2 * L;               // columns per thread
+  using LT = typename L16<S>::t;
+  constexpr int L = L16<S>::W;           // elements per 16-byte vector
+  constexpr int NV = colsum_vectors<S>();
+  constexpr int W = NV * L;              // columns per thread (NV x 16 bytes of A per row)
   __shared__ V4 sV[kRTile];
   const int c0 = (bx * THREADS + threadIdx.x) * W;
   const int r0 = by * rows_per_chunk;
@@ -78,18 +121,25 @@ __device__ __forceinline__ void colsum_body(const F* FCPD_RESTRICT A, int64_t ld
   for (int base = r0; base < r1; base += kRTile) {
     const int cnt = min(kRTile, r1 - base);
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += THREADS) sV[i] = V[base + i];
+    for (int i = threadIdx.x; i < cnt; i += THREADS) {
+      V4 v = V[base + i];
+      if constexpr (sizeof(S) == 2) {          // exact power-of-two pre-scale (see lane_of)
+        const F k = (F)lane_scale<S>();
+        v.x *= k; v.y *= k; v.z *= k;
+      }
+      sV[i] = v;
+    }
     __syncthreads();
     if (c0 < cols) {
-      const F* ap = A + (size_t)base * ldA + c0;
+      const S* ap = A + (size_t)base * ldA + c0;
 #pragma unroll 4
       for (int i = 0; i < cnt; ++i) {
         const LT* row = reinterpret_cast<const LT*>(ap + (size_t)i * ldA);
-        const LT u0 = __ldg(row), u1 = __ldg(row + 1);
+        const LT u0 = __ldg(row), u1 = NV > 1 ? __ldg(row + 1) : u0;
         const V4 r = sV[i];
 #pragma unroll
         for (int w = 0; w < W; ++w) {
-          const F uw = w < L ? lane_of(u0, w) : lane_of(u1, w - L);
+          const F uw = (F)(w < L ? lane_of(u0, w) : lane_of(u1, w - L));
           acc[w][0] = fma(uw, r.x, acc[w][0]);
           acc[w][1] = fma(uw, r.y, acc[w][1]);
           acc[w][2] = fma(uw, r.z, acc[w][2]);
@@ -101,12 +151,15 @@ __device__ __forceinline__ void colsum_body(const F* FCPD_RESTRICT A, int64_t ld
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       F* out = part + ((size_t)by * 3 + d) * ldP + c0;
-      if constexpr (L == 4) {
-        reinterpret_cast<float4*>(out)[0] = make_float4(acc[0][d], acc[1][d], acc[2][d], acc[3][d]);
-        reinterpret_cast<float4*>(out)[1] = make_float4(acc[4][d], acc[5][d], acc[6][d], acc[7][d]);
+      if constexpr (sizeof(F) == 4) {
+#pragma unroll
+        for (int v = 0; v < W / 4; ++v)
+          reinterpret_cast<float4*>(out)[v] =
+              make_float4(acc[4 * v][d], acc[4 * v + 1][d], acc[4 * v + 2][d], acc[4 * v + 3][d]);
       } else {
-        reinterpret_cast<double2*>(out)[0] = make_double2(acc[0][d], acc[1][d]);
-        reinterpret_cast<double2*>(out)[1] = make_double2(acc[2][d], acc[3][d]);
+#pragma unroll
+        for (int v = 0; v < W / 2; ++v)
+          reinterpret_cast<double2*>(out)[v] = make_double2(acc[2 * v][d], acc[2 * v + 1][d]);
       }
     }
   }

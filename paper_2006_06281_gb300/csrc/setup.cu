@@ -51,6 +51,9 @@ __global__ void gram_f64(const V4* __restrict__ X4, int M, double inv2b2, double
 // a column-major M x M matrix V.  The basis kept here is descending (Eq. 19
 // keeps the K largest), stored row-major: U[m * ldU + k] = V[m, M-1-k], with
 // zero padding for K <= k < ldU.  Tiled transpose through shared memory.
+template <typename F> __device__ __forceinline__ F to_basis(double v) { return (F)v; }
+template <> __device__ __forceinline__ __half to_basis<__half>(double v) { return __double2half(v); }
+
 template <typename F>
 __global__ void extract_basis(const double* __restrict__ V, int M, int K, F* __restrict__ U, int64_t ldU) {
   __shared__ double tile[32][33];
@@ -65,7 +68,7 @@ __global__ void extract_basis(const double* __restrict__ V, int M, int K, F* __r
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int m = m0 + r, k = k0 + threadIdx.x;
-    if (m < M && k < ldU) U[(size_t)m * ldU + k] = (F)tile[threadIdx.x][r];
+    if (m < M && k < ldU) U[(size_t)m * ldU + k] = to_basis<F>(tile[threadIdx.x][r]);
   }
 }
 
@@ -76,7 +79,7 @@ __global__ void extract_basis_t(const double* __restrict__ V, int M, int K, F* _
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)K * ldM) return;
   const int k = (int)(i / ldM), m = (int)(i % ldM);
-  Ut[i] = m < M ? (F)V[(size_t)(M - 1 - k) * M + m] : (F)0;
+  Ut[i] = to_basis<F>(m < M ? V[(size_t)(M - 1 - k) * M + m] : 0.0);
 }
 
 __global__ void extract_lambda(const double* __restrict__ w, int M, int K, double* __restrict__ lam) {
@@ -208,6 +211,18 @@ template void launch_residual<float>(const float4*, const float4*, float4*, int6
 template void launch_residual<double>(const dvec4*, const dvec4*, dvec4*, int64_t, cudaStream_t);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s) { state_init<<<1, 1, 0, s>>>(st, sigma2); }
 
+namespace {
+__global__ void basis_to_f32(const __half* __restrict__ U, int64_t M, int64_t K, int64_t ldU, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * K) return;
+  out[i] = __half2float(U[(i / K) * ldU + i % K]);
+}
+}  // namespace
+
+void launch_basis_to_f32(const __half* U, int64_t M, int64_t K, int64_t ldU, float* out, cudaStream_t s) {
+  basis_to_f32<<<(unsigned)cdiv(M * K, kThreads), kThreads, 0, s>>>(U, M, K, ldU, out);
+}
+
 template void launch_pack<float>(const float*, int64_t, float4*, bool, cudaStream_t);
 template void launch_pack<double>(const double*, int64_t, dvec4*, bool, cudaStream_t);
 template void launch_unpack<float>(const float4*, int64_t, float*, cudaStream_t);
@@ -215,6 +230,8 @@ template void launch_unpack<double>(const dvec4*, int64_t, double*, cudaStream_t
 template void launch_extract_basis<float>(const double*, int64_t, int64_t, float*, int64_t, float*, int64_t,
                                           const double*, double*, cudaStream_t);
 template void launch_extract_basis<double>(const double*, int64_t, int64_t, double*, int64_t, double*, int64_t,
+                                           const double*, double*, cudaStream_t);
+template void launch_extract_basis<__half>(const double*, int64_t, int64_t, __half*, int64_t, __half*, int64_t,
                                            const double*, double*, cudaStream_t);
 template void launch_sigma2_init<float>(const float4*, int64_t, const float4*, int64_t, double*, DevState*,
                                         cudaStream_t);

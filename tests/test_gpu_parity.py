@@ -408,3 +408,42 @@ def test_full_size_first_iteration_properties(big, K):
         assert np.linalg.norm(res) <= 1e-4 * np.linalg.norm(R[rows])
     s1_ref = oracle.sigma2_update(o["S"], o["P1"], o["Ytil"], T)
     assert s1 == pytest.approx(s1_ref, rel=1e-4)
+
+
+# ------------------------------------------- mixed precision (FP16 basis)
+# CPD_MIXED stores U and U^T in FP16 (products and sums in FP32).  Its error
+# against the FP64 oracle is measured, stated and bounded here by what FP16
+# storage implies: each basis element carries a relative rounding error of at
+# most 2^-11, the displacement T - X = U s U^T R inherits about that relative
+# error, and the displacement is ~0.15 of |T|; so T's relative error should
+# stay near 2^-11 * 0.15 ~ 7e-5, bounded here at 3e-4.
+MIXED_TOL = 3e-4
+
+
+@pytest.mark.parametrize("K,iters", [(0, 100), (200, 60)])
+def test_mixed_precision_register_against_oracle(K, iters):
+    cfg = datagen.WORKLOADS["fp32_m5000"]
+    ps = pointsets(cfg["M"], amp=cfg["amp"], seed=cfg["seed"])
+    X, Y = ps.X.astype(np.float32), ps.Y.astype(np.float32)
+    ref = oracle.register(X, Y, w=cfg["omega"], beta=cfg["beta"], lam_reg=cfg["lam"], n_iter=iters, K=K)
+    Tm, s2m, it, _ = run_gpu(X, Y, cpd.MIXED, iters, K=K, w=cfg["omega"], lam=cfg["lam"], beta=cfg["beta"])
+    T32, s232, _, _ = run_gpu(X, Y, cpd.FP32, iters, K=K, w=cfg["omega"], lam=cfg["lam"], beta=cfg["beta"])
+    err_m, err_32 = rel(Tm, ref["T"]), rel(T32, ref["T"])
+    print(f"K={K}: relative error of T vs the FP64 oracle: mixed {err_m:.2e}, fp32 {err_32:.2e}")
+    assert it == iters
+    assert err_m <= MIXED_TOL
+    assert s2m == pytest.approx(ref["sigma2"], rel=sigma2_tol(MIXED_TOL, ref["T"], ref["sigma2"]))
+
+
+def test_mixed_precision_basis_is_the_fp16_rounding_of_the_fp32_basis():
+    ps = pointsets(700, seed=9)
+    X = dev(ps.X, cpd.FP32)
+    with cpd.Context(X, precision=cpd.MIXED, K=64) as cm, cpd.Context(X, precision=cpd.FP32, K=64) as c32:
+        Um, lm = cm.basis()
+        U32, l32 = c32.basis()
+    Um, U32 = host(Um), host(U32)
+    np.testing.assert_array_equal(lm, l32)
+    # FP16 rounding of the FP32 values (subnormal FP16 below 2^-14 has an
+    # absolute step of 2^-24)
+    np.testing.assert_allclose(Um, U32, rtol=2.0 ** -11, atol=2.0 ** -24)
+    assert np.abs(Um - U32).max() > 0      # it is really stored in FP16
