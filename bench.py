@@ -43,7 +43,7 @@ UNIT = "EM iters/s"
 PAPER_ITERS_PER_S = 50.0 / (988.430 - 502.663)
 RMSE_TARGET = 5e-3
 ITERS_PER_REGISTRATION = 100
-STATE_BYTES = 136          # sizeof(DevState), read back with sigma2 by cpd_iterate
+STATE_BYTES = 160          # sizeof(DevState), read back with sigma2 by cpd_iterate
 
 
 def parse():
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowrank", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-basis (CPD_MIXED) section")
+    ap.add_argument("--prune", action="store_true",
+                    help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--batch", default="fp32_batch256_m500_3000_k128",
                     help="batched-registration workload to time as well ('none' skips it)")
@@ -565,6 +567,38 @@ def main():
                      note="error against the FP64 oracle is measured in tests/test_gpu_parity.py "
                           "(test_mixed_precision_register_against_oracle, M = N = 5000)")
 
+    # exact pruning (CPD_FLAG_PRUNE), same pair and registration: rate, the
+    # evaluated fraction of Gaussian pairs per iteration, and T against the
+    # default (dense) path's
+    prune = None
+    if args.prune and cfg["K"] == 0:
+        t0 = time.perf_counter()
+        cp = cpd.Context(X, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0,
+                         flags=cpd.FLAG_PRUNE)
+        psetup = time.perf_counter() - t0
+        cp.reset()
+        cp.iterate_profiled(Y, I)
+        torch.cuda.synchronize()
+        ph = np.zeros(9)
+        npr = max(1, min(R, 10))
+        a.record()
+        for _ in range(npr):
+            cp.reset()
+            ph += np.array(cp.iterate_profiled(Y, I)) / npr
+        b.record()
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        cp.reset()
+        Tp, s2p, itp = cp.iterate(Y, I)
+        frac = cp.work(itp)
+        cp.close()
+        dp = (T32.double() - Tp.double()).norm().item() / T32.double().norm().item()
+        prune = dict(flags="CPD_FLAG_PRUNE", iters_per_s=npr * I / (pms / 1e3), setup_s=psetup,
+                     kernel_ms={k: v["ms"] for k, v in roofline_entries(ph, M, N, K, peaks).items()},
+                     evaluated_fraction=dict(mean=float(frac.mean()), first=float(frac[0]), last=float(frac[-1]),
+                                             pruned_iterations=int((frac < 1).sum()), of=int(itp)),
+                     rel_diff_T_vs_dense=dp)
+
     batch = None
     if world == 1 and args.batch != "none":
         batch = run_batch(args, peaks, torch)
@@ -585,7 +619,8 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, setup_s=setup_s, batch=batch,
+                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, setup_s=setup_s,
+                    batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "
                                   "(Table IV, MATLAB on an i7-8750H CPU): context, not a like-for-like target")
         print(json.dumps(line), flush=True)

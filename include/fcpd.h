@@ -94,10 +94,31 @@ typedef struct {
                              1..M-1: the K largest eigenpairs (Eq. 19-20);
                              K > M is rejected with CPD_EINVAL                 */
     int32_t max_iter;     /* iteration count used by cpd_register (> 0)        */
-    int32_t flags;        /* reserved, must be 0                               */
+    int32_t flags;        /* cpd_flags bits (0 = default)                      */
     double  tol;          /* > 0: stop once RMS_m |T_k - T_(k-1)| <= tol;
                              0: run the requested number of iterations        */
 } cpd_params;
+
+/*
+ * cpd_params.flags (0 = default: the points in the caller's order, the dense
+ * E-step).  With CPD_FLAG_PRUNE an FP32 or mixed context keeps its model
+ * points (and every scene) in spatial order -- a 12-bit Morton order, sorted
+ * on the device, stable -- and, once sigma2 is small enough that far tile
+ * pairs of points have FP32 Gaussians that are exactly 0 (ex2 results below
+ * 2^-126 flush to 0), its E-step skips those tile pairs: the sums are
+ * bit-identical to evaluating them.  All arrays a caller passes or receives
+ * stay in the caller's order.  Point sets larger than 2^20 are not sorted
+ * (no pruning).  Pruning pays once sigma2 has collapsed to the noise level;
+ * while it has not, the idle pruned launches cost a few microseconds per
+ * pass, so it is not the default.
+ */
+typedef enum {
+    CPD_FLAG_PRUNE = 1,          /* spatial order + exact pruning of the FP32 E-step       */
+    CPD_FLAG_PRUNE_ALWAYS = 2,   /* (implies PRUNE) pruned layout in every iteration       */
+    CPD_FLAG_PRUNE_NOSKIP = 4    /* (implies PRUNE) pruned layout, every tile pair
+                                    evaluated: the same sums as skipping, bit for bit
+                                    (verification)                                        */
+} cpd_flags;
 
 typedef struct cpd_ctx cpd_ctx;   /* opaque; owned by the library */
 
@@ -262,6 +283,17 @@ cpd_status cpd_estep_noalloc(const void *T, int64_t M, const void *Y, int64_t N,
 cpd_status cpd_register(const void *X, int64_t M, const void *Y, int64_t N, const cpd_params *p,
                         void *stream, void *T_out, void *W_out, double *sigma2_out,
                         int32_t *iters_done);
+
+/*
+ * Work of the pruned E-step: eval_frac[k] (k < n, host) is the fraction of
+ * the 2 M N Gaussian pairs of passes A and B that iteration k+1 evaluated
+ * (1 for dense iterations).  Synchronises.  CPD_EINVAL if n exceeds the
+ * iterations run.
+ */
+cpd_status cpd_get_work(cpd_ctx *ctx, int32_t n, double *eval_frac);
+
+/* 1 if the context keeps its points in spatial order (pruning possible). */
+int32_t cpd_spatial_order(const cpd_ctx *ctx);
 
 /* Free a context (NULL is ignored).  Synchronises its stream first. */
 void cpd_destroy(cpd_ctx *ctx);

@@ -25,12 +25,13 @@ FP64, FP32, MIXED = 0, 1, 2    # MIXED: FP32 points and E-step, FP16 eigenbasis
 STATUS = {0: "CPD_OK", 1: "CPD_EINVAL", 2: "CPD_ENOMEM", 3: "CPD_ECUDA", 4: "CPD_ESOLVER",
           5: "CPD_ENUMERIC", 6: "CPD_ETIMEOUT", 7: "CPD_ESTATE"}
 OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
+FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP = 1, 2, 4
 
 # Every symbol include/fcpd.h declares (checked by the tests).
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
-           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_destroy",
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
            "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_destroy"]
 
@@ -83,6 +84,8 @@ def load():
                 "cpd_estep_noalloc": ([vp, i64, vp, i64, d, d, vp, vp, vp, dp, vp], C.c_int),
                 "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
                 "cpd_destroy": ([vp], None),
+                "cpd_get_work": ([vp, i32, vp], C.c_int),
+                "cpd_spatial_order": ([vp], i32),
                 "cpd_batch_create": ([i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64), pp, d, vp,
                                       C.POINTER(vp)], C.c_int),
                 "cpd_batch_iterate": ([vp, i32], C.c_int),
@@ -155,11 +158,11 @@ def _stream_handle(stream, cuda):
 
 
 def make_params(precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, max_iter=50, tol=0.0,
-                sigma2_init=0.0) -> CpdParams:
+                sigma2_init=0.0, flags=0) -> CpdParams:
     p = CpdParams()
     load().cpd_params_default(C.byref(p))
     p.precision, p.w, p.beta, p.lam, p.K = int(precision), float(w), float(beta), float(lam), int(K)
-    p.max_iter, p.tol, p.sigma2_init = int(max_iter), float(tol), float(sigma2_init)
+    p.max_iter, p.tol, p.sigma2_init, p.flags = int(max_iter), float(tol), float(sigma2_init), int(flags)
     return p
 
 
@@ -168,18 +171,19 @@ class Context:
     then EM iterations against one or more scenes."""
 
     def __init__(self, X, precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, tol=0.0, sigma2_init=0.0,
-                 stream=None):
+                 stream=None, flags=0):
         lib = load()
         self.precision = precision
         self._X, px, self.cuda = _prep(X, precision, "X")
         self.device = self._X.device if self.cuda else None
         self.M = int(self._X.shape[0])
         self.stream = _stream_handle(stream, self.cuda)
-        self.params = make_params(precision, w, beta, lam, K, 0, tol, sigma2_init)
+        self.params = make_params(precision, w, beta, lam, K, 0, tol, sigma2_init, flags)
         h = C.c_void_p()
         _check(lib.cpd_setup(px, self.M, C.byref(self.params), self.stream, C.byref(h)))
         self._h = h
         self.K = int(lib.cpd_basis_rank(h))
+        self.spatial_order = bool(lib.cpd_spatial_order(h))
 
     def iterate(self, Y, n_iter, want_T=True):
         """Runs n_iter EM iterations; returns (T or None, sigma2, iterations so far)."""
@@ -238,6 +242,12 @@ class Context:
         W, pw = _out_like(self.M, 3, self.precision, self.cuda, self.device)
         _check(load().cpd_get_W(self._h, pw))
         return W
+
+    def work(self, n):
+        """Fraction of the 2 M N Gaussian pairs evaluated by each of the first n iterations."""
+        out = np.empty(n)
+        _check(load().cpd_get_work(self._h, int(n), out.ctypes.data))
+        return out
 
     def basis(self):
         U = np.empty((self.M, self.K), dtype=_dtype_of(self.precision))
@@ -410,7 +420,7 @@ def estep_noalloc(T, Y, sigma2, w, stream=None):
 
 
 def register(X, Y, precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, max_iter=50, tol=0.0,
-             sigma2_init=0.0, want_W=False, stream=None):
+             sigma2_init=0.0, want_W=False, stream=None, flags=0):
     """Whole registration through cpd_register.  Returns (T, W or None, sigma2, iters)."""
     Xk, px, xcuda = _prep(X, precision, "X")
     Yk, py, _ = _prep(Y, precision, "Y")
@@ -418,7 +428,7 @@ def register(X, Y, precision=FP32, w=0.1, beta=2.0, lam=2.0, K=0, max_iter=50, t
     dev = Xk.device if xcuda else None
     T, pt = _out_like(M, 3, precision, xcuda, dev)
     W, pw = _out_like(M, 3, precision, xcuda, dev) if want_W else (None, None)
-    p = make_params(precision, w, beta, lam, K, max_iter, tol, sigma2_init)
+    p = make_params(precision, w, beta, lam, K, max_iter, tol, sigma2_init, flags)
     s2, it = C.c_double(0), C.c_int32(0)
     _check(load().cpd_register(px, M, py, int(Yk.shape[0]), C.byref(p), _stream_handle(stream, xcuda),
                                pt, pw, C.byref(s2), C.byref(it)))

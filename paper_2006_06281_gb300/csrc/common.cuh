@@ -57,7 +57,7 @@ struct DevState {
   double tol;           // RMS(T_k - T_(k-1)) stop threshold (0: off)
   double gt_tol;        // RMSE stop threshold (0: off)
   double vsum;          // sum_m V_m / P1_m of the last E-step (Eq. 18 numerator at T)
-  double* hist;         // 3 x kHistCap: sigma2, log-likelihood, RMSE per iteration
+  double* hist;         // 4 x kHistCap: sigma2, log-likelihood, RMSE, evaluated-pair fraction per iteration
   int iter;             // iterations completed
   int iter_target;      // iterations run until iter == iter_target
   int status;           // cpd_status of a device-side failure (0 = none)
@@ -70,9 +70,28 @@ struct DevState {
   unsigned int ticket_b;
   unsigned int ticket_m;
   unsigned int ticket_e;
+  unsigned long long pairs_eval;  // Gaussian pairs evaluated by the pruned passes this iteration
+  double last_eval_frac;          // fraction of the 2 M N pairs of passes A+B evaluated last iteration
+  float prune_r2;                 // pruned passes run while 127 / kappa (FP32 cutoff radius^2) < this
+  int prune_ctl;                  // kPrune* bits (0: dense passes only)
 };
 
-static_assert(sizeof(DevState) == 136, "DevState layout changed: update the benchmark's transfer count");
+static_assert(sizeof(DevState) == 160, "DevState layout changed: update the benchmark's transfer count");
+
+// DevState::prune_ctl bits.
+constexpr int kPruneAllowed = 1;   // points are in spatial order: the pruned passes may run
+constexpr int kPruneAlways = 2;    // run the pruned passes whatever sigma2 (verification)
+constexpr int kPruneNoSkip = 4;    // pruned passes evaluate every tile pair (verification)
+
+// The pruned passes' layout is used this iteration (same answer in every
+// kernel of an E-step: sigma2 does not change within it).
+__device__ __forceinline__ bool prune_active(const DevState* st) {
+  const int c = st->prune_ctl;
+  if (!(c & kPruneAllowed)) return false;
+  if (c & kPruneAlways) return true;
+  const double r2 = 127.0 * 2.0 * st->sigma2 / 1.4426950408889634;   // 127 / kappa, kappa = log2(e) / (2 sigma2)
+  return r2 < (double)st->prune_r2;
+}
 
 // True when the current iteration must not run (target reached, converged,
 // or a device failure recorded).  Read once per block at kernel entry.
@@ -104,6 +123,26 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// ---------------------------------------------------------- spatial order
+// Largest point set the spatial sort handles (larger sets stay unsorted and
+// the E-step does not prune).
+constexpr int64_t kMaxSortPoints = (int64_t)1 << 20;
+bool spatial_sort_supported(int64_t n);
+int64_t spatial_sort_scratch_bytes(int64_t n);
+// out[s] = in[perm[s]] in Morton order (stable); perm may be null.
+cudaError_t launch_spatial_sort(const float4* in, int64_t n, float4* out, int* perm, void* scratch, cudaStream_t s);
+void launch_invert_perm(const int* perm, int64_t n, int* inv, cudaStream_t s);
+// dst[s] = (src point perm[s], |.|^2 or 0): caller order -> sorted order
+template <typename F>
+void launch_pack_gather(const F* src, const int* perm, int64_t n, typename Vec<F>::t4* dst, bool with_norm,
+                        cudaStream_t s);
+// dst point i = src[inv[i]]: sorted order -> caller order
+template <typename F>
+void launch_unpack_gather(const typename Vec<F>::t4* src, const int* inv, int64_t n, F* dst, cudaStream_t s);
+// dst row i (cols floats) = src row inv[i] (stride ld_src)
+void launch_gather_rows_f32(const float* src, int64_t ld_src, const int* inv, int64_t n, int64_t cols, float* dst,
+                            cudaStream_t s);
+
 // Message returned by cpd_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 
@@ -115,8 +154,13 @@ struct EstepPlan {
   int64_t redA_blocks, redB_blocks;                  // reduce grids
   int64_t sums_elems;                                // double scratch for block sums
   int64_t flags_elems;                               // int scratch: flagged rows + columns
+  // pruned FP32 layout (spatially ordered inputs; see estep_dev.cuh)
+  bool pruned;                                       // launch the pruned passes too
+  int pa_col_tiles, pa_row_chunks, pa_rows_per_chunk;
+  int pb_row_tiles, pb_col_chunks, pb_cols_per_chunk;
 };
-EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms);
+// with_pruned: also plan the pruned FP32 layout (partial buffers sized for both).
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned = false);
 
 struct MstepPlan {
   int64_t ldU, ldM;                                  // row strides of U (M x ldU) and U^T (K x ldM)
@@ -254,6 +298,8 @@ template <typename F>
 void launch_unpack(const typename Vec<F>::t4* src, int64_t n, F* dst, cudaStream_t s);
 void launch_begin_iterations(DevState* st, int n_iter, cudaStream_t s);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s);
+// Pruning configuration of a context (kept across state_init, which turns it off).
+void launch_state_prune(DevState* st, float prune_r2, int prune_ctl, cudaStream_t s);
 void launch_state_params(DevState* st, double w, double lambda, double tol, double gt_tol, int has_gt,
                          double* hist, int64_t M, int64_t N, int64_t K, cudaStream_t s);
 template <typename F>

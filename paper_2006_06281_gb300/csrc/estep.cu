@@ -11,10 +11,21 @@ namespace {
 
 using namespace dev;
 
+// The dense FP32 passes step aside (return at once) in iterations that use
+// the pruned layout, and the pruned ones in all others; both are in every
+// captured iteration.
 __global__ void __launch_bounds__(kThreadsA)
 passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
           int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
+  if (prune_active(st)) return;
   dev::passA_f32_body(T4, M, rows_per_chunk, Y4, N, partA, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+__global__ void __launch_bounds__(kThreadsA)
+passA_f32_pruned(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
+                 int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
+  if ((gate && iteration_gated(st)) || !prune_active(st)) return;
+  dev::passA_f32_pruned_body(T4, M, rows_per_chunk, Y4, N, partA, st, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(kThreadsA)
@@ -23,12 +34,14 @@ passA_f64(const dvec4* __restrict__ T4, int M, int rows_per_chunk, const dvec4* 
   dev::passA_f64_body(T4, M, rows_per_chunk, Y4, N, partA, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
+// chunks_pruned: chunk count of the pruned layout (used when it ran).
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
-reduceA(const F* __restrict__ partA, int chunks, int M, const typename Vec<F>::t4* __restrict__ Y4,
+reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int M, const typename Vec<F>::t4* __restrict__ Y4,
         int N, typename Vec<F>::t4* __restrict__ Yb, double* __restrict__ den_out,
         double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
-  dev::reduceA_body<F>(partA, chunks, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  const int ch = prune_active(st) ? chunks_pruned : chunks;
+  dev::reduceA_body<F>(partA, ch, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 __global__ void __launch_bounds__(kThreadsF)
@@ -41,7 +54,15 @@ fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, in
 __global__ void __launch_bounds__(kThreadsB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
           int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
+  if (prune_active(st)) return;
   dev::passB_f32_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+__global__ void __launch_bounds__(kThreadsB)
+passB_f32_pruned(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
+                 int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
+  if ((gate && iteration_gated(st)) || !prune_active(st)) return;
+  dev::passB_f32_pruned_body(T4, M, Yb, N, cols_per_chunk, partB, st, blockIdx.x, blockIdx.y, gridDim.y);
 }
 
 __global__ void __launch_bounds__(kThreadsB)
@@ -52,11 +73,12 @@ passB_f64(const dvec4* __restrict__ T4, int M, const dvec4* __restrict__ Yb, int
 
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
-reduceB(const F* __restrict__ partB, int chunks, int M, const typename Vec<F>::t4* __restrict__ X4,
+reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int M, const typename Vec<F>::t4* __restrict__ X4,
         typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
         double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
         DevState* __restrict__ st, int gate) {
-  dev::reduceB_body<F>(partB, chunks, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  const int ch = prune_active(st) ? chunks_pruned : chunks;
+  dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 __global__ void __launch_bounds__(kThreadsF)
@@ -73,7 +95,7 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Grids for passes A and B: all blocks resident in one wave (blocks <= SMs x
 // resident blocks per SM from the occupancy calculator), with the split of
 // the long dimension chosen so every block gets the same amount of work.
-EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms) {
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned) {
   EstepPlan p{};
   int occA = 0, occB = 0;
   if (fp64) {
@@ -99,6 +121,24 @@ EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms) {
   p.b_col_chunks = (int)cdiv(N, cpc);
   p.partA_elems = (int64_t)p.a_row_chunks * N;
   p.partB_elems = (int64_t)5 * p.b_col_chunks * M;
+  // pruned layout: 1024-point tiles of the owning set; pass A chunks of 256
+  // model rows, pass B chunks of 512 scene points (2 and 4 shared tiles):
+  // small enough that work concentrates where the boxes meet, and the
+  // hardware block scheduler balances the many short blocks.
+  p.pruned = with_pruned && !fp64;
+  p.pa_col_tiles = (int)cdiv(N, kPruneTile);
+  p.pa_rows_per_chunk = 2 * kTileA;
+  p.pa_row_chunks = (int)cdiv(M, p.pa_rows_per_chunk);
+  p.pb_row_tiles = (int)cdiv(M, kPruneTile);
+  p.pb_cols_per_chunk = 4 * kTileB;
+  p.pb_col_chunks = (int)cdiv(N, p.pb_cols_per_chunk);
+  if (p.pruned) {
+    p.partA_elems = std::max(p.partA_elems, (int64_t)p.pa_row_chunks * N);
+    p.partB_elems = std::max(p.partB_elems, (int64_t)5 * p.pb_col_chunks * M);
+  } else {
+    p.pa_row_chunks = p.a_row_chunks;          // never used: prune_active is false
+    p.pb_col_chunks = p.b_col_chunks;
+  }
   p.redA_blocks = cdiv(N, kRedCols);
   p.redB_blocks = cdiv(M, kRedRows);
   p.sums_elems = std::max(p.redA_blocks, p.redB_blocks);
@@ -119,24 +159,30 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   int* flag_cols = flags + M;
   if constexpr (sizeof(F) == 4) {
     passA_f32<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
+    if (pl.pruned)
+      passA_f32_pruned<<<dim3(pl.pa_col_tiles, pl.pa_row_chunks), kThreadsA, 0, s>>>(
+          T4, (int)M, pl.pa_rows_per_chunk, Y4, (int)N, partA, st, g);
   } else {
     passA_f64<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
   }
   record_after(ev, 0, s);
-  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, (int)M, Y4, (int)N, Yb,
-                                                            den_out, sums, flag_cols, st, g);
+  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, (int)M, Y4,
+                                                            (int)N, Yb, den_out, sums, flag_cols, st, g);
   if constexpr (sizeof(F) == 4) {
     fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
   }
   record_after(ev, 1, s);
   if constexpr (sizeof(F) == 4) {
     passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+    if (pl.pruned)
+      passB_f32_pruned<<<dim3(pl.pb_row_tiles, pl.pb_col_chunks), kThreadsB, 0, s>>>(
+          T4, (int)M, Yb, (int)N, pl.pb_cols_per_chunk, partB, st, g);
   } else {
     passB_f64<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
   }
   record_after(ev, 2, s);
-  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, (int)M, X4, Yt4, R4,
-                                                            P1_out, sums, flag_rows, st, g);
+  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, (int)M, X4,
+                                                            Yt4, R4, P1_out, sums, flag_rows, st, g);
   if constexpr (sizeof(F) == 4) {
     fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
   }

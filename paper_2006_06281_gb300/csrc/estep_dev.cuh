@@ -485,6 +485,279 @@ __device__ __forceinline__ void passB_f32_body(const float4* FCPD_RESTRICT T4, i
   }
 }
 
+// ------------------------------------------------ pruned FP32 passes (exact)
+// With model and scene points in spatial (Morton) order, each warp owns 128
+// consecutive points (4 per thread), so its points fill a small box.  Before
+// a shared tile of 128 points of the other set is used, each warp bounds the
+// tile pair's exponents by the boxes (per 32-point sub-tile of the staged
+// tile): in pass A every exponent is
+// -|y' - t'|^2 <= -gap^2, in pass B lid_n - |y' - t'|^2 <= max lid - gap^2
+// (gap: distance between the boxes of the scaled points).  ex2.approx.ftz
+// returns exactly 0 for exponents below -126 (the result would be
+// subnormal), so a tile pair whose bound is below -kPruneExp contributes
+// exactly nothing and is skipped: the sums are bit-identical to evaluating
+// it.  kPruneExp keeps one unit of margin for the FP32 rounding of the
+// scaled coordinates and of the distances (relative 1e-6 of 127).
+constexpr float kPruneExp = 127.0f;
+constexpr int kPrunePts = 4;                          // points per thread
+constexpr int kPruneWarpPts = 32 * kPrunePts;         // consecutive points per warp
+constexpr int kPruneTile = kThreadsA * kPrunePts;     // points per block tile (1024)
+static_assert(kThreadsA == kThreadsB && kTileA == 128 && kTileB == 128, "pruned passes: 256-thread blocks, 128-point tiles");
+
+__shared__ float s_prune_box[4][8];                   // per staging warp: lo[3], hi[3], max lid
+
+__device__ __forceinline__ void warp_box(float (&lo)[3], float (&hi)[3]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+    }
+}
+
+// Squared gap between two boxes (INF if either is empty).
+__device__ __forceinline__ float box_gap2(const float (&alo)[3], const float (&ahi)[3], const float (&blo)[3],
+                                          const float (&bhi)[3]) {
+  float g2 = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float g = fmaxf(0.f, fmaxf(alo[d] - bhi[d], blo[d] - ahi[d]));
+    g2 = fmaf(g, g, g2);
+  }
+  return g2;
+}
+
+// Staged tile boxes: threads < 128 hold one point each (valid or not);
+// warps 0-3 reduce, so s_prune_box[s] bounds points [32 s, 32 s + 32) of the
+// tile (an empty box if none is valid).  Ends with __syncthreads.
+__device__ __forceinline__ void stage_tile_box(bool valid, float x, float y, float z, float l) {
+  if (threadIdx.x < 128) {
+    float a[3] = {valid ? x : INFINITY, valid ? y : INFINITY, valid ? z : INFINITY};
+    float b[3] = {valid ? x : -INFINITY, valid ? y : -INFINITY, valid ? z : -INFINITY};
+    float m = valid ? l : -INFINITY;
+    warp_box(a, b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) {
+      float* w = s_prune_box[threadIdx.x >> 5];
+      w[0] = a[0]; w[1] = a[1]; w[2] = a[2]; w[3] = b[0]; w[4] = b[1]; w[5] = b[2]; w[6] = m;
+    }
+  }
+  __syncthreads();
+}
+
+// Exponent bound of the pairs of this warp's points with staged sub-tile s:
+// max lid - gap^2 (lid = 0 in pass A).  -INF for an empty sub-tile.
+__device__ __forceinline__ float sub_tile_bound(const float (&wlo)[3], const float (&whi)[3], int s) {
+  const float* b = s_prune_box[s];
+  const float lo[3] = {b[0], b[1], b[2]}, hi[3] = {b[3], b[4], b[5]};
+  return b[6] - box_gap2(wlo, whi, lo, hi);
+}
+
+// Pruned pass A: block (bx, by) = scene points [bx * 1024, +1024) (warp w:
+// [.. + 128 w, +128), lane + 32 j) against model rows [by * rows_per_chunk,
+// +rows_per_chunk).  Writes partA[by][n] like the dense pass.
+__device__ __forceinline__ void passA_f32_pruned_body(const float4* FCPD_RESTRICT T4, int M, int rows_per_chunk,
+          const float4* FCPD_RESTRICT Y4, int N, float* FCPD_RESTRICT partA, DevState* FCPD_RESTRICT st, int bx, int by) {
+  constexpr int P = kPrunePts / 2;
+  ulonglong2 (*sT)[2] = s_pass_tile;
+  const bool skip_ok = !(st->prune_ctl & kPruneNoSkip);
+  const float q = scale_q(st->sigma2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nbase = bx * kPruneTile + warp * kPruneWarpPts + lane;
+  f2_t yx[P], yy[P], yz[P];
+  float acc[2 * P];
+  float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int nvalid = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    float c[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = nbase + (2 * p + h) * 32;
+      if (n < N) {
+        const float4 y = Y4[n];
+        c[h][0] = q * y.x; c[h][1] = q * y.y; c[h][2] = q * y.z;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { wlo[d] = fminf(wlo[d], c[h][d]); whi[d] = fmaxf(whi[d], c[h][d]); }
+        ++nvalid;
+      } else {
+        c[h][0] = c[h][1] = c[h][2] = -kFar;
+      }
+    }
+    yx[p] = f2_pack(c[0][0], c[1][0]);
+    yy[p] = f2_pack(c[0][1], c[1][1]);
+    yz[p] = f2_pack(c[0][2], c[1][2]);
+    acc[2 * p] = acc[2 * p + 1] = 0.f;
+  }
+  warp_box(wlo, whi);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
+  unsigned long long evaluated = 0;
+  const int r0 = by * rows_per_chunk;
+  const int r1 = min(M, r0 + rows_per_chunk);
+  for (int base = r0; base < r1; base += kTileA) {
+    __syncthreads();
+    bool in = false;
+    float tx = kFar, ty = kFar, tz = kFar;
+    if (threadIdx.x < kTileA) {
+      const int m = base + threadIdx.x;
+      in = m < r1;
+      if (in) {
+        const float4 t = T4[m];
+        tx = q * t.x; ty = q * t.y; tz = q * t.z;
+      }
+      sT[threadIdx.x][0] = make_ulonglong2(f2_pack(tx, tx), f2_pack(ty, ty));
+      sT[threadIdx.x][1] = make_ulonglong2(f2_pack(tz, tz), 0ull);
+    }
+    stage_tile_box(in, tx, ty, tz, 0.f);     // its __syncthreads also publishes sT
+    const int cnt = min(kTileA, r1 - base);
+#pragma unroll 1
+    for (int sub = 0; sub * 32 < cnt; ++sub) {
+    if (skip_ok && sub_tile_bound(wlo, whi, sub) < -kPruneExp) continue;   // warp-uniform
+    const int i1 = min(cnt, sub * 32 + 32);
+    evaluated += (unsigned long long)(i1 - sub * 32) * (unsigned long long)nvalid;
+#pragma unroll 1
+    for (int i = sub * 32; i < i1; ++i) {
+      const ulonglong2 a = sT[i][0];
+      const f2_t tz2 = sT[i][1].x;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const f2_t dx = f2_sub(yx[p], a.x), dy = f2_sub(yy[p], a.y), dz = f2_sub(yz[p], tz2);
+        f2_t d2 = f2_mul(dx, dx);
+        d2 = f2_fma(dy, dy, d2);
+        d2 = f2_fma(dz, dz, d2);
+        float d0, d1;
+        f2_unpack(d2, d0, d1);
+        acc[2 * p] += ex2_approx(-d0);
+        acc[2 * p + 1] += ex2_approx(-d1);
+      }
+    }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = nbase + (2 * p + h) * 32;
+      if (n < N) partA[(size_t)by * N + n] = acc[2 * p + h];
+    }
+  if (lane == 0 && evaluated) atomicAdd(&st->pairs_eval, evaluated);
+}
+
+// Pruned pass B: block (bx, by) = model points [bx * 1024, +1024) (warp w:
+// [.. + 128 w, +128), lane + 32 j) against scene points [by *
+// cols_per_chunk, +cols_per_chunk).  Writes partB like the dense pass (gy =
+// number of column chunks).
+__device__ __forceinline__ void passB_f32_pruned_body(const float4* FCPD_RESTRICT T4, int M,
+          const float4* FCPD_RESTRICT Yb, int N, int cols_per_chunk, float* FCPD_RESTRICT partB,
+          DevState* FCPD_RESTRICT st, int bx, int by, int gy) {
+  constexpr int P = kPrunePts / 2;
+  if (bx == 0 && by == 0 && threadIdx.x == 0) {   // as the dense pass: both lists are free here
+    st->n_flag_cols = 0;
+    st->n_flag_rows = 0;
+  }
+  ulonglong2 (*sY)[2] = s_pass_tile;
+  const bool skip_ok = !(st->prune_ctl & kPruneNoSkip);
+  const float q = scale_q(st->sigma2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mbase = bx * kPruneTile + warp * kPruneWarpPts + lane;
+  f2_t tx[P], ty[P], tz[P];
+  float p1[2 * P], px[2 * P], py[2 * P], pz[2 * P], v[2 * P];
+  float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int nvalid = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    float c[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = mbase + (2 * p + h) * 32;
+      if (m < M) {
+        const float4 t = T4[m];
+        c[h][0] = q * t.x; c[h][1] = q * t.y; c[h][2] = q * t.z;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { wlo[d] = fminf(wlo[d], c[h][d]); whi[d] = fmaxf(whi[d], c[h][d]); }
+        ++nvalid;
+      } else {
+        c[h][0] = c[h][1] = c[h][2] = kFar;
+      }
+    }
+    tx[p] = f2_pack(c[0][0], c[1][0]);
+    ty[p] = f2_pack(c[0][1], c[1][1]);
+    tz[p] = f2_pack(c[0][2], c[1][2]);
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * P; ++j) p1[j] = px[j] = py[j] = pz[j] = v[j] = 0.f;
+  warp_box(wlo, whi);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
+  unsigned long long evaluated = 0;
+  const int c0 = by * cols_per_chunk;
+  const int c1 = min(N, c0 + cols_per_chunk);
+  for (int base = c0; base < c1; base += kTileB) {
+    __syncthreads();
+    bool in = false;
+    float4 y = make_float4(-kFar, -kFar, -kFar, 0.f);
+    if (threadIdx.x < kTileB) {
+      const int n = base + threadIdx.x;
+      in = n < c1;
+      if (in) y = Yb[n];
+      sY[threadIdx.x][0] = make_ulonglong2(f2_pack(y.x, y.x), f2_pack(y.y, y.y));
+      sY[threadIdx.x][1] = make_ulonglong2(f2_pack(y.z, y.z), f2_pack(y.w, y.w));
+    }
+    stage_tile_box(in, y.x, y.y, y.z, y.w);   // Yb holds scaled coordinates and lid
+    const int cnt = min(kTileB, c1 - base);
+#pragma unroll 1
+    for (int sub = 0; sub * 32 < cnt; ++sub) {
+    if (skip_ok && sub_tile_bound(wlo, whi, sub) < -kPruneExp) continue;   // warp-uniform
+    const int i1 = min(cnt, sub * 32 + 32);
+    evaluated += (unsigned long long)(i1 - sub * 32) * (unsigned long long)nvalid;
+#pragma unroll 1
+    for (int i = sub * 32; i < i1; ++i) {
+      const ulonglong2 a = sY[i][0], b = sY[i][1];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const f2_t dx = f2_sub(tx[p], a.x), dy = f2_sub(ty[p], a.y), dz = f2_sub(tz[p], b.x);
+        f2_t d2 = f2_mul(dx, dx);
+        d2 = f2_fma(dy, dy, d2);
+        d2 = f2_fma(dz, dz, d2);
+        float e0, e1, q0, q1, yx, yy, yz, lid;
+        f2_unpack(f2_sub(b.y, d2), e0, e1);
+        f2_unpack(d2, q0, q1);
+        f2_unpack(a.x, yx, lid);
+        f2_unpack(a.y, yy, lid);
+        f2_unpack(b.x, yz, lid);
+        const float w0 = ex2_approx(e0), w1 = ex2_approx(e1);
+        p1[2 * p] += w0;                         p1[2 * p + 1] += w1;
+        px[2 * p] = fmaf(w0, yx, px[2 * p]);     px[2 * p + 1] = fmaf(w1, yx, px[2 * p + 1]);
+        py[2 * p] = fmaf(w0, yy, py[2 * p]);     py[2 * p + 1] = fmaf(w1, yy, py[2 * p + 1]);
+        pz[2 * p] = fmaf(w0, yz, pz[2 * p]);     pz[2 * p + 1] = fmaf(w1, yz, pz[2 * p + 1]);
+        v[2 * p] = fmaf(w0, q0, v[2 * p]);       v[2 * p + 1] = fmaf(w1, q1, v[2 * p + 1]);
+      }
+    }
+    }
+  }
+  const size_t plane = (size_t)gy * M;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = mbase + (2 * p + h) * 32;
+      const int j = 2 * p + h;
+      if (m < M) {
+        const size_t o = (size_t)by * M + m;
+        partB[o] = p1[j];
+        partB[o + plane] = px[j];
+        partB[o + 2 * plane] = py[j];
+        partB[o + 3 * plane] = pz[j];
+        partB[o + 4 * plane] = v[j];
+      }
+    }
+  if (lane == 0 && evaluated) atomicAdd(&st->pairs_eval, evaluated);
+}
+
+
 __device__ __forceinline__ void passB_f64_body(const dvec4* FCPD_RESTRICT T4, int M, const dvec4* FCPD_RESTRICT Yb, int N,
           int cols_per_chunk, double* FCPD_RESTRICT partB, const DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
   if (gate && iteration_gated(st)) return;

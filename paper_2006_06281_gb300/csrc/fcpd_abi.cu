@@ -108,7 +108,8 @@ cpd_status validate_params(const cpd_params* p) {
   if (std::isnan(p->sigma2_init) || std::isinf(p->sigma2_init)) return fail(CPD_EINVAL, "sigma2_init not finite");
   if (p->K < 0) return fail(CPD_EINVAL, "K must be >= 0");
   if (p->max_iter < 0) return fail(CPD_EINVAL, "max_iter must be >= 0");
-  if (p->flags != 0) return fail(CPD_EINVAL, "flags must be 0");
+  if (p->flags & ~(CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP))
+    return fail(CPD_EINVAL, "unknown bits in flags");
   if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return fail(CPD_EINVAL, "tol must be >= 0");
   return CPD_OK;
 }
@@ -136,6 +137,12 @@ struct cpd_ctx {
   Buf st, st_aux;
   Buf Y4, Yb, partA, partB, partP, sums, flags, stage;
   Buf auxT4, auxR4, auxB4, auxC4;
+  // spatial order (FP32 paths): model points sorted at setup, scenes at upload
+  bool sorted_model = false;     // X4, T4, U rows ... are in Morton order
+  bool scene_sorted = false;     // the current scene is in Morton order
+  Buf permX, invX;               // sorted -> caller index, caller -> sorted index
+  Buf sort_scratch, sort_tmp;
+  float prune_r2 = 0.f;          // pruned passes below this squared FP32 cutoff radius
   EstepPlan ep{};
   MstepPlan mp{};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
@@ -150,7 +157,8 @@ struct cpd_ctx {
   ~cpd_ctx() {
     drop_graphs();
     for (Buf* b : {&X4, &T4, &U, &Ut, &lam, &Yt4, &R4, &B4, &C4, &Yhat4, &W4, &hist, &st, &st_aux, &Y4, &Yb,
-                   &partA, &partB, &partP, &sums, &flags, &stage, &auxT4, &auxR4, &auxB4, &auxC4})
+                   &partA, &partB, &partP, &sums, &flags, &stage, &auxT4, &auxR4, &auxB4, &auxC4, &permX, &invX,
+                   &sort_scratch, &sort_tmp})
       b->release();
     if (cap) cudaStreamDestroy(cap);
   }
@@ -207,6 +215,60 @@ cpd_status download_points(const void* src, int64_t n, void* dst, Buf& stage, bo
     CUDA_TRY(cudaStreamSynchronize(s));
   }
   return CPD_OK;
+}
+
+// Per-model-point arrays in the caller's order <-> the context's (sorted)
+// order.  Without spatial order these are upload_points / download_points.
+cpd_status upload_model(cpd_ctx* c, const void* src, void* dst4) {
+  if (!c->sorted_model) return upload_points(c, src, c->M, dst4, false, c->stage, c->fp64, c->stream);
+  const float* dev = static_cast<const float*>(src);
+  if (!is_device_ptr(src)) {
+    STATUS_TRY(c->stage.ensure((size_t)c->M * 3 * sizeof(float)));
+    CUDA_TRY(cudaMemcpyAsync(c->stage.p, src, (size_t)c->M * 3 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    dev = c->stage.as<float>();
+  }
+  launch_pack_gather<float>(dev, c->permX.as<int>(), c->M, static_cast<float4*>(dst4), false, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  return CPD_OK;
+}
+
+cpd_status download_model(cpd_ctx* c, const void* src4, void* dst) {
+  if (!c->sorted_model) return download_points(src4, c->M, dst, c->stage, c->fp64, c->stream);
+  const bool dev = is_device_ptr(dst);
+  float* out = static_cast<float*>(dst);
+  if (!dev) {
+    STATUS_TRY(c->stage.ensure((size_t)c->M * 3 * sizeof(float)));
+    out = c->stage.as<float>();
+  }
+  launch_unpack_gather<float>(static_cast<const float4*>(src4), c->invX.as<int>(), c->M, out, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (!dev) {
+    CUDA_TRY(cudaMemcpyAsync(dst, out, (size_t)c->M * 3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return CPD_OK;
+}
+
+// Sorts n float4 points in place (Morton order); perm (sorted -> original)
+// may be null.
+cpd_status sort_points(cpd_ctx* c, void* pts4, int64_t n, int* perm) {
+  STATUS_TRY(c->sort_scratch.ensure((size_t)spatial_sort_scratch_bytes(n)));
+  STATUS_TRY(c->sort_tmp.ensure((size_t)n * sizeof(float4)));
+  CUDA_TRY(launch_spatial_sort(static_cast<const float4*>(pts4), n, c->sort_tmp.as<float4>(), perm,
+                               c->sort_scratch.p, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(pts4, c->sort_tmp.p, (size_t)n * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream));
+  return CPD_OK;
+}
+
+// Pruning control of the context for the current scene.
+void apply_prune(cpd_ctx* c) {
+  int ctl = 0;
+  if (c->sorted_model && c->scene_sorted) {
+    ctl = kPruneAllowed;
+    if (c->p.flags & CPD_FLAG_PRUNE_ALWAYS) ctl |= kPruneAlways;
+    if (c->p.flags & CPD_FLAG_PRUNE_NOSKIP) ctl |= kPruneNoSkip;
+  }
+  launch_state_prune(c->dst(), c->prune_r2, ctl, c->stream);
 }
 
 cpd_status read_state(cpd_ctx* c, DevState* h) {
@@ -279,7 +341,7 @@ cpd_status capture_graph(cpd_ctx* c, int which) {
 cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
   if (N == c->N) return CPD_OK;
   c->drop_graphs();
-  c->ep = plan_estep(c->M, N, c->fp64, c->sms);
+  c->ep = plan_estep(c->M, N, c->fp64, c->sms, c->sorted_model);
   STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
   STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
   STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
@@ -308,6 +370,7 @@ cpd_status start_registration(cpd_ctx* c) {
     if (c->fp64) launch_sigma2_init<double>(c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), c->N, nullptr, c->dst(), c->stream);
     else launch_sigma2_init<float>(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, nullptr, c->dst(), c->stream);
   }
+  apply_prune(c);
   CUDA_TRY(cudaGetLastError());
   c->started = true;
   return CPD_OK;
@@ -317,7 +380,10 @@ cpd_status start_registration(cpd_ctx* c) {
 cpd_status prepare_iterate(cpd_ctx* c, const void* Y, int64_t N) {
   STATUS_TRY(ensure_scene(c, N));
   STATUS_TRY(upload_points(c, Y, N, c->Y4.p, true, c->stage, c->fp64, c->stream));
+  c->scene_sorted = c->sorted_model && spatial_sort_supported(N);
+  if (c->scene_sorted) STATUS_TRY(sort_points(c, c->Y4.p, N, nullptr));
   if (!c->started) STATUS_TRY(start_registration(c));
+  else apply_prune(c);
   return CPD_OK;
 }
 
@@ -424,8 +490,27 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   if ((s = c->T4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->st.ensure(sizeof(DevState))) != CPD_OK) return bail(s);
   if ((s = c->st_aux.ensure(sizeof(DevState))) != CPD_OK) return bail(s);
-  if ((s = c->hist.ensure((size_t)3 * kHistCap * sizeof(double))) != CPD_OK) return bail(s);
+  if ((s = c->hist.ensure((size_t)4 * kHistCap * sizeof(double))) != CPD_OK) return bail(s);
   if ((s = upload_points(c, X, M, c->X4.p, false, c->stage, c->fp64, c->stream)) != CPD_OK) return bail(s);
+  // FP32 paths: model points in spatial order (the E-step prunes far tile
+  // pairs exactly); every per-model-point input and output is permuted.
+  if (!c->fp64 && p->flags != 0 && spatial_sort_supported(M)) {
+    if ((s = c->permX.ensure((size_t)M * sizeof(int))) != CPD_OK) return bail(s);
+    if ((s = c->invX.ensure((size_t)M * sizeof(int))) != CPD_OK) return bail(s);
+    if ((s = sort_points(c, c->X4.p, M, c->permX.as<int>())) != CPD_OK) return bail(s);
+    launch_invert_perm(c->permX.as<int>(), M, c->invX.as<int>(), c->stream);
+    float box[6];
+    if (cudaMemcpyAsync(box, c->sort_scratch.p, sizeof(box), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return bail(fail(CPD_ECUDA, "spatial sort of the model points failed"));
+    // pruned passes once the FP32 cutoff radius is below a quarter of the
+    // model's largest extent (box[3..5] = 16 / extent, 0 for a flat axis)
+    float ext = 0.f;
+    for (int d = 0; d < 3; ++d)
+      if (box[3 + d] > 0.f) ext = std::max(ext, 16.f / box[3 + d]);
+    c->prune_r2 = 0.0625f * ext * ext;
+    c->sorted_model = true;
+  }
 
   // The long-lived basis is allocated before the setup temporaries.
   c->mp = plan_mstep(M, c->K, c->fp64, c->sms, 128, (int)c->bes);
@@ -516,7 +601,7 @@ cpd_status cpd_iterate(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, voi
     for (int i = 0; i < nb; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[1], c->stream));
     for (int i = 0; i < n1; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[0], c->stream));
   }
-  if (T_out) STATUS_TRY(download_points(c->T4.p, c->M, T_out, c->stage, c->fp64, c->stream));
+  if (T_out) STATUS_TRY(download_model(c, c->T4.p, T_out));
   if (sigma2_out || iters_done || (T_out && !is_device_ptr(T_out))) {
     DevState h;
     STATUS_TRY(read_state(c, &h));
@@ -567,7 +652,7 @@ cpd_status cpd_set_ground_truth(cpd_ctx* c, const void* Yhat, double rmse_tol) {
   c->drop_graphs();
   if (Yhat) {
     STATUS_TRY(c->Yhat4.ensure((size_t)c->M * c->v4));
-    STATUS_TRY(upload_points(c, Yhat, c->M, c->Yhat4.p, false, c->stage, c->fp64, c->stream));
+    STATUS_TRY(upload_model(c, Yhat, c->Yhat4.p));
     c->has_gt = true;
     c->gt_tol = rmse_tol;
   } else {
@@ -618,35 +703,58 @@ cpd_status cpd_get_W(cpd_ctx* c, void* W_out) {
                                 c->W4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
   else w_f32(c, c->C4.as<float4>(), c->W4.as<float4>(), c->stream);
   CUDA_TRY(cudaGetLastError());
-  return download_points(c->W4.p, c->M, W_out, c->stage, c->fp64, c->stream);
+  return download_model(c, c->W4.p, W_out);
 }
 
 cpd_status cpd_get_basis(cpd_ctx* c, void* U_out, double* lam_out) {
   if (!c) return fail(CPD_EINVAL, "ctx is NULL");
   DeviceGuard guard(c->dev);
-  if (U_out && c->half_basis) {
-    // converted to float on the device, then copied out
-    Buf tmp;
+  if (U_out && !c->sorted_model && !c->half_basis) {
+    CUDA_TRY(cudaMemcpy2DAsync(U_out, (size_t)c->K * c->es, c->U.p, (size_t)c->ldU * c->es, (size_t)c->K * c->es,
+                               (size_t)c->M, cudaMemcpyDefault, c->stream));
+  } else if (U_out) {
+    // float rows (FP16 converted), then in the caller's point order
+    Buf conv, stage;
+    const float* rows = c->U.as<float>();
+    int64_t ld = c->ldU;
+    if (c->half_basis) {
+      STATUS_TRY(conv.ensure((size_t)c->M * c->K * sizeof(float)));
+      launch_basis_to_f32(c->U.as<__half>(), c->M, c->K, c->ldU, conv.as<float>(), c->stream);
+      rows = conv.as<float>();
+      ld = c->K;
+    }
     const bool dev_out = is_device_ptr(U_out);
     float* dst = static_cast<float*>(U_out);
     if (!dev_out) {
-      STATUS_TRY(tmp.ensure((size_t)c->M * c->K * sizeof(float)));
-      dst = tmp.as<float>();
+      STATUS_TRY(stage.ensure((size_t)c->M * c->K * sizeof(float)));
+      dst = stage.as<float>();
     }
-    launch_basis_to_f32(c->U.as<__half>(), c->M, c->K, c->ldU, dst, c->stream);
+    if (c->sorted_model)
+      launch_gather_rows_f32(rows, ld, c->invX.as<int>(), c->M, c->K, dst, c->stream);
+    else
+      CUDA_TRY(cudaMemcpyAsync(dst, rows, (size_t)c->M * c->K * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     CUDA_TRY(cudaGetLastError());
     if (!dev_out)
       CUDA_TRY(cudaMemcpyAsync(U_out, dst, (size_t)c->M * c->K * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-  } else if (U_out) {
-    CUDA_TRY(cudaMemcpy2DAsync(U_out, (size_t)c->K * c->es, c->U.p, (size_t)c->ldU * c->es, (size_t)c->K * c->es,
-                               (size_t)c->M, cudaMemcpyDefault, c->stream));
   }
   if (lam_out)
     CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam.p, (size_t)c->K * sizeof(double), cudaMemcpyDefault, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return CPD_OK;
 }
+
+cpd_status cpd_get_work(cpd_ctx* c, int32_t n, double* eval_frac) {
+  if (!c || !eval_frac) return fail(CPD_EINVAL, "ctx and eval_frac are required");
+  DeviceGuard guard(c->dev);
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  if (n < 0 || n > h.iter || n > kHistCap) return fail(CPD_EINVAL, "n exceeds the recorded iterations");
+  if (n > 0) CUDA_TRY(cudaMemcpy(eval_frac, c->hist.as<double>() + 3 * kHistCap, n * sizeof(double), cudaMemcpyDefault));
+  return CPD_OK;
+}
+
+int32_t cpd_spatial_order(const cpd_ctx* c) { return c && c->sorted_model ? 1 : 0; }
 
 cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, void* W_out) {
   g_err.clear();
@@ -658,7 +766,7 @@ cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, v
   STATUS_TRY(c->auxR4.ensure((size_t)c->M * c->v4));
   STATUS_TRY(c->auxB4.ensure((size_t)c->K * c->v4));
   STATUS_TRY(c->auxC4.ensure((size_t)c->K * c->v4));
-  STATUS_TRY(upload_points(c, Ytil, c->M, c->auxT4.p, false, c->stage, c->fp64, c->stream));
+  STATUS_TRY(upload_model(c, Ytil, c->auxT4.p));
   DevState* sa = c->st_aux.as<DevState>();
   launch_state_init(sa, sigma2, c->stream);
   if (c->fp64) {
@@ -672,13 +780,13 @@ cpd_status cpd_mstep(cpd_ctx* c, const void* Ytil, double sigma2, void* T_out, v
               c->auxC4.as<float4>(), sa, false, c->stream);
   }
   CUDA_TRY(cudaGetLastError());
-  STATUS_TRY(download_points(c->auxT4.p, c->M, T_out, c->stage, c->fp64, c->stream));
+  STATUS_TRY(download_model(c, c->auxT4.p, T_out));
   if (W_out) {
     if (c->fp64) launch_w<double>(c->mp, c->Ut.as<double>(), c->M, c->K, c->auxC4.as<dvec4>(), c->partP.as<double>(),
                                   c->auxR4.as<dvec4>(), c->st_aux.as<DevState>(), c->stream);
     else w_f32(c, c->auxC4.as<float4>(), c->auxR4.as<float4>(), c->stream);
     CUDA_TRY(cudaGetLastError());
-    STATUS_TRY(download_points(c->auxR4.p, c->M, W_out, c->stage, c->fp64, c->stream));
+    STATUS_TRY(download_model(c, c->auxR4.p, W_out));
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return CPD_OK;
@@ -1051,7 +1159,7 @@ cpd_status cpd_batch_get_T(cpd_batch* b, int32_t i, void* T_out) {
   if (i < 0 || i >= b->n) return fail(CPD_EINVAL, "pair index out of range");
   DeviceGuard guard(b->dev);
   cpd_ctx* c = b->ctx[i];
-  return download_points(c->T4.p, c->M, T_out, c->stage, false, b->stream);
+  return download_model(c, c->T4.p, T_out);
 }
 
 cpd_status cpd_batch_info(const cpd_batch* b, int32_t i, int64_t* M, int64_t* N, int64_t* K) {

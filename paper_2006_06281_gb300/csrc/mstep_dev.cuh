@@ -245,10 +245,15 @@ __device__ __forceinline__ void finish_iteration(DevState* FCPD_RESTRICT st, dou
   const int it = st->iter;
   const double s2new = t0 / (3.0 * (double)M);
   const double rm = st->has_gt ? sqrt(t2 / (double)M) : nan("");
+  // passes A and B evaluate 2 M N pairs when dense; the pruned ones count theirs
+  const double frac = prune_active(st) ? (double)st->pairs_eval / (2.0 * (double)M * (double)st->N) : 1.0;
+  st->pairs_eval = 0;
+  st->last_eval_frac = frac;
   if (st->hist && it < kHistCap) {
     st->hist[it] = s2new;
     st->hist[kHistCap + it] = st->loglik;
     st->hist[2 * kHistCap + it] = rm;
+    st->hist[3 * kHistCap + it] = frac;
   }
   st->last_dT2 = t1;
   st->last_rmse = rm;

@@ -160,6 +160,15 @@ __global__ void state_init(DevState* st, double sigma2) {
   st->done = 0;
   st->n_flag_cols = st->n_flag_rows = 0;
   st->ticket_a = st->ticket_b = st->ticket_m = st->ticket_e = 0;
+  st->pairs_eval = 0;
+  st->last_eval_frac = 1.0;
+  st->prune_r2 = 0.f;
+  st->prune_ctl = 0;
+}
+
+__global__ void state_prune(DevState* st, float r2, int ctl) {
+  st->prune_r2 = r2;
+  st->prune_ctl = ctl;
 }
 
 }  // namespace
@@ -210,6 +219,9 @@ void launch_residual(const typename Vec<F>::t4* Yt4, const typename Vec<F>::t4* 
 template void launch_residual<float>(const float4*, const float4*, float4*, int64_t, cudaStream_t);
 template void launch_residual<double>(const dvec4*, const dvec4*, dvec4*, int64_t, cudaStream_t);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s) { state_init<<<1, 1, 0, s>>>(st, sigma2); }
+void launch_state_prune(DevState* st, float prune_r2, int prune_ctl, cudaStream_t s) {
+  state_prune<<<1, 1, 0, s>>>(st, prune_r2, prune_ctl);
+}
 
 namespace {
 __global__ void basis_to_f32(const __half* __restrict__ U, int64_t M, int64_t K, int64_t ldU, float* __restrict__ out) {
