@@ -43,7 +43,7 @@ UNIT = "EM iters/s"
 PAPER_ITERS_PER_S = 50.0 / (988.430 - 502.663)
 RMSE_TARGET = 5e-3
 ITERS_PER_REGISTRATION = 100
-STATE_BYTES = 160          # sizeof(DevState), read back with sigma2 by cpd_iterate
+STATE_BYTES = 168          # sizeof(DevState), read back with sigma2 by cpd_iterate
 
 
 def parse():

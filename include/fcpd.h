@@ -75,10 +75,15 @@ typedef enum {
     CPD_FP32 = 1,      /* float points/basis, FP64 scalar reductions     */
     CPD_MIXED = 2      /* as CPD_FP32, but the eigenbasis U, U^T is stored
                           in FP16 (products and sums in FP32): the M-step
-                          streams half the bytes.  Not a precision the
-                          paper uses; its error against the FP64 oracle is
-                          measured and stated, not bounded by the FP32
-                          tolerance.  Points, outputs: float.            */
+                          streams half the bytes; and while sigma2 is large
+                          (sigma2 >= 4.4e-4 R^2, R the largest point norm)
+                          the E-step's Gaussian exponents come from BF16
+                          tensor-core products (3-way split operands, FP32
+                          accumulation), below it from the FP32 passes.
+                          Not a precision the paper uses; its error against
+                          the FP64 oracle is measured and stated, not
+                          bounded by the FP32 tolerance.  Points, outputs:
+                          float.                                         */
 } cpd_precision;
 
 /* Registration parameters (Sec. IV "Parameter settings": w, beta, lambda). */
@@ -233,7 +238,8 @@ cpd_status cpd_mstep(cpd_ctx *ctx, const void *Ytil, double sigma2, void *T_out,
 /*
  * One E-step, no context needed (Eq. 4 then Eq. 5):
  *   T (M x D), Y (N x D): host or device, element type per `precision`
- *            (CPD_MIXED runs the FP32 E-step: float arrays).
+ *            (CPD_MIXED: float arrays; the tensor-core passes run when
+ *            sigma2 is above their floor, else the FP32 passes).
  *   Ytil_out (M x D, required): sum_n p^_mn y_n, the row-normalised estimate.
  *   P1_out   (M doubles, optional, host or device): row mass sum_n p_mn
  *            before Eq. 5.

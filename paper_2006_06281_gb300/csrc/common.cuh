@@ -73,21 +73,32 @@ struct DevState {
   unsigned long long pairs_eval;  // Gaussian pairs evaluated by the pruned passes this iteration
   double last_eval_frac;          // fraction of the 2 M N pairs of passes A+B evaluated last iteration
   float prune_r2;                 // pruned passes run while 127 / kappa (FP32 cutoff radius^2) < this
-  int prune_ctl;                  // kPrune* bits (0: dense passes only)
+  int prune_ctl;                  // kPrune* / kMmaAllowed bits (0: dense passes only)
+  double mma_s2min;               // tensor-core passes run while sigma2 >= this
 };
 
-static_assert(sizeof(DevState) == 160, "DevState layout changed: update the benchmark's transfer count");
+static_assert(sizeof(DevState) == 168, "DevState layout changed: update the benchmark's transfer count");
 
 // DevState::prune_ctl bits.
 constexpr int kPruneAllowed = 1;   // points are in spatial order: the pruned passes may run
 constexpr int kPruneAlways = 2;    // run the pruned passes whatever sigma2 (verification)
 constexpr int kPruneNoSkip = 4;    // pruned passes evaluate every tile pair (verification)
+constexpr int kMmaAllowed = 8;     // mixed precision: tensor-core distance passes while sigma2 is large
+// The tensor-core passes accumulate exponent terms as large as q^2 |p|^2 in
+// FP32: they run while q^2 R^2 <= ~2000 (R = largest point norm), i.e.
+// sigma2 >= kMmaS2PerR2 * R^2, which keeps the exponent's rounding near 1e-3.
+constexpr double kMmaS2PerR2 = 3.5e-4;
 
-// The pruned passes' layout is used this iteration (same answer in every
-// kernel of an E-step: sigma2 does not change within it).
+// The tensor-core passes' layout is used this iteration (same answer in
+// every kernel of an E-step: sigma2 does not change within it).
+__device__ __forceinline__ bool mma_active(const DevState* st) {
+  return (st->prune_ctl & kMmaAllowed) && st->sigma2 >= st->mma_s2min;
+}
+
+// The pruned passes' layout is used this iteration.
 __device__ __forceinline__ bool prune_active(const DevState* st) {
   const int c = st->prune_ctl;
-  if (!(c & kPruneAllowed)) return false;
+  if (!(c & kPruneAllowed) || mma_active(st)) return false;
   if (c & kPruneAlways) return true;
   const double r2 = 127.0 * 2.0 * st->sigma2 / 1.4426950408889634;   // 127 / kappa, kappa = log2(e) / (2 sigma2)
   return r2 < (double)st->prune_r2;
@@ -147,6 +158,18 @@ void launch_gather_rows_f32(const float* src, int64_t ld_src, const int* inv, in
 void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------- launchers
+struct MmaPlan {
+  int a_row_tiles, a_chunks, a_rows_per_chunk;       // pass A: scene-point tiles x model-point chunks
+  int b_row_tiles, b_chunks, b_cols_per_chunk;       // pass B: model-point tiles x scene-point chunks
+};
+void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p);
+void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,
+                      DevState* st, int gate, cudaStream_t s);
+void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Yb, int64_t N, float* partB,
+                      DevState* st, int gate, cudaStream_t s);
+// sigma2 floor of the tensor-core passes from the largest point norm of X and Y.
+void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s);
+
 struct EstepPlan {
   int a_col_tiles, a_row_chunks, a_rows_per_chunk;   // pass A grid
   int b_row_tiles, b_col_chunks, b_cols_per_chunk;   // pass B grid
@@ -158,9 +181,12 @@ struct EstepPlan {
   bool pruned;                                       // launch the pruned passes too
   int pa_col_tiles, pa_row_chunks, pa_rows_per_chunk;
   int pb_row_tiles, pb_col_chunks, pb_cols_per_chunk;
+  // tensor-core layout (mixed precision; see estep_mma.cu)
+  bool mma;                                          // launch the tensor-core passes too
+  MmaPlan mm;
 };
-// with_pruned: also plan the pruned FP32 layout (partial buffers sized for both).
-EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned = false);
+// with_pruned / with_mma: also plan those layouts (partial buffers sized for all).
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned = false, bool with_mma = false);
 
 struct MstepPlan {
   int64_t ldU, ldM;                                  // row strides of U (M x ldU) and U^T (K x ldM)

@@ -17,7 +17,7 @@ using namespace dev;
 __global__ void __launch_bounds__(kThreadsA)
 passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
           int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
-  if (prune_active(st)) return;
+  if (prune_active(st) || mma_active(st)) return;
   dev::passA_f32_body(T4, M, rows_per_chunk, Y4, N, partA, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -37,10 +37,10 @@ passA_f64(const dvec4* __restrict__ T4, int M, int rows_per_chunk, const dvec4* 
 // chunks_pruned: chunk count of the pruned layout (used when it ran).
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
-reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int M, const typename Vec<F>::t4* __restrict__ Y4,
+reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ Y4,
         int N, typename Vec<F>::t4* __restrict__ Yb, double* __restrict__ den_out,
         double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
-  const int ch = prune_active(st) ? chunks_pruned : chunks;
+  const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
   dev::reduceA_body<F>(partA, ch, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -54,7 +54,7 @@ fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, in
 __global__ void __launch_bounds__(kThreadsB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
           int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
-  if (prune_active(st)) return;
+  if (prune_active(st) || mma_active(st)) return;
   dev::passB_f32_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -73,11 +73,11 @@ passB_f64(const dvec4* __restrict__ T4, int M, const dvec4* __restrict__ Yb, int
 
 template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
-reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int M, const typename Vec<F>::t4* __restrict__ X4,
+reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ X4,
         typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
         double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
         DevState* __restrict__ st, int gate) {
-  const int ch = prune_active(st) ? chunks_pruned : chunks;
+  const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
   dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -95,7 +95,7 @@ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Grids for passes A and B: all blocks resident in one wave (blocks <= SMs x
 // resident blocks per SM from the occupancy calculator), with the split of
 // the long dimension chosen so every block gets the same amount of work.
-EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned) {
+EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned, bool with_mma) {
   EstepPlan p{};
   int occA = 0, occB = 0;
   if (fp64) {
@@ -139,6 +139,16 @@ EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned)
     p.pa_row_chunks = p.a_row_chunks;          // never used: prune_active is false
     p.pb_col_chunks = p.b_col_chunks;
   }
+  p.mma = with_mma && !fp64;
+  if (p.mma) {
+    plan_estep_mma(M, N, sms, p.mm);
+    p.partA_elems = std::max(p.partA_elems, (int64_t)p.mm.a_chunks * N);
+    p.partB_elems = std::max(p.partB_elems, (int64_t)5 * p.mm.b_chunks * M);
+  } else {
+    p.mm = MmaPlan{};
+    p.mm.a_chunks = p.a_row_chunks;            // never used: mma_active is false
+    p.mm.b_chunks = p.b_col_chunks;
+  }
   p.redA_blocks = cdiv(N, kRedCols);
   p.redB_blocks = cdiv(M, kRedRows);
   p.sums_elems = std::max(p.redA_blocks, p.redB_blocks);
@@ -162,11 +172,12 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
     if (pl.pruned)
       passA_f32_pruned<<<dim3(pl.pa_col_tiles, pl.pa_row_chunks), kThreadsA, 0, s>>>(
           T4, (int)M, pl.pa_rows_per_chunk, Y4, (int)N, partA, st, g);
+    if (pl.mma) launch_passA_mma(pl.mm, T4, M, Y4, N, partA, st, g, s);
   } else {
     passA_f64<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
   }
   record_after(ev, 0, s);
-  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, (int)M, Y4,
+  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, pl.mm.a_chunks, (int)M, Y4,
                                                             (int)N, Yb, den_out, sums, flag_cols, st, g);
   if constexpr (sizeof(F) == 4) {
     fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
@@ -177,11 +188,12 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
     if (pl.pruned)
       passB_f32_pruned<<<dim3(pl.pb_row_tiles, pl.pb_col_chunks), kThreadsB, 0, s>>>(
           T4, (int)M, Yb, (int)N, pl.pb_cols_per_chunk, partB, st, g);
+    if (pl.mma) launch_passB_mma(pl.mm, T4, M, Yb, N, partB, st, g, s);
   } else {
     passB_f64<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
   }
   record_after(ev, 2, s);
-  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, (int)M, X4,
+  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, pl.mm.b_chunks, (int)M, X4,
                                                             Yt4, R4, P1_out, sums, flag_rows, st, g);
   if constexpr (sizeof(F) == 4) {
     fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);

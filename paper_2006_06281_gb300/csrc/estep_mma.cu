@@ -1,0 +1,352 @@
+// E-step passes with tensor-core distance tiles (mixed-precision mode).
+//
+// The exponent of every Gaussian of a 16 x 8 tile of (row point, column
+// point) pairs is one warp-level BF16 tensor-core product with FP32
+// accumulation (mma.sync m16n8k16, two K-steps, K = 32):
+//     e = 2 r'.c' - |r'|^2 - |c'|^2 (+ lid_c in pass B)
+// over the coordinates pre-scaled by q = sqrt(log2(e) / (2 sigma2)), so
+// e = -|r' - c'|^2 (+ lid) is the base-2 exponent the FP32 passes compute
+// directly.  Each FP32 value v is split into three BF16 parts v1 + v2 + v3
+// (about 24 significant bits); the cross products kept are those of total
+// order <= 2^-16 (v1w1, v1w2, v2w1, v1w3, v2w2, v3w1), the norms and lid
+// enter as split terms against an exact 1:
+//   k  0..17  row side 2 r_d^(i)           col side c_d^(j)   (d, (i, j) pattern)
+//   k 18..20  row side -|r'|^2 (split)     col side 1
+//   k 21..23  row side 1                   col side -|c'|^2 (split)
+//   k 24..26  row side 1                   col side lid (split; 0 in pass A)
+//   k 27..31  0
+// The products of BF16 values are exact in FP32; what remains is the FP32
+// accumulation of terms as large as |r'|^2, whose rounding grows with
+// 1 / sigma2 -- so these passes run only while sigma2 >= mma_s2min (see
+// kMmaS2PerR2) and the
+// FP32 direct passes take over below it (both are in every captured
+// iteration; each steps aside on the device-side test).  The exponentials
+// and sums are the FP32 passes' own: ex2.approx.ftz, FP32 accumulation,
+// split partials reduced in a fixed order.
+#include "estep_dev.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace fcpd {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kMmaThreads = 256;            // 8 warps
+constexpr int kMmaTilesPerWarp = 2;         // 16-point row tiles per warp
+constexpr int kMmaRowsPerBlock = 8 * 16 * kMmaTilesPerWarp;   // 256 row points per block
+constexpr int kMmaStage = 128;              // column points staged per shared tile
+constexpr int kAugK = 32;                   // augmented dimension
+constexpr int kAugStride = 40;              // bf16 per staged vector (80 bytes: conflict-free ldmatrix)
+
+// Row-side and column-side augmented vectors (BF16) of a scaled point v with
+// squared norm n (and lid for the column side).
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(a);
+  b = __float2bfloat16_rn(r1);
+  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+// pattern of (row part i, column part j) for the six kept cross products
+__device__ __forceinline__ int row_part(int p) { return p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0; }
+__device__ __forceinline__ int col_part(int p) { return p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0; }
+
+__device__ __forceinline__ void row_vector(float x, float y, float z, bool valid, __nv_bfloat16* out) {
+  __nv_bfloat16 s[3][3], nn[3];
+  const float v[3] = {x, y, z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) split3(valid ? 2.0f * v[d] : 0.f, s[d][0], s[d][1], s[d][2]);
+  split3(valid ? -(x * x + y * y + z * z) : 0.f, nn[0], nn[1], nn[2]);
+  const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int p = 0; p < 6; ++p) out[6 * d + p] = s[d][row_part(p)];
+  out[18] = nn[0]; out[19] = nn[1]; out[20] = nn[2];
+#pragma unroll
+  for (int k = 21; k < 27; ++k) out[k] = one;
+#pragma unroll
+  for (int k = 27; k < kAugK; ++k) out[k] = zero;
+}
+
+// Column side; an invalid (padding) point gets a huge negative norm so its
+// exponents are far below -126 (its Gaussians are exactly 0).
+__device__ __forceinline__ void col_vector(float x, float y, float z, float lid, bool valid, __nv_bfloat16* out) {
+  __nv_bfloat16 s[3][3], nn[3], ll[3];
+  const float v[3] = {x, y, z};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) split3(valid ? v[d] : 0.f, s[d][0], s[d][1], s[d][2]);
+  split3(valid ? -(x * x + y * y + z * z) : -1e30f, nn[0], nn[1], nn[2]);
+  split3(valid ? lid : 0.f, ll[0], ll[1], ll[2]);
+  const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int p = 0; p < 6; ++p) out[6 * d + p] = s[d][col_part(p)];
+  out[18] = one; out[19] = one; out[20] = one;
+  out[21] = nn[0]; out[22] = nn[1]; out[23] = nn[2];
+  out[24] = ll[0]; out[25] = ll[1]; out[26] = ll[2];
+#pragma unroll
+  for (int k = 27; k < kAugK; ++k) out[k] = zero;
+}
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned int addr, unsigned int& r0, unsigned int& r1, unsigned int& r2,
+                                        unsigned int& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+// D = A B (+0): 16 x 8 FP32 from BF16 A (16 x 16, row) and B (16 x 8, col).
+__device__ __forceinline__ void mma_bf16(const unsigned int (&a)[4], unsigned int b0, unsigned int b1, float (&d)[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%10, %11, %12, %13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(d[0]), "f"(d[1]), "f"(d[2]), "f"(d[3]));
+}
+
+// Row fragments of a warp: tiles of 16 row points staged as augmented
+// vectors in shared memory; A fragments (two K-steps) via ldmatrix.x4.
+__device__ __forceinline__ void load_row_frags(const __nv_bfloat16 (*sRow)[kAugStride], int tile0,
+                                               unsigned int (&a)[kMmaTilesPerWarp][2][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int g = 0; g < kMmaTilesPerWarp; ++g)
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      // matrices: (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+      const int mat = lane >> 3, r = lane & 7;
+      const int row = 16 * (tile0 + g) + (mat & 1) * 8 + r;
+      const int k = 16 * ks + (mat >> 1) * 8;
+      ldsm_x4(smem_u32(&sRow[row][k]), a[g][ks][0], a[g][ks][1], a[g][ks][2], a[g][ks][3]);
+    }
+}
+
+// ------------------------------------------------------------------ pass A
+// Rows: scene points (block: kMmaRowsPerBlock of them); columns: model
+// points of the block's row chunk, staged kMmaStage at a time.  Writes the
+// split column sums partA[chunk][n] like the FP32 pass A.
+__global__ void __launch_bounds__(kMmaThreads)
+passA_f32_mma(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4, int N,
+              float* __restrict__ partA, DevState* __restrict__ st, int gate) {
+  if ((gate && iteration_gated(st)) || !mma_active(st)) return;
+  __shared__ __align__(16) __nv_bfloat16 sRow[kMmaRowsPerBlock][kAugStride];
+  __shared__ __align__(16) __nv_bfloat16 sCol[kMmaStage][kAugStride];
+  const float q = scale_q(st->sigma2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * kMmaRowsPerBlock;
+  for (int i = threadIdx.x; i < kMmaRowsPerBlock; i += kMmaThreads) {
+    const int n = n0 + i;
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (n < N) y = Y4[n];
+    row_vector(q * y.x, q * y.y, q * y.z, n < N, sRow[i]);
+  }
+  __syncthreads();
+  unsigned int a[kMmaTilesPerWarp][2][4];
+  load_row_frags(sRow, warp * kMmaTilesPerWarp, a);
+  float acc[kMmaTilesPerWarp][2];
+#pragma unroll
+  for (int g = 0; g < kMmaTilesPerWarp; ++g) acc[g][0] = acc[g][1] = 0.f;
+  const int r0 = blockIdx.y * rows_per_chunk;
+  const int r1 = min(M, r0 + rows_per_chunk);
+  for (int base = r0; base < r1; base += kMmaStage) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMmaStage; i += kMmaThreads) {
+      const int m = base + i;
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < r1) t = T4[m];
+      col_vector(q * t.x, q * t.y, q * t.z, 0.f, m < r1, sCol[i]);
+    }
+    __syncthreads();
+    const int cnt = min(kMmaStage, r1 - base);
+#pragma unroll 1
+    for (int j = 0; j < cnt; j += 8) {
+      // B fragments of 8 column points: matrices = k blocks 0-7, 8-15, 16-23, 24-31
+      unsigned int b0, b1, b2, b3;
+      ldsm_x4(smem_u32(&sCol[j + (lane & 7)][8 * (lane >> 3)]), b0, b1, b2, b3);
+#pragma unroll
+      for (int g = 0; g < kMmaTilesPerWarp; ++g) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(a[g][0], b0, b1, d);
+        mma_bf16(a[g][1], b2, b3, d);
+        acc[g][0] += ex2_approx(d[0]) + ex2_approx(d[1]);   // row lane/4, columns 2(lane%4), +1
+        acc[g][1] += ex2_approx(d[2]) + ex2_approx(d[3]);   // row lane/4 + 8
+      }
+    }
+  }
+  // the four lanes of a quad hold the same rows: add their column subsets
+#pragma unroll
+  for (int g = 0; g < kMmaTilesPerWarp; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float v = acc[g][h];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      const int n = n0 + 16 * (warp * kMmaTilesPerWarp + g) + 8 * h + (lane >> 2);
+      if ((lane & 3) == 0 && n < N) partA[(size_t)blockIdx.y * N + n] = v;
+    }
+}
+
+// ------------------------------------------------------------------ pass B
+// Rows: model points; columns: scene points of the block's column chunk
+// (scaled coordinates and lid from Yb).  Writes partB like the FP32 pass B
+// (P1, PY x 3, V = sum_n w d'^2 with d'^2 = lid - e).
+__global__ void __launch_bounds__(kMmaThreads)
+passB_f32_mma(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N, int cols_per_chunk,
+              float* __restrict__ partB, DevState* __restrict__ st, int gate) {
+  if ((gate && iteration_gated(st)) || !mma_active(st)) return;
+  // the column list was consumed by fixA and the row list is filled after
+  // this pass (as in the FP32 pass B)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    st->n_flag_cols = 0;
+    st->n_flag_rows = 0;
+  }
+  __shared__ __align__(16) __nv_bfloat16 sRow[kMmaRowsPerBlock][kAugStride];
+  __shared__ __align__(16) __nv_bfloat16 sCol[kMmaStage][kAugStride];
+  __shared__ float4 sY[kMmaStage];
+  const float q = scale_q(st->sigma2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kMmaRowsPerBlock;
+  for (int i = threadIdx.x; i < kMmaRowsPerBlock; i += kMmaThreads) {
+    const int m = m0 + i;
+    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m < M) t = T4[m];
+    row_vector(q * t.x, q * t.y, q * t.z, m < M, sRow[i]);
+  }
+  __syncthreads();
+  unsigned int a[kMmaTilesPerWarp][2][4];
+  load_row_frags(sRow, warp * kMmaTilesPerWarp, a);
+  float p1[kMmaTilesPerWarp][2], px[kMmaTilesPerWarp][2], py[kMmaTilesPerWarp][2], pz[kMmaTilesPerWarp][2],
+      v[kMmaTilesPerWarp][2];
+#pragma unroll
+  for (int g = 0; g < kMmaTilesPerWarp; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) p1[g][h] = px[g][h] = py[g][h] = pz[g][h] = v[g][h] = 0.f;
+  const int c0 = blockIdx.y * cols_per_chunk;
+  const int c1 = min(N, c0 + cols_per_chunk);
+  for (int base = c0; base < c1; base += kMmaStage) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMmaStage; i += kMmaThreads) {
+      const int n = base + i;
+      float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (n < c1) y = Yb[n];           // q-scaled coordinates, lid = -log2 den_n
+      sY[i] = y;
+      col_vector(y.x, y.y, y.z, y.w, n < c1, sCol[i]);
+    }
+    __syncthreads();
+    const int cnt = min(kMmaStage, c1 - base);
+#pragma unroll 1
+    for (int j = 0; j < cnt; j += 8) {
+      unsigned int b0, b1, b2, b3;
+      ldsm_x4(smem_u32(&sCol[j + (lane & 7)][8 * (lane >> 3)]), b0, b1, b2, b3);
+      const float4 ya = sY[j + 2 * (lane & 3)], yb = sY[j + 2 * (lane & 3) + 1];   // columns of d[0]/d[2], d[1]/d[3]
+#pragma unroll
+      for (int g = 0; g < kMmaTilesPerWarp; ++g) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(a[g][0], b0, b1, d);
+        mma_bf16(a[g][1], b2, b3, d);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float w0 = ex2_approx(d[2 * h]), w1 = ex2_approx(d[2 * h + 1]);   // e_mn / den_n
+          p1[g][h] += w0 + w1;
+          px[g][h] = fmaf(w0, ya.x, fmaf(w1, yb.x, px[g][h]));
+          py[g][h] = fmaf(w0, ya.y, fmaf(w1, yb.y, py[g][h]));
+          pz[g][h] = fmaf(w0, ya.z, fmaf(w1, yb.z, pz[g][h]));
+          v[g][h] = fmaf(w0, ya.w - d[2 * h], fmaf(w1, yb.w - d[2 * h + 1], v[g][h]));   // d'^2 = lid - e
+        }
+      }
+    }
+  }
+  const size_t plane = (size_t)gridDim.y * M;
+#pragma unroll
+  for (int g = 0; g < kMmaTilesPerWarp; ++g)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float s[5] = {p1[g][h], px[g][h], py[g][h], pz[g][h], v[g][h]};
+#pragma unroll
+      for (int qn = 0; qn < 5; ++qn) {
+        s[qn] += __shfl_xor_sync(0xffffffffu, s[qn], 1);
+        s[qn] += __shfl_xor_sync(0xffffffffu, s[qn], 2);
+      }
+      const int m = m0 + 16 * (warp * kMmaTilesPerWarp + g) + 8 * h + (lane >> 2);
+      if ((lane & 3) == 0 && m < M) {
+        const size_t o = (size_t)blockIdx.y * M + m;
+#pragma unroll
+        for (int qn = 0; qn < 5; ++qn) partB[o + qn * plane] = s[qn];
+      }
+    }
+}
+
+__global__ void __launch_bounds__(1024) mma_threshold(const float4* __restrict__ X4, int M, const float4* __restrict__ Y4,
+                                                     int N, DevState* __restrict__ st) {
+  __shared__ float sh[32];
+  float r2 = 0.f;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const float4 p = X4[i];
+    r2 = fmaxf(r2, p.x * p.x + p.y * p.y + p.z * p.z);
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float4 p = Y4[i];
+    r2 = fmaxf(r2, p.x * p.x + p.y * p.y + p.z * p.z);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r2 = fmaxf(r2, sh[w]);
+    r2 = fmaxf(r2, sh[0]);
+    // the deformation moves T by a fraction of the extent: a 25 % margin
+    st->mma_s2min = kMmaS2PerR2 * 1.25 * (double)r2;
+  }
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s) {
+  mma_threshold<<<1, 1024, 0, s>>>(X4, (int)M, Y4, (int)N, st);
+}
+
+// Grids of the tensor-core passes: rows in blocks of 256 points, the other
+// dimension split so that about `slots` blocks run (chunks a multiple of the
+// staged tile).
+void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, passA_f32_mma, kMmaThreads, 0);
+  const int64_t slots = (int64_t)sms * std::max(occ, 1) * 2;
+  p.a_row_tiles = (int)cdiv(N, kMmaRowsPerBlock);
+  int64_t want = std::max<int64_t>(1, slots / p.a_row_tiles);
+  int64_t rpc = cdiv(cdiv(M, want), kMmaStage) * kMmaStage;
+  p.a_rows_per_chunk = (int)rpc;
+  p.a_chunks = (int)cdiv(M, rpc);
+  p.b_row_tiles = (int)cdiv(M, kMmaRowsPerBlock);
+  want = std::max<int64_t>(1, slots / p.b_row_tiles);
+  int64_t cpc = cdiv(cdiv(N, want), kMmaStage) * kMmaStage;
+  p.b_cols_per_chunk = (int)cpc;
+  p.b_chunks = (int)cdiv(N, cpc);
+}
+
+void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,
+                      DevState* st, int gate, cudaStream_t s) {
+  passA_f32_mma<<<dim3(p.a_row_tiles, p.a_chunks), kMmaThreads, 0, s>>>(T4, (int)M, p.a_rows_per_chunk, Y4,
+                                                                         (int)N, partA, st, gate);
+}
+
+void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Yb, int64_t N, float* partB,
+                      DevState* st, int gate, cudaStream_t s) {
+  passB_f32_mma<<<dim3(p.b_row_tiles, p.b_chunks), kMmaThreads, 0, s>>>(T4, (int)M, Yb, (int)N, p.b_cols_per_chunk,
+                                                                         partB, st, gate);
+}
+
+}  // namespace fcpd

@@ -260,7 +260,9 @@ cpd_status sort_points(cpd_ctx* c, void* pts4, int64_t n, int* perm) {
   return CPD_OK;
 }
 
-// Pruning control of the context for the current scene.
+// E-step layout control of the context for the current scene: pruning
+// (spatially ordered points) and, in the mixed-precision mode, the
+// tensor-core passes with their sigma2 floor from the current points.
 void apply_prune(cpd_ctx* c) {
   int ctl = 0;
   if (c->sorted_model && c->scene_sorted) {
@@ -268,7 +270,9 @@ void apply_prune(cpd_ctx* c) {
     if (c->p.flags & CPD_FLAG_PRUNE_ALWAYS) ctl |= kPruneAlways;
     if (c->p.flags & CPD_FLAG_PRUNE_NOSKIP) ctl |= kPruneNoSkip;
   }
+  if (c->half_basis) ctl |= kMmaAllowed;
   launch_state_prune(c->dst(), c->prune_r2, ctl, c->stream);
+  if (c->half_basis) launch_mma_threshold(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, c->dst(), c->stream);
 }
 
 cpd_status read_state(cpd_ctx* c, DevState* h) {
@@ -341,7 +345,7 @@ cpd_status capture_graph(cpd_ctx* c, int which) {
 cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
   if (N == c->N) return CPD_OK;
   c->drop_graphs();
-  c->ep = plan_estep(c->M, N, c->fp64, c->sms, c->sorted_model);
+  c->ep = plan_estep(c->M, N, c->fp64, c->sms, c->sorted_model, c->half_basis);
   STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
   STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
   STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
@@ -799,7 +803,8 @@ cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t
   if (M < 1 || M > kMaxN || N < 1 || N > kMaxN) return fail(CPD_EINVAL, "M and N must be in [1, 2^30]");
   if (precision != CPD_FP64 && precision != CPD_FP32 && precision != CPD_MIXED)
     return fail(CPD_EINVAL, "unknown precision");
-  if (precision == CPD_MIXED) precision = CPD_FP32;    // the mixed mode's E-step is the FP32 one
+  const bool mixed = precision == CPD_MIXED;   // FP32 E-step with tensor-core passes while sigma2 allows
+  if (mixed) precision = CPD_FP32;
   if (!(sigma2 > 0.0) || !std::isfinite(sigma2)) return fail(CPD_EINVAL, "sigma2 must be > 0");
   if (!(w >= 0.0 && w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
   cudaStream_t s = (cudaStream_t)stream;
@@ -808,7 +813,7 @@ cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t
   int dev = 0, sms = 0;
   CUDA_TRY(cudaGetDevice(&dev));
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const EstepPlan ep = plan_estep(M, N, fp64, sms);
+  const EstepPlan ep = plan_estep(M, N, fp64, sms, false, mixed);
   Buf T4, Y4, Yb, Yt4, pA, pB, sums, flags, P1, den, st, stage;
   auto release = [&]() {
     for (Buf* b : {&T4, &Y4, &Yb, &Yt4, &pA, &pB, &sums, &flags, &P1, &den, &st, &stage}) b->release();
@@ -829,6 +834,10 @@ cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t
     STATUS_TRY(upload_points(nullptr, Y, N, Y4.p, true, stage, fp64, s));
     launch_state_init(st.as<DevState>(), sigma2, s);
     launch_state_params(st.as<DevState>(), w, 1.0, 0.0, 0.0, 0, nullptr, M, N, 0, s);
+    if (mixed) {
+      launch_state_prune(st.as<DevState>(), 0.f, kMmaAllowed, s);
+      launch_mma_threshold(T4.as<float4>(), M, Y4.as<float4>(), N, st.as<DevState>(), s);
+    }
     if (fp64)
       launch_estep<double>(ep, T4.as<dvec4>(), nullptr, M, Y4.as<dvec4>(), Yb.as<dvec4>(), N, pA.as<double>(),
                            pB.as<double>(), sums.as<double>(), flags.as<int>(), Yt4.as<dvec4>(), nullptr, P1.as<double>(),

@@ -164,6 +164,7 @@ __global__ void state_init(DevState* st, double sigma2) {
   st->last_eval_frac = 1.0;
   st->prune_r2 = 0.f;
   st->prune_ctl = 0;
+  st->mma_s2min = INFINITY;
 }
 
 __global__ void state_prune(DevState* st, float r2, int ctl) {

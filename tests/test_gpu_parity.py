@@ -447,3 +447,44 @@ def test_mixed_precision_basis_is_the_fp16_rounding_of_the_fp32_basis():
     # absolute step of 2^-24)
     np.testing.assert_allclose(Um, U32, rtol=2.0 ** -11, atol=2.0 ** -24)
     assert np.abs(Um - U32).max() > 0      # it is really stored in FP16
+
+
+# ------------------------------- mixed precision: tensor-core E-step passes
+# While sigma2 >= 4.4e-4 R^2 (R: largest point norm) the CPD_MIXED E-step
+# takes its Gaussian exponents from BF16 tensor-core products of 3-way split
+# operands (FP32 accumulation).  The accumulated terms are as large as
+# q^2 R^2 <= ~2000 units of the base-2 exponent, so its rounding reaches
+# ~1e-3 at the floor and less above it; the errors against the FP64 oracle
+# are printed and bounded here by what that allows: Gaussians within ~1e-3
+# relative, hence den within 2e-3, Ytil within 1e-3 (relative norm).
+@pytest.mark.parametrize("M,N", [(300, 517), (1100, 2100), (2100, 1030)])
+@pytest.mark.parametrize("sigma2", [0.2, 0.05, 0.01])
+def test_estep_mixed_tensor_core_against_oracle(M, N, sigma2):
+    ps = pointsets(M, n_out=max(N - M, 0), n_in=min(M, N), seed=M + 2 * N)
+    T = ps.Yhat.astype(np.float32).astype(np.float64)
+    Y = ps.Y.astype(np.float32).astype(np.float64)
+    r2 = max((T ** 2).sum(1).max(), (Y ** 2).sum(1).max())
+    assert sigma2 >= 4.4e-4 * r2            # the tensor-core passes run at these sigma2
+    o = oracle.estep(T, Y, sigma2, 0.1)
+    g = cpd.estep(dev(T, cpd.FP32), dev(Y, cpd.FP32), sigma2, 0.1, cpd.MIXED)
+    g32 = cpd.estep(dev(T, cpd.FP32), dev(Y, cpd.FP32), sigma2, 0.1, cpd.FP32)
+    den_err = float(np.abs(host(g["den"]) / o["den"] - 1).max())
+    yt_err = rel(g["Ytil"], o["Ytil"])
+    print(f"M={M} N={N} sigma2={sigma2}: den max rel {den_err:.2e}, Ytil rel {yt_err:.2e} "
+          f"(fp32: {np.abs(host(g32['den']) / o['den'] - 1).max():.2e}, {rel(g32['Ytil'], o['Ytil']):.2e})")
+    assert den_err <= 2e-3
+    assert yt_err <= 1e-3
+    p1 = host(g["P1"])
+    assert np.abs(p1 - o["P1"]).max() <= 2e-3 * max(o["P1"].max(), 1.0)
+    # it is the tensor-core path (not bit-identical to the FP32 one)
+    assert not np.array_equal(host(g["Ytil"]), host(g32["Ytil"]))
+
+
+def test_estep_mixed_below_the_floor_is_the_fp32_estep():
+    ps = pointsets(1100, n_out=1000, n_in=1100, seed=77)
+    T, Y = dev(ps.Yhat, cpd.FP32), dev(ps.Y, cpd.FP32)
+    for sigma2 in (1e-4, 3e-4):
+        g = cpd.estep(T, Y, sigma2, 0.1, cpd.MIXED)
+        g32 = cpd.estep(T, Y, sigma2, 0.1, cpd.FP32)
+        np.testing.assert_array_equal(host(g["Ytil"]), host(g32["Ytil"]))
+        np.testing.assert_array_equal(host(g["den"]), host(g32["den"]))
