@@ -1,31 +1,33 @@
 // E-step passes with tensor-core distance tiles (mixed-precision mode).
 //
 // The exponent of every Gaussian of a 16 x 8 tile of (row point, column
-// point) pairs is one warp-level BF16 tensor-core product with FP32
-// accumulation (mma.sync m16n8k16, two K-steps, K = 32):
+// point) pairs is one warp-level FP16 tensor-core product with FP32
+// accumulation (mma.sync m16n8k16, K = 16):
 //     e = 2 r'.c' - |r'|^2 - |c'|^2 (+ lid_c in pass B)
 // over the coordinates pre-scaled by q = sqrt(log2(e) / (2 sigma2)), so
 // e = -|r' - c'|^2 (+ lid) is the base-2 exponent the FP32 passes compute
-// directly.  Each FP32 value v is split into three BF16 parts v1 + v2 + v3
-// (about 24 significant bits); the cross products kept are those of total
-// order <= 2^-16 (v1w1, v1w2, v2w1, v1w3, v2w2, v3w1), the norms and lid
-// enter as split terms against an exact 1:
-//   k  0..17  row side 2 r_d^(i)           col side c_d^(j)   (d, (i, j) pattern)
-//   k 18..20  row side -|r'|^2 (split)     col side 1
-//   k 21..23  row side 1                   col side -|c'|^2 (split)
-//   k 24..26  row side 1                   col side lid (split; 0 in pass A)
-//   k 27..31  0
-// The products of BF16 values are exact in FP32; what remains is the FP32
-// accumulation of terms as large as |r'|^2, whose rounding grows with
-// 1 / sigma2 -- so these passes run only while sigma2 >= mma_s2min (see
-// kMmaS2PerR2) and the
-// FP32 direct passes take over below it (both are in every captured
-// iteration; each steps aside on the device-side test).  The exponentials
-// and sums are the FP32 passes' own: ex2.approx.ftz, FP32 accumulation,
-// split partials reduced in a fixed order.
+// directly.  Each FP32 value v is split into two FP16 parts v1 + v2 (22
+// significant bits); the cross products v1w1, v1w2, v2w1 are kept (v2w2 is
+// 2^-22 of the product), the norms and lid enter as split terms against an
+// exact 1:
+//   k  0..8   row side 2 r_d^(i)           col side c_d^(j)   (d, (i, j) in (1,1) (1,2) (2,1))
+//   k  9..10  row side -|r'|^2 (split)     col side 1
+//   k 11..12  row side 1                   col side -|c'|^2 (split)
+//   k 13..14  row side 1                   col side lid (split; 0 in pass A)
+//   k 15      0
+// Products of FP16 values are exact in FP32; what remains is the FP32
+// accumulation of terms as large as |r'|^2 and the 2^-22 split residue,
+// both growing with 1 / sigma2 -- so these passes run only while sigma2 >=
+// mma_s2min (see kMmaS2PerR2; there q^2 R^2 <= ~2000, well inside FP16's
+// range), and the FP32 direct passes take over below it (both are in every
+// captured iteration; each steps aside on the device-side test).  The
+// exponentials and sums are the FP32 passes' own: ex2.approx.ftz, FP32
+// accumulation, split partials reduced in a fixed order.  (A first version
+// with three BF16 parts and K = 32 measured the legacy tensor pipe 44 %
+// busy in pass A: halving K moves the bound to the exponentials.)
 #include "estep_dev.cuh"
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 
@@ -39,59 +41,55 @@ constexpr int kMmaThreads = 256;            // 8 warps
 constexpr int kMmaTilesPerWarp = 2;         // 16-point row tiles per warp
 constexpr int kMmaRowsPerBlock = 8 * 16 * kMmaTilesPerWarp;   // 256 row points per block
 constexpr int kMmaStage = 128;              // column points staged per shared tile
-constexpr int kAugK = 32;                   // augmented dimension
-constexpr int kAugStride = 40;              // bf16 per staged vector (80 bytes: conflict-free ldmatrix)
+constexpr int kAugK = 16;                   // augmented dimension
+constexpr int kAugStride = 24;              // halves per staged vector (48 bytes: conflict-free ldmatrix)
+constexpr float kPadNorm = -60000.f;        // padding column: exponents far below -126, finite in FP16
 
-// Row-side and column-side augmented vectors (BF16) of a scaled point v with
-// squared norm n (and lid for the column side).
-__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(v);
-  const float r1 = v - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+// Row-side and column-side augmented vectors (FP16) of a scaled point.
+__device__ __forceinline__ void split2(float v, __half& a, __half& b) {
+  a = __float2half_rn(v);
+  b = __float2half_rn(v - __half2float(a));
 }
 
-// pattern of (row part i, column part j) for the six kept cross products
-__device__ __forceinline__ int row_part(int p) { return p == 2 || p == 4 ? 1 : p == 5 ? 2 : 0; }
-__device__ __forceinline__ int col_part(int p) { return p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0; }
+// (row part, column part) of the three kept cross products
+__device__ __forceinline__ int row_part(int p) { return p == 2 ? 1 : 0; }
+__device__ __forceinline__ int col_part(int p) { return p == 1 ? 1 : 0; }
 
-__device__ __forceinline__ void row_vector(float x, float y, float z, bool valid, __nv_bfloat16* out) {
-  __nv_bfloat16 s[3][3], nn[3];
+__device__ __forceinline__ void row_vector(float x, float y, float z, bool valid, __half* out) {
+  __half s[3][2], nn[2];
   const float v[3] = {x, y, z};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) split3(valid ? 2.0f * v[d] : 0.f, s[d][0], s[d][1], s[d][2]);
-  split3(valid ? -(x * x + y * y + z * z) : 0.f, nn[0], nn[1], nn[2]);
-  const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+  for (int d = 0; d < 3; ++d) split2(valid ? 2.0f * v[d] : 0.f, s[d][0], s[d][1]);
+  split2(valid ? -(x * x + y * y + z * z) : 0.f, nn[0], nn[1]);
+  const __half one = __float2half_rn(1.0f), zero = __float2half_rn(0.0f);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int p = 0; p < 6; ++p) out[6 * d + p] = s[d][row_part(p)];
-  out[18] = nn[0]; out[19] = nn[1]; out[20] = nn[2];
+    for (int p = 0; p < 3; ++p) out[3 * d + p] = s[d][row_part(p)];
+  out[9] = nn[0]; out[10] = nn[1];
 #pragma unroll
-  for (int k = 21; k < 27; ++k) out[k] = one;
-#pragma unroll
-  for (int k = 27; k < kAugK; ++k) out[k] = zero;
+  for (int k = 11; k < 15; ++k) out[k] = one;
+  out[15] = zero;
 }
 
-// Column side; an invalid (padding) point gets a huge negative norm so its
+// Column side; an invalid (padding) point gets a large negative norm so its
 // exponents are far below -126 (its Gaussians are exactly 0).
-__device__ __forceinline__ void col_vector(float x, float y, float z, float lid, bool valid, __nv_bfloat16* out) {
-  __nv_bfloat16 s[3][3], nn[3], ll[3];
+__device__ __forceinline__ void col_vector(float x, float y, float z, float lid, bool valid, __half* out) {
+  __half s[3][2], nn[2], ll[2];
   const float v[3] = {x, y, z};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) split3(valid ? v[d] : 0.f, s[d][0], s[d][1], s[d][2]);
-  split3(valid ? -(x * x + y * y + z * z) : -1e30f, nn[0], nn[1], nn[2]);
-  split3(valid ? lid : 0.f, ll[0], ll[1], ll[2]);
-  const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+  for (int d = 0; d < 3; ++d) split2(valid ? v[d] : 0.f, s[d][0], s[d][1]);
+  split2(valid ? -(x * x + y * y + z * z) : kPadNorm, nn[0], nn[1]);
+  split2(valid ? lid : 0.f, ll[0], ll[1]);
+  const __half one = __float2half_rn(1.0f), zero = __float2half_rn(0.0f);
 #pragma unroll
   for (int d = 0; d < 3; ++d)
 #pragma unroll
-    for (int p = 0; p < 6; ++p) out[6 * d + p] = s[d][col_part(p)];
-  out[18] = one; out[19] = one; out[20] = one;
-  out[21] = nn[0]; out[22] = nn[1]; out[23] = nn[2];
-  out[24] = ll[0]; out[25] = ll[1]; out[26] = ll[2];
-#pragma unroll
-  for (int k = 27; k < kAugK; ++k) out[k] = zero;
+    for (int p = 0; p < 3; ++p) out[3 * d + p] = s[d][col_part(p)];
+  out[9] = one; out[10] = one;
+  out[11] = nn[0]; out[12] = nn[1];
+  out[13] = ll[0]; out[14] = ll[1];
+  out[15] = zero;
 }
 
 __device__ __forceinline__ unsigned int smem_u32(const void* p) {
@@ -105,30 +103,37 @@ __device__ __forceinline__ void ldsm_x4(unsigned int addr, unsigned int& r0, uns
                : "r"(addr));
 }
 
-// D = A B (+0): 16 x 8 FP32 from BF16 A (16 x 16, row) and B (16 x 8, col).
-__device__ __forceinline__ void mma_bf16(const unsigned int (&a)[4], unsigned int b0, unsigned int b1, float (&d)[4]) {
+// D = A B: 16 x 8 FP32 from FP16 A (16 x 16, row) and B (16 x 8, col).
+__device__ __forceinline__ void mma_f16(const unsigned int (&a)[4], unsigned int b0, unsigned int b1, float (&d)[4]) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
       "{%10, %11, %12, %13};"
       : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(d[0]), "f"(d[1]), "f"(d[2]), "f"(d[3]));
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f), "f"(0.f), "f"(0.f), "f"(0.f));
 }
 
 // Row fragments of a warp: tiles of 16 row points staged as augmented
 // vectors in shared memory; A fragments (two K-steps) via ldmatrix.x4.
-__device__ __forceinline__ void load_row_frags(const __nv_bfloat16 (*sRow)[kAugStride], int tile0,
-                                               unsigned int (&a)[kMmaTilesPerWarp][2][4]) {
+__device__ __forceinline__ void load_row_frags(const __half (*sRow)[kAugStride], int tile0,
+                                               unsigned int (&a)[kMmaTilesPerWarp][4]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int g = 0; g < kMmaTilesPerWarp; ++g)
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      // matrices: (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
-      const int mat = lane >> 3, r = lane & 7;
-      const int row = 16 * (tile0 + g) + (mat & 1) * 8 + r;
-      const int k = 16 * ks + (mat >> 1) * 8;
-      ldsm_x4(smem_u32(&sRow[row][k]), a[g][ks][0], a[g][ks][1], a[g][ks][2], a[g][ks][3]);
-    }
+  for (int g = 0; g < kMmaTilesPerWarp; ++g) {
+    // matrices: (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+    const int mat = lane >> 3, r = lane & 7;
+    const int row = 16 * (tile0 + g) + (mat & 1) * 8 + r;
+    const int k = (mat >> 1) * 8;
+    ldsm_x4(smem_u32(&sRow[row][k]), a[g][0], a[g][1], a[g][2], a[g][3]);
+  }
+}
+
+// B fragments of two groups of 8 column points (j, j + 8): matrices (cols
+// j.., k 0-7), (cols j.., k 8-15), (cols j+8.., k 0-7), (cols j+8.., k 8-15).
+__device__ __forceinline__ void load_col_frags(const __half (*sCol)[kAugStride], int j, unsigned int& b00,
+                                               unsigned int& b01, unsigned int& b10, unsigned int& b11) {
+  const int lane = threadIdx.x & 31;
+  const int mat = lane >> 3;
+  ldsm_x4(smem_u32(&sCol[j + 8 * (mat >> 1) + (lane & 7)][8 * (mat & 1)]), b00, b01, b10, b11);
 }
 
 // ------------------------------------------------------------------ pass A
@@ -139,8 +144,8 @@ __global__ void __launch_bounds__(kMmaThreads)
 passA_f32_mma(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4, int N,
               float* __restrict__ partA, DevState* __restrict__ st, int gate) {
   if ((gate && iteration_gated(st)) || !mma_active(st)) return;
-  __shared__ __align__(16) __nv_bfloat16 sRow[kMmaRowsPerBlock][kAugStride];
-  __shared__ __align__(16) __nv_bfloat16 sCol[kMmaStage][kAugStride];
+  __shared__ __align__(16) __half sRow[kMmaRowsPerBlock][kAugStride];
+  __shared__ __align__(16) __half sCol[kMmaStage][kAugStride];
   const float q = scale_q(st->sigma2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * kMmaRowsPerBlock;
@@ -151,7 +156,7 @@ passA_f32_mma(const float4* __restrict__ T4, int M, int rows_per_chunk, const fl
     row_vector(q * y.x, q * y.y, q * y.z, n < N, sRow[i]);
   }
   __syncthreads();
-  unsigned int a[kMmaTilesPerWarp][2][4];
+  unsigned int a[kMmaTilesPerWarp][4];
   load_row_frags(sRow, warp * kMmaTilesPerWarp, a);
   float acc[kMmaTilesPerWarp][2];
 #pragma unroll
@@ -169,18 +174,18 @@ passA_f32_mma(const float4* __restrict__ T4, int M, int rows_per_chunk, const fl
     __syncthreads();
     const int cnt = min(kMmaStage, r1 - base);
 #pragma unroll 1
-    for (int j = 0; j < cnt; j += 8) {
-      // B fragments of 8 column points: matrices = k blocks 0-7, 8-15, 16-23, 24-31
-      unsigned int b0, b1, b2, b3;
-      ldsm_x4(smem_u32(&sCol[j + (lane & 7)][8 * (lane >> 3)]), b0, b1, b2, b3);
+    for (int j = 0; j < cnt; j += 16) {       // staged tiles are whole multiples of 16 points
+      unsigned int b[2][2];
+      load_col_frags(sCol, j, b[0][0], b[0][1], b[1][0], b[1][1]);
 #pragma unroll
-      for (int g = 0; g < kMmaTilesPerWarp; ++g) {
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16(a[g][0], b0, b1, d);
-        mma_bf16(a[g][1], b2, b3, d);
-        acc[g][0] += ex2_approx(d[0]) + ex2_approx(d[1]);   // row lane/4, columns 2(lane%4), +1
-        acc[g][1] += ex2_approx(d[2]) + ex2_approx(d[3]);   // row lane/4 + 8
-      }
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int g = 0; g < kMmaTilesPerWarp; ++g) {
+          float d[4];
+          mma_f16(a[g], b[c][0], b[c][1], d);
+          acc[g][0] += ex2_approx(d[0]) + ex2_approx(d[1]);   // row lane/4, columns 2(lane%4), +1
+          acc[g][1] += ex2_approx(d[2]) + ex2_approx(d[3]);   // row lane/4 + 8
+        }
     }
   }
   // the four lanes of a quad hold the same rows: add their column subsets
@@ -210,8 +215,8 @@ passB_f32_mma(const float4* __restrict__ T4, int M, const float4* __restrict__ Y
     st->n_flag_cols = 0;
     st->n_flag_rows = 0;
   }
-  __shared__ __align__(16) __nv_bfloat16 sRow[kMmaRowsPerBlock][kAugStride];
-  __shared__ __align__(16) __nv_bfloat16 sCol[kMmaStage][kAugStride];
+  __shared__ __align__(16) __half sRow[kMmaRowsPerBlock][kAugStride];
+  __shared__ __align__(16) __half sCol[kMmaStage][kAugStride];
   __shared__ float4 sY[kMmaStage];
   const float q = scale_q(st->sigma2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -223,8 +228,10 @@ passB_f32_mma(const float4* __restrict__ T4, int M, const float4* __restrict__ Y
     row_vector(q * t.x, q * t.y, q * t.z, m < M, sRow[i]);
   }
   __syncthreads();
-  unsigned int a[kMmaTilesPerWarp][2][4];
+  unsigned int a[kMmaTilesPerWarp][4];
   load_row_frags(sRow, warp * kMmaTilesPerWarp, a);
+  // per row (h: lane/4, lane/4 + 8): P1, PX, PY, PZ, V over the thread's
+  // columns (scalar: packing two MUFU results would cost moves)
   float p1[kMmaTilesPerWarp][2], px[kMmaTilesPerWarp][2], py[kMmaTilesPerWarp][2], pz[kMmaTilesPerWarp][2],
       v[kMmaTilesPerWarp][2];
 #pragma unroll
@@ -245,23 +252,27 @@ passB_f32_mma(const float4* __restrict__ T4, int M, const float4* __restrict__ Y
     __syncthreads();
     const int cnt = min(kMmaStage, c1 - base);
 #pragma unroll 1
-    for (int j = 0; j < cnt; j += 8) {
-      unsigned int b0, b1, b2, b3;
-      ldsm_x4(smem_u32(&sCol[j + (lane & 7)][8 * (lane >> 3)]), b0, b1, b2, b3);
-      const float4 ya = sY[j + 2 * (lane & 3)], yb = sY[j + 2 * (lane & 3) + 1];   // columns of d[0]/d[2], d[1]/d[3]
+    for (int j = 0; j < cnt; j += 16) {       // staged tiles are whole multiples of 16 points
+      unsigned int b[2][2];
+      load_col_frags(sCol, j, b[0][0], b[0][1], b[1][0], b[1][1]);
 #pragma unroll
-      for (int g = 0; g < kMmaTilesPerWarp; ++g) {
-        float d[4] = {0.f, 0.f, 0.f, 0.f};
-        mma_bf16(a[g][0], b0, b1, d);
-        mma_bf16(a[g][1], b2, b3, d);
+      for (int c = 0; c < 2; ++c) {
+        // columns of d[0]/d[2] and d[1]/d[3]
+        const float4 ya = sY[j + 8 * c + 2 * (lane & 3)], yb = sY[j + 8 * c + 2 * (lane & 3) + 1];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const float w0 = ex2_approx(d[2 * h]), w1 = ex2_approx(d[2 * h + 1]);   // e_mn / den_n
-          p1[g][h] += w0 + w1;
-          px[g][h] = fmaf(w0, ya.x, fmaf(w1, yb.x, px[g][h]));
-          py[g][h] = fmaf(w0, ya.y, fmaf(w1, yb.y, py[g][h]));
-          pz[g][h] = fmaf(w0, ya.z, fmaf(w1, yb.z, pz[g][h]));
-          v[g][h] = fmaf(w0, ya.w - d[2 * h], fmaf(w1, yb.w - d[2 * h + 1], v[g][h]));   // d'^2 = lid - e
+        for (int g = 0; g < kMmaTilesPerWarp; ++g) {
+          float d[4];
+          mma_f16(a[g], b[c][0], b[c][1], d);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float w0 = ex2_approx(d[2 * h]), w1 = ex2_approx(d[2 * h + 1]);   // e_mn / den_n
+            p1[g][h] += w0;
+            p1[g][h] += w1;
+            px[g][h] = fmaf(w1, yb.x, fmaf(w0, ya.x, px[g][h]));
+            py[g][h] = fmaf(w1, yb.y, fmaf(w0, ya.y, py[g][h]));
+            pz[g][h] = fmaf(w1, yb.z, fmaf(w0, ya.z, pz[g][h]));
+            v[g][h] = fmaf(w1, yb.w - d[2 * h + 1], fmaf(w0, ya.w - d[2 * h], v[g][h]));   // d'^2 = lid - e
+          }
         }
       }
     }
