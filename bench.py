@@ -290,6 +290,9 @@ def run_batch(args, peaks, torch):
     t0 = time.perf_counter()
     b = cpd.Batch(Xs, Ys, w=bc["omega"], beta=bc["beta"], lam=bc["lam"], K=bc["K"])
     setup_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tune_e, tune_p, tune_ms = b.autotune(3)  # work-item plan picked by timing (untimed here)
+    tune_s = time.perf_counter() - t0
     n, grid, items = b.launch_shape()
     for _ in range(2):                      # graph capture + warm-up, untimed
         b.reset()
@@ -321,7 +324,10 @@ def run_batch(args, peaks, torch):
                phase_ms_per_iter=dict(zip(["estep_a_with_column_reduction", "estep_b_with_row_reduction",
                                            "projection_with_diag_update", "expansion_with_sigma2"], phase)),
                phase_busy_fraction=busy,
-               setup_s=setup_s, timed_calls=len(ms))
+               setup_s=setup_s, timed_calls=len(ms),
+               autotune=dict(chosen=dict(e_items_per_block=tune_e, proj_kbytes=tune_p), seconds=tune_s,
+                             candidates_ms_3_iters=dict(zip(["e2/p256", "e2/p512", "e4/p256", "e4/p512", "e8/p256",
+                                                             "e8/p512"], tune_ms))))
     if not args.no_batch_baseline:
         # the same registrations one after another, each from its own graph
         ctxs = []

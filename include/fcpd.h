@@ -385,6 +385,19 @@ cpd_status cpd_batch_phase_ms(const cpd_batch *b, float *phase_ms);
  * re-computed from the stored scene.  Synchronises. */
 cpd_status cpd_batch_reset(cpd_batch *b);
 
+/*
+ * Autotuner of the persistent kernel's work items: times n_iter (1..64)
+ * iterations of the batch under each of six work-item plans -- E-step items
+ * per resident block in {2, 4, 8} x projection items of {256, 512} KB of the
+ * basis, in that order -- keeps the fastest, and restarts every
+ * registration (as cpd_batch_reset).  Optional outputs (host): the chosen
+ * e_items and proj_kb, and ms_out[6], the measured milliseconds of each
+ * candidate.  Synchronises.  The results of the registrations do not depend
+ * on the plan beyond summation order.
+ */
+cpd_status cpd_batch_autotune(cpd_batch *b, int32_t n_iter, int32_t *e_items_out, int32_t *proj_kb_out,
+                              float *ms_out);
+
 /* Free a batch and all its pairs (NULL is ignored).  Synchronises first. */
 void cpd_batch_destroy(cpd_batch *b);
 

@@ -33,7 +33,8 @@ EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
-           "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_destroy"]
+           "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_autotune",
+           "cpd_batch_destroy"]
 
 
 class CpdParams(C.Structure):
@@ -95,6 +96,7 @@ def load():
                 "cpd_batch_launch_shape": ([vp, ip, ip, ip], C.c_int),
                 "cpd_batch_phase_ms": ([vp, C.POINTER(C.c_float)], C.c_int),
                 "cpd_batch_reset": ([vp], C.c_int),
+                "cpd_batch_autotune": ([vp, i32, ip, ip, C.POINTER(C.c_float)], C.c_int),
                 "cpd_batch_destroy": ([vp], None),
             }
             for name, (args, res) in sig.items():
@@ -361,6 +363,14 @@ class Batch:
 
     def reset(self):
         _check(load().cpd_batch_reset(self._h))
+
+    def autotune(self, n_iter=3):
+        """Times six work-item plans, keeps the fastest (registrations restart).
+        Returns (e_items, proj_kb, ms per candidate)."""
+        e, p = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 6)()
+        _check(load().cpd_batch_autotune(self._h, int(n_iter), C.byref(e), C.byref(p), ms))
+        return e.value, p.value, list(ms)
 
     def close(self):
         if getattr(self, "_h", None):

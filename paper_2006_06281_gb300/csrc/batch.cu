@@ -437,16 +437,19 @@ int batch_resident_blocks(int sms) {
   return occ * sms;
 }
 
-// Work-item sizes.  Target: about four E-step items per resident block over
-// the whole batch (largest items first, so the queue balances), each item a
-// full 1024-point tile by a run of the other dimension; M-step items of about
-// 128-256 KB of the basis.
-void plan_batch(BatchPair* P, int n_pairs, int resident) {
+// Work-item sizes.  Target: about `e_items_per_block` E-step items per
+// resident block over the whole batch (largest items first, so the queue
+// balances), each item a full 1024-point tile by a run of the other
+// dimension; projection items of about `proj_kbytes` KB of the basis, other
+// M-step items of about 256 KB.  cpd_batch_autotune picks the two numbers by
+// timing.
+void plan_batch(BatchPair* P, int n_pairs, int resident, int e_items_per_block, int proj_kbytes) {
   double total = 0.0;
   for (int i = 0; i < n_pairs; ++i) total += (double)P[i].M * P[i].N;
   const int64_t tileA = (int64_t)dev::kThreadsA * dev::kColsA32;
   const int64_t tileB = (int64_t)dev::kThreadsB * dev::kRowsB32;
-  const double per_item = std::max(total / (4.0 * std::max(resident, 1)), (double)tileA * dev::kTileA);
+  const double per_item = std::max(total / ((double)std::max(e_items_per_block, 1) * std::max(resident, 1)),
+                                    (double)tileA * dev::kTileA);
   for (int i = 0; i < n_pairs; ++i) {
     BatchPair& p = P[i];
     const int64_t M = p.M, N = p.N, K = p.K;
@@ -474,7 +477,7 @@ void plan_batch(BatchPair* P, int n_pairs, int resident) {
     const int64_t colsC = (int64_t)kThreadsBatch * 8;     // columns of one colsum tile
     if (p.narrow) {
       m.p_col_tiles = 1;
-      const int64_t rows = std::max<int64_t>(256, (512 * 1024) / (m.ldU * 4));
+      const int64_t rows = std::max<int64_t>(64, ((int64_t)proj_kbytes * 1024) / (m.ldU * 4));
       m.p_row_chunks = (int)cdiv(M, rows);
     } else {
       m.p_col_tiles = (int)cdiv(m.ldU, colsC);

@@ -246,8 +246,9 @@ struct BatchCtl {
 };
 // Resident blocks of the persistent kernel on `sms` SMs (0 on failure).
 int batch_resident_blocks(int sms);
-// Fills ep, mp and narrow of every pair from its M, N, K.
-void plan_batch(BatchPair* pairs_host, int n_pairs, int resident);
+// Fills ep, mp and narrow of every pair from its M, N, K (work-item sizes:
+// see batch.cu; the defaults are the untuned plan).
+void plan_batch(BatchPair* pairs_host, int n_pairs, int resident, int e_items_per_block = 4, int proj_kbytes = 512);
 // Work items of every phase (phase ph owns items [phase_off[ph], phase_off[ph+1])).
 void batch_items(const BatchPair* pairs_host, int n_pairs, std::vector<BatchItem>& items, std::vector<int>& phase_off);
 // Completion tickets a pair needs (after plan_batch), and the phases per iteration.

@@ -44,6 +44,7 @@ constexpr int kMmaStage = 128;              // column points staged per shared t
 constexpr int kAugK = 16;                   // augmented dimension
 constexpr int kAugStride = 24;              // halves per staged vector (48 bytes: conflict-free ldmatrix)
 constexpr float kPadNorm = -60000.f;        // padding column: exponents far below -126, finite in FP16
+static_assert(kAugStride >= kAugK && (kAugStride * 2) % 16 == 0, "staged vectors: K halves, 16-byte rows");
 
 // Row-side and column-side augmented vectors (FP16) of a scaled point.
 __device__ __forceinline__ void split2(float v, __half& a, __half& b) {

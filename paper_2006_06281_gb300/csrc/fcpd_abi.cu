@@ -915,6 +915,7 @@ struct cpd_batch {
   BatchCtl last{};            // control block after the last call
   int last_iters = 0;
   size_t n_tickets = 0;
+  int tune_e = 0, tune_p = 0; // work-item plan in use (see plan_batch)
 
   ~cpd_batch() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -927,28 +928,32 @@ struct cpd_batch {
 namespace {
 
 constexpr int kMaxBatch = 1 << 16;
+constexpr int kBatchDefaultItems = 4;      // untuned plan: E-step items per resident block
+constexpr int kBatchDefaultProjKB = 512;   // untuned plan: KB of the basis per projection item
 
-// Per-pair buffers sized for the batched plan, scene upload and the start of
-// the registration.
-cpd_status batch_load_pair(cpd_ctx* c, const BatchPair& bp, const void* Y) {
-  if (bp.mp.ldU != c->mp.ldU || bp.mp.ldM != c->mp.ldM)
-    return fail(CPD_ECUDA, "internal: batched basis layout differs from the context's");
+// Scene of one pair: buffers, upload, state parameters.
+cpd_status batch_load_scene(cpd_ctx* c, int64_t N, const void* Y) {
   c->drop_graphs();
-  c->ep = bp.ep;
-  c->mp = bp.mp;
-  const int64_t N = bp.N;
   STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
   STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
+  c->N = N;
+  launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, 0.0, 0, c->hist.as<double>(), c->M, N, c->K,
+                      c->stream);
+  return upload_points(c, Y, N, c->Y4.p, true, c->stage, false, c->stream);
+}
+
+// Per-pair scratch sized for a batched plan.
+cpd_status batch_size_pair(cpd_ctx* c, const BatchPair& bp) {
+  if (bp.mp.ldU != c->mp.ldU || bp.mp.ldM != c->mp.ldM)
+    return fail(CPD_ECUDA, "internal: batched basis layout differs from the context's");
+  c->ep = bp.ep;
+  c->mp = bp.mp;
   STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
   STATUS_TRY(c->partB.ensure((size_t)c->ep.partB_elems * c->es));
   STATUS_TRY(c->partP.ensure((size_t)c->mp.part_elems * c->es));
   STATUS_TRY(c->sums.ensure((size_t)std::max(c->ep.sums_elems, c->mp.sums_elems) * sizeof(double)));
   STATUS_TRY(c->flags.ensure((size_t)c->ep.flags_elems * sizeof(int)));
-  c->N = N;
-  launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, 0.0, 0, c->hist.as<double>(), c->M, N, c->K,
-                      c->stream);
-  STATUS_TRY(upload_points(c, Y, N, c->Y4.p, true, c->stage, false, c->stream));
-  return start_registration(c);
+  return CPD_OK;
 }
 
 BatchPair batch_pointers(cpd_ctx* c, const BatchPair& plan) {
@@ -972,6 +977,45 @@ BatchPair batch_pointers(cpd_ctx* c, const BatchPair& plan) {
   b.flags = c->flags.as<int>();
   b.st = c->dst();
   return b;
+}
+
+// Work-item plan (item sizes e_items per resident block / proj_kb KB, see
+// plan_batch): per-pair scratch, device pair table, item lists, tickets.
+// Invalidates the captured launch.
+cpd_status batch_apply_plan(cpd_batch* b, int e_items, int proj_kb) {
+  const int n = b->n;
+  plan_batch(b->pairs.data(), n, b->grid, e_items, proj_kb);
+  size_t n_tickets = 0;
+  for (int i = 0; i < n; ++i) n_tickets += (size_t)batch_tickets(b->pairs[i]);
+  STATUS_TRY(b->tickets.ensure(n_tickets * sizeof(unsigned int)));
+  b->n_tickets = n_tickets;
+  for (int i = 0, off = 0; i < n; ++i) {
+    STATUS_TRY(batch_size_pair(b->ctx[i], b->pairs[i]));
+    const int nt = batch_tickets(b->pairs[i]);
+    b->pairs[i] = batch_pointers(b->ctx[i], b->pairs[i]);
+    b->pairs[i].tix = b->tickets.as<unsigned int>() + off;
+    off += nt;
+  }
+  std::vector<BatchItem> items;
+  batch_items(b->pairs.data(), n, items, b->phase_off_host);
+  b->n_items = (int)items.size();
+  STATUS_TRY(b->pairs_dev.ensure(sizeof(BatchPair) * (size_t)n));
+  STATUS_TRY(b->items.ensure(sizeof(BatchItem) * items.size()));
+  STATUS_TRY(b->phase_off.ensure(sizeof(int) * b->phase_off_host.size()));
+  CUDA_TRY(cudaMemsetAsync(b->tickets.p, 0, n_tickets * sizeof(unsigned int), b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->pairs_dev.p, b->pairs.data(), sizeof(BatchPair) * (size_t)n, cudaMemcpyHostToDevice,
+                           b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->items.p, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->phase_off.p, b->phase_off_host.data(), sizeof(int) * b->phase_off_host.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));      // the host vectors above are reused
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->graph_iters = -1;
+  b->tune_e = e_items;
+  b->tune_p = proj_kb;
+  return CPD_OK;
 }
 
 cpd_status batch_capture(cpd_batch* b, int n_iter, int extra) {
@@ -1090,37 +1134,15 @@ cpd_status cpd_batch_create(int32_t n_pairs, const void* const* X, const int64_t
     b->pairs[i].N = (int)N[i];
     b->pairs[i].K = (int)b->ctx[i]->K;
   }
-  plan_batch(b->pairs.data(), n_pairs, b->grid);
   cpd_status s;
-  size_t n_tickets = 0;
-  for (int i = 0; i < n_pairs; ++i) n_tickets += (size_t)batch_tickets(b->pairs[i]);
-  if ((s = b->tickets.ensure(n_tickets * sizeof(unsigned int))) != CPD_OK) return bail(s);
-  b->n_tickets = n_tickets;
-  if (cudaMemsetAsync(b->tickets.p, 0, n_tickets * sizeof(unsigned int), b->stream) != cudaSuccess)
-    return bail(fail(CPD_ECUDA, "clearing the completion tickets failed"));
-  for (int i = 0, off = 0; i < n_pairs; ++i) {
-    if ((s = batch_load_pair(b->ctx[i], b->pairs[i], Y[i])) != CPD_OK) return bail(s);
-    const int nt = batch_tickets(b->pairs[i]);
-    b->pairs[i] = batch_pointers(b->ctx[i], b->pairs[i]);
-    b->pairs[i].tix = b->tickets.as<unsigned int>() + off;
-    off += nt;
-  }
-  std::vector<BatchItem> items;
-  batch_items(b->pairs.data(), n_pairs, items, b->phase_off_host);
-  b->n_items = (int)items.size();
-  if ((s = b->pairs_dev.ensure(sizeof(BatchPair) * (size_t)n_pairs)) != CPD_OK) return bail(s);
-  if ((s = b->items.ensure(sizeof(BatchItem) * items.size())) != CPD_OK) return bail(s);
-  if ((s = b->phase_off.ensure(sizeof(int) * b->phase_off_host.size())) != CPD_OK) return bail(s);
+  for (int i = 0; i < n_pairs; ++i)
+    if ((s = batch_load_scene(b->ctx[i], N[i], Y[i])) != CPD_OK) return bail(s);
   if ((s = b->ctl.ensure(sizeof(BatchCtl))) != CPD_OK) return bail(s);
   if ((s = b->states.ensure(sizeof(DevState) * (size_t)n_pairs)) != CPD_OK) return bail(s);
-  if (cudaMemcpyAsync(b->pairs_dev.p, b->pairs.data(), sizeof(BatchPair) * (size_t)n_pairs, cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(b->items.p, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
-                      b->stream) != cudaSuccess ||
-      cudaMemcpyAsync(b->phase_off.p, b->phase_off_host.data(), sizeof(int) * b->phase_off_host.size(),
-                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess)
-    return bail(fail(CPD_ECUDA, "upload of the batch plan failed"));
+  if ((s = batch_apply_plan(b, kBatchDefaultItems, kBatchDefaultProjKB)) != CPD_OK) return bail(s);
+  for (int i = 0; i < n_pairs; ++i)
+    if ((s = start_registration(b->ctx[i])) != CPD_OK) return bail(s);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bail(fail(CPD_ECUDA, "batch setup failed"));
   *out = b;
   return CPD_OK;
 }
@@ -1197,6 +1219,47 @@ cpd_status cpd_batch_phase_ms(const cpd_batch* b, float* phase_ms) {
     phase_ms[ph] = (float)(span / 1e6 / b->last_iters);
     phase_ms[np + ph] = span > 0 ? (float)((double)b->last.busy_ns[ph] / ((double)b->grid * span)) : 0.f;
   }
+  return CPD_OK;
+}
+
+cpd_status cpd_batch_autotune(cpd_batch* b, int32_t n_iter, int32_t* e_items_out, int32_t* proj_kb_out,
+                              float* ms_out) {
+  g_err.clear();
+  if (!b) return fail(CPD_EINVAL, "batch is NULL");
+  if (n_iter < 1 || n_iter > 64) return fail(CPD_EINVAL, "n_iter must be in [1, 64]");
+  DeviceGuard guard(b->dev);
+  static const int cand[][2] = {{2, 256}, {2, 512}, {4, 256}, {4, 512}, {8, 256}, {8, 512}};
+  const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(CPD_ECUDA, "cudaEventCreate failed");
+  }
+  cpd_status st = CPD_OK;
+  float best = INFINITY;
+  int bi = -1;
+  for (int c = 0; c < nc && st == CPD_OK; ++c) {
+    if ((st = batch_apply_plan(b, cand[c][0], cand[c][1])) != CPD_OK) break;
+    if ((st = cpd_batch_reset(b)) != CPD_OK) break;
+    if ((st = cpd_batch_iterate(b, n_iter)) != CPD_OK) break;       // capture + warm-up
+    if ((st = cpd_batch_reset(b)) != CPD_OK) break;
+    cudaEventRecord(e0, b->stream);
+    if ((st = cpd_batch_iterate(b, n_iter)) != CPD_OK) break;
+    cudaEventRecord(e1, b->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_out) ms_out[c] = ms;
+    if (ms < best) { best = ms; bi = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != CPD_OK) return st;
+  STATUS_TRY(batch_apply_plan(b, cand[bi][0], cand[bi][1]));
+  STATUS_TRY(cpd_batch_reset(b));
+  if (e_items_out) *e_items_out = cand[bi][0];
+  if (proj_kb_out) *proj_kb_out = cand[bi][1];
   return CPD_OK;
 }
 

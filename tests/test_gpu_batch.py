@@ -177,3 +177,21 @@ def test_batch256_sampled_pairs_against_oracle():
             ref = oracle.register(f32(ps.X).astype(np.float64), f32(ps.Y).astype(np.float64), w=cfg["omega"],
                                   beta=cfg["beta"], lam_reg=cfg["lam"], n_iter=iters, K=cfg["K"])
             assert rel(b.T(i, device="cuda").cpu().numpy(), ref["T"]) <= FP32_TOL, (i, sizes[i])
+
+
+def test_autotuner_keeps_results_and_reports_candidates(scenes):
+    Xs = [f32(ps.X) for ps in scenes]
+    Ys = [f32(ps.Y) for ps in scenes]
+    with cpd.Batch(Xs, Ys, K=128) as ref:
+        ref.iterate(12)
+        Tref = [ref.T(i) for i in range(len(Xs))]
+    with cpd.Batch(Xs, Ys, K=128) as b:
+        e, p, ms = b.autotune(2)
+        assert e in (2, 4, 8) and p in (256, 512)
+        assert len(ms) == 6 and all(m > 0 for m in ms)
+        assert min(ms) == pytest.approx(ms[[2, 4, 8].index(e) * 2 + [256, 512].index(p)])
+        assert not b.state()[1].any()          # registrations restarted
+        b.iterate(12)
+        for i in range(len(Xs)):
+            # a different work-item plan changes only the summation order
+            assert rel(b.T(i), Tref[i].astype(np.float64)) <= 5e-5
