@@ -301,6 +301,51 @@ cpd_status cpd_get_work(cpd_ctx *ctx, int32_t n, double *eval_frac);
 /* 1 if the context keeps its points in spatial order (pruning possible). */
 int32_t cpd_spatial_order(const cpd_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Warm start (not in the paper).  In the top-K basis the displacement of
+ * every iteration lies in span(U) (Eq. 20), so T - X = U c with c = U^T
+ * (T - X): K x 3 eigen-coefficients.  A learned predictor of c (and of
+ * sigma2) for a new scene can start the EM loop near its end; W = 0 stays
+ * the fallback.  CPD_FP32 contexts.
+ * ---------------------------------------------------------------------- */
+
+/* coef_out (n_coef x 3 floats, host or device) = U[:, :n_coef]^T (T - X) of
+ * the current T.  Synchronises.  CPD_ESTATE before a registration started. */
+cpd_status cpd_coefficients(cpd_ctx *ctx, int32_t n_coef, void *coef_out);
+
+/* Start the next registration at T = X + U[:, :n_coef] coef (coef: n_coef x 3
+ * floats, host or device; n_coef = 0 gives T = X) with variance sigma2_0,
+ * iteration count 0: the following cpd_iterate continues from there
+ * (instead of T = X and the data variance).  Synchronises. */
+cpd_status cpd_warm_start(cpd_ctx *ctx, int32_t n_coef, const void *coef, double sigma2_0);
+
+/*
+ * The warm-start network: a point-set encoder -- a shared per-point MLP
+ * 3 -> 128 -> 128 -> 256 (ReLU), the maximum over the points, a head
+ * 256 -> 256 (ReLU) -> n_out -- trained on the GPU with the mean-squared
+ * error and Adam (beta1 0.9, beta2 0.999, eps 1e-8), all in FP32 CUDA
+ * kernels of this library.  Parameter layout: per layer the weights
+ * (fan_in x fan_out, row-major) then the biases, layers in order.
+ *   create:   n_out 1..4096; max_batch 1..1024 scenes of n_points points
+ *             (max_batch * n_points <= 2^24); seed of the initial weights.
+ *   forward / gradients / train_step: Y = B x n_points x 3 floats in DEVICE
+ *             memory (B <= max_batch); pred_out (B x n_out), target
+ *             (B x n_out), grad_out (num_params) host or device.  Each
+ *             synchronises the network's stream.
+ */
+typedef struct cpd_net cpd_net;
+cpd_status cpd_net_create(int32_t n_out, int32_t max_batch, int32_t n_points, uint64_t seed, void *stream,
+                          cpd_net **out);
+int64_t cpd_net_num_params(const cpd_net *net);
+cpd_status cpd_net_get_params(cpd_net *net, float *out);
+cpd_status cpd_net_set_params(cpd_net *net, const float *in);
+cpd_status cpd_net_forward(cpd_net *net, const float *Y, int32_t B, float *pred_out);
+cpd_status cpd_net_gradients(cpd_net *net, const float *Y, const float *target, int32_t B, float *grad_out,
+                             float *loss_out);
+cpd_status cpd_net_train_step(cpd_net *net, const float *Y, const float *target, int32_t B, float lr,
+                              float *loss_out);
+void cpd_net_destroy(cpd_net *net);
+
 /* Free a context (NULL is ignored).  Synchronises its stream first. */
 void cpd_destroy(cpd_ctx *ctx);
 

@@ -32,6 +32,8 @@ EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_destroy",
+           "cpd_coefficients", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
+           "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
            "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_autotune",
            "cpd_batch_destroy"]
@@ -86,6 +88,16 @@ def load():
                 "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
                 "cpd_destroy": ([vp], None),
                 "cpd_get_work": ([vp, i32, vp], C.c_int),
+                "cpd_coefficients": ([vp, i32, vp], C.c_int),
+                "cpd_warm_start": ([vp, i32, vp, d], C.c_int),
+                "cpd_net_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
+                "cpd_net_num_params": ([vp], i64),
+                "cpd_net_get_params": ([vp, vp], C.c_int),
+                "cpd_net_set_params": ([vp, vp], C.c_int),
+                "cpd_net_forward": ([vp, vp, i32, vp], C.c_int),
+                "cpd_net_gradients": ([vp, vp, vp, i32, vp, vp], C.c_int),
+                "cpd_net_train_step": ([vp, vp, vp, i32, C.c_float, vp], C.c_int),
+                "cpd_net_destroy": ([vp], None),
                 "cpd_spatial_order": ([vp], i32),
                 "cpd_batch_create": ([i32, C.POINTER(vp), C.POINTER(i64), C.POINTER(vp), C.POINTER(i64), pp, d, vp,
                                       C.POINTER(vp)], C.c_int),
@@ -250,6 +262,17 @@ class Context:
         out = np.empty(n)
         _check(load().cpd_get_work(self._h, int(n), out.ctypes.data))
         return out
+
+    def coefficients(self, n_coef):
+        """U[:, :n_coef]^T (T - X) of the current T (n_coef x 3, numpy)."""
+        out = np.empty((int(n_coef), 3), dtype=np.float32)
+        _check(load().cpd_coefficients(self._h, int(n_coef), out.ctypes.data))
+        return out
+
+    def warm_start(self, coef, sigma2_0):
+        """Next registration starts at T = X + U[:, :n] coef with variance sigma2_0."""
+        c = np.ascontiguousarray(coef, dtype=np.float32).reshape(-1, 3)
+        _check(load().cpd_warm_start(self._h, int(c.shape[0]), c.ctypes.data, float(sigma2_0)))
 
     def basis(self):
         U = np.empty((self.M, self.K), dtype=_dtype_of(self.precision))

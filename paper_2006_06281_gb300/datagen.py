@@ -109,6 +109,27 @@ def gen(M: int, n_out: int = 0, amp: float = 0.15, noise: float = 0.01,
     return PointSets(X=X, Y=allY[perm].copy(), Yhat=Yhat, n_inliers=noisy.shape[0], perm=perm)
 
 
+def gen_from_template(X: np.ndarray, seed: int, amp: float = 0.15, noise: float = 0.01, centers: int = 32,
+                      beta_gen: float = 2.0) -> PointSets:
+    """A new deformation of a fixed model X (same recipe as gen: a random
+    Gaussian-RBF displacement of RMS `amp`, noise, seeded permutation); many
+    such scenes against one template X are the warm-start training pairs."""
+    X = np.asarray(X, dtype=np.float64)
+    M = X.shape[0]
+    s = Stream(seed)
+    C = s.uniform(3 * centers).reshape(centers, 3) * 2.0 - 1.0
+    A = s.normal(3 * centers).reshape(centers, 3)
+    d2 = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+    V = np.exp(-d2 / (2.0 * beta_gen * beta_gen)) @ A
+    rms = np.sqrt((V * V).sum(1).mean())
+    if rms > 0:
+        V *= amp / rms
+    Yhat = X + V
+    noisy = Yhat + noise * s.normal(3 * M).reshape(M, 3)
+    perm = np.argsort(s.uniform(M), kind="stable")
+    return PointSets(X=X, Y=noisy[perm].copy(), Yhat=Yhat, n_inliers=M, perm=perm)
+
+
 def pair_sizes(n_pairs: int, lo: int, hi: int, seed: int) -> list[tuple[int, int]]:
     """(M_i, N_i) for a batch of registrations: both drawn independently and
     uniformly from the integers lo..hi (one SplitMix64 stream)."""
@@ -155,6 +176,21 @@ WORKLOADS = {
     # outlier case: M = 20000, N = 25000 (20% extra uniform outliers), K = 200
     "fp32_m20000_n25000_k200": dict(M=20000, n_out=5000, amp=0.15, noise=0.01, seed=0,
                                     omega=0.2, lam=3.0, beta=2.0, iters=150, K=200),
+}
+
+# Learned warm start: one template X (gen(M, seed=seed_x).X) and scenes
+# gen_from_template(X, seed0 + i); K eigen-coefficients; training pairs
+# registered from W = 0 for `iters` iterations.
+WARMSTART_WORKLOADS = {
+    # the template size and rank of the warm-start configuration (M = N =
+    # 2048, K = 64), with a training set of a few thousand scenes
+    "fp32_warmstart_m2048_k64": dict(M=2048, K=64, seed_x=7, amp=0.15, noise=0.01, omega=0.1, lam=2.0, beta=2.0,
+                                     iters=100, n_train=2048, n_val=64, n_test=32, seed0=100000,
+                                     steps=4000, batch=32, lr=3e-4),
+    # small version for tests
+    "fp32_warmstart_m512_k32": dict(M=512, K=32, seed_x=7, amp=0.15, noise=0.01, omega=0.1, lam=2.0, beta=2.0,
+                                    iters=80, n_train=768, n_val=32, n_test=16, seed0=200000,
+                                    steps=2000, batch=32, lr=3e-4),
 }
 
 # Batches of independent registrations (gen_batch): n_pairs pairs with M_i,
