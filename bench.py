@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lowrank", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP16-basis (CPD_MIXED) section")
+    ap.add_argument("--warmstart", default="none",
+                    help="also train and evaluate the learned warm start on this workload "
+                         "(e.g. fp32_warmstart_m2048_k64)")
     ap.add_argument("--prune", action="store_true",
                     help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -353,6 +356,65 @@ def run_batch(args, peaks, torch):
     return out
 
 
+def run_warmstart(args, torch):
+    """Learned warm start: training data from the method itself (registrations
+    from W = 0 on deformations of one template), GPU training, then on
+    held-out scenes the iterations and time until RMSE(T, T_end) <= 1e-3
+    from W = 0 and from the prediction (T_end: the registration's end point
+    after 150 iterations)."""
+    from paper_2006_06281_gb300 import cpd, datagen, warmstart
+    cfg = datagen.WARMSTART_WORKLOADS[args.warmstart]
+    X = datagen.gen(cfg["M"], seed=cfg["seed_x"]).X.astype(np.float32)
+    ntr, nva, nte = cfg["n_train"], cfg["n_val"], cfg["n_test"]
+    t0 = time.perf_counter()
+    Ys = np.stack([datagen.gen_from_template(X, cfg["seed0"] + i, amp=cfg["amp"], noise=cfg["noise"]).Y
+                   .astype(np.float32) for i in range(ntr + nva + nte)])
+    ctx = cpd.Context(torch.tensor(X, device="cuda"), precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"],
+                      lam=cfg["lam"], K=cfg["K"])
+    t1 = time.perf_counter()
+    targets = warmstart.registration_targets(ctx, Ys[:ntr + nva], cfg["K"], cfg["iters"])
+    t2 = time.perf_counter()
+    ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3)
+    losses = ws.fit(Ys[:ntr], targets[:ntr], cfg["steps"], cfg["batch"], cfg["lr"])
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    ws.calibrate(Ys[ntr:ntr + nva], targets[ntr:ntr + nva], cfg["M"])
+    c, _ = ws.predict(Ys[ntr:ntr + nva])
+    ct = targets[ntr:ntr + nva, :-1].reshape(c.shape)
+    err = float(np.linalg.norm(c - ct) / np.linalg.norm(ct))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for Y in Ys[ntr + nva:]:
+        Yd = torch.tensor(Y, device="cuda")
+        ctx.reset()
+        Tend, _, _ = ctx.iterate(Yd, 150)
+        ctx.set_ground_truth(Tend, 1e-3)
+        ctx.reset()
+        torch.cuda.synchronize()
+        ev0.record()
+        _, _, itc = ctx.iterate(Yd, 150, want_T=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        msc = ev0.elapsed_time(ev1)
+        ev0.record()
+        ws.start(ctx, Y)                                   # network inference + T = X + U c
+        _, _, itw = ctx.iterate(Yd, 150, want_T=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        msw = ev0.elapsed_time(ev1)
+        ctx.set_ground_truth(None)
+        rows.append((itc, itw, msc, msw))
+    ctx.close()
+    r = np.array(rows, dtype=np.float64)
+    return dict(workload=args.warmstart, M=cfg["M"], K=cfg["K"], train_scenes=ntr, steps=cfg["steps"],
+                data_s=t2 - t1, data_gen_host_s=t1 - t0, train_s=t3 - t2,
+                loss_first=float(np.mean(losses[:20])), loss_last=float(np.mean(losses[-50:])),
+                heldout_coef_rel_err=err, start_sigma2=ws.sigma2_floor,
+                test_scenes=nte, iters_to_rmse_1e3=dict(cold=float(r[:, 0].mean()), warm=float(r[:, 1].mean())),
+                ms_to_rmse_1e3=dict(cold=float(r[:, 2].mean()), warm=float(r[:, 3].mean())),
+                note="warm time includes the network forward pass and the warm-start kernel")
+
+
 def workload_config(cfg, M, N, K):
     return dict(workload=f"M={M} N={N} D=3 synthetic deformed pair (uniform model points, Gaussian-RBF "
                          f"deformation amp {cfg['amp']}, noise {cfg['noise']}, {cfg['n_out']} outliers), "
@@ -605,6 +667,10 @@ def main():
                                              pruned_iterations=int((frac < 1).sum()), of=int(itp)),
                      rel_diff_T_vs_dense=dp)
 
+    warm = None
+    if world == 1 and args.warmstart != "none":
+        warm = run_warmstart(args, torch)
+
     batch = None
     if world == 1 and args.batch != "none":
         batch = run_batch(args, peaks, torch)
@@ -625,7 +691,8 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, setup_s=setup_s,
+                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, learned_warm_start=warm,
+                    setup_s=setup_s,
                     batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "
                                   "(Table IV, MATLAB on an i7-8750H CPU): context, not a like-for-like target")
