@@ -156,7 +156,7 @@ def roofline_entries(phase_ms, M, N, K, peaks, es=4):
 
 
 TRAFFIC_SOURCES = {"e_pass_a": ["estep.cu", "estep_dev.cuh"], "e_pass_b": ["estep.cu", "estep_dev.cuh"],
-                   "colsum": ["mstep.cu", "mstep_dev.cuh"]}
+                   "colsum_bulk": ["mstep.cu", "mstep_dev.cuh"]}
 
 
 def source_digest(kernel):
@@ -186,8 +186,8 @@ def traffic_for(kernel):
 
 def dominant_kernel(roof):
     """The kernel with the largest time per iteration.  The two M-step
-    products are launches of one kernel (colsum): they count together, and
-    its per-launch figures are their average."""
+    products are launches of one kernel (colsum_bulk): they count together,
+    and its per-launch figures are their average."""
     cands = {}
     for k in ("e_pass_a", "e_pass_b"):
         if k in roof:
@@ -196,7 +196,7 @@ def dominant_kernel(roof):
         a, b = roof["m_project"], roof["m_expand"]
         t = (a["ms"] + b["ms"]) / 2
         byts = (a["bytes"] + b["bytes"]) / 2
-        cands["colsum"] = (2 * t, dict(bound="hbm", achieved=byts / (t / 1e3) / 1e9, peak=a["peak"], unit="GB/s",
+        cands["colsum_bulk"] = (2 * t, dict(bound="hbm", achieved=byts / (t / 1e3) / 1e9, peak=a["peak"], unit="GB/s",
                                        frac=byts / (t / 1e3) / 1e9 / a["peak"], ms=t, launches_per_iter=2))
     name = max(cands, key=lambda k: cands[k][0])
     return name, cands[name][1]

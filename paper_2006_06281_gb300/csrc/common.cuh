@@ -203,6 +203,7 @@ struct MstepPlan {
   int e_blocks;                                      // expansion reduction grid
   int64_t part_elems;                                // scratch (elements of F), shared by both
   int64_t sums_elems;                                // double scratch for block sums
+  bool bulk;                                         // products by colsum_bulk (bulk-copy ring)
 };
 // `colsum_threads`: block size of the streaming kernel the plan is for (128
 // for the per-pair launches, 256 inside the batched persistent kernel).

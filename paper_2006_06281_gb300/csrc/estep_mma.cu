@@ -331,22 +331,36 @@ void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t
 }
 
 // Grids of the tensor-core passes: rows in blocks of 256 points, the other
-// dimension split so that about `slots` blocks run (chunks a multiple of the
-// staged tile).
+// dimension split into chunks (multiples of the 16-point tile) chosen so the
+// blocks fill whole waves of the pass's own occupancy: the cost of a split is
+// its number of waves x (chunk length + a per-block overhead), and the
+// cheapest split wins (fewer chunks on ties, so fewer partial sums).
+namespace {
+void split_fill(int64_t L, int64_t tiles, int64_t slots, int& len, int& chunks) {
+  constexpr int64_t kGran = 16, kMinLen = 64, kOverhead = 32;
+  int64_t best = -1;
+  const int64_t cmax = 4 * std::max<int64_t>(1, slots / tiles) + 2;
+  for (int64_t c = 1; c <= cmax; ++c) {
+    const int64_t ln = std::max(kMinLen, cdiv(cdiv(L, c), kGran) * kGran);
+    const int64_t ch = cdiv(L, ln);
+    const int64_t cost = cdiv(tiles * ch, slots) * (ln + kOverhead);
+    if (best < 0 || cost < best) {
+      best = cost;
+      len = (int)ln;
+      chunks = (int)ch;
+    }
+  }
+}
+}  // namespace
+
 void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, passA_f32_mma, kMmaThreads, 0);
-  const int64_t slots = (int64_t)sms * std::max(occ, 1) * 2;
+  int occA = 0, occB = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, passA_f32_mma, kMmaThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, passB_f32_mma, kMmaThreads, 0);
   p.a_row_tiles = (int)cdiv(N, kMmaRowsPerBlock);
-  int64_t want = std::max<int64_t>(1, slots / p.a_row_tiles);
-  int64_t rpc = cdiv(cdiv(M, want), kMmaStage) * kMmaStage;
-  p.a_rows_per_chunk = (int)rpc;
-  p.a_chunks = (int)cdiv(M, rpc);
+  split_fill(M, p.a_row_tiles, (int64_t)sms * std::max(occA, 1), p.a_rows_per_chunk, p.a_chunks);
   p.b_row_tiles = (int)cdiv(M, kMmaRowsPerBlock);
-  want = std::max<int64_t>(1, slots / p.b_row_tiles);
-  int64_t cpc = cdiv(cdiv(N, want), kMmaStage) * kMmaStage;
-  p.b_cols_per_chunk = (int)cpc;
-  p.b_chunks = (int)cdiv(N, cpc);
+  split_fill(N, p.b_row_tiles, (int64_t)sms * std::max(occB, 1), p.b_cols_per_chunk, p.b_chunks);
 }
 
 void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,

@@ -4,6 +4,7 @@
 #include "mstep_dev.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace fcpd {
 
@@ -17,6 +18,213 @@ colsum(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename 
        int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
        int clear_row_flags) {
   dev::colsum_body<F, S, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+
+// ------------------------------------------------- colsum, bulk-copy ring
+// The same product and partial-sum layout as colsum, with the rows of A
+// streamed into shared memory by the copy engine: one thread issues
+// cp.async.bulk copies (a tile row of A per copy, plus the slot's rows of V)
+// into a ring of slots, each completing on its own mbarrier, and the block
+// consumes slot k while the next slots are in flight.  The bytes in flight
+// per SM are then set by the ring rather than by the registers a thread can
+// hold loads in.  Thread t owns 16-byte vectors t, t + THREADS, .. of each
+// tile row (conflict-free shared-memory reads).  A is read once: its copies
+// carry an L2 evict-first hint.  Every wait is bounded (kBulkWaitNs): on
+// expiry the block records CPD_ETIMEOUT, waits (bounded) for the copies it
+// issued and returns without writing.
+// Ring geometry, measured at M = N = 20000 (full basis): an FP32 basis 128
+// threads and 3 slots of 32 KB (2 blocks per SM; 6.66 TB/s against 6.36 for
+// the register-streaming colsum); an FP16 basis, whose threads do twice the
+// arithmetic per byte, 256 threads and 2 slots of 32 KB (3 blocks, 24 warps
+// per SM: 6.27 TB/s; 128 threads 4.8, 256 threads x 3 slots 5.6, 512 threads
+// 5.8-5.9, 16-24 KB slots 5.6-5.9).
+#ifndef FCPD_BULK_THREADS_H
+#define FCPD_BULK_THREADS_H 256
+#endif
+#ifndef FCPD_BULK_STAGES_H
+#define FCPD_BULK_STAGES_H 2
+#endif
+#ifndef FCPD_BULK_SLOT_KB_H
+#define FCPD_BULK_SLOT_KB_H 32
+#endif
+constexpr unsigned long long kBulkWaitNs = 2000000000ull;
+
+template <typename S> struct BulkGeom {
+  static constexpr bool H = sizeof(S) == 2;
+  static constexpr int THREADS = H ? FCPD_BULK_THREADS_H : 128;
+  static constexpr int STAGES = H ? FCPD_BULK_STAGES_H : 3;
+  static constexpr int SLOT = (H ? FCPD_BULK_SLOT_KB_H : 32) * 1024;   // bytes of A per slot
+  static constexpr int L = L16<S>::W;                  // elements per 16-byte vector
+  static constexpr int NV = colsum_vectors<S>();       // vectors per thread and row
+  static constexpr int VPR = THREADS * NV;             // vectors per tile row
+  static constexpr int COLS = VPR * L;                 // tile columns
+  static constexpr int ROWS = SLOT / (VPR * 16);       // tile rows per slot
+  static_assert(ROWS >= 1 && SLOT % (VPR * 16) == 0, "a slot holds whole tile rows");
+};
+
+template <typename F, typename S> constexpr size_t bulk_smem_bytes() {
+  using G = BulkGeom<S>;
+  return G::STAGES * ((size_t)G::SLOT + G::ROWS * sizeof(typename Vec<F>::t4)) +
+         G::STAGES * sizeof(unsigned long long);
+}
+
+__device__ __forceinline__ unsigned int smem_addr(const void* p) {
+  return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned int bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity) {
+  unsigned int ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of `bar` with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity,
+                                          unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of
+// 16), completion counted on `bar` in bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned int bytes, unsigned long long* bar,
+                                         unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+      : "memory");
+}
+
+template <typename F, typename S>
+__global__ void __launch_bounds__(BulkGeom<S>::THREADS)
+colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
+            int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
+            int clear_row_flags) {
+  if (gate && iteration_gated(st)) return;
+  if (clear_row_flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
+  using G = BulkGeom<S>;
+  using V4 = typename Vec<F>::t4;
+  using LT = typename L16<S>::t;
+  constexpr int W = G::NV * G::L;
+  extern __shared__ __align__(128) unsigned char smem[];
+  LT* tiles = reinterpret_cast<LT*>(smem);
+  V4* vt = reinterpret_cast<V4*>(smem + (size_t)G::STAGES * G::SLOT);
+  unsigned long long* bar =
+      reinterpret_cast<unsigned long long*>(smem + (size_t)G::STAGES * (G::SLOT + G::ROWS * sizeof(V4)));
+  const int tid = threadIdx.x;
+  const int64_t cb = (int64_t)blockIdx.x * G::COLS;
+  // 16-byte vectors of a tile row inside the row stride (ldA is a multiple of W)
+  const int vecs = (int)((ldA - cb) / G::L < G::VPR ? (ldA - cb) / G::L : G::VPR);
+  const unsigned int row_bytes = (unsigned int)vecs * 16u;
+  const int r0 = blockIdx.y * rows_per_chunk;
+  const int r1 = min(rows, r0 + rows_per_chunk);
+  const int nst = r0 < r1 ? (r1 - r0 + G::ROWS - 1) / G::ROWS : 0;
+  unsigned long long pol_a = 0, pol_v = 0;
+  if (tid == 0) {
+    for (int k = 0; k < G::STAGES; ++k) mbar_init(&bar[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol_a));
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol_v));
+  }
+  __syncthreads();
+  auto issue = [&](int k) {
+    const int slot = k % G::STAGES;
+    const int ra = r0 + k * G::ROWS;
+    const int nr = min(G::ROWS, r1 - ra);
+    mbar_expect_tx(&bar[slot], (unsigned int)nr * (row_bytes + (unsigned int)sizeof(V4)));
+    LT* dst = tiles + (size_t)slot * (G::SLOT / 16);
+    for (int i = 0; i < nr; ++i)
+      bulk_g2s(dst + (size_t)i * G::VPR, A + (size_t)(ra + i) * ldA + cb, row_bytes, &bar[slot], pol_a);
+    bulk_g2s(vt + (size_t)slot * G::ROWS, V + ra, (unsigned int)(nr * sizeof(V4)), &bar[slot], pol_v);
+  };
+  if (tid == 0)
+    for (int k = 0; k < min(nst, G::STAGES); ++k) issue(k);
+  F acc[W][3];
+#pragma unroll
+  for (int w = 0; w < W; ++w) acc[w][0] = acc[w][1] = acc[w][2] = (F)0;
+  const F scale = (F)lane_scale<S>();
+  int failed_at = -1;
+  for (int k = 0; k < nst; ++k) {
+    const int slot = k % G::STAGES;
+    const bool ok = mbar_wait(&bar[slot], (unsigned int)(k / G::STAGES) & 1u, kBulkWaitNs);
+    const LT* tile = tiles + (size_t)slot * (G::SLOT / 16);
+    const V4* vv = vt + (size_t)slot * G::ROWS;
+    const int nr = min(G::ROWS, r1 - (r0 + k * G::ROWS));
+#pragma unroll 4
+    for (int i = 0; i < nr; ++i) {
+      LT u[G::NV];
+#pragma unroll
+      for (int v = 0; v < G::NV; ++v) u[v] = tile[(size_t)i * G::VPR + tid + v * G::THREADS];
+      V4 r = vv[i];
+      if constexpr (sizeof(S) == 2) {          // exact power-of-two pre-scale (see lane_of)
+        r.x *= scale; r.y *= scale; r.z *= scale;
+      }
+#pragma unroll
+      for (int v = 0; v < G::NV; ++v)
+#pragma unroll
+        for (int l = 0; l < G::L; ++l) {
+          const F uw = (F)lane_of(u[v], l);
+          F* a = acc[v * G::L + l];
+          a[0] = fma(uw, r.x, a[0]);
+          a[1] = fma(uw, r.y, a[1]);
+          a[2] = fma(uw, r.z, a[2]);
+        }
+    }
+    // every thread is done with the slot (and learns whether any wait expired)
+    if (__syncthreads_or(!ok)) {
+      failed_at = k;
+      break;
+    }
+    if (tid == 0 && k + G::STAGES < nst) issue(k + G::STAGES);
+  }
+  if (failed_at >= 0) {
+    if (tid == 0) {
+      atomicExch(&st->status, (int)CPD_ETIMEOUT);
+      // the copies issued and not yet consumed: stages failed_at .. failed_at + G::STAGES - 1
+      for (int j = failed_at; j < min(nst, failed_at + G::STAGES); ++j)
+        mbar_wait(&bar[j % G::STAGES], (unsigned int)(j / G::STAGES) & 1u, kBulkWaitNs);
+    }
+    __syncthreads();
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < G::NV; ++v) {
+    const int vec = tid + v * G::THREADS;
+    if (vec >= vecs) continue;
+    const int64_t c = cb + (int64_t)vec * G::L;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      F* out = part + ((size_t)blockIdx.y * 3 + d) * ldP + c;
+      if constexpr (sizeof(F) == 4) {
+#pragma unroll
+        for (int q = 0; q < G::L / 4; ++q)
+          reinterpret_cast<float4*>(out)[q] = make_float4(acc[v * G::L + 4 * q][d], acc[v * G::L + 4 * q + 1][d],
+                                                          acc[v * G::L + 4 * q + 2][d], acc[v * G::L + 4 * q + 3][d]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < G::L / 2; ++q)
+          reinterpret_cast<double2*>(out)[q] = make_double2(acc[v * G::L + 2 * q][d], acc[v * G::L + 2 * q + 1][d]);
+      }
+    }
+  }
+  (void)cols;
 }
 
 template <typename F>
@@ -52,6 +260,36 @@ void plan_colsum(int64_t rows, int64_t ld, int64_t es, int sms, int W, int threa
   chunks = (int)cdiv(rows, r);
 }
 
+// Grid of colsum_bulk over a rows x ld matrix: one resident wave (slots =
+// SMs x resident blocks), the rows of each column tile split into equal
+// chunks of whole slots, at least 4 slots of rows per block.
+void plan_colsum_bulk(int64_t rows, int64_t ld, int64_t slots, int tile_cols, int slot_rows, int& col_tiles,
+                      int& chunks, int& rpc) {
+  col_tiles = (int)cdiv(ld, tile_cols);
+  int64_t ch = std::max<int64_t>(1, slots / col_tiles);
+  ch = std::min<int64_t>(ch, std::max<int64_t>(1, rows / (4 * (int64_t)slot_rows)));
+  const int64_t r = cdiv(cdiv(rows, ch), slot_rows) * slot_rows;
+  rpc = (int)r;
+  chunks = (int)cdiv(rows, r);
+}
+
+template <typename F, typename S> int64_t bulk_slots(int sms) {
+  const int bytes = (int)bulk_smem_bytes<F, S>();
+  cudaFuncSetAttribute(colsum_bulk<F, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, colsum_bulk<F, S>, BulkGeom<S>::THREADS, bytes);
+  return (int64_t)sms * std::max(occ, 1);
+}
+
+// colsum_bulk for the per-registration launches of FP32 and FP16 bases (the
+// register-streaming colsum for FP32 when built with FCPD_COLSUM_REG_F32; FP64
+// and the batched kernel always use it).
+#ifdef FCPD_COLSUM_REG_F32
+constexpr bool kBulkF32 = false;
+#else
+constexpr bool kBulkF32 = true;
+#endif
+
 }  // namespace
 
 MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads, int basis_bytes) {
@@ -61,12 +299,36 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_thread
   const int W = (int)(16 * nv / es);   // columns per colsum thread; row strides padded to it
   p.ldU = cdiv(K, W) * W;
   p.ldM = cdiv(M, W) * W;
-  plan_colsum(M, p.ldU, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
-  plan_colsum(K, p.ldM, es, sms, W, colsum_threads, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+  p.bulk = colsum_threads == kThreadsP && (es == 2 || (es == 4 && kBulkF32));
+  if (p.bulk) {
+    const int64_t slots = es == 2 ? bulk_slots<float, __half>(sms) : bulk_slots<float, float>(sms);
+    const int tc = es == 2 ? BulkGeom<__half>::COLS : BulkGeom<float>::COLS;
+    const int tr = es == 2 ? BulkGeom<__half>::ROWS : BulkGeom<float>::ROWS;
+    plan_colsum_bulk(M, p.ldU, slots, tc, tr, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+    plan_colsum_bulk(K, p.ldM, slots, tc, tr, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+  } else {
+    plan_colsum(M, p.ldU, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+    plan_colsum(K, p.ldM, es, sms, W, colsum_threads, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+  }
   p.part_elems = std::max((int64_t)p.p_row_chunks * 3 * p.ldU, (int64_t)p.e_row_chunks * 3 * p.ldM);
   p.e_blocks = (int)cdiv(M, kMRedCols);
   p.sums_elems = (int64_t)p.e_blocks * 3;
   return p;
+}
+
+// out partials of A^T V over the plan's grid (colsum or colsum_bulk).
+template <typename F, typename S>
+void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA, int64_t rows, int64_t cols,
+                   const typename Vec<F>::t4* V, F* part, DevState* st, int gate, int clear_row_flags,
+                   cudaStream_t s) {
+  const dim3 grid = expansion ? dim3(pl.e_col_tiles, pl.e_row_chunks) : dim3(pl.p_col_tiles, pl.p_row_chunks);
+  const int rpc = expansion ? pl.e_rows_per_chunk : pl.p_rows_per_chunk;
+  if (pl.bulk && !std::is_same<F, double>::value)
+    colsum_bulk<F, S><<<grid, BulkGeom<S>::THREADS, bulk_smem_bytes<F, S>(), s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part,
+                                                                         ldA, st, gate, clear_row_flags);
+  else
+    colsum<F, S><<<grid, kThreadsP, 0, s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part, ldA, st, gate,
+                                            clear_row_flags);
 }
 
 template <typename F, typename S>
@@ -76,16 +338,12 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums, typename Vec<F>::t4* B4,
                   typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev) {
   const int g = iteration ? 1 : 0;
-  colsum<F, S><<<dim3(pl.p_col_tiles, pl.p_row_chunks), kThreadsP, 0, s>>>(U, pl.ldU, (int)M, (int)K, R4,
-                                                                      pl.p_rows_per_chunk, part, pl.ldU, st, g,
-                                                                      g);
+  launch_colsum<F, S>(pl, false, U, pl.ldU, M, K, R4, part, st, g, g, s);
   record_after(ev, 0, s);
   diag_update<F><<<(unsigned)cdiv(K, kMRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
                                                                    B4, C4, st, g);
   record_after(ev, 1, s);
-  colsum<F, S><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, B4,
-                                                                      pl.e_rows_per_chunk, part, pl.ldM, st, g,
-                                                                      0);
+  launch_colsum<F, S>(pl, true, Ut, pl.ldM, K, M, B4, part, st, g, 0, s);
   record_after(ev, 2, s);
   if (iteration) {
     expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
@@ -100,8 +358,7 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
 template <typename F, typename S>
 void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
               typename Vec<F>::t4* W4, DevState* st, cudaStream_t s) {
-  colsum<F, S><<<dim3(pl.e_col_tiles, pl.e_row_chunks), kThreadsP, 0, s>>>(Ut, pl.ldM, (int)K, (int)M, C4,
-                                                                      pl.e_rows_per_chunk, part, pl.ldM, st, 0, 0);
+  launch_colsum<F, S>(pl, true, Ut, pl.ldM, K, M, C4, part, st, 0, 0, s);
   expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
                                                             nullptr, W4, nullptr, nullptr, st, 0);
 }
