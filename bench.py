@@ -43,7 +43,7 @@ UNIT = "EM iters/s"
 PAPER_ITERS_PER_S = 50.0 / (988.430 - 502.663)
 RMSE_TARGET = 5e-3
 ITERS_PER_REGISTRATION = 100
-STATE_BYTES = 168          # sizeof(DevState), read back with sigma2 by cpd_iterate
+STATE_BYTES = 184          # sizeof(DevState), read back with sigma2 by cpd_iterate
 
 
 def parse():
@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--warmstart", default="none",
                     help="also train and evaluate the learned warm start on this workload "
                          "(e.g. fp32_warmstart_m2048_k64)")
+    ap.add_argument("--no-trim", action="store_true",
+                    help="skip timing the same registration with CPD_FLAG_SPECTRAL_TRIM")
     ap.add_argument("--prune", action="store_true",
                     help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -667,9 +669,53 @@ def main():
                                              pruned_iterations=int((frac < 1).sum()), of=int(itp)),
                      rel_diff_T_vs_dense=dp)
 
-    warm = None
+    # spectral trim (CPD_FLAG_SPECTRAL_TRIM), same pair and registration:
+    # rate, the kept directions, the iterations that ran the trimmed M-step,
+    # and T against the full M-step's
+    trim = None
+    if not args.no_trim and cfg["K"] == 0:
+        t0 = time.perf_counter()
+        ct = cpd.Context(X, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0,
+                         flags=cpd.FLAG_SPECTRAL_TRIM)
+        tsetup = time.perf_counter() - t0
+        ct.reset()
+        ct.iterate_profiled(Y, I)
+        torch.cuda.synchronize()
+        ph = np.zeros(9)
+        ntr = max(1, min(R, 10))
+        a.record()
+        for _ in range(ntr):
+            ct.reset()
+            ph += np.array(ct.iterate_profiled(Y, I)) / ntr
+        b.record()
+        torch.cuda.synchronize()
+        tms = a.elapsed_time(b)
+        ct.reset()
+        Tt, s2t, itt = ct.iterate(Y, I)
+        k_cap, n_trim = ct.trim_info()
+        # time to the RMSE target with the trim
+        ct.reset()
+        ct.set_ground_truth(Yhat, ttt["rmse_target"])
+        torch.cuda.synchronize()
+        a.record()
+        _, _, it_tol = ct.iterate(Y, 500, want_T=False)
+        b.record()
+        torch.cuda.synchronize()
+        ttt_trim = dict(iters=int(it_tol), ms=a.elapsed_time(b))
+        ct.close()
+        dt = (T32.double() - Tt.double()).norm().item() / T32.double().norm().item()
+        troof = roofline_entries(ph, M, N, k_cap, peaks)
+        trim = dict(flags="CPD_FLAG_SPECTRAL_TRIM", iters_per_s=ntr * I / (tms / 1e3), setup_s=tsetup,
+                    k_cap=int(k_cap), trimmed_iterations=int(n_trim), of=int(itt),
+                    kernel_ms={k: v["ms"] for k, v in troof.items()},
+                    rel_diff_T_vs_full=dt, sigma2_rel_diff_vs_full=abs(s2t - s232) / s232,
+                    time_to_tolerance=ttt_trim,
+                    note="the M-step keeps the directions with s_k = l_k/(l_k + lambda sigma2) >= 2^-24; "
+                         "the dropped part of T is below one FP32 rounding (|dT| <= 2^-24 |R|)")
+
+    warm_start = None
     if world == 1 and args.warmstart != "none":
-        warm = run_warmstart(args, torch)
+        warm_start = run_warmstart(args, torch)
 
     batch = None
     if world == 1 and args.batch != "none":
@@ -691,7 +737,7 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, learned_warm_start=warm,
+                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, spectral_trim=trim, learned_warm_start=warm_start,
                     setup_s=setup_s,
                     batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "

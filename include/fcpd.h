@@ -120,10 +120,30 @@ typedef struct {
 typedef enum {
     CPD_FLAG_PRUNE = 1,          /* spatial order + exact pruning of the FP32 E-step       */
     CPD_FLAG_PRUNE_ALWAYS = 2,   /* (implies PRUNE) pruned layout in every iteration       */
-    CPD_FLAG_PRUNE_NOSKIP = 4    /* (implies PRUNE) pruned layout, every tile pair
+    CPD_FLAG_PRUNE_NOSKIP = 4,   /* (implies PRUNE) pruned layout, every tile pair
                                     evaluated: the same sums as skipping, bit for bit
                                     (verification)                                        */
+    CPD_FLAG_SPECTRAL_TRIM = 8   /* FP32 / mixed: M-step over the leading directions only
+                                    while the dropped ones are below FP32 rounding        */
 } cpd_flags;
+
+/*
+ * CPD_FLAG_SPECTRAL_TRIM (Eq. 17).  Direction k of the eigenbasis enters T
+ * through s_k (U^T R)_k with s_k = l_k / (l_k + lambda sigma2); the Gaussian
+ * Gram matrix's spectrum decays so fast that, for all but a few hundred
+ * directions, s_k < 2^-24.  The dropped part of U diag(s) U^T R then has norm
+ * <= 2^-24 |R| (U orthonormal): below one FP32 rounding of T.  At setup the
+ * context keeps the leading k_cap directions (those that can reach 2^-24
+ * while sigma2 >= 1e-4 x the model points' variance per axis, rounded up to
+ * 16); each iteration the device tests the largest dropped eigenvalue
+ * against the current sigma2 and runs the M-step over the k_cap columns
+ * when the bound holds, the full M-step when it does not.  T and sigma2
+ * agree with the full M-step within FP32 rounding.  cpd_get_W then returns
+ * the component of W in the kept directions (Phi W = T - X is preserved to
+ * the same bound; W itself is ill-posed in the dropped ones).  Not for
+ * CPD_FP64 or batched registrations (CPD_EINVAL); K <= k_cap leaves the
+ * context unchanged.
+ */
 
 typedef struct cpd_ctx cpd_ctx;   /* opaque; owned by the library */
 
@@ -300,6 +320,15 @@ cpd_status cpd_get_work(cpd_ctx *ctx, int32_t n, double *eval_frac);
 
 /* 1 if the context keeps its points in spatial order (pruning possible). */
 int32_t cpd_spatial_order(const cpd_ctx *ctx);
+
+/*
+ * Spectral trim of a context (CPD_FLAG_SPECTRAL_TRIM): *k_cap (host) = the
+ * directions the trimmed M-step keeps (0: no trim -- flag unset or nothing
+ * to drop); *trimmed_iters (host) = iterations of the current registration
+ * that ran the trimmed M-step (0 before any).  Synchronises.  CPD_EINVAL
+ * for a null argument.
+ */
+cpd_status cpd_get_trim(cpd_ctx *ctx, int64_t *k_cap, int32_t *trimmed_iters);
 
 /* ------------------------------------------------------------------------
  * Warm start (not in the paper).  In the top-K basis the displacement of

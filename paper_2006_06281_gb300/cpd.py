@@ -25,13 +25,13 @@ FP64, FP32, MIXED = 0, 1, 2    # MIXED: FP32 points and E-step, FP16 eigenbasis
 STATUS = {0: "CPD_OK", 1: "CPD_EINVAL", 2: "CPD_ENOMEM", 3: "CPD_ECUDA", 4: "CPD_ESOLVER",
           5: "CPD_ENUMERIC", 6: "CPD_ETIMEOUT", 7: "CPD_ESTATE"}
 OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
-FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP = 1, 2, 4
+FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP, FLAG_SPECTRAL_TRIM = 1, 2, 4, 8
 
 # Every symbol include/fcpd.h declares (checked by the tests).
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
-           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_destroy",
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_destroy",
            "cpd_coefficients", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
            "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
@@ -88,6 +88,7 @@ def load():
                 "cpd_register": ([vp, i64, vp, i64, pp, vp, vp, vp, dp, ip], C.c_int),
                 "cpd_destroy": ([vp], None),
                 "cpd_get_work": ([vp, i32, vp], C.c_int),
+                "cpd_get_trim": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
                 "cpd_coefficients": ([vp, i32, vp], C.c_int),
                 "cpd_warm_start": ([vp, i32, vp, d], C.c_int),
                 "cpd_net_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
@@ -256,6 +257,14 @@ class Context:
         W, pw = _out_like(self.M, 3, self.precision, self.cuda, self.device)
         _check(load().cpd_get_W(self._h, pw))
         return W
+
+    def trim_info(self):
+        """(k_cap, trimmed_iters): directions kept by the spectral trim (0: none)
+        and iterations of this registration that ran the trimmed M-step."""
+        k = C.c_int64()
+        n = C.c_int32()
+        _check(load().cpd_get_trim(self._h, C.byref(k), C.byref(n)))
+        return k.value, n.value
 
     def work(self, n):
         """Fraction of the 2 M N Gaussian pairs evaluated by each of the first n iterations."""

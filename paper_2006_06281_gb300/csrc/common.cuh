@@ -75,9 +75,12 @@ struct DevState {
   float prune_r2;                 // pruned passes run while 127 / kappa (FP32 cutoff radius^2) < this
   int prune_ctl;                  // kPrune* / kMmaAllowed bits (0: dense passes only)
   double mma_s2min;               // tensor-core passes run while sigma2 >= this
+  double trim_lam;                // spectral trim: largest eigenvalue the trimmed M-step drops (< 0: off)
+  int trim_now;                   // the trimmed M-step runs in this iteration (set by trim_decide)
+  int trim_iters;                 // iterations of this registration that ran the trimmed M-step
 };
 
-static_assert(sizeof(DevState) == 168, "DevState layout changed: update the benchmark's transfer count");
+static_assert(sizeof(DevState) == 184, "DevState layout changed: update the benchmark's transfer count");
 
 // DevState::prune_ctl bits.
 constexpr int kPruneAllowed = 1;   // points are in spatial order: the pruned passes may run
@@ -88,6 +91,17 @@ constexpr int kMmaAllowed = 8;     // mixed precision: tensor-core distance pass
 // FP32: they run while q^2 R^2 <= ~2000 (R = largest point norm), i.e.
 // sigma2 >= kMmaS2PerR2 * R^2, which keeps the exponent's rounding near 1e-3.
 constexpr double kMmaS2PerR2 = 3.5e-4;
+
+// Spectral trim of the M-step (Eq. 17 with only the leading directions):
+// a direction k enters T through s_k a_k, s_k = l_k / (l_k + lambda sigma2).
+// When every dropped direction has s_k < kTrimEps, the dropped part of
+// U diag(s) U^T R has norm <= kTrimEps |R| (U orthonormal) -- below one FP32
+// rounding of T -- and the trimmed M-step over the top K_cap columns runs.
+constexpr double kTrimEps = 0x1p-24;
+__device__ __forceinline__ bool trim_active(const DevState* st) {
+  const double l = st->trim_lam;
+  return l >= 0.0 && l < kTrimEps * (l + st->lambda * st->sigma2);
+}
 
 // The tensor-core passes' layout is used this iteration (same answer in
 // every kernel of an E-step: sigma2 does not change within it).
@@ -204,12 +218,17 @@ struct MstepPlan {
   int64_t part_elems;                                // scratch (elements of F), shared by both
   int64_t sums_elems;                                // double scratch for block sums
   bool bulk;                                         // products by colsum_bulk (bulk-copy ring)
+  int64_t K;                                         // basis columns the plan streams
+  int64_t ldPp;                                      // row stride of the projection partials
 };
 // `colsum_threads`: block size of the streaming kernel the plan is for (128
 // for the per-pair launches, 256 inside the batched persistent kernel).
 // basis_bytes: element size of the stored basis (0: that of the working
 // precision; 2 for the FP16 basis of the mixed-precision mode).
 MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads = 128, int basis_bytes = 0);
+// Plan of the trimmed M-step: the leading K_cap columns of the basis laid
+// out by `full` (same row strides).
+MstepPlan plan_mstep_trim(const MstepPlan& full, int64_t M, int64_t K_cap, bool fp64, int sms, int basis_bytes);
 
 // ------------------------------------------------------------ batched mode
 // One registration inside the batched persistent kernel: its sizes, plans
@@ -302,13 +321,18 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
 // With `iteration` false the state is not advanced (standalone M-step:
 // T4 receives T, no sigma2 update, st supplies sigma2 and lambda).
 // S: storage type of the basis (F, or __half in the mixed-precision mode).
+// With `trim` (an iteration of a context with the spectral trim) a one-thread
+// kernel decides on the device whether the trimmed M-step (plan *trim) or
+// the full one (pl) runs this iteration; both are enqueued, step by step,
+// and the other steps aside.  The trimmed M-step sets B and C to 0 for the
+// dropped directions.
 template <typename F, typename S = F>
 void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums,
                   typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, DevState* st,
-                  bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                  bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr, const MstepPlan* trim = nullptr);
 
 // W = U C (C from the last M-step), written as 4-vectors.
 template <typename F, typename S = F>
@@ -336,6 +360,9 @@ void launch_begin_iterations(DevState* st, int n_iter, cudaStream_t s);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s);
 // Pruning configuration of a context (kept across state_init, which turns it off).
 void launch_state_prune(DevState* st, float prune_r2, int prune_ctl, cudaStream_t s);
+// Spectral trim threshold of a registration (the largest dropped eigenvalue;
+// < 0 switches the trim off).
+void launch_state_trim(DevState* st, double trim_lam, cudaStream_t s);
 void launch_state_params(DevState* st, double w, double lambda, double tol, double gt_tol, int has_gt,
                          double* hist, int64_t M, int64_t N, int64_t K, cudaStream_t s);
 template <typename F>

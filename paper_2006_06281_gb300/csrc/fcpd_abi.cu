@@ -97,6 +97,8 @@ struct Buf {
   template <typename T> T* as() const { return static_cast<T*>(p); }
 };
 
+constexpr int32_t kPruneFlags = CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP;
+
 cpd_status validate_params(const cpd_params* p) {
   if (!p) return fail(CPD_EINVAL, "params is NULL");
   if (p->D != 3) return fail(CPD_EINVAL, "only D = 3 is implemented");
@@ -108,8 +110,10 @@ cpd_status validate_params(const cpd_params* p) {
   if (std::isnan(p->sigma2_init) || std::isinf(p->sigma2_init)) return fail(CPD_EINVAL, "sigma2_init not finite");
   if (p->K < 0) return fail(CPD_EINVAL, "K must be >= 0");
   if (p->max_iter < 0) return fail(CPD_EINVAL, "max_iter must be >= 0");
-  if (p->flags & ~(CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP))
+  if (p->flags & ~(CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP | CPD_FLAG_SPECTRAL_TRIM))
     return fail(CPD_EINVAL, "unknown bits in flags");
+  if ((p->flags & CPD_FLAG_SPECTRAL_TRIM) && p->precision == CPD_FP64)
+    return fail(CPD_EINVAL, "the spectral trim bounds its error at FP32 rounding: not for CPD_FP64");
   if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return fail(CPD_EINVAL, "tol must be >= 0");
   return CPD_OK;
 }
@@ -145,6 +149,9 @@ struct cpd_ctx {
   float prune_r2 = 0.f;          // pruned passes below this squared FP32 cutoff radius
   EstepPlan ep{};
   MstepPlan mp{};
+  MstepPlan mp_trim{};           // spectral trim: the M-step over the leading k_cap directions
+  int64_t k_cap = 0;             // > 0: the trimmed M-step is captured beside the full one
+  double trim_lam = -1.0;        // largest eigenvalue the trimmed M-step drops
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
   cudaGraphExec_t prof_graph = nullptr;             // n iterations with timing events
   int prof_iters = 0;
@@ -272,7 +279,40 @@ void apply_prune(cpd_ctx* c) {
   }
   if (c->half_basis) ctl |= kMmaAllowed;
   launch_state_prune(c->dst(), c->prune_r2, ctl, c->stream);
+  launch_state_trim(c->dst(), c->k_cap > 0 ? c->trim_lam : -1.0, c->stream);
   if (c->half_basis) launch_mma_threshold(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, c->dst(), c->stream);
+}
+
+// Spectral trim: the leading directions kept by the trimmed M-step.  With
+// the variance floor s2f = kTrimFloor x the model points' variance per axis,
+// every direction with l_k >= kTrimEps lambda s2f / (1 - kTrimEps) is kept
+// (rounded up to 16 columns); the dropped ones then have s_k < kTrimEps in
+// every iteration whose sigma2 >= s2f, and iterations further below run the
+// full M-step (the device test uses the largest dropped eigenvalue).
+constexpr double kTrimFloor = 1e-4;
+cpd_status plan_trim(cpd_ctx* c) {
+  std::vector<double> lam((size_t)c->K);
+  std::vector<float4> x((size_t)c->M);
+  CUDA_TRY(cudaMemcpyAsync(lam.data(), c->lam.p, lam.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(x.data(), c->X4.p, x.size() * sizeof(float4), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double mean[3] = {0, 0, 0}, var = 0;
+  for (const float4& v : x) { mean[0] += v.x; mean[1] += v.y; mean[2] += v.z; }
+  for (double& m : mean) m /= (double)c->M;
+  for (const float4& v : x) {
+    const double dx = v.x - mean[0], dy = v.y - mean[1], dz = v.z - mean[2];
+    var += dx * dx + dy * dy + dz * dz;
+  }
+  var /= 3.0 * (double)c->M;
+  const double thr = kTrimEps * c->p.lambda * kTrimFloor * var / (1.0 - kTrimEps);
+  int64_t n = 0;
+  while (n < c->K && lam[(size_t)n] >= thr) ++n;
+  const int64_t kcap = std::max<int64_t>(16, (n + 15) / 16 * 16);
+  if (kcap >= c->K) return CPD_OK;                 // nothing to drop
+  c->k_cap = kcap;
+  c->trim_lam = lam[(size_t)kcap];
+  c->mp_trim = plan_mstep_trim(c->mp, c->M, kcap, c->fp64, c->sms, (int)c->bes);
+  return CPD_OK;
 }
 
 cpd_status read_state(cpd_ctx* c, DevState* h) {
@@ -284,14 +324,15 @@ cpd_status read_state(cpd_ctx* c, DevState* h) {
 // M-step launches of an FP32-point context, for either basis storage.
 void mstep_f32(cpd_ctx* c, const float4* R4, const float4* Yt4, float4* T4, const float4* Yhat4, float4* B4,
                float4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const MstepPlan* trim = iteration && c->k_cap > 0 ? &c->mp_trim : nullptr;
   if (c->half_basis)
     launch_mstep<float, __half>(c->mp, c->U.as<__half>(), c->Ut.as<__half>(), c->lam.as<double>(), c->M, c->K,
                                 c->X4.as<float4>(), R4, Yt4, T4, Yhat4, c->partP.as<float>(), c->sums.as<double>(),
-                                B4, C4, st, iteration, s, ev);
+                                B4, C4, st, iteration, s, ev, trim);
   else
     launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
                         c->X4.as<float4>(), R4, Yt4, T4, Yhat4, c->partP.as<float>(), c->sums.as<double>(), B4, C4,
-                        st, iteration, s, ev);
+                        st, iteration, s, ev, trim);
 }
 
 void w_f32(cpd_ctx* c, const float4* C4, float4* W4, cudaStream_t s) {
@@ -498,7 +539,7 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   if ((s = upload_points(c, X, M, c->X4.p, false, c->stage, c->fp64, c->stream)) != CPD_OK) return bail(s);
   // FP32 paths: model points in spatial order (the E-step prunes far tile
   // pairs exactly); every per-model-point input and output is permuted.
-  if (!c->fp64 && p->flags != 0 && spatial_sort_supported(M)) {
+  if (!c->fp64 && (p->flags & kPruneFlags) && spatial_sort_supported(M)) {
     if ((s = c->permX.ensure((size_t)M * sizeof(int))) != CPD_OK) return bail(s);
     if ((s = c->invX.ensure((size_t)M * sizeof(int))) != CPD_OK) return bail(s);
     if ((s = sort_points(c, c->X4.p, M, c->permX.as<int>())) != CPD_OK) return bail(s);
@@ -564,12 +605,15 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
                                    c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
   free_setup();
+  if ((p->flags & CPD_FLAG_SPECTRAL_TRIM) && (s = plan_trim(c)) != CPD_OK) return bail(s);
 
   if ((s = c->Yt4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->R4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->B4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->C4.ensure((size_t)c->K * c->v4)) != CPD_OK) return bail(s);
-  if ((s = c->partP.ensure((size_t)c->mp.part_elems * c->es)) != CPD_OK) return bail(s);
+  if ((s = c->partP.ensure((size_t)std::max(c->mp.part_elems, c->k_cap > 0 ? c->mp_trim.part_elems : 0) * c->es)) !=
+      CPD_OK)
+    return bail(s);
   if ((s = c->sums.ensure((size_t)c->mp.sums_elems * sizeof(double))) != CPD_OK) return bail(s);
   launch_state_init(c->dst(), 0.0, c->stream);
   launch_state_params(c->dst(), p->w, p->lambda, p->tol, 0.0, 0, c->hist.as<double>(), M, 0, c->K, c->stream);
@@ -759,6 +803,19 @@ cpd_status cpd_get_work(cpd_ctx* c, int32_t n, double* eval_frac) {
 }
 
 int32_t cpd_spatial_order(const cpd_ctx* c) { return c && c->sorted_model ? 1 : 0; }
+
+cpd_status cpd_get_trim(cpd_ctx* c, int64_t* k_cap, int32_t* trimmed_iters) {
+  g_err.clear();
+  if (!c || !k_cap || !trimmed_iters) return fail(CPD_EINVAL, "ctx, k_cap and trimmed_iters are required");
+  *k_cap = c->k_cap;
+  *trimmed_iters = 0;
+  if (!c->started) return CPD_OK;
+  DeviceGuard guard(c->dev);
+  DevState h;
+  STATUS_TRY(read_state(c, &h));
+  *trimmed_iters = h.trim_iters;
+  return CPD_OK;
+}
 
 cpd_status cpd_coefficients(cpd_ctx* c, int32_t n_coef, void* coef_out) {
   g_err.clear();
@@ -1092,6 +1149,7 @@ cpd_status cpd_batch_create(int32_t n_pairs, const void* const* X, const int64_t
   if (n_pairs < 1 || n_pairs > kMaxBatch) return fail(CPD_EINVAL, "n_pairs must be in [1, 65536]");
   if (!X || !M || !Y || !N) return fail(CPD_EINVAL, "X, M, Y and N are required");
   if (p->precision != CPD_FP32) return fail(CPD_EINVAL, "batched registrations run in FP32 only");
+  if (p->flags & CPD_FLAG_SPECTRAL_TRIM) return fail(CPD_EINVAL, "batched registrations take no spectral trim");
   if (barrier_timeout_s == 0.0) barrier_timeout_s = 5.0;
   if (!(barrier_timeout_s > 0.0 && barrier_timeout_s <= 60.0))
     return fail(CPD_EINVAL, "barrier_timeout_s must be in (0, 60] (0 selects 5 s)");

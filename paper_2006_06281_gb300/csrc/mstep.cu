@@ -12,11 +12,25 @@ namespace {
 
 using namespace dev;
 
+// trim: 0 = no spectral trim in this context; 1 = the full M-step of a
+// context with the trim (steps aside when the trimmed one runs); 2 = the
+// trimmed M-step (runs only then).  trim_now is set once per iteration,
+// before the M-step, by trim_decide.
+__device__ __forceinline__ bool trim_skip(const DevState* st, int trim) {
+  return trim != 0 && ((trim == 2) != (st->trim_now != 0));
+}
+
+__global__ void trim_decide(DevState* st) {
+  if (iteration_gated(st)) return;
+  st->trim_now = trim_active(st) ? 1 : 0;
+}
+
 template <typename F, typename S>
 __global__ void __launch_bounds__(kThreadsP)
 colsum(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
        int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
-       int clear_row_flags) {
+       int clear_row_flags, int trim) {
+  if (trim_skip(st, trim)) return;
   dev::colsum_body<F, S, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -116,8 +130,8 @@ template <typename F, typename S>
 __global__ void __launch_bounds__(BulkGeom<S>::THREADS)
 colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
             int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
-            int clear_row_flags) {
-  if (gate && iteration_gated(st)) return;
+            int clear_row_flags, int trim) {
+  if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
   if (clear_row_flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
   using G = BulkGeom<S>;
   using V4 = typename Vec<F>::t4;
@@ -130,8 +144,11 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
       reinterpret_cast<unsigned long long*>(smem + (size_t)G::STAGES * (G::SLOT + G::ROWS * sizeof(V4)));
   const int tid = threadIdx.x;
   const int64_t cb = (int64_t)blockIdx.x * G::COLS;
-  // 16-byte vectors of a tile row inside the row stride (ldA is a multiple of W)
-  const int vecs = (int)((ldA - cb) / G::L < G::VPR ? (ldA - cb) / G::L : G::VPR);
+  // 16-byte vectors of a tile row: the columns rounded up to W (<= ldA, a
+  // multiple of W)
+  const int64_t wcols = ((int64_t)cols + W - 1) / W * W;
+  const int64_t lim = (wcols < ldA ? wcols : ldA) - cb;
+  const int vecs = (int)(lim / G::L < G::VPR ? lim / G::L : G::VPR);
   const unsigned int row_bytes = (unsigned int)vecs * 16u;
   const int r0 = blockIdx.y * rows_per_chunk;
   const int r1 = min(rows, r0 + rows_per_chunk);
@@ -224,24 +241,38 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
       }
     }
   }
-  (void)cols;
 }
 
+// Diagonal update of the first K columns; columns K .. k_zero - 1 (the
+// directions a trimmed M-step drops) get B = C = 0.
 template <typename F>
 __global__ void __launch_bounds__(kThreadsD)
-diag_update(const F* __restrict__ partP, int chunks, int64_t ldU, int K, const double* __restrict__ lam,
+diag_update(const F* __restrict__ partP, int chunks, int64_t ldP, int K, int k_zero, const double* __restrict__ lam,
             typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
-            const DevState* __restrict__ st, int gate) {
-  dev::diag_update_body<F>(partP, chunks, ldU, K, lam, B4, C4, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+            const DevState* __restrict__ st, int gate, int trim) {
+  if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
+  dev::diag_update_body<F>(partP, chunks, ldP, K, lam, B4, C4, st, 0, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  const int k = blockIdx.x * kMRedCols + threadIdx.x;
+  if (threadIdx.x < kMRedCols && k >= K && k < k_zero) {
+    typename Vec<F>::t4 z;
+    z.x = z.y = z.z = z.w = (F)0;
+    B4[k] = z;
+    C4[k] = z;
+  }
 }
 
+// With EPI (an iteration) a trimmed M-step (trim == 2) is counted in
+// st->trim_iters by the block that completes the iteration.
 template <typename F, bool EPI>
 __global__ void __launch_bounds__(kThreadsD)
 expand_finish(const F* __restrict__ partE, int chunks, int64_t ldM, int M,
               const typename Vec<F>::t4* __restrict__ X4, const typename Vec<F>::t4* __restrict__ Yt4,
               typename Vec<F>::t4* __restrict__ Tout, const typename Vec<F>::t4* __restrict__ Yhat4,
-              double* __restrict__ sums, DevState* __restrict__ st, int gate) {
-  dev::expand_finish_body<F, EPI>(partE, chunks, ldM, M, X4, Yt4, Tout, Yhat4, sums, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+              double* __restrict__ sums, DevState* __restrict__ st, int gate, int trim) {
+  if (trim_skip(st, trim)) return;
+  const bool last = dev::expand_finish_body<F, EPI>(partE, chunks, ldM, M, X4, Yt4, Tout, Yhat4, sums, st, gate,
+                                                    blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  if (EPI && last && trim == 2 && threadIdx.x == 0) st->trim_iters += 1;
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -292,43 +323,70 @@ constexpr bool kBulkF32 = true;
 
 }  // namespace
 
-MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads, int basis_bytes) {
-  MstepPlan p{};
-  const int64_t es = basis_bytes > 0 ? basis_bytes : (fp64 ? 8 : 4);
-  const int nv = es == 2 ? colsum_vectors<__half>() : 2;
-  const int W = (int)(16 * nv / es);   // columns per colsum thread; row strides padded to it
-  p.ldU = cdiv(K, W) * W;
-  p.ldM = cdiv(M, W) * W;
-  p.bulk = colsum_threads == kThreadsP && (es == 2 || (es == 4 && kBulkF32));
+namespace {
+// Grids of both products over a U with `cols_p` streamed columns (row stride
+// of the partials ldPp) and a U^T with `rows_e` streamed rows.
+void plan_products(MstepPlan& p, int64_t M, int64_t cols_p, int64_t rows_e, int64_t es, int sms, int W,
+                   int colsum_threads) {
   if (p.bulk) {
     const int64_t slots = es == 2 ? bulk_slots<float, __half>(sms) : bulk_slots<float, float>(sms);
     const int tc = es == 2 ? BulkGeom<__half>::COLS : BulkGeom<float>::COLS;
     const int tr = es == 2 ? BulkGeom<__half>::ROWS : BulkGeom<float>::ROWS;
-    plan_colsum_bulk(M, p.ldU, slots, tc, tr, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
-    plan_colsum_bulk(K, p.ldM, slots, tc, tr, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+    plan_colsum_bulk(M, p.ldPp, slots, tc, tr, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+    plan_colsum_bulk(rows_e, p.ldM, slots, tc, tr, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
   } else {
-    plan_colsum(M, p.ldU, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
-    plan_colsum(K, p.ldM, es, sms, W, colsum_threads, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
+    plan_colsum(M, p.ldPp, es, sms, W, colsum_threads, p.p_col_tiles, p.p_row_chunks, p.p_rows_per_chunk);
+    plan_colsum(rows_e, p.ldM, es, sms, W, colsum_threads, p.e_col_tiles, p.e_row_chunks, p.e_rows_per_chunk);
   }
-  p.part_elems = std::max((int64_t)p.p_row_chunks * 3 * p.ldU, (int64_t)p.e_row_chunks * 3 * p.ldM);
+  (void)cols_p;
+  p.part_elems = std::max((int64_t)p.p_row_chunks * 3 * p.ldPp, (int64_t)p.e_row_chunks * 3 * p.ldM);
   p.e_blocks = (int)cdiv(M, kMRedCols);
   p.sums_elems = (int64_t)p.e_blocks * 3;
+}
+
+int colsum_width(int64_t es) {
+  const int nv = es == 2 ? colsum_vectors<__half>() : 2;
+  return (int)(16 * nv / es);   // columns per colsum thread; row strides padded to it
+}
+}  // namespace
+
+MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_threads, int basis_bytes) {
+  MstepPlan p{};
+  const int64_t es = basis_bytes > 0 ? basis_bytes : (fp64 ? 8 : 4);
+  const int W = colsum_width(es);
+  p.K = K;
+  p.ldU = cdiv(K, W) * W;
+  p.ldPp = p.ldU;
+  p.ldM = cdiv(M, W) * W;
+  p.bulk = colsum_threads == kThreadsP && (es == 2 || (es == 4 && kBulkF32));
+  plan_products(p, M, K, K, es, sms, W, colsum_threads);
   return p;
 }
 
-// out partials of A^T V over the plan's grid (colsum or colsum_bulk).
+MstepPlan plan_mstep_trim(const MstepPlan& full, int64_t M, int64_t K_cap, bool fp64, int sms, int basis_bytes) {
+  MstepPlan p = full;
+  const int64_t es = basis_bytes > 0 ? basis_bytes : (fp64 ? 8 : 4);
+  const int W = colsum_width(es);
+  p.K = K_cap;
+  p.ldPp = std::min(full.ldU, cdiv(K_cap, W) * W);
+  plan_products(p, M, K_cap, K_cap, es, sms, W, kThreadsP);
+  return p;
+}
+
+// Partials of A^T V over the plan's grid (colsum or colsum_bulk); ldP: row
+// stride of the partials.
 template <typename F, typename S>
-void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA, int64_t rows, int64_t cols,
-                   const typename Vec<F>::t4* V, F* part, DevState* st, int gate, int clear_row_flags,
-                   cudaStream_t s) {
+void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA, int64_t ldP, int64_t rows,
+                   int64_t cols, const typename Vec<F>::t4* V, F* part, DevState* st, int gate, int clear_row_flags,
+                   int trim, cudaStream_t s) {
   const dim3 grid = expansion ? dim3(pl.e_col_tiles, pl.e_row_chunks) : dim3(pl.p_col_tiles, pl.p_row_chunks);
   const int rpc = expansion ? pl.e_rows_per_chunk : pl.p_rows_per_chunk;
   if (pl.bulk && !std::is_same<F, double>::value)
-    colsum_bulk<F, S><<<grid, BulkGeom<S>::THREADS, bulk_smem_bytes<F, S>(), s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part,
-                                                                         ldA, st, gate, clear_row_flags);
+    colsum_bulk<F, S><<<grid, BulkGeom<S>::THREADS, bulk_smem_bytes<F, S>(), s>>>(
+        A, ldA, (int)rows, (int)cols, V, rpc, part, ldP, st, gate, clear_row_flags, trim);
   else
-    colsum<F, S><<<grid, kThreadsP, 0, s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part, ldA, st, gate,
-                                            clear_row_flags);
+    colsum<F, S><<<grid, kThreadsP, 0, s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part, ldP, st, gate,
+                                            clear_row_flags, trim);
 }
 
 template <typename F, typename S>
@@ -336,21 +394,34 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums, typename Vec<F>::t4* B4,
-                  typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev) {
+                  typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev,
+                  const MstepPlan* trim) {
   const int g = iteration ? 1 : 0;
-  launch_colsum<F, S>(pl, false, U, pl.ldU, M, K, R4, part, st, g, g, s);
+  const MstepPlan* tr = iteration ? trim : nullptr;
+  const int mf = tr ? 1 : 0;      // the full M-step's trim mode
+  const unsigned dblocks = (unsigned)cdiv(K, kMRedCols);
+  if (tr) trim_decide<<<1, 1, 0, s>>>(st);
+  if (tr) launch_colsum<F, S>(*tr, false, U, tr->ldU, tr->ldPp, M, tr->K, R4, part, st, g, g, 2, s);
+  launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
   record_after(ev, 0, s);
-  diag_update<F><<<(unsigned)cdiv(K, kMRedCols), kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldU, (int)K, lam,
-                                                                   B4, C4, st, g);
+  if (tr)
+    diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4,
+                                                 st, g, 2);
+  diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g,
+                                               mf);
   record_after(ev, 1, s);
-  launch_colsum<F, S>(pl, true, Ut, pl.ldM, K, M, B4, part, st, g, 0, s);
+  if (tr) launch_colsum<F, S>(*tr, true, Ut, tr->ldM, tr->ldM, tr->K, M, B4, part, st, g, 0, 2, s);
+  launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, B4, part, st, g, 0, mf, s);
   record_after(ev, 2, s);
   if (iteration) {
+    if (tr)
+      expand_finish<F, true><<<tr->e_blocks, kThreadsD, 0, s>>>(part, tr->e_row_chunks, tr->ldM, (int)M, X4, Yt4,
+                                                                T4, Yhat4, sums, st, g, 2);
     expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
-                                                             Yhat4, sums, st, g);
+                                                             Yhat4, sums, st, g, mf);
   } else {
     expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
-                                                              T4, nullptr, sums, st, 0);
+                                                              T4, nullptr, sums, st, 0, 0);
   }
   record_after(ev, 3, s);
 }
@@ -358,23 +429,23 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
 template <typename F, typename S>
 void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
               typename Vec<F>::t4* W4, DevState* st, cudaStream_t s) {
-  launch_colsum<F, S>(pl, true, Ut, pl.ldM, K, M, C4, part, st, 0, 0, s);
+  launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, C4, part, st, 0, 0, 0, s);
   expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
-                                                            nullptr, W4, nullptr, nullptr, st, 0);
+                                                            nullptr, W4, nullptr, nullptr, st, 0, 0);
 }
 
 template void launch_mstep<float, float>(const MstepPlan&, const float*, const float*, const double*, int64_t,
                                          int64_t, const float4*, const float4*, const float4*, float4*,
                                          const float4*, float*, double*, float4*, float4*, DevState*, bool,
-                                         cudaStream_t, cudaEvent_t*);
+                                         cudaStream_t, cudaEvent_t*, const MstepPlan*);
 template void launch_mstep<double, double>(const MstepPlan&, const double*, const double*, const double*, int64_t,
                                            int64_t, const dvec4*, const dvec4*, const dvec4*, dvec4*, const dvec4*,
                                            double*, double*, dvec4*, dvec4*, DevState*, bool, cudaStream_t,
-                                           cudaEvent_t*);
+                                           cudaEvent_t*, const MstepPlan*);
 template void launch_mstep<float, __half>(const MstepPlan&, const __half*, const __half*, const double*, int64_t,
                                           int64_t, const float4*, const float4*, const float4*, float4*,
                                           const float4*, float*, double*, float4*, float4*, DevState*, bool,
-                                          cudaStream_t, cudaEvent_t*);
+                                          cudaStream_t, cudaEvent_t*, const MstepPlan*);
 template void launch_w<float, float>(const MstepPlan&, const float*, int64_t, int64_t, const float4*, float*,
                                      float4*, DevState*, cudaStream_t);
 template void launch_w<double, double>(const MstepPlan&, const double*, int64_t, int64_t, const dvec4*, double*,

@@ -165,7 +165,12 @@ __global__ void state_init(DevState* st, double sigma2) {
   st->prune_r2 = 0.f;
   st->prune_ctl = 0;
   st->mma_s2min = INFINITY;
+  st->trim_lam = -1.0;
+  st->trim_now = 0;
+  st->trim_iters = 0;
 }
+
+__global__ void state_trim(DevState* st, double trim_lam) { st->trim_lam = trim_lam; }
 
 __global__ void state_prune(DevState* st, float r2, int ctl) {
   st->prune_r2 = r2;
@@ -220,6 +225,7 @@ void launch_residual(const typename Vec<F>::t4* Yt4, const typename Vec<F>::t4* 
 template void launch_residual<float>(const float4*, const float4*, float4*, int64_t, cudaStream_t);
 template void launch_residual<double>(const dvec4*, const dvec4*, dvec4*, int64_t, cudaStream_t);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s) { state_init<<<1, 1, 0, s>>>(st, sigma2); }
+void launch_state_trim(DevState* st, double trim_lam, cudaStream_t s) { state_trim<<<1, 1, 0, s>>>(st, trim_lam); }
 void launch_state_prune(DevState* st, float prune_r2, int prune_ctl, cudaStream_t s) {
   state_prune<<<1, 1, 0, s>>>(st, prune_r2, prune_ctl);
 }

@@ -57,7 +57,7 @@ def _setup(lib, X, p):
 
 
 @pytest.mark.parametrize("field,value", [("D", 2), ("precision", 7), ("w", 1.0), ("w", -0.1),
-                                         ("beta", 0.0), ("lam", -1.0), ("K", -1), ("flags", 8), ("flags", 17),
+                                         ("beta", 0.0), ("lam", -1.0), ("K", -1), ("flags", 16), ("flags", 17),
                                          ("tol", -1.0), ("max_iter", -1),
                                          ("sigma2_init", float("nan"))])
 def test_setup_rejects_bad_params_without_device_work(lib, field, value):
@@ -68,6 +68,27 @@ def test_setup_rejects_bad_params_without_device_work(lib, field, value):
     assert st == cpd.EINVAL
     assert h.value is None
     assert lib.cpd_last_error() != b""
+
+
+def test_spectral_trim_is_rejected_for_fp64_and_batches(lib):
+    X = np.zeros((4, 3), dtype=np.float64)
+    p = cpd.make_params(precision=cpd.FP64, flags=cpd.FLAG_SPECTRAL_TRIM)
+    st, h = _setup(lib, X, p)
+    assert st == cpd.EINVAL and h.value is None
+    assert b"FP64" in lib.cpd_last_error()
+    X32 = np.zeros((4, 3), dtype=np.float32)
+    p = cpd.make_params(flags=cpd.FLAG_SPECTRAL_TRIM)
+    b = C.c_void_p()
+    M = (C.c_int64 * 1)(4)
+    ptr = (C.c_void_p * 1)(X32.ctypes.data)
+    assert lib.cpd_batch_create(1, ptr, M, ptr, M, C.byref(p), 0.0, None, C.byref(b)) == cpd.EINVAL
+    assert b.value is None
+
+
+def test_get_trim_rejects_null_arguments(lib):
+    k = C.c_int64()
+    n = C.c_int32()
+    assert lib.cpd_get_trim(None, C.byref(k), C.byref(n)) == cpd.EINVAL
 
 
 def test_setup_rejects_bad_shapes(lib):
