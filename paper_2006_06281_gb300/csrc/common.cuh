@@ -76,7 +76,7 @@ struct DevState {
   int prune_ctl;                  // kPrune* / kMmaAllowed bits (0: dense passes only)
   double mma_s2min;               // tensor-core passes run while sigma2 >= this
   double trim_lam;                // spectral trim: largest eigenvalue the trimmed M-step drops (< 0: off)
-  int trim_now;                   // the trimmed M-step runs in this iteration (set by trim_decide)
+  int trim_now;                   // the trimmed M-step runs in this iteration (set by fixB_f32)
   int trim_iters;                 // iterations of this registration that ran the trimmed M-step
 };
 
@@ -146,6 +146,37 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
   }
   return r;
+}
+
+// Sums of three doubles over the first `warps` warps of a block (the other
+// warps' values are ignored; every thread of the block must call it).  One
+// pair of barriers for the three sums; fixed order.  Results valid in
+// thread 0.  `sh` holds >= 32 x 3 doubles.
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double (*sh)[3], int warps) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < warps) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+  }
+  __syncthreads();
+  if (warp < warps && lane == 0) {
+    sh[warp][0] = a;
+    sh[warp][1] = b;
+    sh[warp][2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = sh[0][0]; b = sh[0][1]; c = sh[0][2];
+    for (int w = 1; w < warps; ++w) {
+      a += sh[w][0];
+      b += sh[w][1];
+      c += sh[w][2];
+    }
+  }
 }
 
 // ---------------------------------------------------------- spatial order
@@ -321,10 +352,10 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
 // With `iteration` false the state is not advanced (standalone M-step:
 // T4 receives T, no sigma2 update, st supplies sigma2 and lambda).
 // S: storage type of the basis (F, or __half in the mixed-precision mode).
-// With `trim` (an iteration of a context with the spectral trim) a one-thread
-// kernel decides on the device whether the trimmed M-step (plan *trim) or
-// the full one (pl) runs this iteration; both are enqueued, step by step,
-// and the other steps aside.  The trimmed M-step sets B and C to 0 for the
+// With `trim` (an iteration of a context with the spectral trim) the device
+// state's trim_now -- set by the E-step's last launch -- selects the trimmed
+// M-step (plan *trim) or the full one (pl) for this iteration; both are
+// enqueued, step by step, and the other steps aside.  The trimmed M-step sets B and C to 0 for the
 // dropped directions.
 template <typename F, typename S = F>
 void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,

@@ -85,6 +85,10 @@ __global__ void __launch_bounds__(kThreadsF)
 fixB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
          const float4* __restrict__ X4, float4* __restrict__ Yt4, float4* __restrict__ R4,
          double* __restrict__ P1_out, const int* __restrict__ flag_rows, DevState* __restrict__ st, int gate) {
+  // the E-step's last launch also takes the iteration's spectral-trim
+  // decision for the M-step that follows (sigma2 is the same in both)
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !(gate && iteration_gated(st)))
+    st->trim_now = trim_active(st) ? 1 : 0;
   dev::fixB_f32_body(T4, M, Yb, N, X4, Yt4, R4, P1_out, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 

@@ -244,7 +244,8 @@ __device__ __forceinline__ void passA_f64_body(const dvec4* FCPD_RESTRICT T4, in
 
 __device__ __forceinline__ double outlier_c(const DevState* st, int M, int N) {
   const double w = st->w;
-  return pow(2.0 * kPi * st->sigma2, 1.5) * (w / (1.0 - w)) * ((double)M / (double)N);
+  const double t = 2.0 * kPi * st->sigma2;         // (2 pi sigma2)^(D/2), D = 3
+  return t * sqrt(t) * (w / (1.0 - w)) * ((double)M / (double)N);
 }
 
 // ------------------------------------------------- pass A reduction (+ c)
@@ -273,7 +274,7 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
   __shared__ double c_sh;
   const double s2 = st->sigma2;
   const double w = st->w;
-  if (threadIdx.x == 0) c_sh = outlier_c(st, M, N);   // FP64 pow once per block
+  if (threadIdx.x == 0) c_sh = outlier_c(st, M, N);   // once per block
   const int col = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
   const int n = bx * kRedCols + col;
   F s = (F)0;   // FP32 partials summed in FP32 (fixed order), FP64 in FP64

@@ -15,14 +15,9 @@ using namespace dev;
 // trim: 0 = no spectral trim in this context; 1 = the full M-step of a
 // context with the trim (steps aside when the trimmed one runs); 2 = the
 // trimmed M-step (runs only then).  trim_now is set once per iteration,
-// before the M-step, by trim_decide.
+// before the M-step, by the E-step's last launch (fixB_f32).
 __device__ __forceinline__ bool trim_skip(const DevState* st, int trim) {
   return trim != 0 && ((trim == 2) != (st->trim_now != 0));
-}
-
-__global__ void trim_decide(DevState* st) {
-  if (iteration_gated(st)) return;
-  st->trim_now = trim_active(st) ? 1 : 0;
 }
 
 template <typename F, typename S>
@@ -400,7 +395,6 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
   const MstepPlan* tr = iteration ? trim : nullptr;
   const int mf = tr ? 1 : 0;      // the full M-step's trim mode
   const unsigned dblocks = (unsigned)cdiv(K, kMRedCols);
-  if (tr) trim_decide<<<1, 1, 0, s>>>(st);
   if (tr) launch_colsum<F, S>(*tr, false, U, tr->ldU, tr->ldPp, M, tr->K, R4, part, st, g, g, 2, s);
   launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
   record_after(ev, 0, s);

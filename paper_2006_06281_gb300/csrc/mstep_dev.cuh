@@ -274,7 +274,7 @@ __device__ __forceinline__ bool expand_finish_body(const F* FCPD_RESTRICT partE,
   if (gate && iteration_gated(st)) return false;
   using V4 = typename Vec<F>::t4;
   __shared__ F part[kMRedSub][3][kMRedCols];
-  __shared__ double sh[32];
+  __shared__ double sh3[32][3];
   __shared__ bool last;
   const int m = bx * kMRedCols + threadIdx.x % kMRedCols;
   F a[3];
@@ -289,13 +289,12 @@ __device__ __forceinline__ bool expand_finish_body(const F* FCPD_RESTRICT partE,
     Tout[m] = tn;
   }
   if constexpr (EPI) {
-    const double b0 = block_sum(contrib, sh);
-    const double b1 = block_sum(dT2, sh);
-    const double b2 = block_sum(gt2, sh);
+    // only the first kMRedCols threads hold a row's terms
+    block_sum3(contrib, dT2, gt2, sh3, (kMRedCols + 31) / 32);
     if (threadIdx.x == 0) {
-      sums[(size_t)bx * 3] = b0;
-      sums[(size_t)bx * 3 + 1] = b1;
-      sums[(size_t)bx * 3 + 2] = b2;
+      sums[(size_t)bx * 3] = contrib;
+      sums[(size_t)bx * 3 + 1] = dT2;
+      sums[(size_t)bx * 3 + 2] = gt2;
       __threadfence();
       last = atomicAdd(&st->ticket_e, 1u) == gx - 1;
     }
@@ -308,11 +307,9 @@ __device__ __forceinline__ bool expand_finish_body(const F* FCPD_RESTRICT partE,
         a1 += __ldcg(sums + (size_t)i * 3 + 1);
         a2 += __ldcg(sums + (size_t)i * 3 + 2);
       }
-      const double t0 = block_sum(a0, sh);
-      const double t1 = block_sum(a1, sh);
-      const double t2 = block_sum(a2, sh);
+      block_sum3(a0, a1, a2, sh3, (int)(blockDim.x >> 5));
       if (threadIdx.x == 0) {
-        finish_iteration(st, t0, t1, t2, M);
+        finish_iteration(st, a0, a1, a2, M);
         st->ticket_e = 0;
       }
     }
