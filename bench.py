@@ -724,10 +724,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(ps, cfg, M, N, K)
-    # per iteration: pass A, reduce A, fix A, pass B, reduce B, fix B, project,
-    # diagonal update, expansion; per registration: scene packing, state
-    # init, initial variance, iteration target
-    launches = 9 * steps + 4 * R
+    # per iteration: pass A, reduce A, fix A, pass B, reduce B, fix B,
+    # projection, diagonal update, expansion, expansion finish (T, Eq. 18);
+    # per registration: scene packing, state init, initial variance, E-step
+    # layout control, iteration target
+    launches = 10 * steps + 5 * R
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=steps, warmup=warm,

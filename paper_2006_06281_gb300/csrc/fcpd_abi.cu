@@ -279,7 +279,7 @@ void apply_prune(cpd_ctx* c) {
   }
   if (c->half_basis) ctl |= kMmaAllowed;
   launch_state_prune(c->dst(), c->prune_r2, ctl, c->stream);
-  launch_state_trim(c->dst(), c->k_cap > 0 ? c->trim_lam : -1.0, c->stream);
+  if (c->k_cap > 0) launch_state_trim(c->dst(), c->trim_lam, c->stream);   // state_init switched it off
   if (c->half_basis) launch_mma_threshold(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, c->dst(), c->stream);
 }
 
