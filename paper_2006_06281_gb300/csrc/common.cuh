@@ -73,7 +73,7 @@ struct DevState {
   unsigned long long pairs_eval;  // Gaussian pairs evaluated by the pruned passes this iteration
   double last_eval_frac;          // fraction of the 2 M N pairs of passes A+B evaluated last iteration
   float prune_r2;                 // pruned passes run while 127 / kappa (FP32 cutoff radius^2) < this
-  int prune_ctl;                  // kPrune* / kMmaAllowed bits (0: dense passes only)
+  int prune_ctl;                  // kPrune* / kMmaAllowed / kBulkWaitFault bits (0: dense passes only)
   double mma_s2min;               // tensor-core passes run while sigma2 >= this
   double trim_lam;                // spectral trim: largest eigenvalue the trimmed M-step drops (< 0: off)
   int trim_now;                   // the trimmed M-step runs in this iteration (set by fixB_f32)
@@ -87,6 +87,12 @@ constexpr int kPruneAllowed = 1;   // points are in spatial order: the pruned pa
 constexpr int kPruneAlways = 2;    // run the pruned passes whatever sigma2 (verification)
 constexpr int kPruneNoSkip = 4;    // pruned passes evaluate every tile pair (verification)
 constexpr int kMmaAllowed = 8;     // mixed precision: tensor-core distance passes while sigma2 is large
+// Verification of the M-step's bounded waits (host fault injection): the
+// bulk-copy colsum expects 16 bytes more than it copies, so no slot's phase
+// completes and every wait runs out after kBulkFaultWaitNs; the kernel
+// records CPD_ETIMEOUT.  All its copies land; none is left in flight.
+constexpr int kBulkWaitFault = 16;
+constexpr unsigned long long kBulkFaultWaitNs = 50000000ull;   // 50 ms
 // The tensor-core passes accumulate exponent terms as large as q^2 |p|^2 in
 // FP32: they run while q^2 R^2 <= ~2000 (R = largest point norm), i.e.
 // sigma2 >= kMmaS2PerR2 * R^2, which keeps the exponent's rounding near 1e-3.

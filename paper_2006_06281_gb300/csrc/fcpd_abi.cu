@@ -278,6 +278,7 @@ void apply_prune(cpd_ctx* c) {
     if (c->p.flags & CPD_FLAG_PRUNE_NOSKIP) ctl |= kPruneNoSkip;
   }
   if (c->half_basis) ctl |= kMmaAllowed;
+  if (fault_enabled("bulk_wait")) ctl |= kBulkWaitFault;
   launch_state_prune(c->dst(), c->prune_r2, ctl, c->stream);
   if (c->k_cap > 0) launch_state_trim(c->dst(), c->trim_lam, c->stream);   // state_init switched it off
   if (c->half_basis) launch_mma_threshold(c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->N, c->dst(), c->stream);
@@ -655,7 +656,7 @@ cpd_status cpd_iterate(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, voi
     STATUS_TRY(read_state(c, &h));
     if (sigma2_out) *sigma2_out = h.sigma2;
     if (iters_done) *iters_done = h.iter;
-    if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+    if (h.status != 0) return fail((cpd_status)h.status, "the device reported a failure during the iterations");
   }
   return CPD_OK;
 }
@@ -688,7 +689,7 @@ cpd_status cpd_iterate_profiled(cpd_ctx* c, const void* Y, int64_t N, int32_t n_
   phase_ms[kPhases] = total;
   DevState h;
   STATUS_TRY(read_state(c, &h));
-  if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+  if (h.status != 0) return fail((cpd_status)h.status, "the device reported a failure during the iterations");
   return CPD_OK;
 }
 
@@ -952,7 +953,7 @@ cpd_status cpd_estep(const void* T, int64_t M, const void* Y, int64_t N, int32_t
       sums_out[0] = h.vsum;
       sums_out[1] = h.loglik;
     }
-    if (h.status != 0) return fail((cpd_status)h.status, "device reported a numeric failure");
+    if (h.status != 0) return fail((cpd_status)h.status, "the device reported a failure during the iterations");
     return CPD_OK;
   };
   const cpd_status r = run();

@@ -148,6 +148,9 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
   const int r0 = blockIdx.y * rows_per_chunk;
   const int r1 = min(rows, r0 + rows_per_chunk);
   const int nst = r0 < r1 ? (r1 - r0 + G::ROWS - 1) / G::ROWS : 0;
+  const bool fault = (st->prune_ctl & kBulkWaitFault) != 0;
+  const unsigned int extra_tx = fault ? 16u : 0u;
+  const unsigned long long wait_ns = fault ? kBulkFaultWaitNs : kBulkWaitNs;
   unsigned long long pol_a = 0, pol_v = 0;
   if (tid == 0) {
     for (int k = 0; k < G::STAGES; ++k) mbar_init(&bar[k], 1);
@@ -160,7 +163,7 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
     const int slot = k % G::STAGES;
     const int ra = r0 + k * G::ROWS;
     const int nr = min(G::ROWS, r1 - ra);
-    mbar_expect_tx(&bar[slot], (unsigned int)nr * (row_bytes + (unsigned int)sizeof(V4)));
+    mbar_expect_tx(&bar[slot], (unsigned int)nr * (row_bytes + (unsigned int)sizeof(V4)) + extra_tx);
     LT* dst = tiles + (size_t)slot * (G::SLOT / 16);
     for (int i = 0; i < nr; ++i)
       bulk_g2s(dst + (size_t)i * G::VPR, A + (size_t)(ra + i) * ldA + cb, row_bytes, &bar[slot], pol_a);
@@ -175,7 +178,7 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
   int failed_at = -1;
   for (int k = 0; k < nst; ++k) {
     const int slot = k % G::STAGES;
-    const bool ok = mbar_wait(&bar[slot], (unsigned int)(k / G::STAGES) & 1u, kBulkWaitNs);
+    const bool ok = mbar_wait(&bar[slot], (unsigned int)(k / G::STAGES) & 1u, wait_ns);
     const LT* tile = tiles + (size_t)slot * (G::SLOT / 16);
     const V4* vv = vt + (size_t)slot * G::ROWS;
     const int nr = min(G::ROWS, r1 - (r0 + k * G::ROWS));
@@ -211,7 +214,7 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
       atomicExch(&st->status, (int)CPD_ETIMEOUT);
       // the copies issued and not yet consumed: stages failed_at .. failed_at + G::STAGES - 1
       for (int j = failed_at; j < min(nst, failed_at + G::STAGES); ++j)
-        mbar_wait(&bar[j % G::STAGES], (unsigned int)(j / G::STAGES) & 1u, kBulkWaitNs);
+        mbar_wait(&bar[j % G::STAGES], (unsigned int)(j / G::STAGES) & 1u, wait_ns);
     }
     __syncthreads();
     return;

@@ -344,6 +344,29 @@ def test_injected_nan_variance_reports_enumeric(monkeypatch):
         assert it == 3 and math.isfinite(s2)
 
 
+def test_injected_bulk_copy_wait_timeout_is_reported_and_recoverable(monkeypatch):
+    # the M-step's bulk-copy ring expects 16 bytes more than it copies: no
+    # slot completes, each bounded wait runs out (50 ms), the kernel records
+    # CPD_ETIMEOUT and the iteration's later kernels step aside
+    ps = pointsets(300, seed=19)
+    X, Y = dev(ps.X, cpd.FP32), dev(ps.Y, cpd.FP32)
+    with cpd.Context(X) as ctx:
+        monkeypatch.setenv("CPD_FAULT", "bulk_wait")
+        with pytest.raises(cpd.CpdError) as ei:
+            ctx.iterate(Y, 2)
+        assert ei.value.status == cpd.ETIMEOUT
+        monkeypatch.delenv("CPD_FAULT")
+        _, _, ds = ctx.state()
+        assert ds == cpd.ETIMEOUT
+        ctx.reset()
+        T, s2, it = ctx.iterate(Y, 5)
+        assert it == 5
+    with cpd.Context(X) as fresh:
+        T2, s2b, _ = fresh.iterate(Y, 5)
+    np.testing.assert_array_equal(host(T), host(T2))
+    assert s2 == s2b
+
+
 def test_model_point_far_from_scene_reports_enumeric():
     ps = pointsets(100, seed=18)
     X = np.vstack([ps.X, [[40.0, 40.0, 40.0]]])
