@@ -169,10 +169,10 @@ def source_digest(kernel):
     return h.hexdigest()
 
 
-def traffic_for(kernel):
-    """dram bytes per launch recorded by ncu in profiles/, if the kernel's
-    source files are unchanged since (their sha256 is recorded beside the
-    figure)."""
+def traffic_for(kernel, workload):
+    """dram bytes per launch recorded by ncu in profiles/ for this workload,
+    if the kernel's source files are unchanged since (their sha256 is
+    recorded beside the figure)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if kernel not in TRAFFIC_SOURCES or not os.path.exists(path):
         return None
@@ -181,7 +181,7 @@ def traffic_for(kernel):
         if line.startswith("#"):
             continue
         kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
-        if kv.get("kernel") == kernel and kv.get("source_sha256") == sha:
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256") == sha:
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -529,7 +529,7 @@ def main():
     # per-kernel roofline from the events inside the timed region
     roof = roofline_entries(phases, M, N, K, peaks)
     dominant, rd = dominant_kernel(roof)
-    tr = traffic_for(dominant)
+    tr = traffic_for(dominant, args.workload)
     roofline = dict(kernel=dominant, bound=rd["bound"], achieved=rd["achieved"], peak=rd["peak"], unit=rd["unit"],
                     frac=rd["frac"], traffic=tr, ms_per_launch=rd["ms"], peak_source=peaks["source"])
     e_ms = sum(phases[:4])
