@@ -61,6 +61,9 @@ def parse():
                          "(e.g. fp32_warmstart_m2048_k64)")
     ap.add_argument("--no-trim", action="store_true",
                     help="skip timing the same registration with CPD_FLAG_SPECTRAL_TRIM")
+    ap.add_argument("--shared", type=int, default=0,
+                    help="also register this many scenes (deformations of the workload's model) against one model "
+                         "with cpd_iterate_shared, against the same scenes one at a time")
     ap.add_argument("--prune", action="store_true",
                     help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -728,6 +731,41 @@ def main():
                     note="the M-step keeps the directions with s_k = l_k/(l_k + lambda sigma2) >= 2^-24; "
                          "the dropped part of T is below one FP32 rounding (|dT| <= 2^-24 |R|)")
 
+    # several scenes against one model (cpd_iterate_shared): scene-iterations/s
+    # against the same scenes registered one at a time, and the largest
+    # difference of their T
+    shared = None
+    if world == 1 and args.shared > 0 and cfg["K"] == 0:
+        S = args.shared
+        Xh = ps.X.astype(np.float32)
+        Ys = [torch.tensor(datagen.gen_from_template(Xh, 5000 + i, amp=cfg["amp"], noise=cfg["noise"]).Y,
+                           dtype=torch.float32, device="cuda") for i in range(S)]
+        csh = cpd.Context(X, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0)
+        csh.iterate_shared(Ys, 3)
+        for Yi in Ys:
+            csh.reset()
+            csh.iterate(Yi, I)
+        torch.cuda.synchronize()
+        a.record()
+        res = csh.iterate_shared(Ys, I)
+        b.record()
+        torch.cuda.synchronize()
+        sh_ms = a.elapsed_time(b)
+        a.record()
+        seq = []
+        for Yi in Ys:
+            csh.reset()
+            seq.append(csh.iterate(Yi, I)[0])
+        b.record()
+        torch.cuda.synchronize()
+        seq_ms = a.elapsed_time(b)
+        dmax = max((r[0].double() - t.double()).norm().item() / t.double().norm().item() for r, t in zip(res, seq))
+        csh.close()
+        shared = dict(scenes=S, iters=I, scene_iters_per_s=S * I / (sh_ms / 1e3),
+                      one_at_a_time_scene_iters_per_s=S * I / (seq_ms / 1e3), speedup=seq_ms / sh_ms,
+                      max_rel_diff_T_vs_one_at_a_time=dmax,
+                      note="the M-step products of up to 8 scenes share one pass over U and U^T; E-steps per scene")
+
     warm_start = None
     if world == 1 and args.warmstart != "none":
         warm_start = run_warmstart(args, torch)
@@ -753,7 +791,7 @@ def main():
                     gpu_launches=launches, clocks=clocks, time_to_tolerance=ttt,
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
-                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, spectral_trim=trim, learned_warm_start=warm_start,
+                    lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, spectral_trim=trim, shared_model=shared, learned_warm_start=warm_start,
                     setup_s=setup_s,
                     batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "

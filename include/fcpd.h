@@ -322,6 +322,24 @@ cpd_status cpd_get_work(cpd_ctx *ctx, int32_t n, double *eval_frac);
 int32_t cpd_spatial_order(const cpd_ctx *ctx);
 
 /*
+ * Several registrations against the context's model (Eq. 17 with one
+ * eigenbasis for all scenes).  Scene i (Y[i]: N[i] x 3 FP32, row-major, host
+ * or device) is registered from W = 0 (sigma2_0 from the data, or the
+ * context's sigma2_init) for exactly n_iter iterations; T_out[i] (M x 3 FP32,
+ * host or device, caller-owned) receives its T and sigma2_out[i] (host) its
+ * final sigma2.  Up to 8 scenes at a time share each pass over U and U^T:
+ * their projections U^T R_i and expansions U B_i are one streaming kernel
+ * with 3 S right-hand sides, so the M-step's basis traffic is paid once per
+ * group instead of once per scene.  The E-steps, diagonal updates and Eq. 18
+ * epilogues stay per scene (the same kernels as cpd_iterate).  The context's
+ * own registration state is not touched.  Requires a CPD_FP32 context
+ * without flags (CPD_EINVAL otherwise).  Synchronises.  A device failure of
+ * any scene is returned (CPD_ENUMERIC, CPD_ETIMEOUT).
+ */
+cpd_status cpd_iterate_shared(cpd_ctx *ctx, int32_t n_scenes, const void *const *Y, const int64_t *N,
+                              int32_t n_iter, void *const *T_out, double *sigma2_out);
+
+/*
  * Spectral trim of a context (CPD_FLAG_SPECTRAL_TRIM): *k_cap (host) = the
  * directions the trimmed M-step keeps (0: no trim -- flag unset or nothing
  * to drop); *trimmed_iters (host) = iterations of the current registration

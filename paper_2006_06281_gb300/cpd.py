@@ -31,7 +31,7 @@ FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP, FLAG_SPECTRAL_TRIM = 1, 2, 4, 
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
-           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_destroy",
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_iterate_shared", "cpd_destroy",
            "cpd_coefficients", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
            "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
@@ -89,6 +89,7 @@ def load():
                 "cpd_destroy": ([vp], None),
                 "cpd_get_work": ([vp, i32, vp], C.c_int),
                 "cpd_get_trim": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
+                "cpd_iterate_shared": ([vp, i32, C.POINTER(vp), C.POINTER(i64), i32, C.POINTER(vp), dp], C.c_int),
                 "cpd_coefficients": ([vp, i32, vp], C.c_int),
                 "cpd_warm_start": ([vp, i32, vp, d], C.c_int),
                 "cpd_net_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
@@ -207,6 +208,20 @@ class Context:
         s2, it = C.c_double(0), C.c_int32(0)
         _check(load().cpd_iterate(self._h, py, int(Yk.shape[0]), int(n_iter), pt, C.byref(s2), C.byref(it)))
         return T, s2.value, it.value
+
+    def iterate_shared(self, Ys, n_iter):
+        """Registers each scene of Ys against this context's model (fresh,
+        n_iter iterations each; the M-step products of up to 8 scenes share
+        one pass over the basis).  Returns [(T, sigma2)] in the order of Ys."""
+        n = len(Ys)
+        keep = [_prep(Y, self.precision, f"Ys[{i}]") for i, Y in enumerate(Ys)]
+        outs = [_out_like(self.M, 3, self.precision, k[2], self.device) for k in keep]
+        ys = (C.c_void_p * n)(*[k[1] for k in keep])
+        ns = (C.c_int64 * n)(*[int(k[0].shape[0]) for k in keep])
+        ts = (C.c_void_p * n)(*[o[1] for o in outs])
+        s2 = (C.c_double * n)()
+        _check(load().cpd_iterate_shared(self._h, n, ys, ns, int(n_iter), ts, s2))
+        return [(outs[i][0], s2[i]) for i in range(n)]
 
     def iterate_into(self, Y, n_iter, T_out):
         """Runs n_iter iterations writing T into the caller's buffer T_out

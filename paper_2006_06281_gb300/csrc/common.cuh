@@ -371,6 +371,25 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
                   typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, DevState* st,
                   bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr, const MstepPlan* trim = nullptr);
 
+// Several registrations against one model (multi.cu): the M-step of S
+// scenes with both products in one pass over U and U^T each (FP32 basis).
+struct MultiPlan {
+  int S;                                             // scenes per pass (1..8)
+  int p_col_tiles, p_chunks, p_rpc;                  // projection grid (rows of U)
+  int e_col_tiles, e_chunks, e_rpc;                  // expansion grid (rows of U^T)
+  int e_blocks;                                      // per-scene epilogue grid
+  int64_t part_elems, sums_elems;                    // scratch (floats, doubles)
+};
+constexpr int kMaxScenesPerPass = 8;
+MultiPlan plan_multi(int64_t M, int64_t K, int64_t ldU, int64_t ldM, int S, int sms);
+// R4, Yt4, T4: S x M rows; B4, C4: S x K rows; st: S device states (host
+// array of device pointers); status: device int receiving CPD_ETIMEOUT if a
+// bounded wait of the streaming kernel runs out.
+void launch_mstep_multi(const MultiPlan& p, const float* U, int64_t ldU, const float* Ut, int64_t ldM,
+                        const double* lam, int64_t M, int64_t K, const float4* X4, const float4* R4,
+                        const float4* Yt4, float4* T4, float4* B4, float4* C4, DevState* const* st, float* part,
+                        double* sums, int* status, cudaStream_t s);
+
 // W = U C (C from the last M-step), written as 4-vectors.
 template <typename F, typename S = F>
 void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,

@@ -316,6 +316,92 @@ cpd_status plan_trim(cpd_ctx* c) {
   return CPD_OK;
 }
 
+// Up to kMaxScenesPerPass registrations of scenes against the context's
+// model: fresh registrations (T = X, sigma2_0 from each scene) of n_iter
+// iterations each; per-scene E-steps, the M-step products of all scenes in
+// one pass over U and U^T (multi.cu), per-scene diagonal updates and Eq. 18.
+struct ScratchSet {
+  std::vector<Buf> b;
+  explicit ScratchSet(size_t n) : b(n) {}
+  ~ScratchSet() {
+    for (Buf& x : b) x.release();
+  }
+};
+
+cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* N, int n_iter, void* const* T_out,
+                        double* s2_out) {
+  const int64_t M = c->M, K = c->K;
+  const MultiPlan mp = plan_multi(M, K, c->ldU, c->mp.ldM, S, c->sms);
+  std::vector<EstepPlan> ep((size_t)S);
+  std::vector<int64_t> yoff((size_t)S);
+  int64_t pa = 0, pb = 0, sm = mp.sums_elems, fl = 0, nmax = 0, ytot = 0;
+  for (int i = 0; i < S; ++i) {
+    ep[(size_t)i] = plan_estep(M, N[i], false, c->sms, false, false);
+    pa = std::max(pa, ep[(size_t)i].partA_elems);
+    pb = std::max(pb, ep[(size_t)i].partB_elems);
+    sm = std::max(sm, ep[(size_t)i].sums_elems);
+    fl = std::max(fl, ep[(size_t)i].flags_elems);
+    nmax = std::max(nmax, N[i]);
+    yoff[(size_t)i] = ytot;
+    ytot += N[i];
+  }
+  enum { kY4, kYb, kPA, kPB, kPP, kSums, kFlags, kT4, kYt4, kR4, kB4, kC4, kSt, kStatus, kCount };
+  ScratchSet sc(kCount);
+  Buf* b = sc.b.data();
+  STATUS_TRY(b[kY4].ensure((size_t)ytot * sizeof(float4)));
+  STATUS_TRY(b[kYb].ensure((size_t)nmax * sizeof(float4)));
+  STATUS_TRY(b[kPA].ensure((size_t)pa * sizeof(float)));
+  STATUS_TRY(b[kPB].ensure((size_t)pb * sizeof(float)));
+  STATUS_TRY(b[kPP].ensure((size_t)mp.part_elems * sizeof(float)));
+  STATUS_TRY(b[kSums].ensure((size_t)sm * sizeof(double)));
+  STATUS_TRY(b[kFlags].ensure((size_t)fl * sizeof(int)));
+  for (int k : {(int)kT4, (int)kYt4, (int)kR4}) STATUS_TRY(b[k].ensure((size_t)S * M * sizeof(float4)));
+  for (int k : {(int)kB4, (int)kC4}) STATUS_TRY(b[k].ensure((size_t)S * K * sizeof(float4)));
+  STATUS_TRY(b[kSt].ensure((size_t)S * sizeof(DevState)));
+  STATUS_TRY(b[kStatus].ensure(sizeof(int)));
+  cudaStream_t s = c->stream;
+  CUDA_TRY(cudaMemsetAsync(b[kStatus].p, 0, sizeof(int), s));
+  float4* Y4 = b[kY4].as<float4>();
+  float4* T4 = b[kT4].as<float4>();
+  std::vector<DevState*> st((size_t)S);
+  for (int i = 0; i < S; ++i) {
+    st[(size_t)i] = b[kSt].as<DevState>() + i;
+    STATUS_TRY(upload_points(c, Y[i], N[i], Y4 + yoff[(size_t)i], true, c->stage, false, s));
+    CUDA_TRY(cudaMemcpyAsync(T4 + (size_t)i * M, c->X4.p, (size_t)M * sizeof(float4), cudaMemcpyDeviceToDevice, s));
+    const bool from_data = !(c->p.sigma2_init > 0.0);
+    launch_state_init(st[(size_t)i], from_data ? 0.0 : c->p.sigma2_init, s);
+    launch_state_params(st[(size_t)i], c->p.w, c->p.lambda, 0.0, 0.0, 0, nullptr, M, N[i], K, s);
+    if (from_data) launch_sigma2_init<float>(c->X4.as<float4>(), M, Y4 + yoff[(size_t)i], N[i], nullptr,
+                                             st[(size_t)i], s);
+    launch_begin_iterations(st[(size_t)i], n_iter, s);
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    for (int i = 0; i < S; ++i)
+      launch_estep<float>(ep[(size_t)i], T4 + (size_t)i * M, c->X4.as<float4>(), M, Y4 + yoff[(size_t)i],
+                          b[kYb].as<float4>(), N[i], b[kPA].as<float>(), b[kPB].as<float>(), b[kSums].as<double>(),
+                          b[kFlags].as<int>(), b[kYt4].as<float4>() + (size_t)i * M,
+                          b[kR4].as<float4>() + (size_t)i * M, nullptr, nullptr, st[(size_t)i], true, s);
+    launch_mstep_multi(mp, c->U.as<float>(), c->ldU, c->Ut.as<float>(), c->mp.ldM, c->lam.as<double>(), M, K,
+                       c->X4.as<float4>(), b[kR4].as<float4>(), b[kYt4].as<float4>(), T4, b[kB4].as<float4>(),
+                       b[kC4].as<float4>(), st.data(), b[kPP].as<float>(), b[kSums].as<double>(),
+                       b[kStatus].as<int>(), s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  for (int i = 0; i < S; ++i) STATUS_TRY(download_points(T4 + (size_t)i * M, M, T_out[i], c->stage, false, s));
+  std::vector<DevState> h((size_t)S);
+  int status = 0;
+  CUDA_TRY(cudaMemcpyAsync(h.data(), b[kSt].p, (size_t)S * sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(&status, b[kStatus].p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (status != 0) return fail((cpd_status)status, "a bounded wait of the shared-model M-step ran out");
+  for (int i = 0; i < S; ++i) {
+    if (h[(size_t)i].status != 0)
+      return fail((cpd_status)h[(size_t)i].status, "scene " + std::to_string(i) + ": the device reported a failure");
+    s2_out[i] = h[(size_t)i].sigma2;
+  }
+  return CPD_OK;
+}
+
 cpd_status read_state(cpd_ctx* c, DevState* h) {
   CUDA_TRY(cudaMemcpyAsync(h, c->st.p, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -804,6 +890,27 @@ cpd_status cpd_get_work(cpd_ctx* c, int32_t n, double* eval_frac) {
 }
 
 int32_t cpd_spatial_order(const cpd_ctx* c) { return c && c->sorted_model ? 1 : 0; }
+
+cpd_status cpd_iterate_shared(cpd_ctx* c, int32_t n_scenes, const void* const* Y, const int64_t* N, int32_t n_iter,
+                              void* const* T_out, double* sigma2_out) {
+  g_err.clear();
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (n_scenes < 1 || n_scenes > 4096) return fail(CPD_EINVAL, "n_scenes must be in [1, 4096]");
+  if (!Y || !N || !T_out || !sigma2_out) return fail(CPD_EINVAL, "Y, N, T_out and sigma2_out are required");
+  if (n_iter < 1 || n_iter > 100000) return fail(CPD_EINVAL, "n_iter must be in [1, 100000]");
+  if (c->fp64 || c->half_basis || c->sorted_model || c->k_cap > 0)
+    return fail(CPD_EINVAL, "shared-model registrations need a CPD_FP32 context without flags");
+  for (int i = 0; i < n_scenes; ++i) {
+    if (!Y[i] || !T_out[i]) return fail(CPD_EINVAL, "scene " + std::to_string(i) + ": Y or T_out is NULL");
+    if (N[i] < 1 || N[i] > kMaxN) return fail(CPD_EINVAL, "scene " + std::to_string(i) + ": N must be in [1, 2^30]");
+  }
+  DeviceGuard guard(c->dev);
+  for (int g0 = 0; g0 < n_scenes; g0 += kMaxScenesPerPass) {
+    const int S = std::min(kMaxScenesPerPass, n_scenes - g0);
+    STATUS_TRY(shared_group(c, S, Y + g0, N + g0, n_iter, T_out + g0, sigma2_out + g0));
+  }
+  return CPD_OK;
+}
 
 cpd_status cpd_get_trim(cpd_ctx* c, int64_t* k_cap, int32_t* trimmed_iters) {
   g_err.clear();

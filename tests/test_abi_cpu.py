@@ -114,6 +114,10 @@ def test_other_entry_points_reject_null_context(lib):
     assert lib.cpd_mstep(None, Y.ctypes.data, 1.0, Y.ctypes.data, None) == cpd.EINVAL
     assert lib.cpd_set_ground_truth(None, None, 0.0) == cpd.EINVAL
     assert lib.cpd_get_history(None, 0, None, None, None) == cpd.EINVAL
+    ys = (C.c_void_p * 1)(Y.ctypes.data)
+    ns = (C.c_int64 * 1)(4)
+    s2 = (C.c_double * 1)()
+    assert lib.cpd_iterate_shared(None, 1, ys, ns, 1, ys, s2) == cpd.EINVAL
     lib.cpd_destroy(None)   # ignored
 
 
