@@ -33,6 +33,8 @@ MUTANTS = {
     "sigma2_init_denominator": ("return total / ((double)D * (double)M * (double)N);",
                                 "return total / ((double)M * (double)N);"),
     "second_moment_wrong": ("yy += Y[n * D + d] * Y[n * D + d];", "yy += Y[n * D + d];"),
+    "rmse_missing_root": ("return sqrt(s / (double)M);", "return s / (double)M;"),
+    "rmse_per_coordinate_mean": ("return sqrt(s / (double)M);", "return sqrt(s / ((double)D * (double)M));"),
     "loglik_prior_term_sign": ("ll += (double)N * log((1.0 - w) / (double)M)",
                                "ll -= (double)N * log((1.0 - w) / (double)M)"),
 }

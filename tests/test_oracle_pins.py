@@ -261,3 +261,24 @@ def test_recovers_synthetic_deformation():
     after = oracle.rmse(res["T"], ps.Yhat)
     assert after < 0.25 * before
     assert after < 0.02
+
+
+# ---------------------------------------------------------------- Eq. 22
+def test_rmse_hand_values():
+    """Eq. 22: the root of the mean over the M model points of the squared
+    Euclidean error (not a mean over the D M coordinates, not squared).  Two
+    points, one off by (3, 4, 0) and one exact: sqrt(25 / 2)."""
+    T = np.array([[3.0, 4.0, 0.0], [1.0, -2.0, 0.5]])
+    Yhat = np.array([[0.0, 0.0, 0.0], [1.0, -2.0, 0.5]])
+    assert oracle.rmse(T, Yhat) == pytest.approx(math.sqrt(25.0 / 2.0), rel=1e-15)
+    # the same error in two dimensions: the divisor is M, whatever D
+    assert oracle.rmse(T[:, :2], Yhat[:, :2]) == pytest.approx(math.sqrt(25.0 / 2.0), rel=1e-15)
+
+
+def test_rmse_of_a_translation_is_its_length():
+    """A rigid translation by v moves every point by |v|: RMSE = |v| for any
+    point set (here 37 points, v = (0.3, -1.2, 0.4), |v| = 1.3)."""
+    X, _ = _rng_points(11, 37, 1)
+    v = np.array([0.3, -1.2, 0.4])
+    assert oracle.rmse(X + v, X) == pytest.approx(1.3, rel=1e-13)
+    assert oracle.rmse(X, X) == 0.0
