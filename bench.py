@@ -66,6 +66,8 @@ def parse():
                          "with cpd_iterate_shared, against the same scenes one at a time")
     ap.add_argument("--prune", action="store_true",
                     help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
+    ap.add_argument("--no-outlier-config", action="store_true",
+                    help="skip the M=20000, N=25000 (20%% outliers), K=200 configuration in FP32 and CPD_MIXED")
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--batch", default="fp32_batch256_m500_3000_k128",
                     help="batched-registration workload to time as well ('none' skips it)")
@@ -358,6 +360,72 @@ def run_batch(args, peaks, torch):
             c.close()
         out["per_pair_sequential"] = dict(ms=ts * 1e3, pair_iters_per_s=n * I / ts, setup_s=seq_setup)
         out["speedup_vs_per_pair"] = ts / t
+    return out
+
+
+def run_outlier_config(args, peaks, torch):
+    """The outlier configuration: M = 20000 model points, N = 25000 scene
+    points (5000 uniform outliers), top-200 basis (Eq. 20), w = 0.2,
+    lambda = 3, 150 iterations, in CPD_FP32 and CPD_MIXED on the same pair:
+    EM iterations/s over timed registrations, per-kernel milliseconds, time
+    to RMSE <= 5e-3, setup time, and the mixed path's T against the FP32
+    path's after the full 150 iterations."""
+    from paper_2006_06281_gb300 import cpd, datagen
+    cfg = datagen.WORKLOADS["fp32_m20000_n25000_k200"]
+    ps = datagen.gen(cfg["M"], cfg["n_out"], cfg["amp"], cfg["noise"], cfg["seed"])
+    M, N, K, I = cfg["M"], ps.Y.shape[0], cfg["K"], cfg["iters"]
+    X = torch.tensor(ps.X, dtype=torch.float32, device="cuda")
+    Y = torch.tensor(ps.Y, dtype=torch.float32, device="cuda")
+    Yhat = torch.tensor(ps.Yhat, dtype=torch.float32, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = dict(workload="fp32_m20000_n25000_k200", M=M, N=N, K=K, iters=I, w=cfg["omega"], lam=cfg["lam"],
+               beta=cfg["beta"])
+    Ts = {}
+    for name, prec in (("fp32", cpd.FP32), ("mixed", cpd.MIXED)):
+        t0 = time.perf_counter()
+        c = cpd.Context(X, precision=prec, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=K)
+        setup = time.perf_counter() - t0
+        c.reset()
+        c.iterate_profiled(Y, I)                      # graph capture, untimed
+        reps = 3
+        ph = np.zeros(9)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            c.reset()
+            ph += np.array(c.iterate_profiled(Y, I)) / reps
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        c.reset()
+        T, s2, it = c.iterate(Y, I)
+        Ts[name] = (T.double(), s2)
+        c.reset()
+        c.set_ground_truth(Yhat, RMSE_TARGET)
+        c.iterate(Y, 9, want_T=False)
+        c.reset()
+        torch.cuda.synchronize()
+        a.record()
+        _, _, it_tol = c.iterate(Y, 500, want_T=False)
+        b.record()
+        torch.cuda.synchronize()
+        rm = c.history(it_tol)["rmse"]
+        c.close()
+        roof = roofline_entries(ph, M, N, K, peaks, es=2 if prec == cpd.MIXED else 4)
+        e_ms = float(sum(ph[:4]))
+        out[name] = dict(iters_per_s=reps * I / (ms / 1e3), setup_s=setup, sigma2_final=s2,
+                         kernel_ms={k: v["ms"] for k, v in roof.items()},
+                         estep_pairs_per_s=M * N / (e_ms / 1e3),
+                         pass_a_frac=roof["e_pass_a"]["frac"] if "e_pass_a" in roof else None,
+                         pass_b_frac=roof["e_pass_b"]["frac"] if "e_pass_b" in roof else None,
+                         time_to_tolerance=dict(rmse_target=RMSE_TARGET, iters=int(it_tol),
+                                                ms=a.elapsed_time(b), final_rmse=float(rm[-1]),
+                                                reached=bool(rm[-1] <= RMSE_TARGET)))
+    t32, tm = Ts["fp32"][0], Ts["mixed"][0]
+    out["mixed"]["rel_diff_T_vs_fp32_after"] = dict(iters=I, value=(t32 - tm).norm().item() / t32.norm().item())
+    out["mixed"]["sigma2_rel_diff_vs_fp32"] = abs(Ts["mixed"][1] - Ts["fp32"][1]) / Ts["fp32"][1]
+    out["note"] = ("error against the FP64 oracle: tests/test_gpu_c3.py (150 iterations at M = 4000, N = 5000, "
+                   "K = 40; 6 iterations at full size)")
     return out
 
 
@@ -766,6 +834,10 @@ def main():
                       max_rel_diff_T_vs_one_at_a_time=dmax,
                       note="the M-step products of up to 8 scenes share one pass over U and U^T; E-steps per scene")
 
+    outlier = None
+    if world == 1 and not args.no_outlier_config:
+        outlier = run_outlier_config(args, peaks, torch)
+
     warm_start = None
     if world == 1 and args.warmstart != "none":
         warm_start = run_warmstart(args, torch)
@@ -792,6 +864,7 @@ def main():
                     gaussian_pairs_per_s=estep["pairs_per_s"] * world, estep=estep,
                     kernels={k: {kk: vv for kk, vv in v.items() if kk != "basis"} for k, v in roof.items()},
                     lowrank_k200=lowrank, mixed_fp16_basis=mixed, exact_pruning=prune, spectral_trim=trim, shared_model=shared, learned_warm_start=warm_start,
+                    outlier_m20000_n25000_k200=outlier,
                     setup_s=setup_s,
                     batch=batch,
                     baseline_note="vs_baseline divides by the paper's own fast-CPD rate at M=N=20000 "

@@ -77,13 +77,14 @@ typedef enum {
                           in FP16 (products and sums in FP32): the M-step
                           streams half the bytes; and while sigma2 is large
                           (sigma2 >= 4.4e-4 R^2, R the largest point norm)
-                          the E-step's Gaussian exponents come from BF16
-                          tensor-core products (3-way split operands, FP32
-                          accumulation), below it from the FP32 passes.
-                          Not a precision the paper uses; its error against
-                          the FP64 oracle is measured and stated, not
-                          bounded by the FP32 tolerance.  Points, outputs:
-                          float.                                         */
+                          the E-step's Gaussian exponents come from FP16
+                          tensor-core products (warp-level mma.sync
+                          m16n8k16, operands split into two FP16 parts,
+                          K = 16, FP32 accumulation), below it from the
+                          FP32 passes.  Not a precision the paper uses; its
+                          error against the FP64 oracle is measured and
+                          stated, not bounded by the FP32 tolerance.
+                          Points, outputs: float.                        */
 } cpd_precision;
 
 /* Registration parameters (Sec. IV "Parameter settings": w, beta, lambda). */
@@ -277,25 +278,29 @@ cpd_status cpd_estep(const void *T, int64_t M, const void *Y, int64_t N, int32_t
 /*
  * cpd_estep without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
- * when they need an E-step -- code running while another framework captures
- * a CUDA graph (allocation cannot be captured), loops that must not stall on
- * the device synchronisation cudaMalloc/cudaFree may cause, and programs
- * that reserve all device memory up front.  It computes exactly what
- * cpd_estep computes for precision CPD_FP32, with the same kernels, but takes
- * all scratch from one 24 MiB array that the library holds (as a static
- * device variable) for its lifetime on every GPU that loads it.
+ * when they need an E-step -- loops that must not stall on the device
+ * synchronisation cudaMalloc/cudaFree may cause, programs that reserve all
+ * device memory up front under a fixed budget, and runtimes that hand the
+ * library only arrays they already own.  It computes what cpd_estep computes
+ * for precision CPD_FP32, with the same kernels, but takes all scratch from
+ * one 24 MiB array that the library holds (as a static device variable) for
+ * its lifetime on every GPU that loads it.
  *   T (M x 3 floats), Y (N x 3 floats), Ytil_out (M x 3 floats), and the
- *   optional P1_out (M doubles) and den_out (N doubles) must be DEVICE
- *   arrays; sums_out (2 host doubles) is optional, as in cpd_estep.
- *   Limits: 1 <= M, N <= 32768; larger sizes, host arrays or a plan that
- *   does not fit the array return CPD_EINVAL with a message.
+ *   optional P1_out (M doubles) and den_out (N doubles) must be arrays in the
+ *   memory of the CURRENT device; sums_out (2 host doubles) is optional, as
+ *   in cpd_estep.
+ *   Limits: 1 <= M, N <= 32768 (the partial sums are planned so that every
+ *   such size fits the array); larger sizes, host arrays or arrays of
+ *   another device return CPD_EINVAL with a message.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call outside any stream capture.
- * Every call uses the same array, so calls that may overlap on the GPU (on
- * different streams, or from different threads) race and must be
- * serialised by the caller.  The array keeps the last call's contents; the
- * call re-initialises everything that must start from zero.  Synchronises
- * `stream`.
+ * (cudaGetSymbolAddress).  The call reads its results back to the host and
+ * synchronises `stream` before it returns, so it cannot be called while
+ * `stream` is being captured into a CUDA graph.  Every call uses the same
+ * array, so calls that may overlap on the GPU (from different threads, or
+ * enqueued on different streams without the returning synchronisation in
+ * between) race and must be serialised by the caller.  The array keeps the
+ * last call's contents; the call re-initialises everything that must start
+ * from zero.
  */
 cpd_status cpd_estep_noalloc(const void *T, int64_t M, const void *Y, int64_t N, double sigma2, double w,
                              void *Ytil_out, void *P1_out, void *den_out, double *sums_out, void *stream);

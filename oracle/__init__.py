@@ -116,6 +116,17 @@ def eig(X: np.ndarray, beta: float, K: int = 0):
     return U, lam
 
 
+def eig_top(X: np.ndarray, beta: float, K: int):
+    """Eq. 19: the K largest eigenpairs of the Gram matrix of X by the
+    Lanczos method (``scipy.sparse.linalg.eigsh``, a library primitive), for
+    model sets too large for the dense eigensolver on the host.  Same
+    conventions as eig(): descending, clamped at 0."""
+    import scipy.sparse.linalg as sla
+    w, V = sla.eigsh(gram(X, beta), k=int(K), which="LA")
+    order = np.argsort(-w, kind="stable")
+    return np.ascontiguousarray(V[:, order]), np.maximum(w[order], 0.0)
+
+
 def sigma2_init(X: np.ndarray, Y: np.ndarray) -> float:
     """sigma2_0 = sum_mn |y_n - x_m|^2 / (D M N)  (the paper is silent; reading)."""
     X, Y = _c(X), _c(Y)

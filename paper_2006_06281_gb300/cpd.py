@@ -460,19 +460,24 @@ def estep(T, Y, sigma2, w, precision=FP32, stream=None):
 
 def estep_noalloc(T, Y, sigma2, w, stream=None):
     """cpd_estep_noalloc: the FP32 E-step with no device allocation (CUDA
-    tensors only).  Returns dict(Ytil, P1, den, vsum, loglik) like estep()."""
+    tensors of one device only).  The call is made with that device current,
+    on its current stream unless `stream` is given.  Returns dict(Ytil, P1,
+    den, vsum, loglik) like estep()."""
     import torch
     Tk, pt, tcuda = _prep(T, FP32, "T")
     Yk, py, ycuda = _prep(Y, FP32, "Y")
     if not (tcuda and ycuda):
         raise TypeError("estep_noalloc takes CUDA tensors")
+    if Tk.device != Yk.device:
+        raise ValueError(f"estep_noalloc: T is on {Tk.device} and Y on {Yk.device}; they must share a device")
     M, N = int(Tk.shape[0]), int(Yk.shape[0])
-    Ytil = torch.empty((M, 3), dtype=torch.float32, device=Tk.device)
-    P1 = torch.empty(M, dtype=torch.float64, device=Tk.device)
-    den = torch.empty(N, dtype=torch.float64, device=Tk.device)
-    sums = (C.c_double * 2)()
-    _check(load().cpd_estep_noalloc(pt, M, py, N, float(sigma2), float(w), Ytil.data_ptr(), P1.data_ptr(),
-                                    den.data_ptr(), sums, _stream_handle(stream, True)))
+    with torch.cuda.device(Tk.device):
+        Ytil = torch.empty((M, 3), dtype=torch.float32, device=Tk.device)
+        P1 = torch.empty(M, dtype=torch.float64, device=Tk.device)
+        den = torch.empty(N, dtype=torch.float64, device=Tk.device)
+        sums = (C.c_double * 2)()
+        _check(load().cpd_estep_noalloc(pt, M, py, N, float(sigma2), float(w), Ytil.data_ptr(), P1.data_ptr(),
+                                        den.data_ptr(), sums, _stream_handle(stream, True)))
     return dict(Ytil=Ytil, P1=P1, den=den, vsum=sums[0], loglik=sums[1])
 
 

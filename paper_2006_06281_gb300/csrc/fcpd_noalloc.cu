@@ -2,15 +2,20 @@
 // allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need an
-// E-step: code that runs while another framework is capturing a CUDA graph
-// (allocation is not a capturable operation), loops that must not stall on
-// the implicit device synchronisation cudaMalloc/cudaFree can cause, and
-// programs that reserve all device memory up front under a fixed budget.
-// This variant therefore takes all of its scratch -- the 4-vector copies of
-// the points, the split partial sums of passes A and B, the flag lists and
-// the small device state -- from one statically sized device array that the
-// library holds for its lifetime on every GPU that loads it, and it calls no
-// allocating routine.
+// E-step: loops that must not stall on the implicit device synchronisation
+// cudaMalloc/cudaFree can cause, programs that reserve all device memory up
+// front under a fixed budget (a cudaMalloc there fails or evicts memory
+// another component owns), and allocator-free runtimes that hand this
+// library only the arrays they already own.  This variant therefore takes
+// all of its scratch -- the 4-vector copies of the points, the split partial
+// sums of passes A and B, the flag lists and the small device state -- from
+// one statically sized device array that the library holds for its lifetime
+// on every GPU that loads it, and it calls no allocating routine.
+//
+// The call reads its result back to the host and synchronises `stream`
+// before it returns, so it cannot be made while a stream is being captured
+// into a CUDA graph.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -60,13 +65,15 @@ cpd_status scratch_address(int dev, void** out) {
   return CPD_OK;
 }
 
-bool on_device(const void* p) {
+// True for device (or managed) memory of device `dev`: the kernels read the
+// arrays directly, so memory of another GPU is refused as well.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 // Bump allocator over the static array (256-byte aligned pieces).
@@ -91,34 +98,53 @@ extern "C" cpd_status cpd_estep_noalloc(const void* T, int64_t M, const void* Y,
     return fail(CPD_EINVAL, "cpd_estep_noalloc supports 1 <= M, N <= 32768 (its scratch is a fixed 24 MiB array)");
   if (!(sigma2 > 0.0) || !std::isfinite(sigma2)) return fail(CPD_EINVAL, "sigma2 must be > 0");
   if (!(w >= 0.0 && w < 1.0)) return fail(CPD_EINVAL, "w must satisfy 0 <= w < 1");
-  if (!on_device(T) || !on_device(Y) || !on_device(Ytil_out) || (P1_out && !on_device(P1_out)) ||
-      (den_out && !on_device(den_out)))
-    return fail(CPD_EINVAL, "cpd_estep_noalloc takes device arrays only (staging host data would need memory)");
   cudaStream_t s = (cudaStream_t)stream;
+  // An error left by an earlier, unrelated call on this thread is not this
+  // call's: discard it, unless it is sticky (the context is unusable).
+  if (cudaGetLastError() != cudaSuccess && cudaPeekAtLastError() != cudaSuccess)
+    return fail(CPD_ECUDA, "the CUDA context is in an error state from an earlier call");
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return fail(CPD_ECUDA, "no CUDA device");
+  if (!on_device(T, dev) || !on_device(Y, dev) || !on_device(Ytil_out, dev) || (P1_out && !on_device(P1_out, dev)) ||
+      (den_out && !on_device(den_out, dev)))
+    return fail(CPD_EINVAL, "cpd_estep_noalloc takes arrays in the memory of the current device only (staging "
+                            "host data or copying from another GPU would need memory)");
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(CPD_ECUDA, "cannot query the SM count");
   void* base = nullptr;
   cpd_status st = scratch_address(dev, &base);
   if (st != CPD_OK) return st;
 
-  const EstepPlan pl = plan_estep(M, N, false, sms);
+  // The E-step plan splits the long dimension over the resident blocks of
+  // `sms` SMs, so its partial sums grow with the SM count and the occupancy.
+  // If they do not fit, plan for fewer SMs (fewer, longer chunks: the same
+  // sums in a different order); with one SM every M, N <= 32768 fits.
+  EstepPlan pl{};
   Carve c{static_cast<unsigned char*>(base)};
-  DevState* ds = c.take<DevState>(1);
-  float4* T4 = c.take<float4>((size_t)M);
-  float4* Y4 = c.take<float4>((size_t)N);
-  float4* Yb = c.take<float4>((size_t)N);
-  float4* Yt4 = c.take<float4>((size_t)M);
-  float* partA = c.take<float>((size_t)pl.partA_elems);
-  float* partB = c.take<float>((size_t)pl.partB_elems);
-  double* sums = c.take<double>((size_t)pl.sums_elems);
-  int* flags = c.take<int>((size_t)pl.flags_elems);
-  double* P1 = c.take<double>((size_t)M);
-  double* den = c.take<double>((size_t)N);
-  if (c.used > kScratchBytes)
-    return fail(CPD_EINVAL, "these sizes need " + std::to_string(c.used) + " bytes of scratch, more than the 24 MiB "
-                            "static array; use cpd_estep");
+  DevState* ds = nullptr;
+  float4 *T4 = nullptr, *Y4 = nullptr, *Yb = nullptr, *Yt4 = nullptr;
+  float *partA = nullptr, *partB = nullptr;
+  double *sums = nullptr, *P1 = nullptr, *den = nullptr;
+  int* flags = nullptr;
+  for (int plan_sms = sms;; plan_sms = plan_sms / 2) {
+    pl = plan_estep(M, N, false, std::max(plan_sms, 1));
+    c.used = 0;
+    ds = c.take<DevState>(1);
+    T4 = c.take<float4>((size_t)M);
+    Y4 = c.take<float4>((size_t)N);
+    Yb = c.take<float4>((size_t)N);
+    Yt4 = c.take<float4>((size_t)M);
+    partA = c.take<float>((size_t)pl.partA_elems);
+    partB = c.take<float>((size_t)pl.partB_elems);
+    sums = c.take<double>((size_t)pl.sums_elems);
+    flags = c.take<int>((size_t)pl.flags_elems);
+    P1 = c.take<double>((size_t)M);
+    den = c.take<double>((size_t)N);
+    if (c.used <= kScratchBytes) break;
+    if (plan_sms <= 1)
+      return fail(CPD_EINVAL, "these sizes need " + std::to_string(c.used) + " bytes of scratch, more than the "
+                              "24 MiB static array; use cpd_estep");
+  }
 
   // Everything that must start from zero (the device state: counters and
   // tickets) is initialised here; every other piece is fully overwritten.

@@ -39,11 +39,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def sigma2_tol(tol_T, T, sigma2):
-    """sigma2 tolerance implied by a relative tolerance tol_T on T (sigma2 is
-    a mean of |y - t|^2 / D over pairs at distance ~ sqrt(D sigma2))."""
-    t_rms = float(np.sqrt((np.asarray(T) ** 2).sum(1).mean()))
-    return tol_T * max(1.0, 2.0 * t_rms / np.sqrt(3.0 * sigma2))
+def check_sigma2(got, ref, tol, what):
+    """sigma2 within the relative tolerance the FP32 path is held to (the
+    same figure as T); the achieved error is printed."""
+    err = abs(float(got) - float(ref)) / abs(float(ref))
+    print(f"[sigma2] {what}: relative error {err:.3e} (tolerance {tol:.0e})")
+    assert err <= tol, f"{what}: sigma2 relative error {err:.3e} > {tol:.0e}"
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +67,7 @@ def test_batch_matches_oracle(scenes):
                                   n_iter=iters, K=0 if Kr == x.shape[0] else Kr)
             T = b.T(i)
             assert rel(T, ref["T"]) <= FP32_TOL, (i, PAIRS[i], rel(T, ref["T"]))
-            assert s2[i] == pytest.approx(ref["sigma2"], rel=sigma2_tol(FP32_TOL, ref["T"], ref["sigma2"])), i
+            check_sigma2(s2[i], ref["sigma2"], FP32_TOL, f"batch pair {i}")
 
 
 def test_batch_matches_per_pair_contexts(scenes):

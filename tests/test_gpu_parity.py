@@ -42,9 +42,21 @@ def sigma2_tol(tol_T, T, sigma2):
     """sigma2 tolerance implied by a relative tolerance tol_T on T: sigma2 is a
     mean of |y - t|^2 / D over pairs at distance ~ sqrt(D sigma2), so an
     error dt in T moves it by about 2 sqrt(D sigma2) dt / D, i.e. a relative
-    error of 2 |T|_rms tol_T / sqrt(D sigma2)."""
+    error of 2 |T|_rms tol_T / sqrt(D sigma2).  Used only for the mixed
+    precision mode, whose error is stated rather than held to the FP32
+    figure."""
     t_rms = float(np.sqrt((np.asarray(T) ** 2).sum(1).mean()))
     return tol_T * max(1.0, 2.0 * t_rms / math.sqrt(3.0 * sigma2))
+
+
+def check_sigma2(got, ref, tol, what):
+    """sigma2 (a value or a per-iteration history) within the relative
+    tolerance the FP32 / FP64 paths are held to (1e-4 / 1e-10, the same
+    figures as T); the achieved error is printed."""
+    got, ref = np.atleast_1d(np.asarray(got, dtype=np.float64)), np.atleast_1d(np.asarray(ref, dtype=np.float64))
+    err = float(np.max(np.abs(got - ref) / np.abs(ref)))
+    print(f"[sigma2] {what}: max relative error {err:.3e} (tolerance {tol:.0e})")
+    assert err <= tol, f"{what}: sigma2 relative error {err:.3e} > {tol:.0e}"
 
 
 def rel(a, b):
@@ -141,12 +153,11 @@ def test_register_fp64_m500():
                               beta=cfg["beta"], gt=ps.Yhat)
     assert it == cfg["iters"]
     assert rel(T, ref["T"]) <= FP64_TOL
-    stol = sigma2_tol(FP64_TOL, ref["T"], ref["sigma2"])
-    assert s2 == pytest.approx(ref["sigma2"], rel=stol)
-    np.testing.assert_allclose(hist["sigma2"], ref["sigma2_hist"], rtol=stol)
+    check_sigma2(s2, ref["sigma2"], FP64_TOL, "FP64 M=N=500 final")
+    check_sigma2(hist["sigma2"], ref["sigma2_hist"], FP64_TOL, "FP64 M=N=500 history")
     # Eq. 3 carries -(N D / 2) ln sigma2: its absolute error follows sigma2's
     np.testing.assert_allclose(hist["loglik"], ref["loglik_hist"], rtol=1e-10,
-                               atol=ps.Y.shape[0] * 1.5 * stol)
+                               atol=ps.Y.shape[0] * 1.5 * FP64_TOL)
     assert hist["rmse"][-1] == pytest.approx(oracle.rmse(ref["T"], ps.Yhat), rel=1e-9)
 
 
@@ -158,9 +169,8 @@ def test_register_fp32_m5000():
     T, s2, it, hist = run_gpu(X, Y, cpd.FP32, cfg["iters"], w=cfg["omega"], lam=cfg["lam"], beta=cfg["beta"])
     assert it == cfg["iters"]
     assert rel(T, ref["T"]) <= FP32_TOL
-    stol = sigma2_tol(FP32_TOL, ref["T"], ref["sigma2"])
-    assert s2 == pytest.approx(ref["sigma2"], rel=stol)
-    np.testing.assert_allclose(hist["sigma2"], ref["sigma2_hist"], rtol=stol)
+    check_sigma2(s2, ref["sigma2"], FP32_TOL, "FP32 M=N=5000 final")
+    check_sigma2(hist["sigma2"], ref["sigma2_hist"], FP32_TOL, "FP32 M=N=5000 history")
 
 
 # (M = N = 1 collapses sigma2 to the rounding floor within a few iterations;
@@ -185,7 +195,7 @@ def test_register_ragged_sizes(M, N, prec):
     tol = FP64_TOL if prec == cpd.FP64 else FP32_TOL
     assert it == 12
     assert rel(T, ref["T"]) <= tol
-    assert s2 == pytest.approx(ref["sigma2"], rel=sigma2_tol(tol, ref["T"], ref["sigma2"]))
+    check_sigma2(s2, ref["sigma2"], tol, f"ragged M={M} N={N} prec={prec}")
 
 
 def test_single_point_closed_form_on_gpu():
@@ -210,7 +220,7 @@ def test_lowrank_basis(prec, M, K, iters):
     T, s2, it, _ = run_gpu(X, Y, prec, iters, K=K)
     tol = FP64_TOL if prec == cpd.FP64 else FP32_TOL
     assert rel(T, ref["T"]) <= tol
-    assert s2 == pytest.approx(ref["sigma2"], rel=sigma2_tol(tol, ref["T"], ref["sigma2"]))
+    check_sigma2(s2, ref["sigma2"], tol, f"low rank M={M} K={K} prec={prec}")
 
 
 def test_outlier_weight_zero_and_large():
@@ -455,6 +465,7 @@ def test_mixed_precision_register_against_oracle(K, iters):
     print(f"K={K}: relative error of T vs the FP64 oracle: mixed {err_m:.2e}, fp32 {err_32:.2e}")
     assert it == iters
     assert err_m <= MIXED_TOL
+    print(f"[sigma2] mixed: relative error {abs(s2m - ref['sigma2']) / ref['sigma2']:.3e}")
     assert s2m == pytest.approx(ref["sigma2"], rel=sigma2_tol(MIXED_TOL, ref["T"], ref["sigma2"]))
 
 
@@ -474,8 +485,9 @@ def test_mixed_precision_basis_is_the_fp16_rounding_of_the_fp32_basis():
 
 # ------------------------------- mixed precision: tensor-core E-step passes
 # While sigma2 >= 4.4e-4 R^2 (R: largest point norm) the CPD_MIXED E-step
-# takes its Gaussian exponents from BF16 tensor-core products of 3-way split
-# operands (FP32 accumulation).  The accumulated terms are as large as
+# takes its Gaussian exponents from FP16 tensor-core products (warp-level
+# mma.sync m16n8k16, each operand split into two FP16 parts, K = 16, FP32
+# accumulation).  The accumulated terms are as large as
 # q^2 R^2 <= ~2000 units of the base-2 exponent, so its rounding reaches
 # ~1e-3 at the floor and less above it; the errors against the FP64 oracle
 # are printed and bounded here by what that allows: Gaussians within ~1e-3

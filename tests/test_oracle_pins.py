@@ -282,3 +282,17 @@ def test_rmse_of_a_translation_is_its_length():
     v = np.array([0.3, -1.2, 0.4])
     assert oracle.rmse(X + v, X) == pytest.approx(1.3, rel=1e-13)
     assert oracle.rmse(X, X) == 0.0
+
+
+def test_lanczos_top_k_equals_dense_top_k():
+    """eig_top (Lanczos) gives the dense solver's leading eigenvalues, and
+    the low-rank registration (Eq. 20) on either basis gives the same T:
+    the eigenvectors agree up to sign (and rotation inside the noise-level
+    tail, which enters T with weight s_k ~ 0)."""
+    X, Y = _rng_points(12, 300, 320)
+    U0, l0 = oracle.eig(X, 2.0, 30)
+    U1, l1 = oracle.eig_top(X, 2.0, 30)
+    np.testing.assert_allclose(l1, l0, rtol=0, atol=1e-11 * l0[0])
+    a = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=8, eigpairs=(U0, l0))
+    b = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=8, eigpairs=(U1, l1))
+    assert np.linalg.norm(a["T"] - b["T"]) <= 1e-10 * np.linalg.norm(a["T"])

@@ -1,10 +1,11 @@
 """cpd_estep_noalloc against cpd_estep (GPU).
 
 cpd_estep_noalloc is for callers that cannot allocate device memory when they
-need an E-step (for instance while a CUDA graph is being captured, or under a
-fixed, pre-reserved memory budget): it takes its scratch from a static device
-array instead of cudaMalloc.  It must give what cpd_estep gives, call after
-call, even though every call reuses the same array.  This file is collected
+need an E-step (loops that must not stall on cudaMalloc/cudaFree, programs
+that reserve all device memory up front under a fixed budget): it takes its
+scratch from a static device array instead of cudaMalloc.  It must give what
+cpd_estep gives, call after call, even though every call reuses the same
+array.  This file is collected
 last so a failure here does not stop the rest of the suite.
 """
 import math
@@ -74,3 +75,32 @@ def test_rejects_what_it_cannot_hold():
     st = cpd.load().cpd_estep_noalloc(Th.ctypes.data, 64, Y.data_ptr(), 64, 1e-3, 0.1, out.data_ptr(), None, None,
                                       None, None)
     assert st == cpd.EINVAL
+
+
+@pytest.mark.parametrize("M,N", [(32768, 32768), (2048, 32768)])
+def test_largest_sizes_fit_and_match_cpd_estep(M, N):
+    """The declared limit M, N <= 32768 holds: the widest partial-sum layouts
+    fit the static array and give what cpd_estep gives."""
+    T, Y = _case(M, N, 34)
+    sigma2 = 2e-3
+    ref = cpd.estep(T, Y, sigma2, 0.1, cpd.FP32)
+    got = cpd.estep_noalloc(T, Y, sigma2, 0.1)
+    torch.cuda.synchronize()
+    _compare(ref, got, sigma2)
+
+
+def test_two_streams_one_after_the_other():
+    """Each call synchronises its own stream before it returns, so calls on two
+    streams made one after the other (not overlapping) both stay correct even
+    though they share the array."""
+    cases = [(1500, 1700, 1e-3, 0.1, 35), (900, 1300, 3e-4, 0.3, 36)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    refs, outs = [], []
+    for (M, N, sigma2, w, seed), st in zip(cases, streams):
+        T, Y = _case(M, N, seed)
+        refs.append(cpd.estep(T, Y, sigma2, w, cpd.FP32))
+        with torch.cuda.stream(st):
+            outs.append(cpd.estep_noalloc(T, Y, sigma2, w, stream=st))
+    torch.cuda.synchronize()
+    for ref, got, (M, N, sigma2, w, seed) in zip(refs, outs, cases):
+        _compare(ref, got, sigma2)
