@@ -124,8 +124,10 @@ typedef enum {
     CPD_FLAG_PRUNE_NOSKIP = 4,   /* (implies PRUNE) pruned layout, every tile pair
                                     evaluated: the same sums as skipping, bit for bit
                                     (verification)                                        */
-    CPD_FLAG_SPECTRAL_TRIM = 8   /* FP32 / mixed: M-step over the leading directions only
+    CPD_FLAG_SPECTRAL_TRIM = 8,  /* FP32 / mixed: M-step over the leading directions only
                                     while the dropped ones are below FP32 rounding        */
+    CPD_FLAG_FULL_EIG = 16       /* top-K basis (0 < K < M) from the full eigensolver
+                                    instead of subspace iteration (verification)          */
 } cpd_flags;
 
 /*
@@ -168,10 +170,17 @@ void cpd_params_default(cpd_params *p);
  *   stream cudaStream_t all work of this context is enqueued on.
  *   out    receives the new context (owned by the caller; free with
  *          cpd_destroy).
- * Builds Phi in FP64 on the device, eigendecomposes it in FP64 (cuSOLVER,
- * the one library call of the path, setup only), clamps the eigenvalues at 0,
- * keeps the K largest (or all) eigenpairs in descending order, stores the
- * basis in the working precision and frees Phi.  Synchronises `stream`.
+ * Builds Phi in FP64 on the device and eigendecomposes it in FP64, clamps
+ * the eigenvalues at 0, keeps the K largest (or all) eigenpairs in
+ * descending order, stores the basis in the working precision and frees Phi.
+ * The full basis comes from the dense symmetric eigensolver (cuSOLVER).  A
+ * top-K basis with K + max(16, K/4) <= M/2 comes from subspace iteration
+ * with Rayleigh-Ritz steps on a random start block (FP64 cuBLAS products,
+ * cuSOLVER QR and a small (K + p) x (K + p) eigenproblem), stopped when every
+ * kept pair has |Phi u - theta u| <= 1e-13 theta_max -- the dense solver's
+ * rounding level -- at O(M^2 K) instead of O(M^3) work; if that does not
+ * converge in 100 steps (or with CPD_FLAG_FULL_EIG) the dense solver is used.
+ * All of it is setup only.  Synchronises `stream`.
  * Errors: CPD_EINVAL (arguments), CPD_ENOMEM, CPD_ESOLVER, CPD_ECUDA; *out is
  * left untouched on error.
  */
@@ -247,6 +256,12 @@ cpd_status cpd_get_W(cpd_ctx *ctx, void *W_out);
  * descending, clamped at 0; may be NULL).  K is cpd_basis_rank(ctx). */
 cpd_status cpd_get_basis(cpd_ctx *ctx, void *U_out, double *lam_out);
 int64_t cpd_basis_rank(const cpd_ctx *ctx);
+
+/* How the context's basis was computed: *method = 0 (dense eigensolver) or 1
+ * (top-K subspace iteration); *steps = its Rayleigh-Ritz steps (0 for the
+ * dense solver unless subspace iteration ran first and did not converge).
+ * Either pointer may be NULL.  CPD_EINVAL for a NULL context. */
+cpd_status cpd_eig_info(const cpd_ctx *ctx, int32_t *method, int32_t *steps);
 
 /*
  * One M-step on the context's basis (Eq. 17 / 20), without touching the

@@ -2,7 +2,7 @@
 
 Each .cu file under csrc/ is compiled in parallel for sm_103a only, then
 linked into paper_2006_06281_gb300/libfcpd.so against the shared CUDA runtime
-and cuSOLVER (used once, for the setup eigendecomposition).  A rebuild happens
+and cuSOLVER / cuBLAS (used once, for the setup eigendecomposition).  A rebuild happens
 only when a source or header is newer than the library.
 """
 from __future__ import annotations
@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     libdir = os.path.join(cuda, "lib64")
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-L", libdir, "-lcusolver", "-Xlinker", "-rpath=" + libdir]
+        "-L", libdir, "-lcusolver", "-lcublas", "-Xlinker", "-rpath=" + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

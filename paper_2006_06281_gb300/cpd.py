@@ -25,12 +25,12 @@ FP64, FP32, MIXED = 0, 1, 2    # MIXED: FP32 points and E-step, FP16 eigenbasis
 STATUS = {0: "CPD_OK", 1: "CPD_EINVAL", 2: "CPD_ENOMEM", 3: "CPD_ECUDA", 4: "CPD_ESOLVER",
           5: "CPD_ENUMERIC", 6: "CPD_ETIMEOUT", 7: "CPD_ESTATE"}
 OK, EINVAL, ENOMEM, ECUDA, ESOLVER, ENUMERIC, ETIMEOUT, ESTATE = range(8)
-FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP, FLAG_SPECTRAL_TRIM = 1, 2, 4, 8
+FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP, FLAG_SPECTRAL_TRIM, FLAG_FULL_EIG = 1, 2, 4, 8, 16
 
 # Every symbol include/fcpd.h declares (checked by the tests).
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
-           "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_mstep",
+           "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_eig_info", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_iterate_shared", "cpd_destroy",
            "cpd_coefficients", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
            "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
@@ -82,6 +82,7 @@ def load():
                 "cpd_get_W": ([vp, vp], C.c_int),
                 "cpd_get_basis": ([vp, vp, vp], C.c_int),
                 "cpd_basis_rank": ([vp], i64),
+                "cpd_eig_info": ([vp, ip, ip], C.c_int),
                 "cpd_mstep": ([vp, vp, d, vp, vp], C.c_int),
                 "cpd_estep": ([vp, i64, vp, i64, i32, d, d, vp, vp, vp, dp, vp], C.c_int),
                 "cpd_estep_noalloc": ([vp, i64, vp, i64, d, d, vp, vp, vp, dp, vp], C.c_int),
@@ -272,6 +273,13 @@ class Context:
         W, pw = _out_like(self.M, 3, self.precision, self.cuda, self.device)
         _check(load().cpd_get_W(self._h, pw))
         return W
+
+    def eig_info(self):
+        """(method, steps): 0 = dense eigensolver, 1 = top-K subspace
+        iteration, and the subspace iteration's Rayleigh-Ritz steps."""
+        m, n = C.c_int32(), C.c_int32()
+        _check(load().cpd_eig_info(self._h, C.byref(m), C.byref(n)))
+        return m.value, n.value
 
     def trim_info(self):
         """(k_cap, trimmed_iters): directions kept by the spectral trim (0: none)

@@ -397,9 +397,24 @@ void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const type
 
 // Setup helpers.
 void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double* Phi, cudaStream_t s);
+// V: M x nv column-major eigenvectors with eigenvalues w[nv] ascending (the
+// eigensolvers' order); the K largest pairs are kept, descending.
 template <typename F>
-void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
+void launch_extract_basis(const double* V, int64_t M, int64_t nv, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
                           const double* w, double* lam, cudaStream_t s);
+
+// Top-K eigenpairs of the M x M FP64 Gram matrix Phi (eig.cu: subspace
+// iteration with Rayleigh-Ritz steps, FP64, cuBLAS / cuSOLVER).  Used when
+// topk_eig_applies(M, K).  On CPD_OK: *V_out (M x *nv_out column-major,
+// device, cudaMalloc'd, freed by the caller with cudaFree) and *w_out (*nv_out
+// device doubles, ascending) hold Ritz pairs whose largest K have residuals
+// |Phi u - theta u| <= tol * theta_max; *steps_out = Rayleigh-Ritz steps.
+// Returns a cpd_status, or -1 if max_steps were not enough (the caller then
+// uses the full eigensolver).  Synchronises `s`.
+bool topk_eig_applies(int64_t M, int64_t K);
+int topk_oversampling(int64_t K);
+int topk_eigh(const double* Phi, int64_t M, int64_t K, double tol, int max_steps, cudaStream_t s, double** V_out,
+              double** w_out, int64_t* nv_out, int* steps_out, std::string* err);
 // FP16 basis (mixed-precision mode) -> M x K FP32, row-major, unpadded.
 void launch_basis_to_f32(const __half* U, int64_t M, int64_t K, int64_t ldU, float* out, cudaStream_t s);
 template <typename F>

@@ -110,7 +110,8 @@ cpd_status validate_params(const cpd_params* p) {
   if (std::isnan(p->sigma2_init) || std::isinf(p->sigma2_init)) return fail(CPD_EINVAL, "sigma2_init not finite");
   if (p->K < 0) return fail(CPD_EINVAL, "K must be >= 0");
   if (p->max_iter < 0) return fail(CPD_EINVAL, "max_iter must be >= 0");
-  if (p->flags & ~(CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP | CPD_FLAG_SPECTRAL_TRIM))
+  if (p->flags & ~(CPD_FLAG_PRUNE | CPD_FLAG_PRUNE_ALWAYS | CPD_FLAG_PRUNE_NOSKIP | CPD_FLAG_SPECTRAL_TRIM |
+                   CPD_FLAG_FULL_EIG))
     return fail(CPD_EINVAL, "unknown bits in flags");
   if ((p->flags & CPD_FLAG_SPECTRAL_TRIM) && p->precision == CPD_FP64)
     return fail(CPD_EINVAL, "the spectral trim bounds its error at FP32 rounding: not for CPD_FP64");
@@ -118,7 +119,12 @@ cpd_status validate_params(const cpd_params* p) {
   return CPD_OK;
 }
 
-constexpr int64_t kMaxM = 46340;          // M*M doubles indexable by the 32-bit eigensolver API
+constexpr int64_t kMaxM = 46340;
+// Subspace iteration for the top-K basis: residual |Phi u - theta u| of every
+// kept Ritz pair below kTopkTol x the largest eigenvalue (rounding level of
+// an FP64 product with Phi), at most kTopkMaxSteps Rayleigh-Ritz steps.
+constexpr double kTopkTol = 1e-13;
+constexpr int kTopkMaxSteps = 100;          // M*M doubles indexable by the 32-bit eigensolver API
 constexpr int64_t kMaxN = 1LL << 30;
 
 }  // namespace
@@ -152,6 +158,8 @@ struct cpd_ctx {
   MstepPlan mp_trim{};           // spectral trim: the M-step over the leading k_cap directions
   int64_t k_cap = 0;             // > 0: the trimmed M-step is captured beside the full one
   double trim_lam = -1.0;        // largest eigenvalue the trimmed M-step drops
+  int eig_method = 0;            // 0: full eigensolver, 1: top-K subspace iteration
+  int eig_steps = 0;             // Rayleigh-Ritz steps of the subspace iteration
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
   cudaGraphExec_t prof_graph = nullptr;             // n iterations with timing events
   int prof_iters = 0;
@@ -586,6 +594,13 @@ void cpd_params_default(cpd_params* p) {
 
 int64_t cpd_basis_rank(const cpd_ctx* ctx) { return ctx ? ctx->K : 0; }
 
+cpd_status cpd_eig_info(const cpd_ctx* c, int32_t* method, int32_t* steps) {
+  if (!c) return fail(CPD_EINVAL, "ctx is NULL");
+  if (method) *method = c->eig_method;
+  if (steps) *steps = c->eig_steps;
+  return CPD_OK;
+}
+
 cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream, cpd_ctx** out) {
   g_err.clear();
   STATUS_TRY(validate_params(p));
@@ -655,42 +670,80 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   Buf phi, wv, info, work;
   auto free_setup = [&]() { phi.release(); wv.release(); info.release(); work.release(); };
   if ((s = phi.ensure((size_t)M * M * sizeof(double))) != CPD_OK) return bail(s);
-  if ((s = wv.ensure((size_t)M * sizeof(double))) != CPD_OK) { free_setup(); return bail(s); }
-  if ((s = info.ensure(sizeof(int))) != CPD_OK) { free_setup(); return bail(s); }
   launch_gram_f64(c->X4.p, c->fp64, M, p->beta, phi.as<double>(), c->stream);
-  cusolverDnHandle_t h = nullptr;
-  if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) { free_setup(); return bail(fail(CPD_ESOLVER, "cusolverDnCreate failed")); }
-  cusolverDnSetStream(h, c->stream);
-  int lwork = 0;
-  cusolverStatus_t cs = cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M,
-                                                    phi.as<double>(), (int)M, wv.as<double>(), &lwork);
-  if (cs == CUSOLVER_STATUS_SUCCESS) {
-    if ((s = work.ensure((size_t)std::max(lwork, 1) * sizeof(double))) != CPD_OK) {
-      cusolverDnDestroy(h); free_setup(); return bail(s);
+  const double* V = phi.as<double>();     // eigenvectors (columns, ascending) ...
+  const double* wasc = nullptr;           // ... and their eigenvalues
+  int64_t nv = M;
+  double* topV = nullptr;
+  double* topw = nullptr;
+  auto free_top = [&]() {
+    if (topV) cudaFree(topV);
+    if (topw) cudaFree(topw);
+    topV = topw = nullptr;
+  };
+  // Eq. 19 with K << M: the K largest pairs by subspace iteration (eig.cu);
+  // otherwise (or if it does not converge) the full FP64 eigensolver.
+  c->eig_method = 0;
+  c->eig_steps = 0;
+  if (!(p->flags & CPD_FLAG_FULL_EIG) && topk_eig_applies(M, c->K) && !fault_enabled("solver")) {
+    std::string msg;
+    int steps = 0;
+    const int r = topk_eigh(phi.as<double>(), M, c->K, kTopkTol, kTopkMaxSteps, c->stream, &topV, &topw, &nv,
+                            &steps, &msg);
+    if (r == CPD_OK) {
+      V = topV;
+      wasc = topw;
+      c->eig_method = 1;
+      c->eig_steps = steps;
+    } else if (r != -1) {
+      free_top();
+      free_setup();
+      return bail(fail((cpd_status)r, msg));
+    } else {
+      free_top();
+      nv = M;
+      c->eig_steps = steps;
     }
-    cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M, phi.as<double>(), (int)M,
-                          wv.as<double>(), work.as<double>(), lwork, info.as<int>());
   }
-  int hinfo = 0;
-  if (cs == CUSOLVER_STATUS_SUCCESS) {
-    cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    cudaStreamSynchronize(c->stream);
+  if (c->eig_method == 0) {
+    if ((s = wv.ensure((size_t)M * sizeof(double))) != CPD_OK) { free_setup(); return bail(s); }
+    if ((s = info.ensure(sizeof(int))) != CPD_OK) { free_setup(); return bail(s); }
+    cusolverDnHandle_t h = nullptr;
+    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) { free_setup(); return bail(fail(CPD_ESOLVER, "cusolverDnCreate failed")); }
+    cusolverDnSetStream(h, c->stream);
+    int lwork = 0;
+    cusolverStatus_t cs = cusolverDnDsyevd_bufferSize(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M,
+                                                      phi.as<double>(), (int)M, wv.as<double>(), &lwork);
+    if (cs == CUSOLVER_STATUS_SUCCESS) {
+      if ((s = work.ensure((size_t)std::max(lwork, 1) * sizeof(double))) != CPD_OK) {
+        cusolverDnDestroy(h); free_setup(); return bail(s);
+      }
+      cs = cusolverDnDsyevd(h, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, (int)M, phi.as<double>(), (int)M,
+                            wv.as<double>(), work.as<double>(), lwork, info.as<int>());
+    }
+    int hinfo = 0;
+    if (cs == CUSOLVER_STATUS_SUCCESS) {
+      cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+    }
+    cusolverDnDestroy(h);
+    work.release();
+    if (cs != CUSOLVER_STATUS_SUCCESS || hinfo != 0 || fault_enabled("solver")) {
+      free_setup();
+      return bail(fail(CPD_ESOLVER, "eigensolver failed (status " + std::to_string((int)cs) + ", info " +
+                                        std::to_string(hinfo) + (fault_enabled("solver") ? ", injected" : "") + ")"));
+    }
+    wasc = wv.as<double>();
   }
-  cusolverDnDestroy(h);
-  work.release();
-  if (cs != CUSOLVER_STATUS_SUCCESS || hinfo != 0 || fault_enabled("solver")) {
-    free_setup();
-    return bail(fail(CPD_ESOLVER, "eigensolver failed (status " + std::to_string((int)cs) + ", info " +
-                                      std::to_string(hinfo) + (fault_enabled("solver") ? ", injected" : "") + ")"));
-  }
-  if (c->fp64) launch_extract_basis<double>(phi.as<double>(), M, c->K, c->U.as<double>(), c->ldU, c->Ut.as<double>(),
-                                            c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
+  if (c->fp64) launch_extract_basis<double>(V, M, nv, c->K, c->U.as<double>(), c->ldU, c->Ut.as<double>(),
+                                            c->mp.ldM, wasc, c->lam.as<double>(), c->stream);
   else if (c->half_basis)
-    launch_extract_basis<__half>(phi.as<double>(), M, c->K, c->U.as<__half>(), c->ldU, c->Ut.as<__half>(),
-                                 c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
-  else launch_extract_basis<float>(phi.as<double>(), M, c->K, c->U.as<float>(), c->ldU, c->Ut.as<float>(),
-                                   c->mp.ldM, wv.as<double>(), c->lam.as<double>(), c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
+    launch_extract_basis<__half>(V, M, nv, c->K, c->U.as<__half>(), c->ldU, c->Ut.as<__half>(),
+                                 c->mp.ldM, wasc, c->lam.as<double>(), c->stream);
+  else launch_extract_basis<float>(V, M, nv, c->K, c->U.as<float>(), c->ldU, c->Ut.as<float>(),
+                                   c->mp.ldM, wasc, c->lam.as<double>(), c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { free_top(); free_setup(); return bail(fail(CPD_ECUDA, "setup kernels failed")); }
+  free_top();
   free_setup();
   if ((p->flags & CPD_FLAG_SPECTRAL_TRIM) && (s = plan_trim(c)) != CPD_OK) return bail(s);
 

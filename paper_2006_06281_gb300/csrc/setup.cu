@@ -47,22 +47,23 @@ __global__ void gram_f64(const V4* __restrict__ X4, int M, double inv2b2, double
   Phi[(size_t)i * M + j] = exp(-(dx * dx + dy * dy + dz * dz) * inv2b2);
 }
 
-// The eigensolver returns eigenvalues ascending and eigenvectors as columns of
-// a column-major M x M matrix V.  The basis kept here is descending (Eq. 19
-// keeps the K largest), stored row-major: U[m * ldU + k] = V[m, M-1-k], with
-// zero padding for K <= k < ldU.  Tiled transpose through shared memory.
+// The eigensolvers return eigenvalues ascending and eigenvectors as columns of
+// a column-major M x nv matrix V (nv = M for the full solver).  The basis kept
+// here is descending (Eq. 19 keeps the K largest), stored row-major:
+// U[m * ldU + k] = V[m, nv-1-k], with zero padding for K <= k < ldU.  Tiled
+// transpose through shared memory.
 template <typename F> __device__ __forceinline__ F to_basis(double v) { return (F)v; }
 template <> __device__ __forceinline__ __half to_basis<__half>(double v) { return __double2half(v); }
 
 template <typename F>
-__global__ void extract_basis(const double* __restrict__ V, int M, int K, F* __restrict__ U, int64_t ldU) {
+__global__ void extract_basis(const double* __restrict__ V, int M, int nv, int K, F* __restrict__ U, int64_t ldU) {
   __shared__ double tile[32][33];
   const int k0 = blockIdx.x * 32, m0 = blockIdx.y * 32;
   // read: for output columns k0..k0+31, source column M-1-k is contiguous in m
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int k = k0 + r, m = m0 + threadIdx.x;
     double v = 0.0;
-    if (k < K && m < M) v = V[(size_t)(M - 1 - k) * M + m];
+    if (k < K && m < M) v = V[(size_t)(nv - 1 - k) * M + m];
     tile[r][threadIdx.x] = v;
   }
   __syncthreads();
@@ -72,19 +73,19 @@ __global__ void extract_basis(const double* __restrict__ V, int M, int K, F* __r
   }
 }
 
-// U^T row k is eigenvector M-1-k: a contiguous column of V, cast to F, with
+// U^T row k is eigenvector nv-1-k: a contiguous column of V, cast to F, with
 // zero padding for M <= m < ldM.
 template <typename F>
-__global__ void extract_basis_t(const double* __restrict__ V, int M, int K, F* __restrict__ Ut, int64_t ldM) {
+__global__ void extract_basis_t(const double* __restrict__ V, int M, int nv, int K, F* __restrict__ Ut, int64_t ldM) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)K * ldM) return;
   const int k = (int)(i / ldM), m = (int)(i % ldM);
-  Ut[i] = to_basis<F>(m < M ? V[(size_t)(M - 1 - k) * M + m] : 0.0);
+  Ut[i] = to_basis<F>(m < M ? V[(size_t)(nv - 1 - k) * M + m] : 0.0);
 }
 
-__global__ void extract_lambda(const double* __restrict__ w, int M, int K, double* __restrict__ lam) {
+__global__ void extract_lambda(const double* __restrict__ w, int nv, int K, double* __restrict__ lam) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < K) lam[k] = fmax(w[M - 1 - k], 0.0);   // clamp: Phi is PSD, LAPACK-level noise can be < 0
+  if (k < K) lam[k] = fmax(w[nv - 1 - k], 0.0);   // clamp: Phi is PSD, rounding-level noise can be < 0
 }
 
 // sigma2_0 = sum_m sum_n |y_n - x_m|^2 / (D M N), evaluated in closed form
@@ -198,12 +199,12 @@ void launch_gram_f64(const void* X4, bool x_fp64, int64_t M, double beta, double
 }
 
 template <typename F>
-void launch_extract_basis(const double* V, int64_t M, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
+void launch_extract_basis(const double* V, int64_t M, int64_t nv, int64_t K, F* U, int64_t ldU, F* Ut, int64_t ldM,
                           const double* w, double* lam, cudaStream_t s) {
   dim3 grid((unsigned)cdiv(ldU, 32), (unsigned)cdiv(M, 32));
-  extract_basis<F><<<grid, dim3(32, 8), 0, s>>>(V, (int)M, (int)K, U, ldU);
-  extract_basis_t<F><<<(unsigned)cdiv(K * ldM, kThreads), kThreads, 0, s>>>(V, (int)M, (int)K, Ut, ldM);
-  extract_lambda<<<(unsigned)cdiv(K, kThreads), kThreads, 0, s>>>(w, (int)M, (int)K, lam);
+  extract_basis<F><<<grid, dim3(32, 8), 0, s>>>(V, (int)M, (int)nv, (int)K, U, ldU);
+  extract_basis_t<F><<<(unsigned)cdiv(K * ldM, kThreads), kThreads, 0, s>>>(V, (int)M, (int)nv, (int)K, Ut, ldM);
+  extract_lambda<<<(unsigned)cdiv(K, kThreads), kThreads, 0, s>>>(w, (int)nv, (int)K, lam);
 }
 
 template <typename F>
@@ -246,11 +247,11 @@ template void launch_pack<float>(const float*, int64_t, float4*, bool, cudaStrea
 template void launch_pack<double>(const double*, int64_t, dvec4*, bool, cudaStream_t);
 template void launch_unpack<float>(const float4*, int64_t, float*, cudaStream_t);
 template void launch_unpack<double>(const dvec4*, int64_t, double*, cudaStream_t);
-template void launch_extract_basis<float>(const double*, int64_t, int64_t, float*, int64_t, float*, int64_t,
+template void launch_extract_basis<float>(const double*, int64_t, int64_t, int64_t, float*, int64_t, float*, int64_t,
                                           const double*, double*, cudaStream_t);
-template void launch_extract_basis<double>(const double*, int64_t, int64_t, double*, int64_t, double*, int64_t,
+template void launch_extract_basis<double>(const double*, int64_t, int64_t, int64_t, double*, int64_t, double*, int64_t,
                                            const double*, double*, cudaStream_t);
-template void launch_extract_basis<__half>(const double*, int64_t, int64_t, __half*, int64_t, __half*, int64_t,
+template void launch_extract_basis<__half>(const double*, int64_t, int64_t, int64_t, __half*, int64_t, __half*, int64_t,
                                            const double*, double*, cudaStream_t);
 template void launch_sigma2_init<float>(const float4*, int64_t, const float4*, int64_t, double*, DevState*,
                                         cudaStream_t);

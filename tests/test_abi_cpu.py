@@ -57,7 +57,7 @@ def _setup(lib, X, p):
 
 
 @pytest.mark.parametrize("field,value", [("D", 2), ("precision", 7), ("w", 1.0), ("w", -0.1),
-                                         ("beta", 0.0), ("lam", -1.0), ("K", -1), ("flags", 16), ("flags", 17),
+                                         ("beta", 0.0), ("lam", -1.0), ("K", -1), ("flags", 32), ("flags", 33),
                                          ("tol", -1.0), ("max_iter", -1),
                                          ("sigma2_init", float("nan"))])
 def test_setup_rejects_bad_params_without_device_work(lib, field, value):
