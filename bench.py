@@ -61,9 +61,10 @@ def parse():
                          "(e.g. fp32_warmstart_m2048_k64)")
     ap.add_argument("--no-trim", action="store_true",
                     help="skip timing the same registration with CPD_FLAG_SPECTRAL_TRIM")
-    ap.add_argument("--shared", type=int, default=0,
-                    help="also register this many scenes (deformations of the workload's model) against one model "
-                         "with cpd_iterate_shared, against the same scenes one at a time")
+    ap.add_argument("--shared", type=int, default=32,
+                    help="register up to this many scenes (deformations of the workload's model) against one "
+                         "CPD_MIXED model with cpd_iterate_shared (tensor-core products), in groups of 8, 16 and "
+                         "32, against the same scenes one at a time (0 skips it)")
     ap.add_argument("--prune", action="store_true",
                     help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--no-outlier-config", action="store_true",
@@ -361,6 +362,50 @@ def run_batch(args, peaks, torch):
         out["per_pair_sequential"] = dict(ms=ts * 1e3, pair_iters_per_s=n * I / ts, setup_s=seq_setup)
         out["speedup_vs_per_pair"] = ts / t
     return out
+
+
+def run_shared(ctx, ps, cfg, args, torch, a, b, iters=50):
+    """Several scenes against one CPD_MIXED model (cpd_iterate_shared): the
+    M-step products of each group run as tcgen05 passes over the FP16 basis.
+    For S in 8, 16, 32 (up to --shared): scene-iterations/s of the group
+    against the same scenes registered one at a time on the same context,
+    and the largest relative difference of their T."""
+    from paper_2006_06281_gb300 import datagen
+    Xh = ps.X.astype(np.float32)
+    Smax = args.shared
+    Ys = [torch.tensor(datagen.gen_from_template(Xh, 5000 + i, amp=cfg["amp"], noise=cfg["noise"]).Y,
+                       dtype=torch.float32, device="cuda") for i in range(Smax)]
+    seq_T = []
+    for Yi in Ys:                           # graph capture of the single-scene path, untimed
+        ctx.reset()
+        ctx.iterate(Yi, iters, want_T=False)
+    torch.cuda.synchronize()
+    a.record()
+    for Yi in Ys:
+        ctx.reset()
+        seq_T.append(ctx.iterate(Yi, iters)[0])
+    b.record()
+    torch.cuda.synchronize()
+    seq_rate = Smax * iters / (a.elapsed_time(b) / 1e3)
+    groups = []
+    for S in [s for s in (8, 16, 32) if s <= Smax]:
+        ctx.iterate_shared(Ys[:S], 2)       # warm-up
+        torch.cuda.synchronize()
+        a.record()
+        res = ctx.iterate_shared(Ys[:S], iters)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        dmax = max((r[0].double() - t.double()).norm().item() / t.double().norm().item()
+                   for r, t in zip(res, seq_T[:S]))
+        groups.append(dict(scenes=S, scene_iters_per_s=S * iters / (ms / 1e3), ms=ms,
+                           speedup_vs_one_at_a_time=S * iters / (ms / 1e3) / seq_rate,
+                           max_rel_diff_T_vs_one_at_a_time=dmax))
+    return dict(precision="CPD_MIXED (FP16 eigenbasis)", M=ps.X.shape[0], iters=iters,
+                one_at_a_time_scene_iters_per_s=seq_rate, groups=groups,
+                note="products of a group: tcgen05.mma (kind::f16, FP32 accumulation in TMEM) over the FP16 basis "
+                     "staged by TMA, scenes split into FP16 hi/lo parts; E-steps per scene; one graph per group "
+                     "iteration")
 
 
 def run_outlier_config(args, peaks, torch):
@@ -679,6 +724,7 @@ def main():
     # mixed precision (CPD_MIXED: FP16 eigenbasis, FP32 E-step and sums),
     # same pair and registration; its T is compared with the FP32 path's
     mixed = None
+    shared_mixed = None
     if not args.no_mixed and cfg["K"] == 0:
         t0 = time.perf_counter()
         cm = cpd.Context(X, precision=cpd.MIXED, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0)
@@ -708,6 +754,9 @@ def main():
         b.record()
         torch.cuda.synchronize()
         ttt_mixed = dict(iters=int(it_tol_m), ms=a.elapsed_time(b))
+        cm.set_ground_truth(None)
+        if world == 1 and args.shared > 0:
+            shared_mixed = run_shared(cm, ps, cfg, args, torch, a, b)
         cm.close()
         mroof = roofline_entries(ph, M, N, K, peaks, es=2)
         d32 = (T32.double() - Tm.double()).norm().item() / T32.double().norm().item()
@@ -799,40 +848,9 @@ def main():
                     note="the M-step keeps the directions with s_k = l_k/(l_k + lambda sigma2) >= 2^-24; "
                          "the dropped part of T is below one FP32 rounding (|dT| <= 2^-24 |R|)")
 
-    # several scenes against one model (cpd_iterate_shared): scene-iterations/s
-    # against the same scenes registered one at a time, and the largest
-    # difference of their T
     shared = None
-    if world == 1 and args.shared > 0 and cfg["K"] == 0:
-        S = args.shared
-        Xh = ps.X.astype(np.float32)
-        Ys = [torch.tensor(datagen.gen_from_template(Xh, 5000 + i, amp=cfg["amp"], noise=cfg["noise"]).Y,
-                           dtype=torch.float32, device="cuda") for i in range(S)]
-        csh = cpd.Context(X, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0)
-        csh.iterate_shared(Ys, 3)
-        for Yi in Ys:
-            csh.reset()
-            csh.iterate(Yi, I)
-        torch.cuda.synchronize()
-        a.record()
-        res = csh.iterate_shared(Ys, I)
-        b.record()
-        torch.cuda.synchronize()
-        sh_ms = a.elapsed_time(b)
-        a.record()
-        seq = []
-        for Yi in Ys:
-            csh.reset()
-            seq.append(csh.iterate(Yi, I)[0])
-        b.record()
-        torch.cuda.synchronize()
-        seq_ms = a.elapsed_time(b)
-        dmax = max((r[0].double() - t.double()).norm().item() / t.double().norm().item() for r, t in zip(res, seq))
-        csh.close()
-        shared = dict(scenes=S, iters=I, scene_iters_per_s=S * I / (sh_ms / 1e3),
-                      one_at_a_time_scene_iters_per_s=S * I / (seq_ms / 1e3), speedup=seq_ms / sh_ms,
-                      max_rel_diff_T_vs_one_at_a_time=dmax,
-                      note="the M-step products of up to 8 scenes share one pass over U and U^T; E-steps per scene")
+    if shared_mixed is not None:
+        shared = dict(mixed_tensor_core=shared_mixed)
 
     outlier = None
     if world == 1 and not args.no_outlier_config:

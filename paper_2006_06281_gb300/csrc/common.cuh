@@ -390,6 +390,43 @@ void launch_mstep_multi(const MultiPlan& p, const float* U, int64_t ldU, const f
                         const float4* Yt4, float4* T4, float4* B4, float4* C4, DevState* const* st, float* part,
                         double* sums, int* status, cudaStream_t s);
 
+// Tensor-core products for S scenes against one FP16 basis (umma.cu):
+// partials part[s][chunk][d][row] of D = A V^T, A the basis (P rows x Q,
+// row stride ldA, FP16), V the scenes' right-hand sides split into FP16
+// hi / lo parts (npad x ldq, built by launch_pack_rhs from S float4 arrays
+// of Q entries, scene stride ld_src).  The partial layout is that of the
+// single-scene products, so the per-scene reductions are shared.
+struct UmmaPlan {
+  int64_t P, Q;          // rows of D, contraction length
+  int S, npad;           // scenes, MMA columns (2 x 3S rounded up to 16)
+  int tiles, chunks;     // 128-row tiles x contraction chunks (the grid)
+  int kspc;              // 64-element stages per chunk
+  int64_t ldq;           // row stride of V
+};
+int umma_npad(int S);
+// The tensor-core products can run for S scenes (npad <= 256, the driver's
+// tensor-map encoder found).
+bool umma_supported(int S);
+UmmaPlan plan_umma(int64_t P, int64_t Q, int S, int sms);
+int64_t umma_rhs_elems(const UmmaPlan& p);
+void launch_pack_rhs(const UmmaPlan& p, const float4* src, int64_t ld_src, __half* V, cudaStream_t s);
+// fault_wait: host fault injection (every full barrier expects 16 bytes more
+// than its copies: each wait runs out after 50 ms and *status becomes
+// CPD_ETIMEOUT).
+cudaError_t launch_umma_products(const UmmaPlan& p, const __half* A, int64_t ldA, const __half* V, float* part,
+                                 int64_t ldP, int* status, bool fault_wait, cudaStream_t s);
+constexpr int kMaxScenesPerPassMma = 32;
+// doubles of block sums the per-scene Eq. 18 epilogue needs for M points
+int64_t multi_sums_elems(int64_t M);
+// The shared-model M-step with tensor-core products (multi.cu): Vp (pp.npad
+// x pp.ldq) and Ve (pe.npad x pe.ldq) zeroed before the first use; part
+// holds max(S chunks 3 ldU (projection), S chunks 3 ldM (expansion)) floats.
+cudaError_t launch_mstep_multi_mma(const UmmaPlan& pp, const UmmaPlan& pe, const __half* U, int64_t ldU,
+                                   const __half* Ut, int64_t ldM, const double* lam, int64_t M, int64_t K,
+                                   const float4* X4, const float4* R4, const float4* Yt4, float4* T4, float4* B4,
+                                   float4* C4, DevState* const* st, __half* Vp, __half* Ve, float* part,
+                                   double* sums, int* status, bool fault_wait, cudaStream_t s);
+
 // W = U C (C from the last M-step), written as 4-vectors.
 template <typename F, typename S = F>
 void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,

@@ -336,15 +336,33 @@ struct ScratchSet {
   }
 };
 
+// One group of S scenes.  FP32 contexts: the products of the group by the
+// SIMT streaming kernel (multi.cu, S <= 8).  Mixed-precision contexts (FP16
+// basis): the products on the tensor cores (umma.cu, S <= 32) and the
+// mixed E-step (tensor-core distance passes while sigma2 is large).  One
+// iteration of the group is captured once into a CUDA graph and replayed.
 cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* N, int n_iter, void* const* T_out,
                         double* s2_out) {
   const int64_t M = c->M, K = c->K;
-  const MultiPlan mp = plan_multi(M, K, c->ldU, c->mp.ldM, S, c->sms);
+  const bool mixed = c->half_basis;
+  MultiPlan mp{};
+  UmmaPlan pp{}, pe{};
+  int64_t part_elems = 0, sums_elems = 0;
+  if (mixed) {
+    pp = plan_umma(K, M, S, c->sms);
+    pe = plan_umma(M, K, S, c->sms);
+    part_elems = std::max((int64_t)S * pp.chunks * 3 * c->ldU, (int64_t)S * pe.chunks * 3 * c->mp.ldM);
+    sums_elems = multi_sums_elems(M);
+  } else {
+    mp = plan_multi(M, K, c->ldU, c->mp.ldM, S, c->sms);
+    part_elems = mp.part_elems;
+    sums_elems = mp.sums_elems;
+  }
   std::vector<EstepPlan> ep((size_t)S);
   std::vector<int64_t> yoff((size_t)S);
-  int64_t pa = 0, pb = 0, sm = mp.sums_elems, fl = 0, nmax = 0, ytot = 0;
+  int64_t pa = 0, pb = 0, sm = sums_elems, fl = 0, nmax = 0, ytot = 0;
   for (int i = 0; i < S; ++i) {
-    ep[(size_t)i] = plan_estep(M, N[i], false, c->sms, false, false);
+    ep[(size_t)i] = plan_estep(M, N[i], false, c->sms, false, mixed);
     pa = std::max(pa, ep[(size_t)i].partA_elems);
     pb = std::max(pb, ep[(size_t)i].partB_elems);
     sm = std::max(sm, ep[(size_t)i].sums_elems);
@@ -353,14 +371,14 @@ cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* 
     yoff[(size_t)i] = ytot;
     ytot += N[i];
   }
-  enum { kY4, kYb, kPA, kPB, kPP, kSums, kFlags, kT4, kYt4, kR4, kB4, kC4, kSt, kStatus, kCount };
+  enum { kY4, kYb, kPA, kPB, kPP, kSums, kFlags, kT4, kYt4, kR4, kB4, kC4, kSt, kStatus, kVp, kVe, kCount };
   ScratchSet sc(kCount);
   Buf* b = sc.b.data();
   STATUS_TRY(b[kY4].ensure((size_t)ytot * sizeof(float4)));
   STATUS_TRY(b[kYb].ensure((size_t)nmax * sizeof(float4)));
   STATUS_TRY(b[kPA].ensure((size_t)pa * sizeof(float)));
   STATUS_TRY(b[kPB].ensure((size_t)pb * sizeof(float)));
-  STATUS_TRY(b[kPP].ensure((size_t)mp.part_elems * sizeof(float)));
+  STATUS_TRY(b[kPP].ensure((size_t)part_elems * sizeof(float)));
   STATUS_TRY(b[kSums].ensure((size_t)sm * sizeof(double)));
   STATUS_TRY(b[kFlags].ensure((size_t)fl * sizeof(int)));
   for (int k : {(int)kT4, (int)kYt4, (int)kR4}) STATUS_TRY(b[k].ensure((size_t)S * M * sizeof(float4)));
@@ -368,6 +386,12 @@ cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* 
   STATUS_TRY(b[kSt].ensure((size_t)S * sizeof(DevState)));
   STATUS_TRY(b[kStatus].ensure(sizeof(int)));
   cudaStream_t s = c->stream;
+  if (mixed) {
+    STATUS_TRY(b[kVp].ensure((size_t)umma_rhs_elems(pp) * sizeof(__half)));
+    STATUS_TRY(b[kVe].ensure((size_t)umma_rhs_elems(pe) * sizeof(__half)));
+    CUDA_TRY(cudaMemsetAsync(b[kVp].p, 0, (size_t)umma_rhs_elems(pp) * sizeof(__half), s));
+    CUDA_TRY(cudaMemsetAsync(b[kVe].p, 0, (size_t)umma_rhs_elems(pe) * sizeof(__half), s));
+  }
   CUDA_TRY(cudaMemsetAsync(b[kStatus].p, 0, sizeof(int), s));
   float4* Y4 = b[kY4].as<float4>();
   float4* T4 = b[kT4].as<float4>();
@@ -381,19 +405,49 @@ cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* 
     launch_state_params(st[(size_t)i], c->p.w, c->p.lambda, 0.0, 0.0, 0, nullptr, M, N[i], K, s);
     if (from_data) launch_sigma2_init<float>(c->X4.as<float4>(), M, Y4 + yoff[(size_t)i], N[i], nullptr,
                                              st[(size_t)i], s);
+    if (mixed) {
+      launch_state_prune(st[(size_t)i], 0.f, kMmaAllowed, s);
+      launch_mma_threshold(c->X4.as<float4>(), M, Y4 + yoff[(size_t)i], N[i], st[(size_t)i], s);
+    }
     launch_begin_iterations(st[(size_t)i], n_iter, s);
   }
-  for (int it = 0; it < n_iter; ++it) {
-    for (int i = 0; i < S; ++i)
-      launch_estep<float>(ep[(size_t)i], T4 + (size_t)i * M, c->X4.as<float4>(), M, Y4 + yoff[(size_t)i],
-                          b[kYb].as<float4>(), N[i], b[kPA].as<float>(), b[kPB].as<float>(), b[kSums].as<double>(),
-                          b[kFlags].as<int>(), b[kYt4].as<float4>() + (size_t)i * M,
-                          b[kR4].as<float4>() + (size_t)i * M, nullptr, nullptr, st[(size_t)i], true, s);
+  CUDA_TRY(cudaGetLastError());
+  const bool fault = fault_enabled("umma_wait");
+  // one iteration of the whole group, captured once
+  cudaError_t le = cudaSuccess;
+  CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed));
+  for (int i = 0; i < S; ++i)
+    launch_estep<float>(ep[(size_t)i], T4 + (size_t)i * M, c->X4.as<float4>(), M, Y4 + yoff[(size_t)i],
+                        b[kYb].as<float4>(), N[i], b[kPA].as<float>(), b[kPB].as<float>(), b[kSums].as<double>(),
+                        b[kFlags].as<int>(), b[kYt4].as<float4>() + (size_t)i * M,
+                        b[kR4].as<float4>() + (size_t)i * M, nullptr, nullptr, st[(size_t)i], true, c->cap);
+  if (mixed)
+    le = launch_mstep_multi_mma(pp, pe, c->U.as<__half>(), c->ldU, c->Ut.as<__half>(), c->mp.ldM, c->lam.as<double>(),
+                                M, K, c->X4.as<float4>(), b[kR4].as<float4>(), b[kYt4].as<float4>(), T4,
+                                b[kB4].as<float4>(), b[kC4].as<float4>(), st.data(), b[kVp].as<__half>(),
+                                b[kVe].as<__half>(), b[kPP].as<float>(), b[kSums].as<double>(), b[kStatus].as<int>(),
+                                fault, c->cap);
+  else
     launch_mstep_multi(mp, c->U.as<float>(), c->ldU, c->Ut.as<float>(), c->mp.ldM, c->lam.as<double>(), M, K,
                        c->X4.as<float4>(), b[kR4].as<float4>(), b[kYt4].as<float4>(), T4, b[kB4].as<float4>(),
                        b[kC4].as<float4>(), st.data(), b[kPP].as<float>(), b[kSums].as<double>(),
-                       b[kStatus].as<int>(), s);
+                       b[kStatus].as<int>(), c->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(CPD_ECUDA, std::string("capture of the shared-model iteration: ") +
+                               cudaGetErrorString(le != cudaSuccess ? le : e));
   }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  for (int it = 0; it < n_iter && e == cudaSuccess; ++it) e = cudaGraphLaunch(ge, s);
+  cudaStreamSynchronize(s);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
   CUDA_TRY(cudaGetLastError());
   for (int i = 0; i < S; ++i) STATUS_TRY(download_points(T4 + (size_t)i * M, M, T_out[i], c->stage, false, s));
   std::vector<DevState> h((size_t)S);
@@ -401,7 +455,9 @@ cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* 
   CUDA_TRY(cudaMemcpyAsync(h.data(), b[kSt].p, (size_t)S * sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaMemcpyAsync(&status, b[kStatus].p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  if (status != 0) return fail((cpd_status)status, "a bounded wait of the shared-model M-step ran out");
+  if (status != 0)
+    return fail((cpd_status)status, std::string("a bounded wait of the shared-model M-step ran out") +
+                                        (fault ? " (injected: CPD_FAULT=umma_wait)" : ""));
   for (int i = 0; i < S; ++i) {
     if (h[(size_t)i].status != 0)
       return fail((cpd_status)h[(size_t)i].status, "scene " + std::to_string(i) + ": the device reported a failure");
@@ -951,15 +1007,18 @@ cpd_status cpd_iterate_shared(cpd_ctx* c, int32_t n_scenes, const void* const* Y
   if (n_scenes < 1 || n_scenes > 4096) return fail(CPD_EINVAL, "n_scenes must be in [1, 4096]");
   if (!Y || !N || !T_out || !sigma2_out) return fail(CPD_EINVAL, "Y, N, T_out and sigma2_out are required");
   if (n_iter < 1 || n_iter > 100000) return fail(CPD_EINVAL, "n_iter must be in [1, 100000]");
-  if (c->fp64 || c->half_basis || c->sorted_model || c->k_cap > 0)
-    return fail(CPD_EINVAL, "shared-model registrations need a CPD_FP32 context without flags");
+  if (c->fp64 || c->sorted_model || c->k_cap > 0)
+    return fail(CPD_EINVAL, "shared-model registrations need a CPD_FP32 or CPD_MIXED context without flags");
+  if (c->half_basis && !umma_supported(1))
+    return fail(CPD_ECUDA, "the tensor-map encoder of the driver is unavailable");
   for (int i = 0; i < n_scenes; ++i) {
     if (!Y[i] || !T_out[i]) return fail(CPD_EINVAL, "scene " + std::to_string(i) + ": Y or T_out is NULL");
     if (N[i] < 1 || N[i] > kMaxN) return fail(CPD_EINVAL, "scene " + std::to_string(i) + ": N must be in [1, 2^30]");
   }
   DeviceGuard guard(c->dev);
-  for (int g0 = 0; g0 < n_scenes; g0 += kMaxScenesPerPass) {
-    const int S = std::min(kMaxScenesPerPass, n_scenes - g0);
+  const int per_pass = c->half_basis ? kMaxScenesPerPassMma : kMaxScenesPerPass;
+  for (int g0 = 0; g0 < n_scenes; g0 += per_pass) {
+    const int S = std::min(per_pass, n_scenes - g0);
     STATUS_TRY(shared_group(c, S, Y + g0, N + g0, n_iter, T_out + g0, sigma2_out + g0));
   }
   return CPD_OK;

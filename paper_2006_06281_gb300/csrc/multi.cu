@@ -242,6 +242,8 @@ void products(int S, const float* A, int64_t ldA, int64_t rows, int64_t cols, co
 
 }  // namespace
 
+int64_t multi_sums_elems(int64_t M) { return cdiv(M, kMRedCols) * 3; }
+
 MultiPlan plan_multi(int64_t M, int64_t K, int64_t ldU, int64_t ldM, int S, int sms) {
   MultiPlan p{};
   p.S = S;
@@ -271,6 +273,34 @@ void launch_mstep_multi(const MultiPlan& p, const float* U, int64_t ldU, const f
     expand_finish_scene<<<p.e_blocks, kThreadsD, 0, s>>>(part + (size_t)i * p.e_chunks * 3 * ldM, p.e_chunks, ldM,
                                                          (int)M, X4, Yt4 + (size_t)i * M, T4 + (size_t)i * M, sums,
                                                          st[i]);
+}
+
+// The same M-step with the products on the tensor cores (umma.cu), for an
+// FP16 basis: V is packed from the scenes' right-hand sides (hi / lo FP16
+// parts), then one tcgen05 pass over U^T (projection) and one over U
+// (expansion); the partials feed the per-scene diagonal updates and Eq. 18
+// epilogues above.
+cudaError_t launch_mstep_multi_mma(const UmmaPlan& pp, const UmmaPlan& pe, const __half* U, int64_t ldU,
+                                   const __half* Ut, int64_t ldM, const double* lam, int64_t M, int64_t K,
+                                   const float4* X4, const float4* R4, const float4* Yt4, float4* T4, float4* B4,
+                                   float4* C4, DevState* const* st, __half* Vp, __half* Ve, float* part,
+                                   double* sums, int* status, bool fault_wait, cudaStream_t s) {
+  const int S = pp.S;
+  launch_pack_rhs(pp, R4, M, Vp, s);
+  cudaError_t e = launch_umma_products(pp, Ut, ldM, Vp, part, ldU, status, fault_wait, s);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < S; ++i)
+    diag_update_scene<<<(unsigned)cdiv(K, kMRedCols), kThreadsD, 0, s>>>(
+        part + (size_t)i * pp.chunks * 3 * ldU, pp.chunks, ldU, (int)K, lam, B4 + (size_t)i * K, C4 + (size_t)i * K,
+        st[i]);
+  launch_pack_rhs(pe, B4, K, Ve, s);
+  e = launch_umma_products(pe, U, ldU, Ve, part, ldM, status, fault_wait, s);
+  if (e != cudaSuccess) return e;
+  const unsigned eb = (unsigned)cdiv(M, kMRedCols);
+  for (int i = 0; i < S; ++i)
+    expand_finish_scene<<<eb, kThreadsD, 0, s>>>(part + (size_t)i * pe.chunks * 3 * ldM, pe.chunks, ldM, (int)M, X4,
+                                                 Yt4 + (size_t)i * M, T4 + (size_t)i * M, sums, st[i]);
+  return cudaGetLastError();
 }
 
 }  // namespace fcpd
