@@ -373,7 +373,9 @@ cpd_status cpd_get_trim(cpd_ctx *ctx, int64_t *k_cap, int32_t *trimmed_iters);
  * every iteration lies in span(U) (Eq. 20), so T - X = U c with c = U^T
  * (T - X): K x 3 eigen-coefficients.  A learned predictor of c (and of
  * sigma2) for a new scene can start the EM loop near its end; W = 0 stays
- * the fallback.  CPD_FP32 contexts.
+ * the fallback.  CPD_FP32 and CPD_MIXED contexts (the FP16 basis of the
+ * mixed mode is the rounding of the same FP64 eigenvectors, so coefficients
+ * of one apply to the other).
  * ---------------------------------------------------------------------- */
 
 /* coef_out (n_coef x 3 floats, host or device) = U[:, :n_coef]^T (T - X) of

@@ -206,11 +206,14 @@ void launch_gather_rows_f32(const float* src, int64_t ld_src, const int* inv, in
                             cudaStream_t s);
 
 // ---------------------------------------------------------- warm start
-// c[k][d] = sum_m U[m][k] (T[m] - X[m])_d for k < K (FP32 basis).
-void launch_coefficients(const float* U, int64_t ldU, int64_t M, int64_t K, const float4* T4, const float4* X4,
-                         float* c, cudaStream_t s);
+// c[k][d] = sum_m U[m][k] (T[m] - X[m])_d for k < K (basis stored as B:
+// float, or __half in the mixed-precision mode).
+template <typename B>
+void launch_coefficients(const B* U, int64_t ldU, int64_t M, int64_t K, const float4* T4, const float4* X4, float* c,
+                         cudaStream_t s);
 // T[m] = X[m] + sum_{k < nc} U[m][k] c[k].
-void launch_warm_start_T(const float* U, int64_t ldU, int64_t M, int64_t nc, const float* c, const float4* X4,
+template <typename B>
+void launch_warm_start_T(const B* U, int64_t ldU, int64_t M, int64_t nc, const float* c, const float4* X4,
                          float4* T4, cudaStream_t s);
 
 // Message returned by cpd_last_error() on the calling thread.

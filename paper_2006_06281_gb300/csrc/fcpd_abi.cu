@@ -1040,14 +1040,18 @@ cpd_status cpd_get_trim(cpd_ctx* c, int64_t* k_cap, int32_t* trimmed_iters) {
 cpd_status cpd_coefficients(cpd_ctx* c, int32_t n_coef, void* coef_out) {
   g_err.clear();
   if (!c || !coef_out) return fail(CPD_EINVAL, "ctx and coef_out are required");
-  if (c->fp64 || c->half_basis) return fail(CPD_EINVAL, "coefficients need a CPD_FP32 context");
+  if (c->fp64) return fail(CPD_EINVAL, "coefficients need a CPD_FP32 or CPD_MIXED context");
   if (n_coef < 1 || n_coef > c->K) return fail(CPD_EINVAL, "n_coef must be in [1, K]");
   if (!c->started) return fail(CPD_ESTATE, "no registration has started");
   DeviceGuard guard(c->dev);
   Buf tmp;
   STATUS_TRY(tmp.ensure((size_t)n_coef * 3 * sizeof(float)));
-  launch_coefficients(c->U.as<float>(), c->ldU, c->M, n_coef, c->T4.as<float4>(), c->X4.as<float4>(), tmp.as<float>(),
-                      c->stream);
+  if (c->half_basis)
+    launch_coefficients<__half>(c->U.as<__half>(), c->ldU, c->M, n_coef, c->T4.as<float4>(), c->X4.as<float4>(),
+                                tmp.as<float>(), c->stream);
+  else
+    launch_coefficients<float>(c->U.as<float>(), c->ldU, c->M, n_coef, c->T4.as<float4>(), c->X4.as<float4>(),
+                               tmp.as<float>(), c->stream);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(coef_out, tmp.p, (size_t)n_coef * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1057,7 +1061,7 @@ cpd_status cpd_coefficients(cpd_ctx* c, int32_t n_coef, void* coef_out) {
 cpd_status cpd_warm_start(cpd_ctx* c, int32_t n_coef, const void* coef, double sigma2_0) {
   g_err.clear();
   if (!c || !coef) return fail(CPD_EINVAL, "ctx and coef are required");
-  if (c->fp64 || c->half_basis) return fail(CPD_EINVAL, "a warm start needs a CPD_FP32 context");
+  if (c->fp64) return fail(CPD_EINVAL, "a warm start needs a CPD_FP32 or CPD_MIXED context");
   if (n_coef < 0 || n_coef > c->K) return fail(CPD_EINVAL, "n_coef must be in [0, K]");
   if (!(sigma2_0 > 0.0) || !std::isfinite(sigma2_0)) return fail(CPD_EINVAL, "sigma2_0 must be > 0");
   DeviceGuard guard(c->dev);
@@ -1065,8 +1069,12 @@ cpd_status cpd_warm_start(cpd_ctx* c, int32_t n_coef, const void* coef, double s
   STATUS_TRY(tmp.ensure((size_t)std::max(n_coef, 1) * 3 * sizeof(float)));
   if (n_coef > 0)
     CUDA_TRY(cudaMemcpyAsync(tmp.p, coef, (size_t)n_coef * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
-  launch_warm_start_T(c->U.as<float>(), c->ldU, c->M, n_coef, tmp.as<float>(), c->X4.as<float4>(), c->T4.as<float4>(),
-                      c->stream);
+  if (c->half_basis)
+    launch_warm_start_T<__half>(c->U.as<__half>(), c->ldU, c->M, n_coef, tmp.as<float>(), c->X4.as<float4>(),
+                                c->T4.as<float4>(), c->stream);
+  else
+    launch_warm_start_T<float>(c->U.as<float>(), c->ldU, c->M, n_coef, tmp.as<float>(), c->X4.as<float4>(),
+                               c->T4.as<float4>(), c->stream);
   launch_state_init(c->dst(), sigma2_0, c->stream);
   if (c->N > 0) apply_prune(c);
   CUDA_TRY(cudaGetLastError());

@@ -169,15 +169,20 @@ __global__ void adam(float* __restrict__ p, const float* __restrict__ g, float* 
   p[e] -= lr_t * mi / (sqrtf(vi) + eps);
 }
 
+// Basis element as float (FP32 basis, or the FP16 basis of the mixed mode).
+__device__ __forceinline__ float basis_f(float u) { return u; }
+__device__ __forceinline__ float basis_f(__half u) { return __half2float(u); }
+
 // c[k][d] = sum_m U[m][k] (T[m] - X[m])_d, one block per k, fixed order.
-__global__ void __launch_bounds__(256) coefficients(const float* __restrict__ U, int64_t ldU, int M,
+template <typename B>
+__global__ void __launch_bounds__(256) coefficients(const B* __restrict__ U, int64_t ldU, int M,
                                                     const float4* __restrict__ T4, const float4* __restrict__ X4,
                                                     float* __restrict__ c) {
   __shared__ double sh[32];
   const int k = blockIdx.x;
   double s[3] = {0.0, 0.0, 0.0};
   for (int m = threadIdx.x; m < M; m += blockDim.x) {
-    const double u = U[(int64_t)m * ldU + k];
+    const double u = basis_f(U[(int64_t)m * ldU + k]);
     const float4 t = T4[m], x = X4[m];
     s[0] += u * ((double)t.x - x.x);
     s[1] += u * ((double)t.y - x.y);
@@ -190,14 +195,15 @@ __global__ void __launch_bounds__(256) coefficients(const float* __restrict__ U,
 }
 
 // T[m] = X[m] + sum_{k < nc} U[m][k] c[k].
-__global__ void warm_start_T(const float* __restrict__ U, int64_t ldU, int M, int nc, const float* __restrict__ c,
+template <typename B>
+__global__ void warm_start_T(const B* __restrict__ U, int64_t ldU, int M, int nc, const float* __restrict__ c,
                              const float4* __restrict__ X4, float4* __restrict__ T4) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   float4 x = X4[m];
   float a0 = 0.f, a1 = 0.f, a2 = 0.f;
   for (int k = 0; k < nc; ++k) {
-    const float u = U[(int64_t)m * ldU + k];
+    const float u = basis_f(U[(int64_t)m * ldU + k]);
     a0 = fmaf(u, c[3 * k], a0);
     a1 = fmaf(u, c[3 * k + 1], a1);
     a2 = fmaf(u, c[3 * k + 2], a2);
@@ -478,12 +484,22 @@ void cpd_net_destroy(cpd_net* n) {
 
 // ------------------------------------------------ context side (fcpd_abi.cu)
 namespace fcpd {
-void launch_coefficients(const float* U, int64_t ldU, int64_t M, int64_t K, const float4* T4, const float4* X4,
-                         float* c, cudaStream_t s) {
-  coefficients<<<(unsigned)K, 256, 0, s>>>(U, ldU, (int)M, T4, X4, c);
+template <typename B>
+void launch_coefficients(const B* U, int64_t ldU, int64_t M, int64_t K, const float4* T4, const float4* X4, float* c,
+                         cudaStream_t s) {
+  coefficients<B><<<(unsigned)K, 256, 0, s>>>(U, ldU, (int)M, T4, X4, c);
 }
-void launch_warm_start_T(const float* U, int64_t ldU, int64_t M, int64_t nc, const float* c, const float4* X4,
+template <typename B>
+void launch_warm_start_T(const B* U, int64_t ldU, int64_t M, int64_t nc, const float* c, const float4* X4,
                          float4* T4, cudaStream_t s) {
-  warm_start_T<<<(unsigned)cdiv(M, 256), 256, 0, s>>>(U, ldU, (int)M, (int)nc, c, X4, T4);
+  warm_start_T<B><<<(unsigned)cdiv(M, 256), 256, 0, s>>>(U, ldU, (int)M, (int)nc, c, X4, T4);
 }
+template void launch_coefficients<float>(const float*, int64_t, int64_t, int64_t, const float4*, const float4*,
+                                         float*, cudaStream_t);
+template void launch_coefficients<__half>(const __half*, int64_t, int64_t, int64_t, const float4*, const float4*,
+                                          float*, cudaStream_t);
+template void launch_warm_start_T<float>(const float*, int64_t, int64_t, int64_t, const float*, const float4*,
+                                         float4*, cudaStream_t);
+template void launch_warm_start_T<__half>(const __half*, int64_t, int64_t, int64_t, const float*, const float4*,
+                                          float4*, cudaStream_t);
 }  // namespace fcpd
