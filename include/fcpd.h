@@ -382,6 +382,12 @@ cpd_status cpd_get_trim(cpd_ctx *ctx, int64_t *k_cap, int32_t *trimmed_iters);
  * the current T.  Synchronises.  CPD_ESTATE before a registration started. */
 cpd_status cpd_coefficients(cpd_ctx *ctx, int32_t n_coef, void *coef_out);
 
+/* coef_out (n_coef x 3 floats, host or device) = U[:, :n_coef]^T (T - X) of
+ * a caller's T (M x 3 floats, host or device; for instance a T of
+ * cpd_iterate_shared).  The context's own registration is not touched.
+ * Synchronises. */
+cpd_status cpd_coefficients_of(cpd_ctx *ctx, int32_t n_coef, const void *T, void *coef_out);
+
 /* Start the next registration at T = X + U[:, :n_coef] coef (coef: n_coef x 3
  * floats, host or device; n_coef = 0 gives T = X) with variance sigma2_0,
  * iteration count 0: the following cpd_iterate continues from there

@@ -32,7 +32,7 @@ EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_eig_info", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_iterate_shared", "cpd_destroy",
-           "cpd_coefficients", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
+           "cpd_coefficients", "cpd_coefficients_of", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
            "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
            "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_autotune",
@@ -92,6 +92,7 @@ def load():
                 "cpd_get_trim": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
                 "cpd_iterate_shared": ([vp, i32, C.POINTER(vp), C.POINTER(i64), i32, C.POINTER(vp), dp], C.c_int),
                 "cpd_coefficients": ([vp, i32, vp], C.c_int),
+                "cpd_coefficients_of": ([vp, i32, vp, vp], C.c_int),
                 "cpd_warm_start": ([vp, i32, vp, d], C.c_int),
                 "cpd_net_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
                 "cpd_net_num_params": ([vp], i64),
@@ -299,6 +300,13 @@ class Context:
         """U[:, :n_coef]^T (T - X) of the current T (n_coef x 3, numpy)."""
         out = np.empty((int(n_coef), 3), dtype=np.float32)
         _check(load().cpd_coefficients(self._h, int(n_coef), out.ctypes.data))
+        return out
+
+    def coefficients_of(self, T, n_coef):
+        """U[:, :n_coef]^T (T - X) of a given T (n_coef x 3, numpy)."""
+        _, pt, _ = _prep(T, self.precision, "T")
+        out = np.empty((int(n_coef), 3), dtype=np.float32)
+        _check(load().cpd_coefficients_of(self._h, int(n_coef), pt, out.ctypes.data))
         return out
 
     def warm_start(self, coef, sigma2_0):

@@ -893,7 +893,10 @@ cpd_status cpd_set_ground_truth(cpd_ctx* c, const void* Yhat, double rmse_tol) {
   if (!c) return fail(CPD_EINVAL, "ctx is NULL");
   if (!(rmse_tol >= 0.0) || !std::isfinite(rmse_tol)) return fail(CPD_EINVAL, "rmse_tol must be >= 0");
   DeviceGuard guard(c->dev);
-  c->drop_graphs();
+  // the captured iterations hold the ground-truth pointer (or none): they
+  // are re-captured only when that changes
+  const bool had_gt = c->has_gt;
+  const void* old_gt = c->Yhat4.p;
   if (Yhat) {
     STATUS_TRY(c->Yhat4.ensure((size_t)c->M * c->v4));
     STATUS_TRY(upload_model(c, Yhat, c->Yhat4.p));
@@ -903,6 +906,7 @@ cpd_status cpd_set_ground_truth(cpd_ctx* c, const void* Yhat, double rmse_tol) {
     c->has_gt = false;
     c->gt_tol = 0.0;
   }
+  if (had_gt != c->has_gt || old_gt != c->Yhat4.p) c->drop_graphs();
   launch_state_params(c->dst(), c->p.w, c->p.lambda, c->p.tol, c->gt_tol, c->has_gt ? 1 : 0, c->hist.as<double>(),
                       c->M, c->N, c->K, c->stream);
   CUDA_TRY(cudaGetLastError());
@@ -1051,6 +1055,28 @@ cpd_status cpd_coefficients(cpd_ctx* c, int32_t n_coef, void* coef_out) {
                                 tmp.as<float>(), c->stream);
   else
     launch_coefficients<float>(c->U.as<float>(), c->ldU, c->M, n_coef, c->T4.as<float4>(), c->X4.as<float4>(),
+                               tmp.as<float>(), c->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(coef_out, tmp.p, (size_t)n_coef * 3 * sizeof(float), cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return CPD_OK;
+}
+
+cpd_status cpd_coefficients_of(cpd_ctx* c, int32_t n_coef, const void* T, void* coef_out) {
+  g_err.clear();
+  if (!c || !T || !coef_out) return fail(CPD_EINVAL, "ctx, T and coef_out are required");
+  if (c->fp64) return fail(CPD_EINVAL, "coefficients need a CPD_FP32 or CPD_MIXED context");
+  if (n_coef < 1 || n_coef > c->K) return fail(CPD_EINVAL, "n_coef must be in [1, K]");
+  DeviceGuard guard(c->dev);
+  Buf tmp, t4;
+  STATUS_TRY(tmp.ensure((size_t)n_coef * 3 * sizeof(float)));
+  STATUS_TRY(t4.ensure((size_t)c->M * sizeof(float4)));
+  STATUS_TRY(upload_model(c, T, t4.p));
+  if (c->half_basis)
+    launch_coefficients<__half>(c->U.as<__half>(), c->ldU, c->M, n_coef, t4.as<float4>(), c->X4.as<float4>(),
+                                tmp.as<float>(), c->stream);
+  else
+    launch_coefficients<float>(c->U.as<float>(), c->ldU, c->M, n_coef, t4.as<float4>(), c->X4.as<float4>(),
                                tmp.as<float>(), c->stream);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(coef_out, tmp.p, (size_t)n_coef * 3 * sizeof(float), cudaMemcpyDefault, c->stream));

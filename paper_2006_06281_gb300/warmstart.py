@@ -85,16 +85,26 @@ class Net:
             pass
 
 
-def registration_targets(ctx, scenes, n_coef, iters):
+def registration_targets(ctx, scenes, n_coef, iters, group=8):
     """End points of registrations from W = 0: (n, 3 n_coef + 1) float32 rows
-    [c = U^T (T - X) (row-major n_coef x 3), log sigma2]."""
+    [c = U^T (T - X) (row-major n_coef x 3), log sigma2].  The scenes are
+    registered `group` at a time against the context's model
+    (cpd_iterate_shared: one pass over the basis per group and iteration);
+    group = 1 registers them one at a time on the context itself."""
     import torch
     out = np.empty((len(scenes), 3 * n_coef + 1), dtype=np.float32)
-    for i, Y in enumerate(scenes):
-        ctx.reset()
-        _, s2, _ = ctx.iterate(torch.as_tensor(Y, device="cuda"), iters, want_T=False)
-        out[i, :-1] = ctx.coefficients(n_coef).ravel()
-        out[i, -1] = math.log(max(s2, 1e-30))
+    if group <= 1:
+        for i, Y in enumerate(scenes):
+            ctx.reset()
+            _, s2, _ = ctx.iterate(torch.as_tensor(Y, device="cuda"), iters, want_T=False)
+            out[i, :-1] = ctx.coefficients(n_coef).ravel()
+            out[i, -1] = math.log(max(s2, 1e-30))
+        return out
+    for g0 in range(0, len(scenes), group):
+        Ys = [torch.as_tensor(Y, device="cuda") for Y in scenes[g0:g0 + group]]
+        for j, (T, s2) in enumerate(ctx.iterate_shared(Ys, iters)):
+            out[g0 + j, :-1] = ctx.coefficients_of(T, n_coef).ravel()
+            out[g0 + j, -1] = math.log(max(s2, 1e-30))
     return out
 
 

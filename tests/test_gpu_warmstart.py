@@ -116,3 +116,31 @@ def test_learned_warm_start_needs_fewer_iterations():
             warm.append(it_warm)
         print(f"iterations to RMSE(T, T_end) <= 1e-3: cold {np.mean(cold):.1f}, warm {np.mean(warm):.1f}")
         assert np.mean(warm) < 0.8 * np.mean(cold)
+
+
+def test_coefficients_of_a_given_T_and_the_mixed_context():
+    """cpd_coefficients_of(T) equals cpd_coefficients for the context's own
+    T, and shared-model registrations give the targets the one-at-a-time
+    registrations give; a CPD_MIXED context (FP16 basis of the same
+    eigenvectors) takes the same coefficients: its warm-start T = X + U c
+    matches the FP32 context's to the FP16 rounding of U."""
+    M, K = 600, 24
+    X = datagen.gen(M, seed=71).X.astype(np.float32)
+    Ys = [datagen.gen_from_template(X, 7100 + i, amp=0.15, noise=0.01).Y.astype(np.float32) for i in range(5)]
+    Xd = torch.tensor(X, device="cuda")
+    with cpd.Context(Xd, precision=cpd.FP32, K=K) as ctx:
+        T, _, _ = ctx.iterate(torch.tensor(Ys[0], device="cuda"), 20)
+        np.testing.assert_allclose(ctx.coefficients_of(T, K), ctx.coefficients(K), rtol=0, atol=1e-6)
+        seq = warmstart.registration_targets(ctx, Ys, K, 30, group=1)
+        grp = warmstart.registration_targets(ctx, Ys, K, 30, group=4)
+        assert np.abs(seq - grp).max() <= 1e-4 * max(np.abs(seq).max(), 1.0)
+        c = seq[0, :-1].reshape(K, 3)
+        ctx.warm_start(c, 1e-3)
+        T32 = ctx.iterate(torch.tensor(Ys[0], device="cuda"), 0)[0].double().cpu().numpy()
+    with cpd.Context(Xd, precision=cpd.MIXED, K=K) as cm:
+        cm.warm_start(c, 1e-3)
+        Tm = cm.iterate(torch.tensor(Ys[0], device="cuda"), 0)[0].double().cpu().numpy()
+        cm_c = cm.coefficients(K)
+    D = T32 - X.astype(np.float64)
+    assert np.linalg.norm(Tm - T32) <= 2.0 ** -10 * np.linalg.norm(D)
+    np.testing.assert_allclose(cm_c, c, rtol=0, atol=2.0 ** -9 * np.abs(c).max())
