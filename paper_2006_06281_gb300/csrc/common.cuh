@@ -468,6 +468,9 @@ void launch_pack(const F* src, int64_t n, typename Vec<F>::t4* dst, bool with_no
 template <typename F>
 void launch_unpack(const typename Vec<F>::t4* src, int64_t n, F* dst, cudaStream_t s);
 void launch_begin_iterations(DevState* st, int n_iter, cudaStream_t s);
+// Sets the WHILE condition h of a conditional graph node: 1 while another
+// iteration should run (target not reached, no tolerance stop, no failure).
+void launch_loop_control(const DevState* st, cudaGraphConditionalHandle h, cudaStream_t s);
 void launch_state_init(DevState* st, double sigma2, cudaStream_t s);
 // Pruning configuration of a context (kept across state_init, which turns it off).
 void launch_state_prune(DevState* st, float prune_r2, int prune_ctl, cudaStream_t s);

@@ -161,6 +161,7 @@ struct cpd_ctx {
   int eig_method = 0;            // 0: full eigensolver, 1: top-K subspace iteration
   int eig_steps = 0;             // Rayleigh-Ritz steps of the subspace iteration
   cudaGraphExec_t graph[2] = {nullptr, nullptr};   // 1 iteration, kBatch iterations
+  cudaGraphExec_t loop_graph = nullptr;             // device-side loop until the target or a tolerance stop
   cudaGraphExec_t prof_graph = nullptr;             // n iterations with timing events
   int prof_iters = 0;
   std::vector<cudaEvent_t> prof_ev;                 // 9 per sampled iteration
@@ -183,6 +184,8 @@ struct cpd_ctx {
         cudaGraphExecDestroy(g);
         g = nullptr;
       }
+    if (loop_graph) cudaGraphExecDestroy(loop_graph);
+    loop_graph = nullptr;
     if (prof_graph) cudaGraphExecDestroy(prof_graph);
     prof_graph = nullptr;
     prof_iters = 0;
@@ -533,6 +536,44 @@ cpd_status capture_graph(cpd_ctx* c, int which) {
   return CPD_OK;
 }
 
+// A graph whose one node is a conditional WHILE loop over one captured
+// iteration followed by loop_control: the device runs iterations until the
+// target is reached or a tolerance stops the registration, with no host
+// round trip and no launches of iterations that would step aside.
+cpd_status capture_loop_graph(cpd_ctx* c) {
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  // the parameter union has no usable default constructor: zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+  std::memset(npbuf, 0, sizeof(npbuf));
+  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, np));
+  cudaGraph_t body = np->conditional.phGraph_out[0];
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  enqueue_iteration(c, c->cap);
+  launch_loop_control(c->dst(), h, c->cap);
+  cudaGraph_t out = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap, &out);
+  if (e != cudaSuccess) return fail(CPD_ECUDA, std::string("loop graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->loop_graph, g, 0);
+  if (e != cudaSuccess) {
+    c->loop_graph = nullptr;
+    return fail(CPD_ECUDA, std::string("loop graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return CPD_OK;
+}
+
 // Sizes the scene-dependent buffers for N scene points.
 cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
   if (N == c->N) return CPD_OK;
@@ -839,11 +880,17 @@ cpd_status cpd_iterate(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, voi
   if (n_iter > 0) {
     launch_begin_iterations(c->dst(), n_iter, c->stream);
     CUDA_TRY(cudaGetLastError());
-    const int nb = n_iter / cpd_ctx::kBatch, n1 = n_iter % cpd_ctx::kBatch;
-    if (nb > 0 && !c->graph[1]) STATUS_TRY(capture_graph(c, 1));
-    if (n1 > 0 && !c->graph[0]) STATUS_TRY(capture_graph(c, 0));
-    for (int i = 0; i < nb; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[1], c->stream));
-    for (int i = 0; i < n1; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[0], c->stream));
+    if (c->p.tol > 0.0 || (c->has_gt && c->gt_tol > 0.0)) {
+      // a tolerance may stop the registration early: loop on the device
+      if (!c->loop_graph) STATUS_TRY(capture_loop_graph(c));
+      CUDA_TRY(cudaGraphLaunch(c->loop_graph, c->stream));
+    } else {
+      const int nb = n_iter / cpd_ctx::kBatch, n1 = n_iter % cpd_ctx::kBatch;
+      if (nb > 0 && !c->graph[1]) STATUS_TRY(capture_graph(c, 1));
+      if (n1 > 0 && !c->graph[0]) STATUS_TRY(capture_graph(c, 0));
+      for (int i = 0; i < nb; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[1], c->stream));
+      for (int i = 0; i < n1; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[0], c->stream));
+    }
   }
   if (T_out) STATUS_TRY(download_model(c, c->T4.p, T_out));
   if (sigma2_out || iters_done || (T_out && !is_device_ptr(T_out))) {

@@ -126,6 +126,14 @@ __global__ void sigma2_init_k(const V4* __restrict__ X4, int M, const V4* __rest
 
 __global__ void begin_iterations(DevState* st, int n_iter) { st->iter_target = st->iter + n_iter; }
 
+// Condition of the device-side iteration loop: run another iteration while
+// the target is not reached, no tolerance stopped the registration and no
+// failure was recorded.
+__global__ void loop_control(const DevState* st, cudaGraphConditionalHandle h) {
+  const bool more = st->iter < st->iter_target && !st->done && st->status == 0;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 __global__ void state_params(DevState* st, double w, double lambda, double tol, double gt_tol, int has_gt,
                              double* hist, int M, int N, int K) {
   st->w = w;
@@ -214,6 +222,9 @@ void launch_sigma2_init(const typename Vec<F>::t4* X4, int64_t M, const typename
 }
 
 void launch_begin_iterations(DevState* st, int n_iter, cudaStream_t s) { begin_iterations<<<1, 1, 0, s>>>(st, n_iter); }
+void launch_loop_control(const DevState* st, cudaGraphConditionalHandle h, cudaStream_t s) {
+  loop_control<<<1, 1, 0, s>>>(st, h);
+}
 void launch_state_params(DevState* st, double w, double lambda, double tol, double gt_tol, int has_gt,
                          double* hist, int64_t M, int64_t N, int64_t K, cudaStream_t s) {
   state_params<<<1, 1, 0, s>>>(st, w, lambda, tol, gt_tol, has_gt, hist, (int)M, (int)N, (int)K);

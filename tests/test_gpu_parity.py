@@ -364,6 +364,32 @@ def test_ground_truth_tolerance_gives_time_to_tolerance():
     assert oracle.rmse(ref["T"], ps.Yhat) == pytest.approx(h["rmse"][-1], rel=1e-9)
 
 
+def test_device_loop_stops_where_the_fixed_count_path_would():
+    """With a tolerance the iterations run in a device-side loop (a
+    conditional WHILE graph node): it must stop at the first iteration that
+    meets the tolerance, give bit for bit the T of the same number of
+    iterations run without a tolerance, and resume across calls."""
+    ps = pointsets(700, seed=17)
+    X, Y = dev(ps.X, cpd.FP32), dev(ps.Y, cpd.FP32)
+    with cpd.Context(X, precision=cpd.FP32) as ctx:
+        ctx.set_ground_truth(dev(ps.Yhat, cpd.FP32), 8e-3)
+        T_tol, _, it = ctx.iterate(Y, 300)
+        h = ctx.history(it)
+        assert 3 < it < 300 and h["rmse"][-1] <= 8e-3 and np.all(h["rmse"][:-1] > 8e-3)
+        # a second call continues nowhere: the registration has stopped
+        _, _, it2 = ctx.iterate(Y, 50)
+        assert it2 == it
+        # in pieces: 5 iterations, then the rest up to the same stop
+        ctx.reset()
+        ctx.iterate(Y, 5)
+        T_pieces, _, it3 = ctx.iterate(Y, 300)
+        assert it3 == it
+    with cpd.Context(X, precision=cpd.FP32) as ref:
+        T_fixed, _, itf = ref.iterate(Y, it)
+    assert itf == it
+    assert torch.equal(T_tol, T_fixed) and torch.equal(T_pieces, T_fixed)
+
+
 def test_register_entry_point():
     ps = pointsets(300, seed=16)
     ref = oracle.register(ps.X, ps.Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=25)
