@@ -221,14 +221,21 @@ void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------- launchers
 struct MmaPlan {
-  int a_row_tiles, a_chunks, a_rows_per_chunk;       // pass A: scene-point tiles x model-point chunks
-  int b_row_tiles, b_chunks, b_cols_per_chunk;       // pass B: model-point tiles x scene-point chunks
+  int a_row_tiles, a_chunks, a_rows_per_chunk;       // pass A: 128-point scene tiles x model-point chunks
+  int b_row_tiles, b_chunks, b_cols_per_chunk;       // pass B: 128-point model tiles x scene-point chunks
+  int a_tpc, b_tpc;                                  // 128-point column tiles per chunk
+  int64_t prep_floats;                               // column-vector scratch (floats) of either pass
+  int64_t prep_off;                                  // its offset in the pass B partials buffer
 };
 void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p);
+// The tcgen05 passes can run on this device (their shared memory fits).
+bool estep_mma_supported();
+// prep: prep_floats of scratch for the column vectors (in the pass B
+// partials buffer past the partials; unused by pass A's own partials).
 void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,
-                      DevState* st, int gate, cudaStream_t s);
+                      float* prep, DevState* st, int gate, cudaStream_t s);
 void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Yb, int64_t N, float* partB,
-                      DevState* st, int gate, cudaStream_t s);
+                      float* prep, DevState* st, int gate, cudaStream_t s);
 // sigma2 floor of the tensor-core passes from the largest point norm of X and Y.
 void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s);
 

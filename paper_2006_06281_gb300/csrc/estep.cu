@@ -143,7 +143,7 @@ EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned,
     p.pa_row_chunks = p.a_row_chunks;          // never used: prune_active is false
     p.pb_col_chunks = p.b_col_chunks;
   }
-  p.mma = with_mma && !fp64;
+  p.mma = with_mma && !fp64 && estep_mma_supported();
   if (p.mma) {
     plan_estep_mma(M, N, sms, p.mm);
     p.partA_elems = std::max(p.partA_elems, (int64_t)p.mm.a_chunks * N);
@@ -152,6 +152,14 @@ EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned,
     p.mm = MmaPlan{};
     p.mm.a_chunks = p.a_row_chunks;            // never used: mma_active is false
     p.mm.b_chunks = p.b_col_chunks;
+  }
+  // column-vector scratch of the tensor-core passes: past every layout's
+  // pass B partials (pass A does not use that buffer; pass B writes only
+  // the partials in front of it)
+  p.mm.prep_off = 0;
+  if (p.mma) {
+    p.mm.prep_off = cdiv(p.partB_elems, 32) * 32;
+    p.partB_elems = p.mm.prep_off + p.mm.prep_floats;
   }
   p.redA_blocks = cdiv(N, kRedCols);
   p.redB_blocks = cdiv(M, kRedRows);
@@ -176,7 +184,7 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
     if (pl.pruned)
       passA_f32_pruned<<<dim3(pl.pa_col_tiles, pl.pa_row_chunks), kThreadsA, 0, s>>>(
           T4, (int)M, pl.pa_rows_per_chunk, Y4, (int)N, partA, st, g);
-    if (pl.mma) launch_passA_mma(pl.mm, T4, M, Y4, N, partA, st, g, s);
+    if (pl.mma) launch_passA_mma(pl.mm, T4, M, Y4, N, partA, partB + pl.mm.prep_off, st, g, s);
   } else {
     passA_f64<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
   }
@@ -192,7 +200,7 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
     if (pl.pruned)
       passB_f32_pruned<<<dim3(pl.pb_row_tiles, pl.pb_col_chunks), kThreadsB, 0, s>>>(
           T4, (int)M, Yb, (int)N, pl.pb_cols_per_chunk, partB, st, g);
-    if (pl.mma) launch_passB_mma(pl.mm, T4, M, Yb, N, partB, st, g, s);
+    if (pl.mma) launch_passB_mma(pl.mm, T4, M, Yb, N, partB, partB + pl.mm.prep_off, st, g, s);
   } else {
     passB_f64<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
   }

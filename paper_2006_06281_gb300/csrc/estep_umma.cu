@@ -1,0 +1,383 @@
+// E-step passes with tcgen05 distance tiles (mixed-precision mode, Eq. 4-5).
+//
+// The base-2 exponent of every Gaussian of a 128 x 128 tile of (row point,
+// column point) pairs is one tcgen05.mma (kind::f16, M = 128, N = 128, K = 16)
+// of the points' augmented FP16 vectors (estep_aug.cuh: 2 r'.c' - |r'|^2 -
+// |c'|^2 + lid over the q-scaled coordinates, FP32 accumulation), written to
+// tensor memory; the epilogue warps read it with tcgen05.ld, one row per
+// thread, and spend their issue slots on the per-pair exponential and sums
+// only.  The arithmetic, its error and its sigma2 floor are those of the
+// augmented vectors; the exponentials (ex2.approx.ftz) and FP32 sums are the
+// FP32 passes', and the split partials have their layout, so the reductions
+// that follow are shared.
+//
+//   pass A   rows: 128 scene points y_n; columns: model points t_m of the
+//            CTA's chunk; thread (row n) sums 2^e over its columns -> den_n
+//            partial (partA[chunk][n]).
+//   pass B   rows: 128 model points; columns: scene points of the chunk with
+//            lid_n = -log2 den_n folded into the vector; thread (row m) sums
+//            w = 2^e, w y_n (3) and w (lid_n - e) = w d'^2 -> P1, PY, V
+//            partials (partB, five planes).
+//
+// CTA: 8 epilogue warps (warp w reads TMEM lanes 32 (w % 4).. and columns
+// 64 (w / 4).. of each tile) and one control warp (its lane 0 issues the bulk
+// copies of the chunk's column vectors -- prepared for the whole point set by
+// prep_cols -- and the MMAs).  Two TMEM accumulators of 128 columns each: the
+// MMA of tile j + 1 runs while the epilogue reads tile j (mbarriers tfull /
+// tempty).  Operand tiles in shared memory are K-major without swizzle:
+// 8-row x 16-byte core matrices, the two K halves of a group of 8 points 128
+// bytes apart, groups 256 bytes apart.  Every wait is bounded in wall time;
+// on expiry the CTA records CPD_ETIMEOUT, waits (bounded) for its copies and
+// MMAs in flight, frees its TMEM and returns.
+#include "estep_dev.cuh"
+#include "estep_aug.cuh"
+#include "tc05.cuh"
+
+#include <algorithm>
+
+namespace fcpd {
+
+namespace {
+
+using namespace dev;
+using namespace tc05;
+
+constexpr int kEThreads = 288;              // 8 epilogue warps + 1 control warp
+constexpr int kEWarps = 8;
+constexpr int kETile = 128;                 // points per operand tile (rows = TMEM lanes, columns)
+constexpr int kETileBytes = kETile * 32;    // 128 augmented vectors of 16 FP16 values
+constexpr int kEMaxTilesA = 24;             // column tiles per CTA chunk, pass A (96 KB)
+constexpr int kEMaxTilesB = 16;             // pass B (64 KB + 32 KB of scene records)
+constexpr uint32_t kETmemCols = 256;        // two accumulators of 128 columns
+constexpr uint32_t kEIdesc = (1u << 4) | ((uint32_t)(kETile >> 3) << 17) | ((uint32_t)(kETile >> 4) << 24);
+constexpr unsigned long long kEWaitNs = 2000000000ull;
+
+// Byte offset of the 16-byte half h (K values 8h..8h+7) of point r of a tile
+// in the no-swizzle K-major core-matrix layout.
+__host__ __device__ constexpr int aug_offset(int r, int h) { return (r >> 3) * 256 + h * 128 + (r & 7) * 16; }
+
+__device__ __forceinline__ void store_aug(unsigned char* tile, int r, const __half (&v)[kAugK]) {
+  const uint4* src = reinterpret_cast<const uint4*>(v);
+  *reinterpret_cast<uint4*>(tile + aug_offset(r, 0)) = src[0];
+  *reinterpret_cast<uint4*>(tile + aug_offset(r, 1)) = src[1];
+}
+
+// Column vectors of all points, tile by tile (n_pad = points rounded up to
+// 128; points >= n are padding with Gaussians exactly 0).  scene = 0: model
+// points T4 (scaled by q here, lid 0, pass A); scene = 1: scene records Yb
+// (already {q y, lid}, pass B).
+__global__ void __launch_bounds__(256)
+prep_cols(const float4* __restrict__ P4, int n, int n_pad, int scene, DevState* __restrict__ st, int gate,
+          unsigned char* __restrict__ out) {
+  if ((gate && iteration_gated(st)) || !mma_active(st)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  const bool valid = i < n;
+  float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) p = P4[i];
+  float x = p.x, y = p.y, z = p.z, lid = p.w;
+  if (!scene) {
+    const float q = scale_q(st->sigma2);
+    x *= q; y *= q; z *= q; lid = 0.f;
+  }
+  __align__(16) __half v[kAugK];
+  col_vector(x, y, z, lid, valid, v);
+  store_aug(out + (size_t)(i / kETile) * kETileBytes, i % kETile, v);
+}
+
+// Bounded wait made uniform across a warp (the tcgen05.ld that follows is
+// warp-collective): if any lane saw the phase complete, every lane does.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+  bool ok = mbar_wait(bar, parity, kEWaitNs);
+  if (__any_sync(0xffffffffu, ok) && !ok) ok = mbar_wait(bar, parity, 1000000ull);
+  return __all_sync(0xffffffffu, ok);
+}
+
+template <int PASS> __host__ __device__ constexpr int max_tiles() { return PASS == 0 ? kEMaxTilesA : kEMaxTilesB; }
+template <int PASS> constexpr size_t pass_smem_bytes() {
+  return 1024 + kETileBytes + (size_t)max_tiles<PASS>() * kETileBytes +
+         (PASS == 1 ? (size_t)kEMaxTilesB * kETile * sizeof(float4) : 0) + 64 * sizeof(uint64_t);
+}
+
+// One pass (PASS 0: A, 1: B).  Rows4: the row points (A: scene Y4, B: model
+// T4), cols: prep_cols output for the column points, Yb (pass B): scene
+// records {q y, lid} read by the epilogue.  Grid: (row tiles, column chunks
+// of `tpc` tiles).  Writes partA[chunk][n] or the five partB planes.
+template <int PASS>
+__global__ void __launch_bounds__(kEThreads, 2)
+pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __restrict__ cols, int n_cols,
+          const float4* __restrict__ Yb, int tpc, float* __restrict__ part, DevState* __restrict__ st, int gate) {
+  if ((gate && iteration_gated(st)) || !mma_active(st)) return;
+  if (PASS == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    // the column list was consumed by fixA; the row list is filled after this pass
+    st->n_flag_cols = 0;
+    st->n_flag_rows = 0;
+  }
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kETileBytes;
+  float4* sY = reinterpret_cast<float4*>(sB + (size_t)max_tiles<PASS>() * kETileBytes);
+  uint64_t* bfull = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(sY) +
+                                                (PASS == 1 ? (size_t)kEMaxTilesB * kETile * sizeof(float4) : 0));
+  uint64_t* tfull = bfull + max_tiles<PASS>();
+  uint64_t* tempty = tfull + 2;
+  uint64_t* mdone = tempty + 2;
+  uint64_t* yfull = mdone + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(yfull + 1);
+  __shared__ float red[5][kETile];
+  __shared__ volatile int s_fail;
+  __shared__ int s_issued;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntc = (n_cols + kETile - 1) / kETile;           // column tiles of the whole point set
+  const int c0t = blockIdx.y * tpc;
+  const int nt = max(0, min(ntc, c0t + tpc) - c0t);          // >= 1 by the plan
+  const int ncol0 = c0t * kETile;
+  const int nvalid = max(0, min(n_cols, ncol0 + nt * kETile) - ncol0);
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_issued = 0;
+    for (int j = 0; j < nt; ++j) mbar_init(&bfull[j], 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kEWarps);
+    }
+    mbar_init(mdone, 1);
+    mbar_init(yfull, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kETmemCols);
+  // row vectors of the CTA's 128 row points (generic-proxy writes, fenced
+  // for the tensor core's async-proxy reads)
+  const float q = scale_q(st->sigma2);
+  const int row0 = blockIdx.x * kETile;
+  if (threadIdx.x < kETile) {
+    const int r = row0 + threadIdx.x;
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < n_rows) p = Rows4[r];
+    __align__(16) __half v[kAugK];
+    row_vector(q * p.x, q * p.y, q * p.z, r < n_rows, v);
+    store_aug(sA, threadIdx.x, v);
+  }
+  if (PASS == 1)   // padding records of the last tile: zero (their Gaussians are exactly 0)
+    for (int i = nvalid + threadIdx.x; i < nt * kETile; i += blockDim.x) sY[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  if (warp == kEWarps) {
+    if (lane == 0) {
+      // copies of the chunk's column vectors (and, pass B, its scene records)
+      if (PASS == 1 && nvalid > 0) {
+        mbar_expect_tx(yfull, (uint32_t)nvalid * 16u);
+        bulk_load(sY, Yb + ncol0, (uint32_t)nvalid * 16u, yfull);
+      }
+      for (int j = 0; j < nt; ++j) {
+        mbar_expect_tx(&bfull[j], (uint32_t)kETileBytes);
+        bulk_load(sB + (size_t)j * kETileBytes, cols + (size_t)(c0t + j) * kETileBytes, (uint32_t)kETileBytes,
+                  &bfull[j]);
+      }
+      s_issued = nt;
+      // one MMA per column tile, into the accumulator the epilogue released
+      const uint64_t adesc = smem_desc_noswz(saddr(sA), 128, 256);
+      for (int j = 0; j < nt; ++j) {
+        const int b = j & 1;
+        if (s_fail) break;
+        if ((j >= 2 && !mbar_wait(&tempty[b], (uint32_t)((j >> 1) - 1) & 1u, kEWaitNs)) ||
+            !mbar_wait(&bfull[j], 0, kEWaitNs)) {
+          s_fail = 1;
+          break;
+        }
+        fence_after();
+        umma_f16(tmem + (uint32_t)(b * kETile),
+                 adesc, smem_desc_noswz(saddr(sB + (size_t)j * kETileBytes), 128, 256), kEIdesc, 0u);
+        umma_commit(&tfull[b]);
+      }
+      umma_commit(mdone);       // arrives once every MMA issued above has completed
+    }
+  } else {
+    const int quarter = warp & 3, half = warp >> 2;
+    const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+    bool ok = true;
+    if (PASS == 1 && nvalid > 0) ok = warp_wait(yfull, 0);
+    for (int j = 0; j < nt && ok; ++j) {
+      const int b = j & 1;
+      if (!warp_wait(&tfull[b], (uint32_t)(j >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      // the tile's 64 columns of this warp into registers, then the
+      // accumulator goes back to the MMA at once: its next product overlaps
+      // the exponentials below
+      const uint32_t ta = tmem + lanes + (uint32_t)(b * kETile + half * 64);
+      uint32_t e0[32], e1[32];
+      tmem_ld32_nowait(ta, e0);
+      tmem_ld32_nowait(ta + 32u, e1);
+      tmem_wait();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+      const float4* ys = sY + (size_t)j * kETile + half * 64;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        const float e = __uint_as_float(i < 32 ? e0[i] : e1[i - 32]);
+        if (PASS == 0) {
+          acc[i & 3] += ex2_approx(e);
+        } else {
+          const float4 y = ys[i];                     // same address in every lane: broadcast
+          const float w = ex2_approx(e);              // e_mn / den_n
+          acc[0] += w;
+          acc[1] = fmaf(w, y.x, acc[1]);
+          acc[2] = fmaf(w, y.y, acc[2]);
+          acc[3] = fmaf(w, y.z, acc[3]);
+          acc[4] = fmaf(w, y.w - e, acc[4]);          // d'^2 = lid - e
+        }
+      }
+    }
+    if (!ok && lane == 0) s_fail = 1;
+  }
+  if (PASS == 0) acc[0] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  // every MMA has completed (or the CTA gave up) before TMEM is freed
+  const bool ok_done = mbar_wait(mdone, 0, kEWaitNs);
+  __syncthreads();
+  if (!ok_done) s_fail = 1;
+  if (warp < kEWarps && (warp >> 2) == 1) {
+    const int r = (warp & 3) * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < (PASS == 0 ? 1 : 5); ++k) red[k][r] = acc[k];
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ETIMEOUT);
+    if (threadIdx.x == kEWarps * 32) {
+      // copies still landing: wait for them before the CTA's memory is released
+      for (int j = 0; j < s_issued; ++j) mbar_wait(&bfull[j], 0, kEWaitNs);
+      if (PASS == 1 && nvalid > 0 && s_issued > 0) mbar_wait(yfull, 0, kEWaitNs);
+    }
+  } else if (warp < 4) {
+    const int r = warp * 32 + lane, row = row0 + r;
+    if (row < n_rows) {
+      if (PASS == 0) {
+        part[(size_t)blockIdx.y * n_rows + row] = acc[0] + red[0][r];
+      } else {
+        const size_t plane = (size_t)gridDim.y * n_rows, o = (size_t)blockIdx.y * n_rows + row;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) part[o + k * plane] = acc[k] + red[k][r];
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    tmem_dealloc(tmem, kETmemCols);
+  }
+}
+
+// sigma2 floor of the tensor-core passes from the largest point norm R of the
+// model and scene points: the augmented vectors' FP32 accumulation carries
+// terms as large as q^2 R^2, so the passes run while sigma2 >= kMmaS2PerR2 R^2
+// (q^2 R^2 <= ~2000, exponent rounding near 1e-3); the FP32 passes below.
+__global__ void __launch_bounds__(1024) mma_threshold(const float4* __restrict__ X4, int M, const float4* __restrict__ Y4,
+                                                     int N, DevState* __restrict__ st) {
+  __shared__ float sh[32];
+  float r2 = 0.f;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const float4 p = X4[i];
+    r2 = fmaxf(r2, p.x * p.x + p.y * p.y + p.z * p.z);
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float4 p = Y4[i];
+    r2 = fmaxf(r2, p.x * p.x + p.y * p.y + p.z * p.z);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = r2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r2 = fmaxf(r2, sh[w]);
+    r2 = fmaxf(r2, sh[0]);
+    // the deformation moves T by a fraction of the extent: a 25 % margin
+    st->mma_s2min = kMmaS2PerR2 * 1.25 * (double)r2;
+  }
+}
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <int PASS> int pass_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    const int bytes = (int)pass_smem_bytes<PASS>();
+    if (cudaFuncSetAttribute(pass_umma<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      occ = 0;
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_umma<PASS>, kEThreads, bytes);
+    }
+  }
+  return occ;
+}
+
+// Column tiles per chunk: a resident wave costs (tiles per chunk + a fixed
+// per-CTA overhead of two tiles); the cheapest split wins.
+void split_tiles(int64_t row_tiles, int64_t col_tiles, int64_t slots, int max_tpc, int& tpc, int& chunks) {
+  int64_t best = -1;
+  for (int64_t c = cdiv(col_tiles, max_tpc); c <= col_tiles; ++c) {
+    const int64_t t = cdiv(col_tiles, c);
+    const int64_t ch = cdiv(col_tiles, t);
+    const int64_t cost = cdiv(row_tiles * ch, slots) * (t + 2);
+    if (best < 0 || cost < best) {
+      best = cost;
+      tpc = (int)t;
+      chunks = (int)ch;
+    }
+    if (ch * row_tiles > 64 * slots) break;
+  }
+}
+
+}  // namespace
+
+void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
+  const int64_t slotsA = (int64_t)sms * std::max(pass_occupancy<0>(), 1);
+  const int64_t slotsB = (int64_t)sms * std::max(pass_occupancy<1>(), 1);
+  p.a_row_tiles = (int)cdiv(N, kETile);
+  split_tiles(p.a_row_tiles, cdiv(M, kETile), slotsA, kEMaxTilesA, p.a_tpc, p.a_chunks);
+  p.a_rows_per_chunk = p.a_tpc * kETile;
+  p.b_row_tiles = (int)cdiv(M, kETile);
+  split_tiles(p.b_row_tiles, cdiv(N, kETile), slotsB, kEMaxTilesB, p.b_tpc, p.b_chunks);
+  p.b_cols_per_chunk = p.b_tpc * kETile;
+  p.prep_floats = std::max(cdiv(M, kETile), cdiv(N, kETile)) * kETileBytes / 4;
+}
+
+void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s) {
+  mma_threshold<<<1, 1024, 0, s>>>(X4, (int)M, Y4, (int)N, st);
+}
+
+bool estep_mma_supported() { return pass_occupancy<0>() > 0 && pass_occupancy<1>() > 0; }
+
+void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,
+                      float* prep, DevState* st, int gate, cudaStream_t s) {
+  unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
+  const int64_t mpad = cdiv(M, kETile) * kETile;
+  prep_cols<<<(unsigned)cdiv(mpad, 256), 256, 0, s>>>(T4, (int)M, (int)mpad, 0, st, gate, cols);
+  pass_umma<0><<<dim3(p.a_row_tiles, p.a_chunks), kEThreads, pass_smem_bytes<0>(), s>>>(
+      Y4, (int)N, cols, (int)M, nullptr, p.a_tpc, partA, st, gate);
+}
+
+void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Yb, int64_t N, float* partB,
+                      float* prep, DevState* st, int gate, cudaStream_t s) {
+  unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
+  const int64_t npad = cdiv(N, kETile) * kETile;
+  prep_cols<<<(unsigned)cdiv(npad, 256), 256, 0, s>>>(Yb, (int)N, (int)npad, 1, st, gate, cols);
+  pass_umma<1><<<dim3(p.b_row_tiles, p.b_chunks), kEThreads, pass_smem_bytes<1>(), s>>>(
+      T4, (int)M, cols, (int)N, Yb, p.b_tpc, partB, st, gate);
+}
+
+}  // namespace fcpd
