@@ -230,6 +230,7 @@ struct MmaPlan {
 void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p);
 // The tcgen05 passes can run on this device (their shared memory fits).
 bool estep_mma_supported();
+int estep_mma_occupancy(int pass);      // resident CTAs per SM of pass 0 (A) or 1 (B)
 // prep: prep_floats of scratch for the column vectors (in the pass B
 // partials buffer past the partials; unused by pass A's own partials).
 void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float4* Y4, int64_t N, float* partA,

@@ -49,7 +49,6 @@ constexpr int kETileBytes = kETile * 32;    // 128 augmented vectors of 16 FP16 
 constexpr int kEMaxTilesA = 24;             // column tiles per CTA chunk, pass A (96 KB)
 constexpr int kEMaxTilesB = 16;             // pass B (64 KB + 32 KB of scene records)
 constexpr uint32_t kETmemCols = 256;        // two accumulators of 128 columns
-constexpr uint32_t kEIdesc = (1u << 4) | ((uint32_t)(kETile >> 3) << 17) | ((uint32_t)(kETile >> 4) << 24);
 constexpr unsigned long long kEWaitNs = 2000000000ull;
 
 // Byte offset of the 16-byte half h (K values 8h..8h+7) of point r of a tile
@@ -94,19 +93,34 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
 }
 
 template <int PASS> __host__ __device__ constexpr int max_tiles() { return PASS == 0 ? kEMaxTilesA : kEMaxTilesB; }
+// Row tiles per CTA and columns per MMA: pass A one 128-row tile, 128
+// columns; pass B two row tiles (256 model points) and 64 columns, so each
+// scene record an epilogue thread reads from shared memory serves two rows.
+// Either way an accumulator buffer is 128 TMEM columns.
+template <int PASS> __host__ __device__ constexpr int row_tiles() { return PASS == 0 ? 1 : 2; }
+template <int PASS> __host__ __device__ constexpr int mma_cols() { return PASS == 0 ? 128 : 64; }
 template <int PASS> constexpr size_t pass_smem_bytes() {
-  return 1024 + kETileBytes + (size_t)max_tiles<PASS>() * kETileBytes +
+  return 1024 + (size_t)row_tiles<PASS>() * kETileBytes + (size_t)max_tiles<PASS>() * kETileBytes +
          (PASS == 1 ? (size_t)kEMaxTilesB * kETile * sizeof(float4) : 0) + 64 * sizeof(uint64_t);
+}
+__host__ __device__ constexpr uint32_t idesc_m128(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // One pass (PASS 0: A, 1: B).  Rows4: the row points (A: scene Y4, B: model
 // T4), cols: prep_cols output for the column points, Yb (pass B): scene
-// records {q y, lid} read by the epilogue.  Grid: (row tiles, column chunks
-// of `tpc` tiles).  Writes partA[chunk][n] or the five partB planes.
+// records {q y, lid} read by the epilogue.  Grid: (row blocks of
+// 128 row_tiles points, column chunks of `tpc` 128-point tiles).  Writes
+// partA[chunk][n] or the five partB planes.
 template <int PASS>
 __global__ void __launch_bounds__(kEThreads, 2)
 pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __restrict__ cols, int n_cols,
           const float4* __restrict__ Yb, int tpc, float* __restrict__ part, DevState* __restrict__ st, int gate) {
+  constexpr int RT = row_tiles<PASS>();
+  constexpr int NC = mma_cols<PASS>();
+  constexpr int SUB = kETile / NC;                      // MMA column tiles per 128-point operand tile
+  constexpr int WC = NC / 2;                            // columns per epilogue warp per row tile
+  constexpr uint32_t IDESC = idesc_m128(NC);
   if ((gate && iteration_gated(st)) || !mma_active(st)) return;
   if (PASS == 1 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     // the column list was consumed by fixA; the row list is filled after this pass
@@ -114,10 +128,11 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
     st->n_flag_rows = 0;
   }
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned, by an offset from the shared array (an integer round
+  // trip would turn later accesses into generic ones)
+  unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + kETileBytes;
+  unsigned char* sB = smem + (size_t)RT * kETileBytes;
   float4* sY = reinterpret_cast<float4*>(sB + (size_t)max_tiles<PASS>() * kETileBytes);
   uint64_t* bfull = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(sY) +
                                                 (PASS == 1 ? (size_t)kEMaxTilesB * kETile * sizeof(float4) : 0));
@@ -126,7 +141,7 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
   uint64_t* mdone = tempty + 2;
   uint64_t* yfull = mdone + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(yfull + 1);
-  __shared__ float red[5][kETile];
+  __shared__ float red[5][RT * kETile];
   __shared__ volatile int s_fail;
   __shared__ int s_issued;
 
@@ -134,6 +149,7 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
   const int ntc = (n_cols + kETile - 1) / kETile;           // column tiles of the whole point set
   const int c0t = blockIdx.y * tpc;
   const int nt = max(0, min(ntc, c0t + tpc) - c0t);          // >= 1 by the plan
+  const int njt = nt * SUB;                                 // MMA column tiles
   const int ncol0 = c0t * kETile;
   const int nvalid = max(0, min(n_cols, ncol0 + nt * kETile) - ncol0);
 
@@ -150,17 +166,17 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, kETmemCols);
-  // row vectors of the CTA's 128 row points (generic-proxy writes, fenced
-  // for the tensor core's async-proxy reads)
+  // row vectors of the CTA's row points (generic-proxy writes, fenced for
+  // the tensor core's async-proxy reads)
   const float q = scale_q(st->sigma2);
-  const int row0 = blockIdx.x * kETile;
-  if (threadIdx.x < kETile) {
+  const int row0 = blockIdx.x * (RT * kETile);
+  if (threadIdx.x < RT * kETile) {
     const int r = row0 + threadIdx.x;
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
     if (r < n_rows) p = Rows4[r];
     __align__(16) __half v[kAugK];
     row_vector(q * p.x, q * p.y, q * p.z, r < n_rows, v);
-    store_aug(sA, threadIdx.x, v);
+    store_aug(sA + (size_t)(threadIdx.x / kETile) * kETileBytes, threadIdx.x % kETile, v);
   }
   if (PASS == 1)   // padding records of the last tile: zero (their Gaussians are exactly 0)
     for (int i = nvalid + threadIdx.x; i < nt * kETile; i += blockDim.x) sY[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -170,7 +186,11 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  float acc[RT][5];
+#pragma unroll
+  for (int t = 0; t < RT; ++t)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[t][k] = 0.f;
   if (warp == kEWarps) {
     if (lane == 0) {
       // copies of the chunk's column vectors (and, pass B, its scene records)
@@ -184,19 +204,23 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
                   &bfull[j]);
       }
       s_issued = nt;
-      // one MMA per column tile, into the accumulator the epilogue released
-      const uint64_t adesc = smem_desc_noswz(saddr(sA), 128, 256);
-      for (int j = 0; j < nt; ++j) {
+      // per MMA column tile, one MMA per row tile into the accumulator the
+      // epilogue released (row tile t at columns t NC of the buffer)
+      for (int j = 0; j < njt; ++j) {
         const int b = j & 1;
         if (s_fail) break;
         if ((j >= 2 && !mbar_wait(&tempty[b], (uint32_t)((j >> 1) - 1) & 1u, kEWaitNs)) ||
-            !mbar_wait(&bfull[j], 0, kEWaitNs)) {
+            !mbar_wait(&bfull[j / SUB], 0, kEWaitNs)) {
           s_fail = 1;
           break;
         }
         fence_after();
-        umma_f16(tmem + (uint32_t)(b * kETile),
-                 adesc, smem_desc_noswz(saddr(sB + (size_t)j * kETileBytes), 128, 256), kEIdesc, 0u);
+        const uint64_t bdesc = smem_desc_noswz(saddr(sB + (size_t)(j / SUB) * kETileBytes + (j % SUB) * (NC * 32)),
+                                               128, 256);
+#pragma unroll
+        for (int t = 0; t < RT; ++t)
+          umma_f16(tmem + (uint32_t)(b * kETile + t * NC), smem_desc_noswz(saddr(sA + (size_t)t * kETileBytes), 128, 256),
+                   bdesc, IDESC, 0u);
         umma_commit(&tfull[b]);
       }
       umma_commit(mdone);       // arrives once every MMA issued above has completed
@@ -206,52 +230,59 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
     const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
     bool ok = true;
     if (PASS == 1 && nvalid > 0) ok = warp_wait(yfull, 0);
-    for (int j = 0; j < nt && ok; ++j) {
+    for (int j = 0; j < njt && ok; ++j) {
       const int b = j & 1;
       if (!warp_wait(&tfull[b], (uint32_t)(j >> 1) & 1u)) {
         ok = false;
         break;
       }
       fence_after();
-      // the tile's 64 columns of this warp into registers, then the
+      // this warp's columns of every row tile into registers, then the
       // accumulator goes back to the MMA at once: its next product overlaps
       // the exponentials below
-      const uint32_t ta = tmem + lanes + (uint32_t)(b * kETile + half * 64);
+      const uint32_t ta = tmem + lanes + (uint32_t)(b * kETile + half * WC);
       uint32_t e0[32], e1[32];
       tmem_ld32_nowait(ta, e0);
-      tmem_ld32_nowait(ta + 32u, e1);
+      tmem_ld32_nowait(ta + (PASS == 0 ? 32u : (uint32_t)NC), e1);
       tmem_wait();
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[b]);
-      const float4* ys = sY + (size_t)j * kETile + half * 64;
+      if (PASS == 0) {
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
-        const float e = __uint_as_float(i < 32 ? e0[i] : e1[i - 32]);
-        if (PASS == 0) {
-          acc[i & 3] += ex2_approx(e);
-        } else {
+        for (int i = 0; i < 64; ++i) acc[0][i & 3] += ex2_approx(__uint_as_float(i < 32 ? e0[i] : e1[i - 32]));
+      } else {
+        const float4* ys = sY + (size_t)j * NC + half * WC;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
           const float4 y = ys[i];                     // same address in every lane: broadcast
-          const float w = ex2_approx(e);              // e_mn / den_n
-          acc[0] += w;
-          acc[1] = fmaf(w, y.x, acc[1]);
-          acc[2] = fmaf(w, y.y, acc[2]);
-          acc[3] = fmaf(w, y.z, acc[3]);
-          acc[4] = fmaf(w, y.w - e, acc[4]);          // d'^2 = lid - e
+#pragma unroll
+          for (int t = 0; t < RT; ++t) {
+            const float e = __uint_as_float(t == 0 ? e0[i] : e1[i]);
+            const float w = ex2_approx(e);            // e_mn / den_n
+            acc[t][0] += w;
+            acc[t][1] = fmaf(w, y.x, acc[t][1]);
+            acc[t][2] = fmaf(w, y.y, acc[t][2]);
+            acc[t][3] = fmaf(w, y.z, acc[t][3]);
+            acc[t][4] = fmaf(w, y.w - e, acc[t][4]);  // d'^2 = lid - e
+          }
         }
       }
     }
     if (!ok && lane == 0) s_fail = 1;
   }
-  if (PASS == 0) acc[0] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+  if (PASS == 0) acc[0][0] = (acc[0][0] + acc[0][1]) + (acc[0][2] + acc[0][3]);
   // every MMA has completed (or the CTA gave up) before TMEM is freed
   const bool ok_done = mbar_wait(mdone, 0, kEWaitNs);
   __syncthreads();
   if (!ok_done) s_fail = 1;
   if (warp < kEWarps && (warp >> 2) == 1) {
-    const int r = (warp & 3) * 32 + lane;
 #pragma unroll
-    for (int k = 0; k < (PASS == 0 ? 1 : 5); ++k) red[k][r] = acc[k];
+    for (int t = 0; t < RT; ++t) {
+      const int r = t * kETile + (warp & 3) * 32 + lane;
+#pragma unroll
+      for (int k = 0; k < (PASS == 0 ? 1 : 5); ++k) red[k][r] = acc[t][k];
+    }
   }
   __syncthreads();
   if (s_fail) {
@@ -262,14 +293,17 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
       if (PASS == 1 && nvalid > 0 && s_issued > 0) mbar_wait(yfull, 0, kEWaitNs);
     }
   } else if (warp < 4) {
-    const int r = warp * 32 + lane, row = row0 + r;
-    if (row < n_rows) {
-      if (PASS == 0) {
-        part[(size_t)blockIdx.y * n_rows + row] = acc[0] + red[0][r];
-      } else {
-        const size_t plane = (size_t)gridDim.y * n_rows, o = (size_t)blockIdx.y * n_rows + row;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) part[o + k * plane] = acc[k] + red[k][r];
+    for (int t = 0; t < RT; ++t) {
+      const int r = t * kETile + warp * 32 + lane, row = row0 + r;
+      if (row < n_rows) {
+        if (PASS == 0) {
+          part[(size_t)blockIdx.y * n_rows + row] = acc[0][0] + red[0][r];
+        } else {
+          const size_t plane = (size_t)gridDim.y * n_rows, o = (size_t)blockIdx.y * n_rows + row;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) part[o + k * plane] = acc[t][k] + red[k][r];
+        }
       }
     }
   }
@@ -311,47 +345,63 @@ __global__ void __launch_bounds__(1024) mma_threshold(const float4* __restrict__
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Resident CTAs per SM from the kernel's registers and shared memory (the
+// occupancy query reported one CTA where two are resident on GB300, so the
+// count is taken from the resources themselves; 0 if the shared memory does
+// not fit at all).
 template <int PASS> int pass_occupancy() {
   static int occ = -1;
   if (occ < 0) {
+    occ = 0;
     const int bytes = (int)pass_smem_bytes<PASS>();
-    if (cudaFuncSetAttribute(pass_umma<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      occ = 0;
-    } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_umma<PASS>, kEThreads, bytes);
+    cudaFuncAttributes a;
+    int dev = 0, smem_sm = 0, regs_sm = 0, resv = 0;
+    if (cudaFuncSetAttribute(pass_umma<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess &&
+        cudaFuncSetAttribute(pass_umma<PASS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) == cudaSuccess &&
+        cudaFuncGetAttributes(&a, pass_umma<PASS>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+      const int warps = (kEThreads + 31) / 32;
+      const int regs_warp = (a.numRegs * 32 + 255) / 256 * 256;
+      const int by_regs = regs_sm / std::max(1, regs_warp * warps);
+      const int by_smem = smem_sm / std::max(1, (int)a.sharedSizeBytes + bytes + resv);
+      occ = std::max(0, std::min(by_regs, by_smem));
     }
+    cudaGetLastError();
   }
   return occ;
 }
 
-// Column tiles per chunk: a resident wave costs (tiles per chunk + a fixed
-// per-CTA overhead of two tiles); the cheapest split wins.
-void split_tiles(int64_t row_tiles, int64_t col_tiles, int64_t slots, int max_tpc, int& tpc, int& chunks) {
+// Column tiles per chunk.  The passes are bound by each SM's issue and
+// exponential rate, so the cost of a split is the CTAs on the busiest SM
+// times (tiles per CTA + a fixed per-CTA overhead of two tiles); ties go to
+// more CTAs (more warps per SM to hide latency).
+void split_tiles(int64_t row_tiles, int64_t col_tiles, int64_t sms, int max_tpc, int& tpc, int& chunks) {
   int64_t best = -1;
   for (int64_t c = cdiv(col_tiles, max_tpc); c <= col_tiles; ++c) {
     const int64_t t = cdiv(col_tiles, c);
     const int64_t ch = cdiv(col_tiles, t);
-    const int64_t cost = cdiv(row_tiles * ch, slots) * (t + 2);
-    if (best < 0 || cost < best) {
+    const int64_t cost = cdiv(row_tiles * ch, sms) * (t + 2);
+    if (best < 0 || cost <= best) {
+      if (cost == best && ch <= chunks) continue;
       best = cost;
       tpc = (int)t;
       chunks = (int)ch;
     }
-    if (ch * row_tiles > 64 * slots) break;
+    if (ch * row_tiles > 64 * sms) break;
   }
 }
 
 }  // namespace
 
 void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
-  const int64_t slotsA = (int64_t)sms * std::max(pass_occupancy<0>(), 1);
-  const int64_t slotsB = (int64_t)sms * std::max(pass_occupancy<1>(), 1);
   p.a_row_tiles = (int)cdiv(N, kETile);
-  split_tiles(p.a_row_tiles, cdiv(M, kETile), slotsA, kEMaxTilesA, p.a_tpc, p.a_chunks);
+  split_tiles(p.a_row_tiles, cdiv(M, kETile), sms, kEMaxTilesA, p.a_tpc, p.a_chunks);
   p.a_rows_per_chunk = p.a_tpc * kETile;
-  p.b_row_tiles = (int)cdiv(M, kETile);
-  split_tiles(p.b_row_tiles, cdiv(N, kETile), slotsB, kEMaxTilesB, p.b_tpc, p.b_chunks);
+  p.b_row_tiles = (int)cdiv(M, row_tiles<1>() * kETile);
+  split_tiles(p.b_row_tiles, cdiv(N, kETile), sms, kEMaxTilesB, p.b_tpc, p.b_chunks);
   p.b_cols_per_chunk = p.b_tpc * kETile;
   p.prep_floats = std::max(cdiv(M, kETile), cdiv(N, kETile)) * kETileBytes / 4;
 }
@@ -359,6 +409,8 @@ void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
 void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s) {
   mma_threshold<<<1, 1024, 0, s>>>(X4, (int)M, Y4, (int)N, st);
 }
+
+int estep_mma_occupancy(int pass) { return pass == 0 ? pass_occupancy<0>() : pass_occupancy<1>(); }
 
 bool estep_mma_supported() { return pass_occupancy<0>() > 0 && pass_occupancy<1>() > 0; }
 

@@ -79,8 +79,9 @@ umma_products(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
   constexpr uint32_t COLS = tmem_cols(NPAD);
   constexpr uint32_t IDESC = idesc_f16_m128(NPAD);
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned, by an offset from the shared array (an integer round
+  // trip would turn later accesses into generic ones)
+  unsigned char* smem = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kUStages * STAGE);
   uint64_t* empty = full + kUStages;
   uint64_t* done = empty + kUStages;
@@ -249,7 +250,9 @@ bool make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t cols, 
 
 template <int NPAD> int umma_occupancy() {
   const int bytes = (int)umma_smem_bytes<NPAD>();
-  if (cudaFuncSetAttribute(umma_products<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+  if (cudaFuncSetAttribute(umma_products<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+      cudaFuncSetAttribute(umma_products<NPAD>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
