@@ -20,7 +20,6 @@
 #include <stdint.h>
 
 #include <string>
-#include <utility>
 #include <vector>
 
 // Pointer qualifier of the device bodies' arguments.  A translation unit whose
@@ -123,17 +122,6 @@ __device__ __forceinline__ bool prune_active(const DevState* st) {
   if (c & kPruneAlways) return true;
   const double r2 = 127.0 * 2.0 * st->sigma2 / 1.4426950408889634;   // 127 / kappa, kappa = log2(e) / (2 sigma2)
   return r2 < (double)st->prune_r2;
-}
-
-// Programmatic dependent launch (sm_90+): the per-iteration kernels are
-// launched with programmatic stream serialisation, so a kernel's CTAs are
-// scheduled while its predecessor drains instead of after it; each such
-// kernel first waits for its predecessor's completion and memory
-// (griddepcontrol.wait, a no-op without the attribute), then lets its own
-// successor launch.  Must be the first statement of the kernel.
-__device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // True when the current iteration must not run (target reached, converged,
@@ -352,23 +340,6 @@ cudaError_t launch_batch(const BatchPair* pairs_dev, int n_pairs, const BatchIte
 // Copies every pair's device state into out[0..n_pairs).
 void launch_batch_states(const BatchPair* pairs_dev, int n_pairs, DevState* out, cudaStream_t s);
 
-
-// Launch with programmatic stream serialisation (see pdl_entry).
-template <typename... KArgs, typename... Args>
-inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                       Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
-}
 
 // Optional `ev` arrays: an event is recorded (as an external event-record
 // node when captured) after each kernel: 4 for the E-step (pass A, its

@@ -17,7 +17,6 @@ using namespace dev;
 __global__ void __launch_bounds__(kThreadsA)
 passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
           int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   if (prune_active(st) || mma_active(st)) return;
   dev::passA_f32_body(T4, M, rows_per_chunk, Y4, N, partA, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
@@ -25,7 +24,6 @@ passA_f32(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4
 __global__ void __launch_bounds__(kThreadsA)
 passA_f32_pruned(const float4* __restrict__ T4, int M, int rows_per_chunk, const float4* __restrict__ Y4,
                  int N, float* __restrict__ partA, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   if ((gate && iteration_gated(st)) || !prune_active(st)) return;
   dev::passA_f32_pruned_body(T4, M, rows_per_chunk, Y4, N, partA, st, blockIdx.x, blockIdx.y);
 }
@@ -33,7 +31,6 @@ passA_f32_pruned(const float4* __restrict__ T4, int M, int rows_per_chunk, const
 __global__ void __launch_bounds__(kThreadsA)
 passA_f64(const dvec4* __restrict__ T4, int M, int rows_per_chunk, const dvec4* __restrict__ Y4,
           int N, double* __restrict__ partA, const DevState* __restrict__ st, int gate) {
-  pdl_entry();
   dev::passA_f64_body(T4, M, rows_per_chunk, Y4, N, partA, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -43,7 +40,6 @@ __global__ void __launch_bounds__(kThreadsR)
 reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ Y4,
         int N, typename Vec<F>::t4* __restrict__ Yb, double* __restrict__ den_out,
         double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
   dev::reduceA_body<F>(partA, ch, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
@@ -52,14 +48,12 @@ __global__ void __launch_bounds__(kThreadsF)
 fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, int N,
          float4* __restrict__ Yb, double* __restrict__ den_out, const int* __restrict__ flag_cols,
          DevState* __restrict__ st, int gate) {
-  pdl_entry();
   dev::fixA_f32_body(T4, M, Y4, N, Yb, den_out, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
 __global__ void __launch_bounds__(kThreadsB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
           int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   if (prune_active(st) || mma_active(st)) return;
   dev::passB_f32_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
@@ -67,7 +61,6 @@ passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, i
 __global__ void __launch_bounds__(kThreadsB)
 passB_f32_pruned(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
                  int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   if ((gate && iteration_gated(st)) || !prune_active(st)) return;
   dev::passB_f32_pruned_body(T4, M, Yb, N, cols_per_chunk, partB, st, blockIdx.x, blockIdx.y, gridDim.y);
 }
@@ -75,7 +68,6 @@ passB_f32_pruned(const float4* __restrict__ T4, int M, const float4* __restrict_
 __global__ void __launch_bounds__(kThreadsB)
 passB_f64(const dvec4* __restrict__ T4, int M, const dvec4* __restrict__ Yb, int N,
           int cols_per_chunk, double* __restrict__ partB, const DevState* __restrict__ st, int gate) {
-  pdl_entry();
   dev::passB_f64_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
 
@@ -85,7 +77,6 @@ reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int chunks_m
         typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
         double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
         DevState* __restrict__ st, int gate) {
-  pdl_entry();
   const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
   dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
@@ -94,7 +85,6 @@ __global__ void __launch_bounds__(kThreadsF)
 fixB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
          const float4* __restrict__ X4, float4* __restrict__ Yt4, float4* __restrict__ R4,
          double* __restrict__ P1_out, const int* __restrict__ flag_rows, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   // the E-step's last launch also takes the iteration's spectral-trim
   // decision for the M-step that follows (sigma2 is the same in both)
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !(gate && iteration_gated(st)))
@@ -190,35 +180,35 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   int* flag_rows = flags;
   int* flag_cols = flags + M;
   if constexpr (sizeof(F) == 4) {
-    launch_pdl(passA_f32, dim3(ga), dim3(kThreadsA), 0, s, T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
+    passA_f32<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
     if (pl.pruned)
-      launch_pdl(passA_f32_pruned, dim3(dim3(pl.pa_col_tiles, pl.pa_row_chunks)), dim3(kThreadsA), 0, s, 
+      passA_f32_pruned<<<dim3(pl.pa_col_tiles, pl.pa_row_chunks), kThreadsA, 0, s>>>(
           T4, (int)M, pl.pa_rows_per_chunk, Y4, (int)N, partA, st, g);
     if (pl.mma) launch_passA_mma(pl.mm, T4, M, Y4, N, partA, partB + pl.mm.prep_off, st, g, s);
   } else {
-    launch_pdl(passA_f64, dim3(ga), dim3(kThreadsA), 0, s, T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
+    passA_f64<<<ga, kThreadsA, 0, s>>>(T4, (int)M, pl.a_rows_per_chunk, Y4, (int)N, partA, st, g);
   }
   record_after(ev, 0, s);
-  launch_pdl(reduceA<F>, dim3((unsigned)pl.redA_blocks), dim3(kThreadsR), 0, s, partA, pl.a_row_chunks, pl.pa_row_chunks, pl.mm.a_chunks, (int)M, Y4,
+  reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, pl.mm.a_chunks, (int)M, Y4,
                                                             (int)N, Yb, den_out, sums, flag_cols, st, g);
   if constexpr (sizeof(F) == 4) {
-    launch_pdl(fixA_f32, dim3(304), dim3(kThreadsF), 0, s, T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
+    fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
   }
   record_after(ev, 1, s);
   if constexpr (sizeof(F) == 4) {
-    launch_pdl(passB_f32, dim3(gb), dim3(kThreadsB), 0, s, T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+    passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
     if (pl.pruned)
-      launch_pdl(passB_f32_pruned, dim3(dim3(pl.pb_row_tiles, pl.pb_col_chunks)), dim3(kThreadsB), 0, s, 
+      passB_f32_pruned<<<dim3(pl.pb_row_tiles, pl.pb_col_chunks), kThreadsB, 0, s>>>(
           T4, (int)M, Yb, (int)N, pl.pb_cols_per_chunk, partB, st, g);
     if (pl.mma) launch_passB_mma(pl.mm, T4, M, Yb, N, partB, partB + pl.mm.prep_off, st, g, s);
   } else {
-    launch_pdl(passB_f64, dim3(gb), dim3(kThreadsB), 0, s, T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+    passB_f64<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
   }
   record_after(ev, 2, s);
-  launch_pdl(reduceB<F>, dim3((unsigned)pl.redB_blocks), dim3(kThreadsR), 0, s, partB, pl.b_col_chunks, pl.pb_col_chunks, pl.mm.b_chunks, (int)M, X4,
+  reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, pl.mm.b_chunks, (int)M, X4,
                                                             Yt4, R4, P1_out, sums, flag_rows, st, g);
   if constexpr (sizeof(F) == 4) {
-    launch_pdl(fixB_f32, dim3(304), dim3(kThreadsF), 0, s, T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
+    fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
   }
   record_after(ev, 3, s);
 }

@@ -68,7 +68,6 @@ __device__ __forceinline__ void store_aug(unsigned char* tile, int r, const __ha
 __global__ void __launch_bounds__(256)
 prep_cols(const float4* __restrict__ P4, int n, int n_pad, int scene, DevState* __restrict__ st, int gate,
           unsigned char* __restrict__ out) {
-  pdl_entry();
   if ((gate && iteration_gated(st)) || !mma_active(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
@@ -117,7 +116,6 @@ template <int PASS>
 __global__ void __launch_bounds__(kEThreads, 2)
 pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __restrict__ cols, int n_cols,
           const float4* __restrict__ Yb, int tpc, float* __restrict__ part, DevState* __restrict__ st, int gate) {
-  pdl_entry();
   constexpr int RT = row_tiles<PASS>();
   constexpr int NC = mma_cols<PASS>();
   constexpr int SUB = kETile / NC;                      // MMA column tiles per 128-point operand tile
@@ -420,8 +418,8 @@ void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float
                       float* prep, DevState* st, int gate, cudaStream_t s) {
   unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
   const int64_t mpad = cdiv(M, kETile) * kETile;
-  launch_pdl(prep_cols, dim3((unsigned)cdiv(mpad, 256)), dim3(256), 0, s, T4, (int)M, (int)mpad, 0, st, gate, cols);
-  launch_pdl(pass_umma<0>, dim3(p.a_row_tiles, p.a_chunks), dim3(kEThreads), pass_smem_bytes<0>(), s, 
+  prep_cols<<<(unsigned)cdiv(mpad, 256), 256, 0, s>>>(T4, (int)M, (int)mpad, 0, st, gate, cols);
+  pass_umma<0><<<dim3(p.a_row_tiles, p.a_chunks), kEThreads, pass_smem_bytes<0>(), s>>>(
       Y4, (int)N, cols, (int)M, nullptr, p.a_tpc, partA, st, gate);
 }
 
@@ -429,8 +427,8 @@ void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float
                       float* prep, DevState* st, int gate, cudaStream_t s) {
   unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
   const int64_t npad = cdiv(N, kETile) * kETile;
-  launch_pdl(prep_cols, dim3((unsigned)cdiv(npad, 256)), dim3(256), 0, s, Yb, (int)N, (int)npad, 1, st, gate, cols);
-  launch_pdl(pass_umma<1>, dim3(p.b_row_tiles, p.b_chunks), dim3(kEThreads), pass_smem_bytes<1>(), s, 
+  prep_cols<<<(unsigned)cdiv(npad, 256), 256, 0, s>>>(Yb, (int)N, (int)npad, 1, st, gate, cols);
+  pass_umma<1><<<dim3(p.b_row_tiles, p.b_chunks), kEThreads, pass_smem_bytes<1>(), s>>>(
       T4, (int)M, cols, (int)N, Yb, p.b_tpc, partB, st, gate);
 }
 

@@ -25,7 +25,6 @@ __global__ void __launch_bounds__(kThreadsP)
 colsum(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
        int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
        int clear_row_flags, int trim) {
-  pdl_entry();
   if (trim_skip(st, trim)) return;
   dev::colsum_body<F, S, kThreadsP>(A, ldA, rows, cols, V, rows_per_chunk, part, ldP, st, gate, clear_row_flags, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
 }
@@ -127,7 +126,6 @@ __global__ void __launch_bounds__(BulkGeom<S>::THREADS)
 colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const typename Vec<F>::t4* __restrict__ V,
             int rows_per_chunk, F* __restrict__ part, int64_t ldP, DevState* __restrict__ st, int gate,
             int clear_row_flags, int trim) {
-  pdl_entry();
   if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
   if (clear_row_flags && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->n_flag_rows = 0;
   using G = BulkGeom<S>;
@@ -250,7 +248,6 @@ __global__ void __launch_bounds__(kThreadsD)
 diag_update(const F* __restrict__ partP, int chunks, int64_t ldP, int K, int k_zero, const double* __restrict__ lam,
             typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
             const DevState* __restrict__ st, int gate, int trim) {
-  pdl_entry();
   if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
   dev::diag_update_body<F>(partP, chunks, ldP, K, lam, B4, C4, st, 0, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
   const int k = blockIdx.x * kMRedCols + threadIdx.x;
@@ -270,7 +267,6 @@ expand_finish(const F* __restrict__ partE, int chunks, int64_t ldM, int M,
               const typename Vec<F>::t4* __restrict__ X4, const typename Vec<F>::t4* __restrict__ Yt4,
               typename Vec<F>::t4* __restrict__ Tout, const typename Vec<F>::t4* __restrict__ Yhat4,
               double* __restrict__ sums, DevState* __restrict__ st, int gate, int trim) {
-  pdl_entry();
   if (trim_skip(st, trim)) return;
   const bool last = dev::expand_finish_body<F, EPI>(partE, chunks, ldM, M, X4, Yt4, Tout, Yhat4, sums, st, gate,
                                                     blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
@@ -384,10 +380,10 @@ void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA,
   const dim3 grid = expansion ? dim3(pl.e_col_tiles, pl.e_row_chunks) : dim3(pl.p_col_tiles, pl.p_row_chunks);
   const int rpc = expansion ? pl.e_rows_per_chunk : pl.p_rows_per_chunk;
   if (pl.bulk && !std::is_same<F, double>::value)
-    launch_pdl(colsum_bulk<F, S>, grid, dim3(BulkGeom<S>::THREADS), bulk_smem_bytes<F, S>(), s, 
+    colsum_bulk<F, S><<<grid, BulkGeom<S>::THREADS, bulk_smem_bytes<F, S>(), s>>>(
         A, ldA, (int)rows, (int)cols, V, rpc, part, ldP, st, gate, clear_row_flags, trim);
   else
-    launch_pdl(colsum<F, S>, grid, dim3(kThreadsP), 0, s, A, ldA, (int)rows, (int)cols, V, rpc, part, ldP, st, gate,
+    colsum<F, S><<<grid, kThreadsP, 0, s>>>(A, ldA, (int)rows, (int)cols, V, rpc, part, ldP, st, gate,
                                             clear_row_flags, trim);
 }
 
@@ -406,9 +402,9 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
   launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
   record_after(ev, 0, s);
   if (tr)
-    launch_pdl(diag_update<F>, dim3(dblocks), dim3(kThreadsD), 0, s, part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4,
+    diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4,
                                                  st, g, 2);
-  launch_pdl(diag_update<F>, dim3(dblocks), dim3(kThreadsD), 0, s, part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g,
+  diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g,
                                                mf);
   record_after(ev, 1, s);
   if (tr) launch_colsum<F, S>(*tr, true, Ut, tr->ldM, tr->ldM, tr->K, M, B4, part, st, g, 0, 2, s);
@@ -416,12 +412,12 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
   record_after(ev, 2, s);
   if (iteration) {
     if (tr)
-      launch_pdl(expand_finish<F, true>, dim3(tr->e_blocks), dim3(kThreadsD), 0, s, part, tr->e_row_chunks, tr->ldM, (int)M, X4, Yt4,
+      expand_finish<F, true><<<tr->e_blocks, kThreadsD, 0, s>>>(part, tr->e_row_chunks, tr->ldM, (int)M, X4, Yt4,
                                                                 T4, Yhat4, sums, st, g, 2);
-    launch_pdl(expand_finish<F, true>, dim3(pl.e_blocks), dim3(kThreadsD), 0, s, part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
+    expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
                                                              Yhat4, sums, st, g, mf);
   } else {
-    launch_pdl(expand_finish<F, false>, dim3(pl.e_blocks), dim3(kThreadsD), 0, s, part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
+    expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
                                                               T4, nullptr, sums, st, 0, 0);
   }
   record_after(ev, 3, s);
@@ -431,7 +427,7 @@ template <typename F, typename S>
 void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const typename Vec<F>::t4* C4, F* part,
               typename Vec<F>::t4* W4, DevState* st, cudaStream_t s) {
   launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, C4, part, st, 0, 0, 0, s);
-  launch_pdl(expand_finish<F, false>, dim3(pl.e_blocks), dim3(kThreadsD), 0, s, part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
+  expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, nullptr,
                                                             nullptr, W4, nullptr, nullptr, st, 0, 0);
 }
 
