@@ -64,10 +64,12 @@ __device__ __forceinline__ void store_aug(unsigned char* tile, int r, const __ha
 // Column vectors of all points, tile by tile (n_pad = points rounded up to
 // 128; points >= n are padding with Gaussians exactly 0).  scene = 0: model
 // points T4 (scaled by q here, lid 0, pass A); scene = 1: scene records Yb
-// (already {q y, lid}, pass B).
+// (already {q y, lid}, pass B), which are also copied to `rec` pair by pair
+// for pass B's packed epilogue: points 2p, 2p+1 as {x x', y y'} {z z', l l'}
+// (zero for padding).
 __global__ void __launch_bounds__(256)
 prep_cols(const float4* __restrict__ P4, int n, int n_pad, int scene, DevState* __restrict__ st, int gate,
-          unsigned char* __restrict__ out) {
+          unsigned char* __restrict__ out, float* __restrict__ rec) {
   if ((gate && iteration_gated(st)) || !mma_active(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
@@ -82,6 +84,13 @@ prep_cols(const float4* __restrict__ P4, int n, int n_pad, int scene, DevState* 
   __align__(16) __half v[kAugK];
   col_vector(x, y, z, lid, valid, v);
   store_aug(out + (size_t)(i / kETile) * kETileBytes, i % kETile, v);
+  if (rec) {
+    float* r = rec + (size_t)(i >> 1) * 8 + (i & 1);
+    r[0] = valid ? x : 0.f;
+    r[2] = valid ? y : 0.f;
+    r[4] = valid ? z : 0.f;
+    r[6] = valid ? lid : 0.f;
+  }
 }
 
 // Bounded wait made uniform across a warp (the tcgen05.ld that follows is
@@ -108,14 +117,14 @@ __host__ __device__ constexpr uint32_t idesc_m128(int n) {
 }
 
 // One pass (PASS 0: A, 1: B).  Rows4: the row points (A: scene Y4, B: model
-// T4), cols: prep_cols output for the column points, Yb (pass B): scene
-// records {q y, lid} read by the epilogue.  Grid: (row blocks of
+// T4), cols: prep_cols output for the column points, recs (pass B): the
+// scene records paired by prep_cols, read by the epilogue.  Grid: (row blocks of
 // 128 row_tiles points, column chunks of `tpc` 128-point tiles).  Writes
 // partA[chunk][n] or the five partB planes.
 template <int PASS>
 __global__ void __launch_bounds__(kEThreads, 2)
 pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __restrict__ cols, int n_cols,
-          const float4* __restrict__ Yb, int tpc, float* __restrict__ part, DevState* __restrict__ st, int gate) {
+          const float4* __restrict__ recs, int tpc, float* __restrict__ part, DevState* __restrict__ st, int gate) {
   constexpr int RT = row_tiles<PASS>();
   constexpr int NC = mma_cols<PASS>();
   constexpr int SUB = kETile / NC;                      // MMA column tiles per 128-point operand tile
@@ -178,25 +187,23 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
     row_vector(q * p.x, q * p.y, q * p.z, r < n_rows, v);
     store_aug(sA + (size_t)(threadIdx.x / kETile) * kETileBytes, threadIdx.x % kETile, v);
   }
-  if (PASS == 1)   // padding records of the last tile: zero (their Gaussians are exactly 0)
-    for (int i = nvalid + threadIdx.x; i < nt * kETile; i += blockDim.x) sY[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  float acc[RT][5];
+  f2_t acc2[RT][5];      // packed sums over even / odd columns
 #pragma unroll
   for (int t = 0; t < RT; ++t)
 #pragma unroll
-    for (int k = 0; k < 5; ++k) acc[t][k] = 0.f;
+    for (int k = 0; k < 5; ++k) acc2[t][k] = f2_pack(0.f, 0.f);
   if (warp == kEWarps) {
     if (lane == 0) {
       // copies of the chunk's column vectors (and, pass B, its scene records)
-      if (PASS == 1 && nvalid > 0) {
-        mbar_expect_tx(yfull, (uint32_t)nvalid * 16u);
-        bulk_load(sY, Yb + ncol0, (uint32_t)nvalid * 16u, yfull);
+      if (PASS == 1 && nvalid > 0) {   // whole tiles: the padding records are zero
+        mbar_expect_tx(yfull, (uint32_t)nt * kETile * 16u);
+        bulk_load(sY, recs + ncol0, (uint32_t)nt * kETile * 16u, yfull);
       }
       for (int j = 0; j < nt; ++j) {
         mbar_expect_tx(&bfull[j], (uint32_t)kETileBytes);
@@ -237,41 +244,73 @@ pass_umma(const float4* __restrict__ Rows4, int n_rows, const unsigned char* __r
         break;
       }
       fence_after();
-      // this warp's columns of every row tile into registers, then the
-      // accumulator goes back to the MMA at once: its next product overlaps
-      // the exponentials below
       const uint32_t ta = tmem + lanes + (uint32_t)(b * kETile + half * WC);
-      uint32_t e0[32], e1[32];
-      tmem_ld32_nowait(ta, e0);
-      tmem_ld32_nowait(ta + (PASS == 0 ? 32u : (uint32_t)NC), e1);
-      tmem_wait();
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
       if (PASS == 0) {
+        // this warp's 64 columns into registers, the accumulator back to the
+        // MMA at once, then column pairs on packed FP32 (one add per two
+        // Gaussians)
+        uint32_t e0[32], e1[32];
+        tmem_ld32_nowait(ta, e0);
+        tmem_ld32_nowait(ta + 32u, e1);
+        tmem_wait();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
-        for (int i = 0; i < 64; ++i) acc[0][i & 3] += ex2_approx(__uint_as_float(i < 32 ? e0[i] : e1[i - 32]));
+        for (int i = 0; i < 64; i += 2) {
+          const float ea = __uint_as_float(i < 32 ? e0[i] : e1[i - 32]);
+          const float eb = __uint_as_float(i < 32 ? e0[i + 1] : e1[i - 31]);
+          acc2[0][(i >> 1) & 1] = f2_add(acc2[0][(i >> 1) & 1], f2_pack(ex2_approx(ea), ex2_approx(eb)));
+        }
       } else {
-        const float4* ys = sY + (size_t)j * NC + half * WC;
+        // 16 columns of both row tiles at a time (the other accumulator keeps
+        // the MMA busy meanwhile), column pairs on packed FP32; every record
+        // pair (two 16-byte broadcasts) serves both rows of the thread
+        const ulonglong2* ys2 = reinterpret_cast<const ulonglong2*>(sY) + (size_t)j * NC + half * WC;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float4 y = ys[i];                     // same address in every lane: broadcast
+        for (int c = 0; c < WC / 16; ++c) {
+          uint32_t e0[16], e1[16];
+          tmem_ld16_nowait(ta + (uint32_t)(c * 16), e0);
+          tmem_ld16_nowait(ta + (uint32_t)(NC + c * 16), e1);
+          tmem_wait();
 #pragma unroll
-          for (int t = 0; t < RT; ++t) {
-            const float e = __uint_as_float(t == 0 ? e0[i] : e1[i]);
-            const float w = ex2_approx(e);            // e_mn / den_n
-            acc[t][0] += w;
-            acc[t][1] = fmaf(w, y.x, acc[t][1]);
-            acc[t][2] = fmaf(w, y.y, acc[t][2]);
-            acc[t][3] = fmaf(w, y.z, acc[t][3]);
-            acc[t][4] = fmaf(w, y.w - e, acc[t][4]);  // d'^2 = lid - e
+          for (int i = 0; i < 16; i += 2) {
+            const ulonglong2 a = ys2[c * 16 + i], cc = ys2[c * 16 + i + 1];   // {x x', y y'}, {z z', l l'}
+#pragma unroll
+            for (int t = 0; t < RT; ++t) {
+              const float ea = __uint_as_float(t == 0 ? e0[i] : e1[i]);
+              const float eb = __uint_as_float(t == 0 ? e0[i + 1] : e1[i + 1]);
+              const f2_t w = f2_pack(ex2_approx(ea), ex2_approx(eb));   // e_mn / den_n
+              acc2[t][0] = f2_add(acc2[t][0], w);
+              acc2[t][1] = f2_fma(w, a.x, acc2[t][1]);
+              acc2[t][2] = f2_fma(w, a.y, acc2[t][2]);
+              acc2[t][3] = f2_fma(w, cc.x, acc2[t][3]);
+              acc2[t][4] = f2_fma(w, f2_sub(cc.y, f2_pack(ea, eb)), acc2[t][4]);   // d'^2 = lid - e
+            }
           }
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
       }
     }
     if (!ok && lane == 0) s_fail = 1;
   }
-  if (PASS == 0) acc[0][0] = (acc[0][0] + acc[0][1]) + (acc[0][2] + acc[0][3]);
+  float acc[RT][5];
+#pragma unroll
+  for (int t = 0; t < RT; ++t)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      float lo, hi;
+      f2_unpack(acc2[t][k], lo, hi);
+      acc[t][k] = lo + hi;
+    }
+  if (PASS == 0) {
+    float a0, a1, b0, b1;
+    f2_unpack(acc2[0][0], a0, a1);
+    f2_unpack(acc2[0][1], b0, b1);
+    acc[0][0] = (a0 + a1) + (b0 + b1);
+  }
   // every MMA has completed (or the CTA gave up) before TMEM is freed
   const bool ok_done = mbar_wait(mdone, 0, kEWaitNs);
   __syncthreads();
@@ -403,7 +442,9 @@ void plan_estep_mma(int64_t M, int64_t N, int sms, MmaPlan& p) {
   p.b_row_tiles = (int)cdiv(M, row_tiles<1>() * kETile);
   split_tiles(p.b_row_tiles, cdiv(N, kETile), sms, kEMaxTilesB, p.b_tpc, p.b_chunks);
   p.b_cols_per_chunk = p.b_tpc * kETile;
-  p.prep_floats = std::max(cdiv(M, kETile), cdiv(N, kETile)) * kETileBytes / 4;
+  // column vectors (32 bytes per point) of either pass, and pass B's paired
+  // scene records (16 bytes per point) after its vectors
+  p.prep_floats = std::max(cdiv(M, kETile) * kETile * 8, cdiv(N, kETile) * kETile * 12);
 }
 
 void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s) {
@@ -418,7 +459,7 @@ void launch_passA_mma(const MmaPlan& p, const float4* T4, int64_t M, const float
                       float* prep, DevState* st, int gate, cudaStream_t s) {
   unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
   const int64_t mpad = cdiv(M, kETile) * kETile;
-  prep_cols<<<(unsigned)cdiv(mpad, 256), 256, 0, s>>>(T4, (int)M, (int)mpad, 0, st, gate, cols);
+  prep_cols<<<(unsigned)cdiv(mpad, 256), 256, 0, s>>>(T4, (int)M, (int)mpad, 0, st, gate, cols, nullptr);
   pass_umma<0><<<dim3(p.a_row_tiles, p.a_chunks), kEThreads, pass_smem_bytes<0>(), s>>>(
       Y4, (int)N, cols, (int)M, nullptr, p.a_tpc, partA, st, gate);
 }
@@ -427,9 +468,10 @@ void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float
                       float* prep, DevState* st, int gate, cudaStream_t s) {
   unsigned char* cols = reinterpret_cast<unsigned char*>(prep);
   const int64_t npad = cdiv(N, kETile) * kETile;
-  prep_cols<<<(unsigned)cdiv(npad, 256), 256, 0, s>>>(Yb, (int)N, (int)npad, 1, st, gate, cols);
+  float* rec = prep + npad * 8;            // past the column vectors (32 bytes per point)
+  prep_cols<<<(unsigned)cdiv(npad, 256), 256, 0, s>>>(Yb, (int)N, (int)npad, 1, st, gate, cols, rec);
   pass_umma<1><<<dim3(p.b_row_tiles, p.b_chunks), kEThreads, pass_smem_bytes<1>(), s>>>(
-      T4, (int)M, cols, (int)N, Yb, p.b_tpc, partB, st, gate);
+      T4, (int)M, cols, (int)N, reinterpret_cast<const float4*>(rec), p.b_tpc, partB, st, gate);
 }
 
 }  // namespace fcpd
