@@ -65,8 +65,8 @@ def parse():
                     help="register up to this many scenes (deformations of the workload's model) against one "
                          "CPD_MIXED model with cpd_iterate_shared (tensor-core products), in groups of 8, 16 and "
                          "32, against the same scenes one at a time (0 skips it)")
-    ap.add_argument("--prune", action="store_true",
-                    help="also time the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
+    ap.add_argument("--no-prune", action="store_true",
+                    help="skip timing the same registration with CPD_FLAG_PRUNE (exact pruning of the E-step)")
     ap.add_argument("--no-outlier-config", action="store_true",
                     help="skip the M=20000, N=25000 (20%% outliers), K=200 configuration in FP32 and CPD_MIXED")
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -320,6 +320,8 @@ def run_batch(args, peaks, torch):
         ms.append(ev0.elapsed_time(ev1))
     s2, it, st = b.state()
     phase, busy = b.phase_profile()
+    sample = list(range(0, n, max(1, n // 16)))
+    T32 = {i: b.T(i).astype(np.float64) for i in sample}
     b.close()
     t = statistics.median(ms) / 1e3
     gauss = float((MN[:, 0] * MN[:, 1]).sum()) * I
@@ -339,6 +341,32 @@ def run_batch(args, peaks, torch):
                autotune=dict(chosen=dict(e_items_per_block=tune_e, proj_kbytes=tune_p), seconds=tune_s,
                              candidates_ms_3_iters=dict(zip(["e2/p256", "e2/p512", "e4/p256", "e4/p512", "e8/p256",
                                                              "e8/p512"], tune_ms))))
+    # the same pairs in CPD_MIXED: FP16 bases streamed by the M-step phases
+    t0 = time.perf_counter()
+    bm = cpd.Batch(Xs, Ys, w=bc["omega"], beta=bc["beta"], lam=bc["lam"], K=bc["K"], precision=cpd.MIXED)
+    msetup = time.perf_counter() - t0
+    bm.autotune(3)
+    for _ in range(2):
+        bm.reset()
+        bm.iterate(I)
+    mms = []
+    for _ in range(max(1, args.batch_reps)):
+        bm.reset()
+        torch.cuda.synchronize()
+        ev0.record()
+        bm.iterate(I)
+        ev1.record()
+        torch.cuda.synchronize()
+        mms.append(ev0.elapsed_time(ev1))
+    s2m, itm, stm = bm.state()
+    tm = statistics.median(mms) / 1e3
+    dmax = max(float(np.linalg.norm(bm.T(i).astype(np.float64) - T32[i]) / np.linalg.norm(T32[i])) for i in sample)
+    bm.close()
+    out["mixed_fp16_basis"] = dict(precision="CPD_MIXED: FP16 bases in the M-step phases, FP32 E-step phases",
+                                   ms_per_call=tm * 1e3, pair_iters_per_s=float(itm.sum()) / tm,
+                                   estep_alu_floor_frac=floor / tm, setup_s=msetup,
+                                   all_ok=bool((itm == I).all() and not stm.any()),
+                                   max_rel_diff_T_vs_fp32=dmax, sampled_pairs=len(sample))
     if not args.no_batch_baseline:
         # the same registrations one after another, each from its own graph
         ctxs = []
@@ -805,7 +833,7 @@ def main():
     # evaluated fraction of Gaussian pairs per iteration, and T against the
     # default (dense) path's
     prune = None
-    if args.prune and cfg["K"] == 0:
+    if not args.no_prune and cfg["K"] == 0:
         t0 = time.perf_counter()
         cp = cpd.Context(X, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=0,
                          flags=cpd.FLAG_PRUNE)

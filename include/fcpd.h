@@ -446,7 +446,9 @@ typedef struct cpd_batch cpd_batch;   /* opaque; owned by the library */
  *                      device), 1 <= M[i] <= 46340.
  *   Y[i], N[i]         scene points of pair i: N[i] x 3 floats (host or
  *                      device), N[i] >= 1.
- *   p                  shared parameters; precision must be CPD_FP32.  The
+ *   p                  shared parameters; precision CPD_FP32, or CPD_MIXED
+ *                      (each pair's basis stored in FP16 and streamed by the
+ *                      M-step phases; the E-step phases stay FP32).  The
  *                      basis of pair i keeps min(p->K, M[i]) eigenpairs (all
  *                      with p->K = 0).  p->tol > 0 stops each pair on its own.
  *   barrier_timeout_s  wall-time limit of one wait at a grid barrier inside

@@ -346,11 +346,12 @@ class Context:
 
 
 class Batch:
-    """Many independent FP32 registrations (X_i, Y_i) advanced together by one
-    persistent kernel launch per `iterate` call (cpd_batch_*)."""
+    """Many independent registrations (X_i, Y_i) advanced together by one
+    persistent kernel launch per `iterate` call (cpd_batch_*).  Points are
+    FP32; precision MIXED stores the eigenbasis in FP16."""
 
     def __init__(self, Xs, Ys, w=0.1, beta=2.0, lam=2.0, K=0, tol=0.0, sigma2_init=0.0,
-                 barrier_timeout_s=0.0, stream=None):
+                 barrier_timeout_s=0.0, stream=None, precision=FP32):
         lib = load()
         if len(Xs) != len(Ys) or not Xs:
             raise ValueError("Xs and Ys must be non-empty lists of equal length")
@@ -368,7 +369,7 @@ class Batch:
         self.n = n
         self.M, self.N = list(M), list(N)
         self.stream = _stream_handle(stream, True)
-        self.params = make_params(FP32, w, beta, lam, K, 0, tol, sigma2_init)
+        self.params = make_params(precision, w, beta, lam, K, 0, tol, sigma2_init)
         h = C.c_void_p()
         _check(lib.cpd_batch_create(n, px, M, py, N, C.byref(self.params), float(barrier_timeout_s), self.stream,
                                     C.byref(h)))

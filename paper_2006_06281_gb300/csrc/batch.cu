@@ -116,10 +116,28 @@ __device__ bool grid_barrier(BatchCtl* ctl, unsigned int nblocks, unsigned long 
   return ok != 0;
 }
 
+// Eight consecutive basis elements as floats (16-byte aligned): FP32, or the
+// FP16 basis of the mixed-precision mode.
+__device__ __forceinline__ void load8(const float* p, float (&u)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w; u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+}
+__device__ __forceinline__ void load8(const __half* p, float (&u)[8]) {
+  const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+  const __half2* h = reinterpret_cast<const __half2*>(&r);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h[i]);
+    u[2 * i] = f.x;
+    u[2 * i + 1] = f.y;
+  }
+}
+
 // Projection A = U^T R for a basis of at most 128 columns: 16 groups of 8
 // columns x 16 row lanes, the lanes combined in a fixed order through shared
 // memory.  Writes the same chunk partials as colsum_body (row chunk `by`).
-__device__ __forceinline__ void proj_narrow_body(const float* U, int64_t ldU, int M, int K, const float4* R4,
+template <typename B>
+__device__ __forceinline__ void proj_narrow_body(const B* U, int64_t ldU, int M, int K, const float4* R4,
                                                  int rows_per_chunk, float* part, int64_t ldP, DevState* st,
                                                  int by) {
   if (iteration_gated(st)) return;
@@ -136,10 +154,9 @@ __device__ __forceinline__ void proj_narrow_body(const float* U, int64_t ldU, in
   if (c0 < K) {
 #pragma unroll 4
     for (int m = r0 + lane; m < r1; m += kNarrowLanes) {
-      const float4* row = reinterpret_cast<const float4*>(U + (size_t)m * ldU + c0);
-      const float4 u0 = __ldg(row), u1 = __ldg(row + 1);
+      float u[8];
+      load8(U + (size_t)m * ldU + c0, u);
       const float4 r = R4[m];
-      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
       for (int w = 0; w < 8; ++w) {
         acc[w][0] = fmaf(u[w], r.x, acc[w][0]);
@@ -168,7 +185,8 @@ __device__ __forceinline__ void proj_narrow_body(const float* U, int64_t ldU, in
 // U^T (8 points per thread, B staged in shared memory), so T comes out of
 // registers; a per-pair ticket over the tiles lets the block that completes
 // the pair finish the iteration.
-__device__ __forceinline__ void expand_narrow_body(const float* Ut, int64_t ldM, int K, int M, const float4* B4,
+template <typename B>
+__device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int K, int M, const float4* B4,
                                                    const float4* X4, const float4* Yt4, float4* T4,
                                                    const float4* Yhat4, double* sums, DevState* st, int bx, int gx) {
   if (iteration_gated(st)) return;
@@ -184,10 +202,9 @@ __device__ __forceinline__ void expand_narrow_body(const float* Ut, int64_t ldM,
   if (c0 < M) {
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-      const float4* row = reinterpret_cast<const float4*>(Ut + (size_t)k * ldM + c0);
-      const float4 u0 = __ldg(row), u1 = __ldg(row + 1);
+      float u[8];
+      load8(Ut + (size_t)k * ldM + c0, u);
       const float4 b = sB[k];
-      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
       for (int w = 0; w < 8; ++w) {
         acc[w][0] = fmaf(u[w], b.x, acc[w][0]);
@@ -349,11 +366,20 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
       break;
     }
     case PH_P: {
-      if (P.narrow)
-        proj_narrow_body(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, by);
+      if (P.narrow && P.half_basis)
+        proj_narrow_body(static_cast<const __half*>(P.U), m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU,
+                         P.st, by);
+      else if (P.narrow)
+        proj_narrow_body(static_cast<const float*>(P.U), m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU,
+                         P.st, by);
+      else if (P.half_basis)
+        colsum_body<float, __half, kThreadsBatch>(static_cast<const __half*>(P.U), m.ldU, P.M, P.K, P.R4,
+                                                  m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1, bx, by,
+                                                  m.p_col_tiles, m.p_row_chunks);
       else
-        colsum_body<float, float, kThreadsBatch>(P.U, m.ldU, P.M, P.K, P.R4, m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1,
-                                          bx, by, m.p_col_tiles, m.p_row_chunks);
+        colsum_body<float, float, kThreadsBatch>(static_cast<const float*>(P.U), m.ldU, P.M, P.K, P.R4,
+                                                 m.p_rows_per_chunk, P.partP, m.ldU, P.st, 1, 1, bx, by,
+                                                 m.p_col_tiles, m.p_row_chunks);
       if (!tile_done(tP, (unsigned)(m.p_col_tiles * m.p_row_chunks))) break;
       const int nu = (P.K + kMRedCols - 1) / kMRedCols;
       for (int u = 0; u < nu; ++u) {
@@ -364,11 +390,22 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
     }
     case PH_E: {
       if (P.narrow) {
-        expand_narrow_body(P.Ut, m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4, P.sums, P.st, bx, m.e_col_tiles);
+        if (P.half_basis)
+          expand_narrow_body(static_cast<const __half*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4,
+                             P.sums, P.st, bx, m.e_col_tiles);
+        else
+          expand_narrow_body(static_cast<const float*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4,
+                             P.sums, P.st, bx, m.e_col_tiles);
         break;
       }
-      colsum_body<float, float, kThreadsBatch>(P.Ut, m.ldM, P.K, P.M, P.B4, m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx,
-                                        by, m.e_col_tiles, m.e_row_chunks);
+      if (P.half_basis)
+        colsum_body<float, __half, kThreadsBatch>(static_cast<const __half*>(P.Ut), m.ldM, P.K, P.M, P.B4,
+                                                  m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx, by,
+                                                  m.e_col_tiles, m.e_row_chunks);
+      else
+        colsum_body<float, float, kThreadsBatch>(static_cast<const float*>(P.Ut), m.ldM, P.K, P.M, P.B4,
+                                                 m.e_rows_per_chunk, P.partP, m.ldM, P.st, 1, 0, bx, by,
+                                                 m.e_col_tiles, m.e_row_chunks);
       if (!tile_done(tE + bx, (unsigned)m.e_row_chunks)) break;
       const int u1 = min((bx + 1) * (kTileColsE / kMRedCols), m.e_blocks);
       for (int u = bx * (kTileColsE / kMRedCols); u < u1; ++u) {

@@ -287,8 +287,9 @@ struct BatchPair {
   MstepPlan mp;
   const float4* X4;
   float4* T4;
-  const float* U;
-  const float* Ut;
+  const void* U;              // float, or __half with half_basis (mixed precision)
+  const void* Ut;
+  int half_basis;
   const double* lam;
   float4* Yt4;
   float4* R4;

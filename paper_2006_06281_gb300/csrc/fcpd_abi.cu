@@ -1356,8 +1356,9 @@ BatchPair batch_pointers(cpd_ctx* c, const BatchPair& plan) {
   BatchPair b = plan;
   b.X4 = c->X4.as<float4>();
   b.T4 = c->T4.as<float4>();
-  b.U = c->U.as<float>();
-  b.Ut = c->Ut.as<float>();
+  b.U = c->U.p;
+  b.Ut = c->Ut.p;
+  b.half_basis = c->half_basis ? 1 : 0;
   b.lam = c->lam.as<double>();
   b.Yt4 = c->Yt4.as<float4>();
   b.R4 = c->R4.as<float4>();
@@ -1449,7 +1450,8 @@ cpd_status cpd_batch_create(int32_t n_pairs, const void* const* X, const int64_t
   if (!out) return fail(CPD_EINVAL, "out is NULL");
   if (n_pairs < 1 || n_pairs > kMaxBatch) return fail(CPD_EINVAL, "n_pairs must be in [1, 65536]");
   if (!X || !M || !Y || !N) return fail(CPD_EINVAL, "X, M, Y and N are required");
-  if (p->precision != CPD_FP32) return fail(CPD_EINVAL, "batched registrations run in FP32 only");
+  if (p->precision != CPD_FP32 && p->precision != CPD_MIXED)
+    return fail(CPD_EINVAL, "batched registrations run in CPD_FP32 or CPD_MIXED (FP16 basis)");
   if (p->flags & CPD_FLAG_SPECTRAL_TRIM) return fail(CPD_EINVAL, "batched registrations take no spectral trim");
   if (barrier_timeout_s == 0.0) barrier_timeout_s = 5.0;
   if (!(barrier_timeout_s > 0.0 && barrier_timeout_s <= 60.0))

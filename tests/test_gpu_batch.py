@@ -196,3 +196,31 @@ def test_autotuner_keeps_results_and_reports_candidates(scenes):
         for i in range(len(Xs)):
             # a different work-item plan changes only the summation order
             assert rel(b.T(i), Tref[i].astype(np.float64)) <= 5e-5
+
+
+def test_batch_mixed_precision_fp16_basis(scenes):
+    """CPD_MIXED batches stream an FP16 basis in the M-step phases (the
+    E-step phases stay FP32): every pair against the FP64 oracle at the
+    mixed-precision bound (FP16 rounding of the basis, as the single-pair
+    mixed mode), and against the FP32 batch."""
+    Xs = [f32(ps.X) for ps in scenes]
+    Ys = [f32(ps.Y) for ps in scenes]
+    iters, K = 25, 128
+    kw = dict(w=0.1, beta=2.0, lam=2.0, K=K)
+    with cpd.Batch([torch.tensor(x, device="cuda") for x in Xs], Ys, precision=cpd.MIXED, **kw) as bm, \
+            cpd.Batch([torch.tensor(x, device="cuda") for x in Xs], Ys, **kw) as b32:
+        bm.iterate(iters)
+        b32.iterate(iters)
+        s2m, itm, stm = bm.state()
+        assert list(itm) == [iters] * len(Xs) and not stm.any()
+        worst = 0.0
+        for i, (x, y) in enumerate(zip(Xs, Ys)):
+            Kr = min(K, x.shape[0])
+            ref = oracle.register(x.astype(np.float64), y.astype(np.float64), w=0.1, beta=2.0, lam_reg=2.0,
+                                  n_iter=iters, K=0 if Kr == x.shape[0] else Kr)
+            Tm = bm.T(i)
+            err = rel(Tm, ref["T"])
+            worst = max(worst, err)
+            assert err <= 3e-4, (i, PAIRS[i], err)
+            assert rel(Tm, b32.T(i)) <= 3e-4, i
+    print(f"[batch mixed] largest T error against the oracle {worst:.2e}")
