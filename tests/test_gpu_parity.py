@@ -591,3 +591,21 @@ def test_estep_mixed_below_the_floor_is_the_fp32_estep():
         g32 = cpd.estep(T, Y, sigma2, 0.1, cpd.FP32)
         np.testing.assert_array_equal(host(g["Ytil"]), host(g32["Ytil"]))
         np.testing.assert_array_equal(host(g["den"]), host(g32["den"]))
+
+
+def test_full_basis_several_iterations_at_m12000():
+    """The full-basis launch plans at a size where they split into many
+    chunks (pass A/B grids, colsum row chunks over 12000 rows of U and U^T),
+    over several iterations, against the FP64 oracle with its own dense
+    eigendecomposition of the 12000 x 12000 Gram matrix."""
+    import time
+    ps = pointsets(12000, seed=0, amp=0.15)
+    X, Y = ps.X.astype(np.float32).astype(np.float64), ps.Y.astype(np.float32).astype(np.float64)
+    t0 = time.time()
+    ref = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=5)
+    print(f"[full basis M=12000] oracle (dense eigendecomposition + 5 iterations) {time.time() - t0:.1f} s")
+    T, s2, it, hist = run_gpu(X, Y, cpd.FP32, 5)
+    err = rel(T, ref["T"])
+    print(f"[full basis M=12000] T relative error {err:.3e}")
+    assert it == 5 and err <= FP32_TOL
+    check_sigma2(hist["sigma2"], ref["sigma2_hist"], FP32_TOL, "full basis M=N=12000 history")
