@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--warmstart", default="fp32_warmstart_m2048_k64",
                     help="train and evaluate the learned warm start (and the combined mixed-precision + "
                          "warm-start form) on this workload ('none' skips it)")
+    ap.add_argument("--warmstart-net", choices=["bf16", "fp32"], default="bf16",
+                    help="precision of the warm-start network's per-point layers (bf16: tcgen05 tensor cores)")
     ap.add_argument("--no-trim", action="store_true",
                     help="skip timing the same registration with CPD_FLAG_SPECTRAL_TRIM")
     ap.add_argument("--shared", type=int, default=32,
@@ -502,6 +504,28 @@ def run_outlier_config(args, peaks, torch):
     return out
 
 
+def train_step_ms(torch, warmstart, Ys, n_out, n_points, batch, steps=30):
+    """Device time of one training step (forward, backward, Adam) of the
+    network on one batch, FP32 and BF16 per-point layers, the batch resident."""
+    Yd = torch.tensor(np.ascontiguousarray(Ys[:batch]), device="cuda")
+    tgt = np.zeros((batch, n_out), np.float32)
+    out = {}
+    for name, prec in (("fp32", warmstart.NET_FP32), ("bf16", warmstart.NET_BF16)):
+        net = warmstart.Net(n_out, n_points, max_batch=batch, seed=1, precision=prec)
+        for _ in range(3):
+            net.train_step(Yd, tgt, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            net.train_step(Yd, tgt, 1e-4)
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t0) * 1e3 / steps
+        net.close()
+    out["note"] = "wall time per cpd_net_train_step call (it synchronises), batch of %d scenes x %d points" % (
+        batch, n_points)
+    return out
+
+
 def run_warmstart(args, torch):
     """Learned warm start: training data from the method itself (registrations
     from W = 0 on deformations of one template, 8 scenes per shared-model
@@ -526,7 +550,9 @@ def run_warmstart(args, torch):
     t1 = time.perf_counter()
     targets = warmstart.registration_targets(ctx, Ys[:ntr + nva], cfg["K"], cfg["iters"])
     t2 = time.perf_counter()
-    ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3)
+    net_prec = warmstart.NET_BF16 if args.warmstart_net == "bf16" else warmstart.NET_FP32
+    step_ms = train_step_ms(torch, warmstart, Ys[:cfg["batch"]], 3 * cfg["K"] + 1, cfg["M"], cfg["batch"])
+    ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3, precision=net_prec)
     losses = ws.fit(Ys[:ntr], targets[:ntr], cfg["steps"], cfg["batch"], cfg["lr"])
     torch.cuda.synchronize()
     t3 = time.perf_counter()
@@ -576,6 +602,7 @@ def run_warmstart(args, torch):
     cm.close()
     r = np.array(rows, dtype=np.float64)
     return dict(workload=args.warmstart, M=cfg["M"], K=cfg["K"], train_scenes=ntr, steps=cfg["steps"],
+                network_precision=args.warmstart_net, train_step_ms=step_ms,
                 data_s=t2 - t1, data_gen_host_s=t1 - t0, train_s=t3 - t2,
                 loss_first=float(np.mean(losses[:20])), loss_last=float(np.mean(losses[-50:])),
                 heldout_coef_rel_err=err, start_sigma2=ws.sigma2_floor,

@@ -398,19 +398,34 @@ cpd_status cpd_warm_start(cpd_ctx *ctx, int32_t n_coef, const void *coef, double
  * The warm-start network: a point-set encoder -- a shared per-point MLP
  * 3 -> 128 -> 128 -> 256 (ReLU), the maximum over the points, a head
  * 256 -> 256 (ReLU) -> n_out -- trained on the GPU with the mean-squared
- * error and Adam (beta1 0.9, beta2 0.999, eps 1e-8), all in FP32 CUDA
- * kernels of this library.  Parameter layout: per layer the weights
- * (fan_in x fan_out, row-major) then the biases, layers in order.
+ * error and Adam (beta1 0.9, beta2 0.999, eps 1e-8), all in CUDA kernels
+ * of this library.  Parameter layout: per layer the weights (fan_in x
+ * fan_out, row-major) then the biases, layers in order.
  *   create:   n_out 1..4096; max_batch 1..1024 scenes of n_points points
  *             (max_batch * n_points <= 2^24); seed of the initial weights.
+ *             FP32 arithmetic throughout.
+ *   create_ex: as create, with precision CPD_NET_FP32 (= create) or
+ *             CPD_NET_BF16: the per-point layers 128 -> 128 and 128 -> 256
+ *             and their gradient products multiply BF16 operands on the
+ *             tensor cores with FP32 accumulation (master weights, Adam,
+ *             biases, the 3 -> 128 layer, the head and every reduction in
+ *             FP32).  BF16 needs a compute capability 10.x device
+ *             (CPD_EINVAL otherwise) and about 2.3 KB more device memory per
+ *             point of max_batch * n_points.  A tensor-core wait that
+ *             expires fails the call with CPD_ETIMEOUT.
  *   forward / gradients / train_step: Y = B x n_points x 3 floats in DEVICE
  *             memory (B <= max_batch); pred_out (B x n_out), target
  *             (B x n_out), grad_out (num_params) host or device.  Each
  *             synchronises the network's stream.
  */
 typedef struct cpd_net cpd_net;
+enum { CPD_NET_FP32 = 0, CPD_NET_BF16 = 1 };
 cpd_status cpd_net_create(int32_t n_out, int32_t max_batch, int32_t n_points, uint64_t seed, void *stream,
                           cpd_net **out);
+cpd_status cpd_net_create_ex(int32_t n_out, int32_t max_batch, int32_t n_points, uint64_t seed, int32_t precision,
+                             void *stream, cpd_net **out);
+/* CPD_NET_FP32 or CPD_NET_BF16 (-1 for NULL). */
+int32_t cpd_net_precision(const cpd_net *net);
 int64_t cpd_net_num_params(const cpd_net *net);
 cpd_status cpd_net_get_params(cpd_net *net, float *out);
 cpd_status cpd_net_set_params(cpd_net *net, const float *in);

@@ -32,8 +32,8 @@ EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_eig_info", "cpd_mstep",
            "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_iterate_shared", "cpd_destroy",
-           "cpd_coefficients", "cpd_coefficients_of", "cpd_warm_start", "cpd_net_create", "cpd_net_num_params", "cpd_net_get_params",
-           "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
+           "cpd_coefficients", "cpd_coefficients_of", "cpd_warm_start", "cpd_net_create", "cpd_net_create_ex",
+           "cpd_net_precision", "cpd_net_num_params", "cpd_net_get_params", "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
            "cpd_batch_launch_shape", "cpd_batch_phase_ms", "cpd_batch_reset", "cpd_batch_autotune",
            "cpd_batch_destroy"]
@@ -95,6 +95,8 @@ def load():
                 "cpd_coefficients_of": ([vp, i32, vp, vp], C.c_int),
                 "cpd_warm_start": ([vp, i32, vp, d], C.c_int),
                 "cpd_net_create": ([i32, i32, i32, C.c_uint64, vp, C.POINTER(vp)], C.c_int),
+                "cpd_net_create_ex": ([i32, i32, i32, C.c_uint64, i32, vp, C.POINTER(vp)], C.c_int),
+                "cpd_net_precision": ([vp], i32),
                 "cpd_net_num_params": ([vp], i64),
                 "cpd_net_get_params": ([vp, vp], C.c_int),
                 "cpd_net_set_params": ([vp, vp], C.c_int),

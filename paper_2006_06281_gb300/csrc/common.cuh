@@ -15,6 +15,7 @@
 //   partials  split-reduction scratch of the E-step and the M-step
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -438,6 +439,21 @@ cudaError_t launch_mstep_multi_mma(const UmmaPlan& pp, const UmmaPlan& pe, const
                                    const float4* X4, const float4* R4, const float4* Yt4, float4* T4, float4* B4,
                                    float4* C4, DevState* const* st, __half* Vp, __half* Ve, float* part,
                                    double* sums, int* status, bool fault_wait, cudaStream_t s);
+
+// BF16 tensor-core GEMM of the warm-start network (gemm_tc.cu): D = A B^T,
+// A (P x Q, row stride lda) and B (N x Q, row stride ldb) BF16 with the
+// contraction contiguous, N = 128 or 256, FP32 accumulation.  chunks > 1:
+// split-K partials out[chunk][P][ldo] (to be summed in order); else the
+// epilogue + bias, ReLU or the mask (0 where mask[p][n] <= 0) and the FP32
+// result out[P][ldo] with optional BF16 copies (row-major, transposed [N][ld_t]).
+cudaError_t launch_gemm_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int P, int N,
+                           int Q, int chunks, const float* bias, bool relu, const float* mask, int64_t ldm,
+                           float* out, int64_t ldo, __nv_bfloat16* out_bf, int64_t ld_bf, __nv_bfloat16* out_t,
+                           int64_t ld_t, int* status, cudaStream_t s);
+int gemm_tc_chunks(int Q, int chunks);
+void launch_to_bf16(const float* X, int64_t R, int C, __nv_bfloat16* row, __nv_bfloat16* tr, int64_t ldt,
+                    cudaStream_t s);
+void launch_weights_bf16(const float* W, int fi, int fo, __nv_bfloat16* w, __nv_bfloat16* wt, cudaStream_t s);
 
 // W = U C (C from the last M-step), written as 4-vectors.
 template <typename F, typename S = F>

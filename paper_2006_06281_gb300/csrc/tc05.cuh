@@ -163,5 +163,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Host: a 2-D tiled tensor map of a row-major matrix [rows][cols] (row
+// stride ld elements of elem_bytes) with box {64 elements (128 bytes of a
+// 16-bit type), box_rows}, 128-byte swizzle, zero fill outside (umma.cu).
+// False if the driver's encoder is unavailable or rejects the layout.
+bool make_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType type, int64_t rows, int64_t cols,
+                 int64_t ld, int box_rows);
+
 }  // namespace tc05
 }  // namespace fcpd

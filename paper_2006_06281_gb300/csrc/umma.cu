@@ -237,15 +237,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // Row-major FP16 matrix [rows][cols] with row stride ld elements; box
 // {kUK, box_rows}, 128-byte swizzle, zero fill outside.
 bool make_map(CUtensorMap* map, const __half* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
-  auto fn = encode_fn();
-  if (!fn) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kUK, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return tc05::make_map_2d(map, base, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, rows, cols, ld, box_rows);
 }
 
 template <int NPAD> int umma_occupancy() {
@@ -284,6 +276,19 @@ cudaError_t launch_products_npad(const CUtensorMap& a, const CUtensorMap& v, int
 }
 
 }  // namespace
+
+bool tc05::make_map_2d(CUtensorMap* map, const void* base, CUtensorMapDataType type, int64_t rows, int64_t cols,
+                       int64_t ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kUK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, type, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 int umma_npad(int S) {
   const int h = (int)cdiv(3 * S, 16) * 16;

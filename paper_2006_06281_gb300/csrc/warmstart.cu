@@ -13,6 +13,15 @@
 // all B x N points), max-pool forward/backward, ReLU masks, column sums, the
 // mean-squared-error gradient and Adam.  FP32 throughout (results are
 // deterministic: no atomics in any sum).
+//
+// BF16 precision (cpd_net_create_ex): the two wide per-point layers
+// (128 -> 128 and 128 -> 256, over all B x N points) and their three
+// backward products each (the activation gradient and the weight gradient)
+// run on the tensor cores -- tcgen05 BF16 x BF16 -> FP32 (gemm_tc.cu) with
+// bias, ReLU and the ReLU-derivative mask in the epilogue, which also writes
+// the BF16 row-major and transposed operands of the next product.  Master
+// weights, Adam moments, biases, the first layer (3 inputs), the head and all
+// reductions stay FP32.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -30,6 +39,7 @@ constexpr int kGT = 64;       // GEMM tile (rows and columns of C per block)
 constexpr int kGK = 16;       // K step
 constexpr int kGThreads = 256;
 constexpr int kSplitK = 64;   // K splits of the weight-gradient GEMMs
+constexpr int kTcChunks = 128;  // contraction chunks of the BF16 weight-gradient products
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -250,9 +260,15 @@ struct cpd_net {
   int fin[5], fout[5];
   int64_t step = 0;
   DevBuf params, grads, m, v, h1, h2, h3, g, arg, z, pred, dpred, dz, dg, dh3, dh2, dh1, part, loss, tgt;
+  // BF16 precision only: operand copies (row-major [R][F], transposed
+  // [F][ldt]), BF16 weights and the tensor-core kernels' status word.
+  int precision = CPD_NET_FP32;
+  int64_t ldt = 0;
+  bool launch_failed = false;
+  DevBuf h1b, h1t, h2b, h2t, dh3b, dh3t, dh2b, dh2t, wbf, gstat;
   ~cpd_net() {
     for (DevBuf* b : {&params, &grads, &m, &v, &h1, &h2, &h3, &g, &arg, &z, &pred, &dpred, &dz, &dg, &dh3, &dh2,
-                      &dh1, &part, &loss, &tgt})
+                      &dh1, &part, &loss, &tgt, &h1b, &h1t, &h2b, &h2t, &dh3b, &dh3t, &dh2b, &dh2t, &wbf, &gstat})
       b->release();
   }
 };
@@ -292,13 +308,49 @@ void mask(cpd_net* net, float* d, const float* h, int64_t n) {
 float* W(cpd_net* n, DevBuf& b, int l) { return b.as<float>() + n->w_off[l]; }
 float* Bv(cpd_net* n, DevBuf& b, int l) { return b.as<float>() + n->b_off[l]; }
 
-void forward(cpd_net* n, const float* Y, int B) {
+__nv_bfloat16* bf(DevBuf& b) { return b.as<__nv_bfloat16>(); }
+// BF16 weight copies: W2 (128 x 128), W2^T, W3 (128 x 256), W3^T (256 x 128).
+__nv_bfloat16* w2_bf(cpd_net* n) { return bf(n->wbf); }
+__nv_bfloat16* w2t_bf(cpd_net* n) { return bf(n->wbf) + 128 * 128; }
+__nv_bfloat16* w3_bf(cpd_net* n) { return bf(n->wbf) + 2 * 128 * 128; }
+__nv_bfloat16* w3t_bf(cpd_net* n) { return bf(n->wbf) + 2 * 128 * 128 + 128 * 256; }
+
+// out (R x N) = epilogue(A B^T) on the tensor cores, A: R x Q, B: N x Q (BF16).
+void tc(cpd_net* n, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t R, int N, int Q,
+        const float* bias, bool relu, const float* mask_by, float* out, __nv_bfloat16* out_bf, __nv_bfloat16* out_t) {
+  if (launch_gemm_tc(A, lda, B, ldb, (int)R, N, Q, 1, bias, relu, mask_by, N, out, N, out_bf, N, out_t, n->ldt,
+                     n->gstat.as<int>(), n->stream) != cudaSuccess)
+    n->launch_failed = true;
+}
+
+// C (P x N) = A B^T over a long contraction (all points): kTcChunks partials,
+// summed in order.
+void tc_splitk(cpd_net* n, const __nv_bfloat16* A, const __nv_bfloat16* B, int P, int N, int64_t Q, float* C) {
+  const int S = gemm_tc_chunks((int)Q, kTcChunks);
+  if (launch_gemm_tc(A, n->ldt, B, n->ldt, P, N, (int)Q, S, nullptr, false, nullptr, 0, n->part.as<float>(), N,
+                     nullptr, 0, nullptr, 0, n->gstat.as<int>(), n->stream) != cudaSuccess)
+    n->launch_failed = true;
+  sum_splits<<<(unsigned)cdiv((int64_t)P * N, 256), 256, 0, n->stream>>>(n->part.as<float>(), S, (int64_t)P * N, C);
+}
+
+// train: also write the transposed BF16 activations the weight gradients read.
+void forward(cpd_net* n, const float* Y, int B, bool train) {
   const int64_t R = (int64_t)B * n->n_points;
   gemm(n, Y, 3, false, W(n, n->params, 0), 128, false, n->h1.as<float>(), 128, (int)R, 128, 3, Bv(n, n->params, 0), true);
-  gemm(n, n->h1.as<float>(), 128, false, W(n, n->params, 1), 128, false, n->h2.as<float>(), 128, (int)R, 128, 128,
-       Bv(n, n->params, 1), true);
-  gemm(n, n->h2.as<float>(), 128, false, W(n, n->params, 2), 256, false, n->h3.as<float>(), 256, (int)R, 256, 128,
-       Bv(n, n->params, 2), true);
+  if (n->precision == CPD_NET_BF16) {
+    launch_weights_bf16(W(n, n->params, 1), 128, 128, w2_bf(n), w2t_bf(n), n->stream);
+    launch_weights_bf16(W(n, n->params, 2), 128, 256, w3_bf(n), w3t_bf(n), n->stream);
+    launch_to_bf16(n->h1.as<float>(), R, 128, bf(n->h1b), train ? bf(n->h1t) : nullptr, n->ldt, n->stream);
+    tc(n, bf(n->h1b), 128, w2t_bf(n), 128, R, 128, 128, Bv(n, n->params, 1), true, nullptr, n->h2.as<float>(),
+       bf(n->h2b), train ? bf(n->h2t) : nullptr);
+    tc(n, bf(n->h2b), 128, w3t_bf(n), 128, R, 256, 128, Bv(n, n->params, 2), true, nullptr, n->h3.as<float>(), nullptr,
+       nullptr);
+  } else {
+    gemm(n, n->h1.as<float>(), 128, false, W(n, n->params, 1), 128, false, n->h2.as<float>(), 128, (int)R, 128, 128,
+         Bv(n, n->params, 1), true);
+    gemm(n, n->h2.as<float>(), 128, false, W(n, n->params, 2), 256, false, n->h3.as<float>(), 256, (int)R, 256, 128,
+         Bv(n, n->params, 2), true);
+  }
   maxpool_fwd<<<B, 256, 0, n->stream>>>(n->h3.as<float>(), n->n_points, 256, n->g.as<float>(), n->arg.as<int>());
   gemm(n, n->g.as<float>(), 256, false, W(n, n->params, 3), 256, false, n->z.as<float>(), 256, B, 256, 256,
        Bv(n, n->params, 3), true);
@@ -321,18 +373,48 @@ void backward(cpd_net* n, const float* Y, const float* tgt, int B) {
   cudaMemsetAsync(n->dh3.p, 0, (size_t)R * 256 * sizeof(float), n->stream);
   maxpool_bwd<<<B, 256, 0, n->stream>>>(n->dg.as<float>(), n->arg.as<int>(), n->n_points, 256, n->dh3.as<float>());
   mask(n, n->dh3.as<float>(), n->h3.as<float>(), R * 256);
-  gemm_splitk(n, n->h2.as<float>(), 128, true, n->dh3.as<float>(), 256, false, W(n, n->grads, 2), 128, 256, (int)R);
-  col_sum(n, n->dh3.as<float>(), R, 256, Bv(n, n->grads, 2));
-  gemm(n, n->dh3.as<float>(), 256, false, W(n, n->params, 2), 256, true, n->dh2.as<float>(), 128, (int)R, 128, 256,
-       nullptr, false);
-  mask(n, n->dh2.as<float>(), n->h2.as<float>(), R * 128);
-  gemm_splitk(n, n->h1.as<float>(), 128, true, n->dh2.as<float>(), 128, false, W(n, n->grads, 1), 128, 128, (int)R);
-  col_sum(n, n->dh2.as<float>(), R, 128, Bv(n, n->grads, 1));
-  gemm(n, n->dh2.as<float>(), 128, false, W(n, n->params, 1), 128, true, n->dh1.as<float>(), 128, (int)R, 128, 128,
-       nullptr, false);
-  mask(n, n->dh1.as<float>(), n->h1.as<float>(), R * 128);
+  if (n->precision == CPD_NET_BF16) {
+    launch_to_bf16(n->dh3.as<float>(), R, 256, bf(n->dh3b), bf(n->dh3t), n->ldt, n->stream);
+    tc_splitk(n, bf(n->h2t), bf(n->dh3t), 128, 256, R, W(n, n->grads, 2));
+    col_sum(n, n->dh3.as<float>(), R, 256, Bv(n, n->grads, 2));
+    tc(n, bf(n->dh3b), 256, w3_bf(n), 256, R, 128, 256, nullptr, false, n->h2.as<float>(), n->dh2.as<float>(),
+       bf(n->dh2b), bf(n->dh2t));
+    tc_splitk(n, bf(n->h1t), bf(n->dh2t), 128, 128, R, W(n, n->grads, 1));
+    col_sum(n, n->dh2.as<float>(), R, 128, Bv(n, n->grads, 1));
+    tc(n, bf(n->dh2b), 128, w2_bf(n), 128, R, 128, 128, nullptr, false, n->h1.as<float>(), n->dh1.as<float>(), nullptr,
+       nullptr);
+  } else {
+    gemm_splitk(n, n->h2.as<float>(), 128, true, n->dh3.as<float>(), 256, false, W(n, n->grads, 2), 128, 256, (int)R);
+    col_sum(n, n->dh3.as<float>(), R, 256, Bv(n, n->grads, 2));
+    gemm(n, n->dh3.as<float>(), 256, false, W(n, n->params, 2), 256, true, n->dh2.as<float>(), 128, (int)R, 128, 256,
+         nullptr, false);
+    mask(n, n->dh2.as<float>(), n->h2.as<float>(), R * 128);
+    gemm_splitk(n, n->h1.as<float>(), 128, true, n->dh2.as<float>(), 128, false, W(n, n->grads, 1), 128, 128, (int)R);
+    col_sum(n, n->dh2.as<float>(), R, 128, Bv(n, n->grads, 1));
+    gemm(n, n->dh2.as<float>(), 128, false, W(n, n->params, 1), 128, true, n->dh1.as<float>(), 128, (int)R, 128, 128,
+         nullptr, false);
+    mask(n, n->dh1.as<float>(), n->h1.as<float>(), R * 128);
+  }
   gemm_splitk(n, Y, 3, true, n->dh1.as<float>(), 128, false, W(n, n->grads, 0), 3, 128, (int)R);
   col_sum(n, n->dh1.as<float>(), R, 128, Bv(n, n->grads, 0));
+}
+
+// After a synchronisation: a failed tensor-core launch, or a status word
+// that a kernel set (a bounded wait that expired), fails the call.
+cpd_status net_status(cpd_net* n) {
+  if (n->launch_failed) {
+    n->launch_failed = false;
+    return fail(CPD_ECUDA, "a tensor-core GEMM of the network could not be launched");
+  }
+  if (n->precision != CPD_NET_BF16) return CPD_OK;
+  int st = 0;
+  if (cudaMemcpy(&st, n->gstat.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(CPD_ECUDA, "read of the network status failed");
+  if (st != 0) {
+    cudaMemset(n->gstat.p, 0, sizeof(int));
+    return fail((cpd_status)st, "a tensor-core GEMM of the network timed out waiting on its pipeline");
+  }
+  return CPD_OK;
 }
 
 bool on_device(const void* p) {
@@ -350,8 +432,15 @@ extern "C" {
 
 cpd_status cpd_net_create(int32_t n_out, int32_t max_batch, int32_t n_points, uint64_t seed, void* stream,
                           cpd_net** out) {
+  return cpd_net_create_ex(n_out, max_batch, n_points, seed, CPD_NET_FP32, stream, out);
+}
+
+cpd_status cpd_net_create_ex(int32_t n_out, int32_t max_batch, int32_t n_points, uint64_t seed, int32_t precision,
+                             void* stream, cpd_net** out) {
   set_last_error("");
   if (!out) return fail(CPD_EINVAL, "out is NULL");
+  if (precision != CPD_NET_FP32 && precision != CPD_NET_BF16)
+    return fail(CPD_EINVAL, "precision must be CPD_NET_FP32 or CPD_NET_BF16");
   if (n_out < 1 || n_out > 4096) return fail(CPD_EINVAL, "n_out must be in [1, 4096]");
   if (max_batch < 1 || max_batch > 1024) return fail(CPD_EINVAL, "max_batch must be in [1, 1024]");
   if (n_points < 1 || (int64_t)max_batch * n_points > (1LL << 24))
@@ -384,6 +473,19 @@ cpd_status cpd_net_create(int32_t n_out, int32_t max_batch, int32_t n_points, ui
             n->dg.alloc((int64_t)max_batch * 256 * 4) && n->dh3.alloc(R * 256 * 4) && n->dh2.alloc(R * 128 * 4) &&
             n->dh1.alloc(R * 128 * 4) && n->part.alloc(part * 4) && n->loss.alloc(4) &&
             n->tgt.alloc((int64_t)max_batch * n_out * 4);
+  if (ok && precision == CPD_NET_BF16) {
+    int cc_major = 0;
+    cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, n->dev);
+    if (cc_major != 10) { delete n; return fail(CPD_EINVAL, "BF16 precision needs tcgen05 (compute capability 10.x)"); }
+    n->precision = CPD_NET_BF16;
+    n->ldt = (R + 7) / 8 * 8;  // transposed rows start on 16-byte boundaries (TMA strides)
+    const int64_t bf = 2;
+    ok = n->h1b.alloc(R * 128 * bf) && n->h1t.alloc(128 * n->ldt * bf) && n->h2b.alloc(R * 128 * bf) &&
+         n->h2t.alloc(128 * n->ldt * bf) && n->dh3b.alloc(R * 256 * bf) && n->dh3t.alloc(256 * n->ldt * bf) &&
+         n->dh2b.alloc(R * 128 * bf) && n->dh2t.alloc(128 * n->ldt * bf) &&
+         n->wbf.alloc((2 * 128 * 128 + 2 * 128 * 256) * bf) && n->gstat.alloc(sizeof(int)) &&
+         cudaMemsetAsync(n->gstat.p, 0, sizeof(int), n->stream) == cudaSuccess;
+  }
   if (!ok) { delete n; return fail(CPD_ENOMEM, "device allocation for the network failed"); }
   // He-style initialisation from a seeded generator (host, once)
   std::vector<float> h((size_t)o, 0.f);
@@ -403,6 +505,8 @@ cpd_status cpd_net_create(int32_t n_out, int32_t max_batch, int32_t n_points, ui
 }
 
 int64_t cpd_net_num_params(const cpd_net* n) { return n ? n->np : 0; }
+
+int32_t cpd_net_precision(const cpd_net* n) { return n ? n->precision : -1; }
 
 cpd_status cpd_net_get_params(cpd_net* n, float* out) {
   if (!n || !out) return fail(CPD_EINVAL, "net and out are required");
@@ -427,11 +531,11 @@ cpd_status cpd_net_forward(cpd_net* n, const float* Y, int32_t B, float* pred_ou
   if (!n || !Y || !pred_out) return fail(CPD_EINVAL, "net, Y and pred_out are required");
   if (B < 1 || B > n->max_batch) return fail(CPD_EINVAL, "B must be in [1, max_batch]");
   if (!on_device(Y)) return fail(CPD_EINVAL, "Y must be device memory (B x n_points x 3 floats)");
-  forward(n, Y, B);
+  forward(n, Y, B, false);
   if (cudaMemcpyAsync(pred_out, n->pred.p, (size_t)B * n->n_out * 4, cudaMemcpyDefault, n->stream) != cudaSuccess ||
       cudaStreamSynchronize(n->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return fail(CPD_ECUDA, "forward pass failed");
-  return CPD_OK;
+  return net_status(n);
 }
 
 cpd_status cpd_net_gradients(cpd_net* n, const float* Y, const float* target, int32_t B, float* grad_out,
@@ -441,7 +545,7 @@ cpd_status cpd_net_gradients(cpd_net* n, const float* Y, const float* target, in
   if (!on_device(Y)) return fail(CPD_EINVAL, "Y must be device memory (B x n_points x 3 floats)");
   if (cudaMemcpyAsync(n->tgt.p, target, (size_t)B * n->n_out * 4, cudaMemcpyDefault, n->stream) != cudaSuccess)
     return fail(CPD_ECUDA, "copy of the target failed");
-  forward(n, Y, B);
+  forward(n, Y, B, true);
   backward(n, Y, n->tgt.as<float>(), B);
   if (grad_out && cudaMemcpyAsync(grad_out, n->grads.p, n->np * 4, cudaMemcpyDefault, n->stream) != cudaSuccess)
     return fail(CPD_ECUDA, "copy of the gradients failed");
@@ -449,7 +553,7 @@ cpd_status cpd_net_gradients(cpd_net* n, const float* Y, const float* target, in
     return fail(CPD_ECUDA, "copy of the loss failed");
   if (cudaStreamSynchronize(n->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return fail(CPD_ECUDA, "backward pass failed");
-  return CPD_OK;
+  return net_status(n);
 }
 
 cpd_status cpd_net_train_step(cpd_net* n, const float* Y, const float* target, int32_t B, float lr, float* loss_out) {
@@ -460,7 +564,7 @@ cpd_status cpd_net_train_step(cpd_net* n, const float* Y, const float* target, i
   if (!on_device(Y)) return fail(CPD_EINVAL, "Y must be device memory (B x n_points x 3 floats)");
   if (cudaMemcpyAsync(n->tgt.p, target, (size_t)B * n->n_out * 4, cudaMemcpyDefault, n->stream) != cudaSuccess)
     return fail(CPD_ECUDA, "copy of the target failed");
-  forward(n, Y, B);
+  forward(n, Y, B, true);
   backward(n, Y, n->tgt.as<float>(), B);
   ++n->step;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -471,7 +575,7 @@ cpd_status cpd_net_train_step(cpd_net* n, const float* Y, const float* target, i
     return fail(CPD_ECUDA, "copy of the loss failed");
   if (cudaStreamSynchronize(n->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
     return fail(CPD_ECUDA, "training step failed");
-  return CPD_OK;
+  return net_status(n);
 }
 
 void cpd_net_destroy(cpd_net* n) {

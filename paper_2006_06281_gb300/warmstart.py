@@ -20,15 +20,21 @@ import numpy as np
 from . import cpd
 
 
-class Net:
-    """The network (cpd_net_*): n_out outputs, scenes of n_points points."""
+NET_FP32, NET_BF16 = 0, 1    # cpd_net_create_ex precisions
 
-    def __init__(self, n_out, n_points, max_batch=32, seed=0, stream=None):
+
+class Net:
+    """The network (cpd_net_*): n_out outputs, scenes of n_points points.
+    precision NET_BF16 runs the wide per-point layers and their gradients on
+    the BF16 tensor cores (FP32 accumulation and master weights)."""
+
+    def __init__(self, n_out, n_points, max_batch=32, seed=0, stream=None, precision=NET_FP32):
         lib = cpd.load()
         self.n_out, self.n_points, self.max_batch = int(n_out), int(n_points), int(max_batch)
         h = C.c_void_p()
-        cpd._check(lib.cpd_net_create(self.n_out, self.max_batch, self.n_points, int(seed),
-                                      cpd._stream_handle(stream, True), C.byref(h)))
+        cpd._check(lib.cpd_net_create_ex(self.n_out, self.max_batch, self.n_points, int(seed), int(precision),
+                                         cpd._stream_handle(stream, True), C.byref(h)))
+        self.precision = int(lib.cpd_net_precision(h))
         self._h = h
         self.n_params = int(lib.cpd_net_num_params(h))
 
@@ -111,9 +117,9 @@ def registration_targets(ctx, scenes, n_coef, iters, group=8):
 class WarmStart:
     """Network + target normalisation + start-variance calibration."""
 
-    def __init__(self, n_coef, n_points, max_batch=32, seed=0):
+    def __init__(self, n_coef, n_points, max_batch=32, seed=0, precision=NET_FP32):
         self.n_coef = int(n_coef)
-        self.net = Net(3 * self.n_coef + 1, n_points, max_batch, seed)
+        self.net = Net(3 * self.n_coef + 1, n_points, max_batch, seed, precision=precision)
         self.mean = np.zeros(3 * self.n_coef + 1, dtype=np.float32)
         self.std = np.ones(3 * self.n_coef + 1, dtype=np.float32)
         self.sigma2_floor = 0.0

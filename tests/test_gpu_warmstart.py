@@ -44,13 +44,161 @@ def test_forward_and_gradients_match_the_fp64_reference():
     net.close()
 
 
-def test_training_reduces_the_loss():
+# --- BF16 precision: the per-point products on the tensor cores -------------
+
+def _bf16(x):
+    """Nearest BF16 (ties to even; torch's conversion) as float64."""
+    return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _random_params(n_out, seed):
+    """He-scaled weights and small nonzero biases (the epilogue adds them)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for fi, fo in ref.shapes(n_out):
+        out.append(rng.normal(0, np.sqrt(2.0 / fi), fi * fo))
+        out.append(rng.normal(0, 0.05, fo))
+    return np.concatenate(out).astype(np.float32)
+
+
+def _bf16_operand_reference(p, Y, tgt, n_out):
+    """The FP64 network with the operands of the tensor-core products rounded
+    to BF16 exactly where the BF16 precision rounds them: h1, h2, W2, W3
+    forward; h1, h2, dh3, dh2, W2, W3 in the backward products.  Everything
+    else (first layer, max-pool, head, bias gradients) is the FP64 reference.
+    Returns the prediction, the flat gradients, and h3 (B, N, 256)."""
+    (W0, b0), (W1, b1), (W2, b2), (W3, b3), (W4, b4) = ref.unpack(np.asarray(p, np.float64), n_out)
+    B, N, _ = Y.shape
+    x = np.asarray(Y, np.float64).reshape(B * N, 3)
+    h1 = np.maximum(x @ W0 + b0, 0)
+    h2 = np.maximum(_bf16(h1) @ _bf16(W1) + b1, 0)
+    h3 = np.maximum(_bf16(h2) @ _bf16(W2) + b2, 0)
+    H3 = h3.reshape(B, N, 256)
+    g, arg = H3.max(1), H3.argmax(1)
+    z = np.maximum(g @ W3 + b3, 0)
+    pred = z @ W4 + b4
+    dpred = 2.0 * (pred - np.asarray(tgt, np.float64)) / pred.size
+    grads = [None] * 5
+    grads[4] = (z.T @ dpred, dpred.sum(0))
+    dz = (dpred @ W4.T) * (z > 0)
+    grads[3] = (g.T @ dz, dz.sum(0))
+    dg = dz @ W3.T
+    dh3 = np.zeros((B, N, 256))
+    bi, fi = np.meshgrid(np.arange(B), np.arange(256), indexing="ij")
+    dh3[bi, arg, fi] = dg
+    dh3 = dh3.reshape(B * N, 256) * (h3 > 0)
+    grads[2] = (_bf16(h2).T @ _bf16(dh3), dh3.sum(0))
+    dh2 = (_bf16(dh3) @ _bf16(W2).T) * (h2 > 0)
+    grads[1] = (_bf16(h1).T @ _bf16(dh2), dh2.sum(0))
+    dh1 = (_bf16(dh2) @ _bf16(W1).T) * (h1 > 0)
+    grads[0] = (x.T @ dh1, dh1.sum(0))
+    flat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    return pred, flat, H3
+
+
+def _max_gap(H3):
+    """Smallest relative gap between the largest and second-largest value of
+    a live (positive) max-pool feature; routing is unambiguous above it."""
+    s = np.sort(H3, axis=1)
+    top = s[:, -1, :]
+    sec = s[:, -2, :] if H3.shape[1] > 1 else np.zeros_like(top)
+    live = top > 0
+    return float(((top - sec) / np.where(live, top, 1.0))[live].min()) if live.any() else 1.0
+
+
+def _per_layer(a, b, n_out, frac):
+    o = 0
+    for fi, fo in ref.shapes(n_out):
+        for size in (fi * fo, fo):
+            x, y = a[o:o + size], b[o:o + size]
+            np.testing.assert_allclose(x, y, rtol=0, atol=frac * max(np.abs(y).max(), 1e-12))
+            o += size
+
+
+# BF16 bound against the FP64 network: each product rounds both operands
+# (relative 2^-9 each) and errors pass through at most five rounded products
+# on the way to a gradient, 5 * 2 * 2^-9 < 2^-5, taken relative to the
+# layer's largest entry.  Against the BF16-operand reference only FP32
+# accumulation and rare BF16 rounding-boundary flips remain: 1e-3.
+BF16_VS_FP64 = 2.0 ** -5
+BF16_VS_EMULATED = 1e-3
+
+
+@pytest.mark.parametrize("B,N,seed", [(1, 5, 19), (3, 100, 15)])
+def test_bf16_forward_and_gradients_match_the_bf16_operand_reference(B, N, seed):
+    # R = B N points: one ragged row tile, and three tiles with a ragged tail
+    # (also in the contraction of the weight gradients: 300 = 4 x 64 + 44)
+    n_out = 7
+    rng = np.random.default_rng(seed)
+    Y = rng.uniform(-1, 1, (B, N, 3)).astype(np.float32)
+    tgt = rng.normal(0, 1, (B, n_out)).astype(np.float32)
+    p = _random_params(n_out, 100 + seed)
+    pred_e, g_e, H3 = _bf16_operand_reference(p, Y, tgt, n_out)
+    # the seeds are chosen so that no max-pool feature is near a tie
+    assert _max_gap(H3) > 5e-4
+    net = warmstart.Net(n_out, N, max_batch=B, seed=0, precision=warmstart.NET_BF16)
+    assert net.precision == warmstart.NET_BF16
+    net.set_params(p)
+    Yd = torch.tensor(Y, device="cuda")
+    pred = net.forward(Yd)
+    scale = np.abs(pred_e).max()
+    np.testing.assert_allclose(pred, pred_e, rtol=0, atol=BF16_VS_EMULATED * scale)
+    pred_ref, _ = ref.forward(p.astype(np.float64), Y.astype(np.float64), n_out)
+    np.testing.assert_allclose(pred, pred_ref, rtol=0, atol=BF16_VS_FP64 * np.abs(pred_ref).max())
+    g, loss = net.gradients(Yd, tgt)
+    assert loss == pytest.approx(ref.loss(pred_e, tgt), rel=1e-3)
+    _per_layer(g, g_e, n_out, BF16_VS_EMULATED)
+    net.close()
+
+
+def test_bf16_gradients_within_the_bf16_bound_of_the_fp64_network():
+    # one point per scene: the max-pool routes nothing, so the FP64 network's
+    # gradients are the target; 300 scenes = three row tiles, ragged
+    n_out, B, N = 5, 300, 1
+    rng = np.random.default_rng(21)
+    Y = rng.uniform(-1, 1, (B, N, 3)).astype(np.float32)
+    tgt = rng.normal(0, 1, (B, n_out)).astype(np.float32)
+    p = _random_params(n_out, 22)
+    net = warmstart.Net(n_out, N, max_batch=B, seed=0, precision=warmstart.NET_BF16)
+    net.set_params(p)
+    g, _ = net.gradients(torch.tensor(Y, device="cuda"), tgt)
+    g_ref = ref.gradients(p.astype(np.float64), Y.astype(np.float64), tgt.astype(np.float64), n_out)
+    _per_layer(g, g_ref, n_out, BF16_VS_FP64)
+    _, g_e, _ = _bf16_operand_reference(p, Y, tgt, n_out)
+    _per_layer(g, g_e, n_out, BF16_VS_EMULATED)
+    net.close()
+
+
+def test_bf16_long_contraction_and_many_tiles():
+    # 4 scenes x 4096 points: 128 row tiles, and weight-gradient contractions
+    # of 16384 points split into 128 chunks of two 64-point steps.  Forward:
+    # random points.  Gradients: every scene repeats one point, so which
+    # point the max-pool routes to cannot change a gradient.
+    n_out, B, N = 9, 4, 4096
+    rng = np.random.default_rng(31)
+    p = _random_params(n_out, 32)
+    net = warmstart.Net(n_out, N, max_batch=B, seed=0, precision=warmstart.NET_BF16)
+    net.set_params(p)
+    Y = rng.uniform(-1, 1, (B, N, 3)).astype(np.float32)
+    tgt = rng.normal(0, 1, (B, n_out)).astype(np.float32)
+    pred = net.forward(torch.tensor(Y, device="cuda"))
+    pred_e, _, _ = _bf16_operand_reference(p, Y, tgt, n_out)
+    np.testing.assert_allclose(pred, pred_e, rtol=0, atol=BF16_VS_EMULATED * np.abs(pred_e).max())
+    Yr = np.repeat(rng.uniform(-1, 1, (B, 1, 3)), N, axis=1).astype(np.float32)
+    g, _ = net.gradients(torch.tensor(Yr, device="cuda"), tgt)
+    _, g_e, _ = _bf16_operand_reference(p, Yr, tgt, n_out)
+    _per_layer(g, g_e, n_out, BF16_VS_EMULATED)
+    net.close()
+
+
+@pytest.mark.parametrize("precision", [warmstart.NET_FP32, warmstart.NET_BF16])
+def test_training_reduces_the_loss(precision):
     # a target that depends on the point set: its centroid and extent
     N, B = 64, 16
     rng = np.random.default_rng(7)
     Y = rng.uniform(-1, 1, (256, N, 3)).astype(np.float32) * rng.uniform(0.3, 1.0, (256, 1, 3)).astype(np.float32)
     tgt = np.concatenate([Y.mean(1), Y.max(1) - Y.min(1)], axis=1).astype(np.float32)
-    net = warmstart.Net(6, N, max_batch=B, seed=1)
+    net = warmstart.Net(6, N, max_batch=B, seed=1, precision=precision)
     Yd = torch.tensor(Y, device="cuda")
     first = last = None
     for s in range(400):
@@ -80,7 +228,9 @@ def test_coefficients_and_warm_start_round_trip():
         np.testing.assert_array_equal(T0.cpu().numpy(), ps.X.astype(np.float32))
 
 
-def test_learned_warm_start_needs_fewer_iterations():
+@pytest.fixture(scope="module")
+def _ws_data():
+    """Scenes and method-generated targets of the small warm-start workload."""
     cfg = datagen.WARMSTART_WORKLOADS["fp32_warmstart_m512_k32"]
     X = datagen.gen(cfg["M"], seed=cfg["seed_x"]).X.astype(np.float32)
     n = cfg["n_train"] + cfg["n_val"] + cfg["n_test"]
@@ -88,9 +238,17 @@ def test_learned_warm_start_needs_fewer_iterations():
     Ys = np.stack([s.Y.astype(np.float32) for s in sets])
     with cpd.Context(torch.tensor(X, device="cuda"), precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"],
                      lam=cfg["lam"], K=cfg["K"]) as ctx:
+        targets = warmstart.registration_targets(ctx, Ys[:cfg["n_train"] + cfg["n_val"]], cfg["K"], cfg["iters"])
+    return cfg, X, Ys, targets
+
+
+@pytest.mark.parametrize("precision", [warmstart.NET_FP32, warmstart.NET_BF16])
+def test_learned_warm_start_needs_fewer_iterations(_ws_data, precision):
+    cfg, X, Ys, targets = _ws_data
+    with cpd.Context(torch.tensor(X, device="cuda"), precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"],
+                     lam=cfg["lam"], K=cfg["K"]) as ctx:
         tr, va = cfg["n_train"], cfg["n_train"] + cfg["n_val"]
-        targets = warmstart.registration_targets(ctx, Ys[:va], cfg["K"], cfg["iters"])
-        ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3)
+        ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3, precision=precision)
         losses = ws.fit(Ys[:tr], targets[:tr], cfg["steps"], cfg["batch"], cfg["lr"])
         assert np.mean(losses[-50:]) < 0.5 * np.mean(losses[:20])
         ws.calibrate(Ys[tr:va], targets[tr:va], cfg["M"])
