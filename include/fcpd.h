@@ -78,10 +78,11 @@ typedef enum {
                           streams half the bytes; and while sigma2 is large
                           (sigma2 >= 4.4e-4 R^2, R the largest point norm)
                           the E-step's Gaussian exponents come from FP16
-                          tensor-core products (warp-level mma.sync
-                          m16n8k16, operands split into two FP16 parts,
-                          K = 16, FP32 accumulation), below it from the
-                          FP32 passes.  Not a precision the paper uses; its
+                          tensor-core products (tcgen05.mma kind::f16,
+                          M = 128 tiles accumulated in tensor memory,
+                          operands split into two FP16 parts, K = 16,
+                          FP32 accumulation), below it from the FP32
+                          passes.  Not a precision the paper uses; its
                           error against the FP64 oracle is measured and
                           stated, not bounded by the FP32 tolerance.
                           Points, outputs: float.                        */

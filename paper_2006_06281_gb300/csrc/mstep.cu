@@ -243,15 +243,16 @@ colsum_bulk(const S* __restrict__ A, int64_t ldA, int rows, int cols, const type
 
 // Diagonal update of the first K columns; columns K .. k_zero - 1 (the
 // directions a trimmed M-step drops) get B = C = 0.
-template <typename F>
+template <typename F, int COLS>
 __global__ void __launch_bounds__(kThreadsD)
 diag_update(const F* __restrict__ partP, int chunks, int64_t ldP, int K, int k_zero, const double* __restrict__ lam,
             typename Vec<F>::t4* __restrict__ B4, typename Vec<F>::t4* __restrict__ C4,
             const DevState* __restrict__ st, int gate, int trim) {
   if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
-  dev::diag_update_body<F>(partP, chunks, ldP, K, lam, B4, C4, st, 0, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
-  const int k = blockIdx.x * kMRedCols + threadIdx.x;
-  if (threadIdx.x < kMRedCols && k >= K && k < k_zero) {
+  dev::diag_update_body<F, COLS>(partP, chunks, ldP, K, lam, B4, C4, st, 0, blockIdx.x, blockIdx.y, gridDim.x,
+                                 gridDim.y);
+  const int k = blockIdx.x * COLS + threadIdx.x;
+  if (threadIdx.x < COLS && k >= K && k < k_zero) {
     typename Vec<F>::t4 z;
     z.x = z.y = z.z = z.w = (F)0;
     B4[k] = z;
@@ -387,6 +388,24 @@ void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA,
                                             clear_row_flags, trim);
 }
 
+// diag_update over columns 0 .. k_zero - 1 with as few columns per block as
+// keep each thread's share of the `chunks` partial rows at about 8 (64
+// columns per block for few chunks, down to 8 for hundreds).
+template <typename F>
+void launch_diag(const F* part, int chunks, int64_t ldP, int K, int k_zero, const double* lam,
+                 typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, const DevState* st, int gate, int trim,
+                 cudaStream_t s) {
+  const int sub = (chunks + 7) / 8;
+  const int cols = sub > 16 ? 8 : sub > 8 ? 16 : sub > 4 ? 32 : 64;
+  const unsigned blocks = (unsigned)cdiv(k_zero, cols);
+  switch (cols) {
+    case 8: diag_update<F, 8><<<blocks, kThreadsD, 0, s>>>(part, chunks, ldP, K, k_zero, lam, B4, C4, st, gate, trim); break;
+    case 16: diag_update<F, 16><<<blocks, kThreadsD, 0, s>>>(part, chunks, ldP, K, k_zero, lam, B4, C4, st, gate, trim); break;
+    case 32: diag_update<F, 32><<<blocks, kThreadsD, 0, s>>>(part, chunks, ldP, K, k_zero, lam, B4, C4, st, gate, trim); break;
+    default: diag_update<F, 64><<<blocks, kThreadsD, 0, s>>>(part, chunks, ldP, K, k_zero, lam, B4, C4, st, gate, trim); break;
+  }
+}
+
 template <typename F, typename S>
 void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
@@ -397,15 +416,11 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
   const int g = iteration ? 1 : 0;
   const MstepPlan* tr = iteration ? trim : nullptr;
   const int mf = tr ? 1 : 0;      // the full M-step's trim mode
-  const unsigned dblocks = (unsigned)cdiv(K, kMRedCols);
   if (tr) launch_colsum<F, S>(*tr, false, U, tr->ldU, tr->ldPp, M, tr->K, R4, part, st, g, g, 2, s);
   launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
   record_after(ev, 0, s);
-  if (tr)
-    diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4,
-                                                 st, g, 2);
-  diag_update<F><<<dblocks, kThreadsD, 0, s>>>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g,
-                                               mf);
+  if (tr) launch_diag<F>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4, st, g, 2, s);
+  launch_diag<F>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g, mf, s);
   record_after(ev, 1, s);
   if (tr) launch_colsum<F, S>(*tr, true, Ut, tr->ldM, tr->ldM, tr->K, M, B4, part, st, g, 0, 2, s);
   launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, B4, part, st, g, 0, mf, s);

@@ -167,16 +167,19 @@ __device__ __forceinline__ void colsum_body(const S* FCPD_RESTRICT A, int64_t ld
 
 // Sum of the chunk partials of column `col` (accumulated in F: FP32 partials
 // are summed in FP32 -- GB300's FP64 rate is a small fraction of FP32 -- in a
-// fixed order; the FP64 path sums in FP64).  kMRedSub threads per column each
-// take a strided subset; the subsets are added in order through `part`.
-template <typename F>
+// fixed order; the FP64 path sums in FP64).  A block serves COLS columns;
+// kThreadsD / COLS threads per column each take a strided subset; the subsets
+// are added in order through `part`.  Fewer columns per block shorten each
+// thread's chain of dependent loads when there are many chunks.
+template <typename F, int COLS = kMRedCols>
 __device__ __forceinline__ void chunk_sums(const F* FCPD_RESTRICT partials, int chunks, int64_t ldP, int col,
-                                           int ncols, F (&a)[3], F (*part)[3][kMRedCols]) {
-  const int c = threadIdx.x % kMRedCols, sub = threadIdx.x / kMRedCols;
+                                           int ncols, F (&a)[3], F (*part)[3][COLS]) {
+  constexpr int SUB = kThreadsD / COLS;
+  const int c = threadIdx.x % COLS, sub = threadIdx.x / COLS;
   F s[3] = {(F)0, (F)0, (F)0};
   if (col < ncols) {
 #pragma unroll 4
-    for (int k = sub; k < chunks; k += kMRedSub)
+    for (int k = sub; k < chunks; k += SUB)
 #pragma unroll
       for (int d = 0; d < 3; ++d) s[d] += __ldcg(partials + ((size_t)k * 3 + d) * ldP + col);
   }
@@ -187,25 +190,27 @@ __device__ __forceinline__ void chunk_sums(const F* FCPD_RESTRICT partials, int 
   for (int d = 0; d < 3; ++d) {
     F t = (F)0;
 #pragma unroll
-    for (int j = 0; j < kMRedSub; ++j) t += part[j][d][c];
+    for (int j = 0; j < SUB; ++j) t += part[j][d][c];
     a[d] = t;
   }
 }
 
 // Diagonal update (once per column k) with the sigma2 of this iteration's
-// E-step: B_k = s_k a_k, C_k = a_k / (l_k + lambda sigma2).
-template <typename F>
+// E-step: B_k = s_k a_k, C_k = a_k / (l_k + lambda sigma2).  COLS columns per
+// block (as chunk_sums).
+template <typename F, int COLS = kMRedCols>
 __device__ __forceinline__ void diag_update_body(const F* FCPD_RESTRICT partP, int chunks, int64_t ldU, int K, const double* FCPD_RESTRICT lam,
             typename Vec<F>::t4* FCPD_RESTRICT B4, typename Vec<F>::t4* FCPD_RESTRICT C4,
             const DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+  static_assert(COLS <= kThreadsD && kThreadsD % COLS == 0, "columns per block must divide the block");
   if (gate && iteration_gated(st)) return;
-  __shared__ F part[kMRedSub][3][kMRedCols];
+  __shared__ F part[kThreadsD / COLS][3][COLS];
   __shared__ double lamsig;
   if (threadIdx.x == 0) lamsig = st->lambda * st->sigma2;
-  const int k = bx * kMRedCols + threadIdx.x % kMRedCols;
+  const int k = bx * COLS + threadIdx.x % COLS;
   F a[3];
-  chunk_sums<F>(partP, chunks, ldU, k, K, a, part);
-  if (threadIdx.x >= kMRedCols || k >= K) return;
+  chunk_sums<F, COLS>(partP, chunks, ldU, k, K, a, part);
+  if (threadIdx.x >= COLS || k >= K) return;
   const double inv = 1.0 / (lam[k] + lamsig);          // one FP64 division per column
   const double s = lam[k] * inv;
   using V4 = typename Vec<F>::t4;

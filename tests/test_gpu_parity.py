@@ -553,9 +553,9 @@ def test_mixed_precision_basis_is_the_fp16_rounding_of_the_fp32_basis():
 
 # ------------------------------- mixed precision: tensor-core E-step passes
 # While sigma2 >= 4.4e-4 R^2 (R: largest point norm) the CPD_MIXED E-step
-# takes its Gaussian exponents from FP16 tensor-core products (warp-level
-# mma.sync m16n8k16, each operand split into two FP16 parts, K = 16, FP32
-# accumulation).  The accumulated terms are as large as
+# takes its Gaussian exponents from FP16 tensor-core products (tcgen05.mma
+# kind::f16 with M = 128 tiles in tensor memory, each operand split into two
+# FP16 parts, K = 16, FP32 accumulation).  The accumulated terms are as large as
 # q^2 R^2 <= ~2000 units of the base-2 exponent, so its rounding reaches
 # ~1e-3 at the floor and less above it; the errors against the FP64 oracle
 # are printed and bounded here by what that allows: Gaussians within ~1e-3
