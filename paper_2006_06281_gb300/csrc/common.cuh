@@ -355,16 +355,25 @@ inline void record_after(cudaEvent_t* ev, int i, cudaStream_t s) {
   else cudaEventRecord(ev[i], s);
 }
 
+// Side stream of an iteration's E-step: the log-likelihood total is formed
+// there, beside pass B (fork after the column fix-up, join at the E-step's
+// end); the iterations then also skip the sum of V_m / P1_m.
+struct EstepSide {
+  cudaStream_t s;
+  cudaEvent_t fork, join;
+};
+
 // E-step: passes A and B with their reductions.  Reads T4, Y4 and st->sigma2;
 // writes Yt4, R4 (R4 needs X4; may be null to skip) and per-row P1 (double,
 // optional), per-column den (double, optional).  Gated by `gate` (iteration mode)
-// or always run (standalone).
+// or always run (standalone).  Without `side`, st->loglik and st->vsum are
+// complete when the last kernel ends.
 template <typename F>
 void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
-                  bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr);
+                  bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr, const EstepSide* side = nullptr);
 
 // M-step: projection a = U^T R, diagonal update, expansion T = X + U B and
 // the Eq. 18 variance in the epilogue.  U is M x ldU, Ut = U^T is K x ldM.

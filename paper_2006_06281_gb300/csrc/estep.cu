@@ -39,9 +39,27 @@ template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
 reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ Y4,
         int N, typename Vec<F>::t4* __restrict__ Yb, double* __restrict__ den_out,
-        double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate) {
+        double* __restrict__ sums, int* __restrict__ flag_cols, DevState* __restrict__ st, int gate, int defer) {
   const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
-  dev::reduceA_body<F>(partA, ch, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  dev::reduceA_body<F>(partA, ch, M, Y4, N, Yb, den_out, sums, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x,
+                       gridDim.y, defer);
+}
+
+// Eq. 3 from reduceA's block sums (deferred form): one block, launched on a
+// side stream after fixA so that it overlaps pass B; fixA's exact terms of
+// flagged columns are already in st->loglik.  Same summation order as the
+// last block of reduceA.
+__global__ void __launch_bounds__(kThreadsR)
+loglik_finish(const double* __restrict__ sums, int nsums, DevState* __restrict__ st, int M, int N, int gate) {
+  if (gate && iteration_gated(st)) return;
+  __shared__ double sh[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nsums; i += blockDim.x) v += __ldcg(sums + i);
+  const double tot = block_sum(v, sh);
+  if (threadIdx.x == 0) {
+    const double s2 = st->sigma2, w = st->w;
+    st->loglik += tot + (double)N * log((1.0 - w) / (double)M) - 1.5 * (double)N * log(2.0 * kPi * s2);
+  }
 }
 
 __global__ void __launch_bounds__(kThreadsF)
@@ -76,9 +94,10 @@ __global__ void __launch_bounds__(kThreadsR)
 reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ X4,
         typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
         double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
-        DevState* __restrict__ st, int gate) {
+        DevState* __restrict__ st, int gate, int skip_vsum) {
   const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
-  dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y,
+                       gridDim.x, gridDim.y, skip_vsum);
 }
 
 __global__ void __launch_bounds__(kThreadsF)
@@ -173,8 +192,9 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
-                  bool gate, cudaStream_t s, cudaEvent_t* ev) {
+                  bool gate, cudaStream_t s, cudaEvent_t* ev, const EstepSide* side) {
   const int g = gate ? 1 : 0;
+  const int defer = side ? 1 : 0;
   dim3 ga(pl.a_col_tiles, pl.a_row_chunks);
   dim3 gb(pl.b_row_tiles, pl.b_col_chunks);
   int* flag_rows = flags;
@@ -190,9 +210,16 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   }
   record_after(ev, 0, s);
   reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, pl.mm.a_chunks, (int)M, Y4,
-                                                            (int)N, Yb, den_out, sums, flag_cols, st, g);
+                                                            (int)N, Yb, den_out, sums, flag_cols, st, g, defer);
   if constexpr (sizeof(F) == 4) {
     fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
+  }
+  if (side) {
+    // the log-likelihood's total on the side stream, beside pass B
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->s, side->fork, 0);
+    loglik_finish<<<1, kThreadsR, 0, side->s>>>(sums, (int)pl.redA_blocks, st, (int)M, (int)N, g);
+    cudaEventRecord(side->join, side->s);
   }
   record_after(ev, 1, s);
   if constexpr (sizeof(F) == 4) {
@@ -206,18 +233,19 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   }
   record_after(ev, 2, s);
   reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, pl.mm.b_chunks, (int)M, X4,
-                                                            Yt4, R4, P1_out, sums, flag_rows, st, g);
+                                                            Yt4, R4, P1_out, sums, flag_rows, st, g, defer);
   if constexpr (sizeof(F) == 4) {
     fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
   }
+  if (side) cudaStreamWaitEvent(s, side->join, 0);
   record_after(ev, 3, s);
 }
 
 template void launch_estep<float>(const EstepPlan&, const float4*, const float4*, int64_t, const float4*,
                                   float4*, int64_t, float*, float*, double*, int*, float4*, float4*, double*,
-                                  double*, DevState*, bool, cudaStream_t, cudaEvent_t*);
+                                  double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*);
 template void launch_estep<double>(const EstepPlan&, const dvec4*, const dvec4*, int64_t, const dvec4*,
                                    dvec4*, int64_t, double*, double*, double*, int*, dvec4*, dvec4*, double*,
-                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*);
+                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*);
 
 }  // namespace fcpd

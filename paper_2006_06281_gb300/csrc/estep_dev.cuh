@@ -263,10 +263,13 @@ static_assert(kRedCols * kRedSub == kThreadsR, "columns per block must divide th
 
 template <typename F>
 // Returns true in the block that completed the reduction over all gx blocks
-// (the one that wrote the log-likelihood).
+// (the one that wrote the log-likelihood).  defer: only the block sums are
+// written (and the log-likelihood zeroed, for fixA's terms); loglik_finish,
+// off the critical path, adds them up.
 __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT Y4,
         int N, typename Vec<F>::t4* FCPD_RESTRICT Yb, double* FCPD_RESTRICT den_out,
-        double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_cols, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+        double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_cols, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy,
+        int defer = 0) {
   if (gate && iteration_gated(st)) return false;
   __shared__ double sh[32];
   __shared__ F part[kRedSub][kRedCols];
@@ -315,6 +318,13 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ENUMERIC);
   const double bs = block_sum(lnden, sh);
+  if (defer) {
+    if (threadIdx.x == 0) {
+      sums[bx] = bs;
+      if (bx == 0) st->loglik = 0.0;
+    }
+    return false;
+  }
   if (threadIdx.x == 0) {
     sums[bx] = bs;
     __threadfence();
@@ -854,10 +864,12 @@ static_assert(kRedRows * kRedRowSub == kThreadsR && kRedRows % 32 == 0, "rows pe
 
 template <typename F>
 // Returns true in the block that completed the reduction over all gx blocks.
+// skip_vsum: the EM iterations, which do not use the Eq. 18 sum of V_m / P1_m
+// as such (each row carries its share to the M-step), skip its reduction.
 __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT X4,
         typename Vec<F>::t4* FCPD_RESTRICT Yt4, typename Vec<F>::t4* FCPD_RESTRICT R4,
         double* FCPD_RESTRICT P1_out, double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_rows,
-        DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+        DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy, int skip_vsum = 0) {
   if (gate && iteration_gated(st)) return false;
   __shared__ double sh[32];
   __shared__ F part[kRedRowSub][5][kRedRows];
@@ -905,6 +917,7 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ENUMERIC);
+  if (skip_vsum) return false;
   const double bs = block_sum(vrow, sh);
   if (threadIdx.x == 0) {
     sums[bx] = bs;

@@ -143,6 +143,7 @@ struct cpd_ctx {
   int64_t M = 0, K = 0, ldU = 0, N = 0;
   cudaStream_t stream = nullptr; // caller's stream
   cudaStream_t cap = nullptr;    // internal stream used only for graph capture
+  EstepSide side{};              // captured side branch of each iteration's E-step
   Buf X4, T4, U, Ut, lam, Yt4, R4, B4, C4, Yhat4, W4, hist;
   Buf st, st_aux;
   Buf Y4, Yb, partA, partB, partP, sums, flags, stage;
@@ -177,6 +178,9 @@ struct cpd_ctx {
                    &sort_scratch, &sort_tmp})
       b->release();
     if (cap) cudaStreamDestroy(cap);
+    if (side.s) cudaStreamDestroy(side.s);
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.join) cudaEventDestroy(side.join);
   }
   void drop_graphs() {
     for (auto& g : graph)
@@ -423,7 +427,8 @@ cpd_status shared_group(cpd_ctx* c, int S, const void* const* Y, const int64_t* 
     launch_estep<float>(ep[(size_t)i], T4 + (size_t)i * M, c->X4.as<float4>(), M, Y4 + yoff[(size_t)i],
                         b[kYb].as<float4>(), N[i], b[kPA].as<float>(), b[kPB].as<float>(), b[kSums].as<double>(),
                         b[kFlags].as<int>(), b[kYt4].as<float4>() + (size_t)i * M,
-                        b[kR4].as<float4>() + (size_t)i * M, nullptr, nullptr, st[(size_t)i], true, c->cap);
+                        b[kR4].as<float4>() + (size_t)i * M, nullptr, nullptr, st[(size_t)i], true, c->cap,
+                        nullptr, &c->side);
   if (mixed)
     le = launch_mstep_multi_mma(pp, pe, c->U.as<__half>(), c->ldU, c->Ut.as<__half>(), c->mp.ldM, c->lam.as<double>(),
                                 M, K, c->X4.as<float4>(), b[kR4].as<float4>(), b[kYt4].as<float4>(), T4,
@@ -509,7 +514,7 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   if (c->fp64) {
     launch_estep<double>(c->ep, c->T4.as<dvec4>(), c->X4.as<dvec4>(), c->M, c->Y4.as<dvec4>(), c->Yb.as<dvec4>(),
                          c->N, c->partA.as<double>(), c->partB.as<double>(), c->sums.as<double>(), c->flags.as<int>(),
-                         c->Yt4.as<dvec4>(), c->R4.as<dvec4>(), nullptr, nullptr, st, true, s, ee);
+                         c->Yt4.as<dvec4>(), c->R4.as<dvec4>(), nullptr, nullptr, st, true, s, ee, &c->side);
     launch_mstep<double>(c->mp, c->U.as<double>(), c->Ut.as<double>(), c->lam.as<double>(), c->M, c->K,
                          c->X4.as<dvec4>(), c->R4.as<dvec4>(), c->Yt4.as<dvec4>(), c->T4.as<dvec4>(),
                          c->has_gt ? c->Yhat4.as<dvec4>() : nullptr, c->partP.as<double>(), c->sums.as<double>(),
@@ -517,7 +522,7 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   } else {
     launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
                         c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
-                        c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, ee);
+                        c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, ee, &c->side);
     mstep_f32(c, c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
               c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->B4.as<float4>(), c->C4.as<float4>(), st, true, s, em);
   }
@@ -726,8 +731,11 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(fail(CPD_ECUDA, "no CUDA device"));
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
     return bail(fail(CPD_ECUDA, "cannot query the SM count"));
-  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(fail(CPD_ECUDA, "cannot create the capture stream"));
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(CPD_ECUDA, "cannot create the capture streams"));
 
   cpd_status s;
   if ((s = c->X4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
