@@ -45,16 +45,24 @@ reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int chunks_m
                        gridDim.y, defer);
 }
 
-// Eq. 3 from reduceA's block sums (deferred form): one block, launched on a
-// side stream after fixA so that it overlaps pass B; fixA's exact terms of
-// flagged columns are already in st->loglik.  Same summation order as the
-// last block of reduceA.
+// Eq. 3 in the deferred form: one block, launched on a side stream after
+// fixA so that it overlaps pass B.  FP32: the sum of ln den_n =
+// -ln 2 * (-log2 den_n) over the exponent offsets that reduceA and fixA
+// left in Yb; FP64: the sum of reduceA's block sums (with fixA's nothing
+// to add).  Fixed summation order.
+template <typename F>
 __global__ void __launch_bounds__(kThreadsR)
-loglik_finish(const double* __restrict__ sums, int nsums, DevState* __restrict__ st, int M, int N, int gate) {
+loglik_finish(const double* __restrict__ sums, int nsums, const typename Vec<F>::t4* __restrict__ Yb,
+              DevState* __restrict__ st, int M, int N, int gate) {
   if (gate && iteration_gated(st)) return;
   __shared__ double sh[32];
   double v = 0.0;
-  for (int i = threadIdx.x; i < nsums; i += blockDim.x) v += __ldcg(sums + i);
+  if constexpr (sizeof(F) == 4) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) v += (double)Yb[i].w;
+    v *= -0.69314718055994531;
+  } else {
+    for (int i = threadIdx.x; i < nsums; i += blockDim.x) v += __ldcg(sums + i);
+  }
   const double tot = block_sum(v, sh);
   if (threadIdx.x == 0) {
     const double s2 = st->sigma2, w = st->w;
@@ -65,8 +73,9 @@ loglik_finish(const double* __restrict__ sums, int nsums, DevState* __restrict__
 __global__ void __launch_bounds__(kThreadsF)
 fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, int N,
          float4* __restrict__ Yb, double* __restrict__ den_out, const int* __restrict__ flag_cols,
-         DevState* __restrict__ st, int gate) {
-  dev::fixA_f32_body(T4, M, Y4, N, Yb, den_out, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+         DevState* __restrict__ st, int gate, int defer) {
+  dev::fixA_f32_body(T4, M, Y4, N, Yb, den_out, flag_cols, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
+                     defer);
 }
 
 __global__ void __launch_bounds__(kThreadsB)
@@ -212,13 +221,13 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   reduceA<F><<<(unsigned)pl.redA_blocks, kThreadsR, 0, s>>>(partA, pl.a_row_chunks, pl.pa_row_chunks, pl.mm.a_chunks, (int)M, Y4,
                                                             (int)N, Yb, den_out, sums, flag_cols, st, g, defer);
   if constexpr (sizeof(F) == 4) {
-    fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g);
+    fixA_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Y4, (int)N, Yb, den_out, flag_cols, st, g, defer);
   }
   if (side) {
     // the log-likelihood's total on the side stream, beside pass B
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->s, side->fork, 0);
-    loglik_finish<<<1, kThreadsR, 0, side->s>>>(sums, (int)pl.redA_blocks, st, (int)M, (int)N, g);
+    loglik_finish<F><<<1, kThreadsR, 0, side->s>>>(sums, (int)pl.redA_blocks, Yb, st, (int)M, (int)N, g);
     cudaEventRecord(side->join, side->s);
   }
   record_after(ev, 1, s);

@@ -247,6 +247,14 @@ __device__ __forceinline__ double outlier_c(const DevState* st, int M, int N) {
   const double t = 2.0 * kPi * st->sigma2;         // (2 pi sigma2)^(D/2), D = 3
   return t * sqrt(t) * (w / (1.0 - w)) * ((double)M / (double)N);
 }
+// The same constant in FP32 arithmetic (relative error a few 2^-24, below
+// that of the FP32 Gaussian sums it is added to): GB300's FP64 square root
+// and divisions would stand on the critical path of every reduction block.
+__device__ __forceinline__ double outlier_c_f32(const DevState* st, int M, int N) {
+  const float w = (float)st->w;
+  const float t = (float)(2.0 * kPi * st->sigma2);
+  return (double)(t * sqrtf(t) * (w / (1.f - w)) * ((float)M / (float)N));
+}
 
 // ------------------------------------------------- pass A reduction (+ c)
 // den_n = sum of the split partials + c (Eq. 4).  Prepares pass B's scene
@@ -263,9 +271,10 @@ static_assert(kRedCols * kRedSub == kThreadsR, "columns per block must divide th
 
 template <typename F>
 // Returns true in the block that completed the reduction over all gx blocks
-// (the one that wrote the log-likelihood).  defer: only the block sums are
-// written (and the log-likelihood zeroed, for fixA's terms); loglik_finish,
-// off the critical path, adds them up.
+// (the one that wrote the log-likelihood).  defer: the log-likelihood is
+// zeroed (for fixA's terms) and left to loglik_finish, off the critical
+// path, which sums the FP32 exponent offsets -log2 den_n in Yb (FP32) or
+// the block sums written here (FP64).
 __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT Y4,
         int N, typename Vec<F>::t4* FCPD_RESTRICT Yb, double* FCPD_RESTRICT den_out,
         double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_cols, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy,
@@ -277,7 +286,7 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
   __shared__ double c_sh;
   const double s2 = st->sigma2;
   const double w = st->w;
-  if (threadIdx.x == 0) c_sh = outlier_c(st, M, N);   // once per block
+  if (threadIdx.x == 0) c_sh = sizeof(F) == 4 ? outlier_c_f32(st, M, N) : outlier_c(st, M, N);   // once per block
   const int col = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
   const int n = bx * kRedCols + col;
   F s = (F)0;   // FP32 partials summed in FP32 (fixed order), FP64 in FP64
@@ -317,6 +326,10 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
     }
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&st->status, (int)CPD_ENUMERIC);
+  if (sizeof(F) == 4 && defer) {
+    if (bx == 0 && threadIdx.x == 0) st->loglik = 0.0;
+    return false;
+  }
   const double bs = block_sum(lnden, sh);
   if (defer) {
     if (threadIdx.x == 0) {
@@ -346,9 +359,10 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
 
 // Exact FP32 column denominators in the log domain for the listed columns:
 // den_n = 2^a (sum_m 2^(-d'^2_mn - a)) + c with a = max_m (-d'^2_mn).
+// defer_loglik: the column's Eq. 3 term is taken from Yb by loglik_finish.
 __device__ __forceinline__ void fixA_f32_body(const float4* FCPD_RESTRICT T4, int M, const float4* FCPD_RESTRICT Y4, int N,
          float4* FCPD_RESTRICT Yb, double* FCPD_RESTRICT den_out, const int* FCPD_RESTRICT flag_cols,
-         DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+         DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy, int defer_loglik = 0) {
   if (gate && iteration_gated(st)) return;
   const int count = st->n_flag_cols;
   if (count == 0) return;
@@ -388,7 +402,7 @@ __device__ __forceinline__ void fixA_f32_body(const float4* FCPD_RESTRICT T4, in
         const float lid = (float)(-log2(den));
         Yb[n].w = lid;
         if (den_out) den_out[n] = den;
-        atomicAdd(&st->loglik, -0.69314718055994531 * (double)lid);
+        if (!defer_loglik) atomicAdd(&st->loglik, -0.69314718055994531 * (double)lid);
       }
     }
   }

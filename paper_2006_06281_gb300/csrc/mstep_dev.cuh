@@ -282,15 +282,25 @@ __device__ __forceinline__ bool expand_finish_body(const F* FCPD_RESTRICT partE,
   __shared__ double sh3[32][3];
   __shared__ bool last;
   const int m = bx * kMRedCols + threadIdx.x % kMRedCols;
+  // the row's own inputs are loaded first, in flight during the chunk sums
+  const bool row = threadIdx.x < kMRedCols && m < M;
+  V4 x{}, to{}, yt{}, yh{};
+  if (row) {
+    if (X4) x = X4[m];
+    if constexpr (EPI) {
+      to = Tout[m];
+      yt = Yt4[m];
+      if (Yhat4) yh = Yhat4[m];
+    }
+  }
   F a[3];
   chunk_sums<F>(partE, chunks, ldM, m, M, a, part);
   double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
-  if (threadIdx.x < kMRedCols && m < M) {
-    double x0 = 0, x1 = 0, x2 = 0;
-    if (X4) { const V4 x = X4[m]; x0 = x.x; x1 = x.y; x2 = x.z; }
+  if (row) {
     V4 tn;
-    tn.x = (F)(x0 + (double)a[0]); tn.y = (F)(x1 + (double)a[1]); tn.z = (F)(x2 + (double)a[2]); tn.w = (F)0;
-    if constexpr (EPI) point_terms<V4>(Tout[m], tn, Yt4[m], Yhat4, m, contrib, dT2, gt2);
+    tn.x = (F)((double)x.x + (double)a[0]); tn.y = (F)((double)x.y + (double)a[1]);
+    tn.z = (F)((double)x.z + (double)a[2]); tn.w = (F)0;
+    if constexpr (EPI) point_terms<V4>(to, tn, yt, Yhat4 ? &yh : nullptr, 0, contrib, dT2, gt2);
     Tout[m] = tn;
   }
   if constexpr (EPI) {
