@@ -139,15 +139,27 @@ KERNELS = ["e_pass_a", "e_reduce_a", "e_pass_b", "e_reduce_b", "m_project", "m_d
 OPS_PER_PAIR = {"e_pass_a": 7, "e_pass_b": 12}      # FP32 pipe ops per Gaussian pair (kernel mix)
 
 
+ROWS_MAX_K = 256    # narrow bases: the expansion and its epilogue are one launch (expand_rows)
+
+
 def roofline_entries(phase_ms, M, N, K, peaks, es=4):
     """Algorithmic work per launch / measured average launch duration
-    (phase_ms: milliseconds per launch of each kernel)."""
+    (phase_ms: milliseconds per launch of each kernel).  With a narrow basis
+    (K <= ROWS_MAX_K, FP32 working precision) the expansion runs inside the
+    last M-step launch: its time is in m_finish, and m_expand is left out."""
     clk = peaks["sm_max_mhz"] * 1e6
     sms = 152
+    rows = K <= ROWS_MAX_K and es != 8
     out = {}
     for i, name in enumerate(KERNELS):
         t = phase_ms[i] / 1e3                       # s per launch
-        if t <= 0:
+        if t <= 0 or (rows and name == "m_expand"):
+            continue
+        if rows and name == "m_finish":
+            byts = M * K * es + M * 16 * 4          # U once + X, T, Ytil read and T written
+            out[name] = dict(bound="hbm", achieved=byts / t / 1e9, peak=peaks["hbm_gbs"], unit="GB/s",
+                             frac=byts / t / 1e9 / peaks["hbm_gbs"], ms=t * 1e3, bytes=byts,
+                             kernel="expand_rows (T = X + U B with the Eq. 18 epilogue, one launch)")
             continue
         if name in OPS_PER_PAIR:
             pairs = M * N

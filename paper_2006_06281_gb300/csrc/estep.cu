@@ -50,20 +50,32 @@ reduceA(const F* __restrict__ partA, int chunks, int chunks_pruned, int chunks_m
 // -ln 2 * (-log2 den_n) over the exponent offsets that reduceA and fixA
 // left in Yb; FP64: the sum of reduceA's block sums (with fixA's nothing
 // to add).  Fixed summation order.
+// 1024 threads, four independent partial sums per thread (loads in flight
+// together rather than one per dependent add).
+constexpr int kThreadsL = 1024;
 template <typename F>
-__global__ void __launch_bounds__(kThreadsR)
+__global__ void __launch_bounds__(kThreadsL)
 loglik_finish(const double* __restrict__ sums, int nsums, const typename Vec<F>::t4* __restrict__ Yb,
               DevState* __restrict__ st, int M, int N, int gate) {
   if (gate && iteration_gated(st)) return;
   __shared__ double sh[32];
-  double v = 0.0;
-  if constexpr (sizeof(F) == 4) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) v += (double)Yb[i].w;
-    v *= -0.69314718055994531;
-  } else {
-    for (int i = threadIdx.x; i < nsums; i += blockDim.x) v += __ldcg(sums + i);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int n = sizeof(F) == 4 ? N : nsums;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 4 * kThreadsL) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = i0 + j * kThreadsL;
+      if (i < n) {
+        if constexpr (sizeof(F) == 4)
+          v[j] += (double)Yb[i].w;
+        else
+          v[j] += __ldcg(sums + i);
+      }
+    }
   }
-  const double tot = block_sum(v, sh);
+  double t = (v[0] + v[1]) + (v[2] + v[3]);
+  if constexpr (sizeof(F) == 4) t *= -0.69314718055994531;
+  const double tot = block_sum(t, sh);
   if (threadIdx.x == 0) {
     const double s2 = st->sigma2, w = st->w;
     st->loglik += tot + (double)N * log((1.0 - w) / (double)M) - 1.5 * (double)N * log(2.0 * kPi * s2);
@@ -227,7 +239,7 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
     // the log-likelihood's total on the side stream, beside pass B
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->s, side->fork, 0);
-    loglik_finish<F><<<1, kThreadsR, 0, side->s>>>(sums, (int)pl.redA_blocks, Yb, st, (int)M, (int)N, g);
+    loglik_finish<F><<<1, kThreadsL, 0, side->s>>>(sums, (int)pl.redA_blocks, Yb, st, (int)M, (int)N, g);
     cudaEventRecord(side->join, side->s);
   }
   record_after(ev, 1, s);

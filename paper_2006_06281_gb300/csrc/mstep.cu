@@ -274,6 +274,121 @@ expand_finish(const F* __restrict__ partE, int chunks, int64_t ldM, int M,
   if (EPI && last && trim == 2 && threadIdx.x == 0) st->trim_iters += 1;
 }
 
+// ---------------------------------------- narrow basis: row expansion
+// T = X + U B and the Eq. 18 epilogue in ONE launch when the basis is narrow
+// (K <= kRowsMaxK: the low-rank and trimmed M-steps).  There the column-
+// parallel expansion over U^T (colsum_bulk) is latency-bound -- K rows of
+// 16-byte vectors split over few blocks -- and its partials need the
+// expand_finish launch.  Here one thread owns one model point: it reads its
+// row of U once in 16-byte vectors (eight in flight), multiplies with B from
+// shared memory (every thread reads the same element: a broadcast) in a
+// fixed order, forms t_m and the row's Eq. 18 terms in FP64 -- the epilogue
+// of all 32 rows of a warp in parallel -- and the block sums (FP64) meet in
+// the last block to finish (ticket), which ends the iteration as
+// expand_finish does.  (Four threads per point, 64 points per block,
+// measured slower: 26 against 19 us per launch at M = 20000, K = 200.)
+constexpr int kRowsMaxK = 256;
+constexpr int kRowsThreads = 128;
+
+__device__ __forceinline__ void row_load(const float* p, float (&u)[8]) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
+}
+__device__ __forceinline__ void row_load(const __half* p, float (&u)[8]) {
+  const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+  const __half2* h = reinterpret_cast<const __half2*>(&r);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __half22float2(h[i]);
+    u[2 * i] = f.x;
+    u[2 * i + 1] = f.y;
+  }
+}
+
+template <typename S, bool EPI>
+__global__ void __launch_bounds__(kRowsThreads)
+expand_rows(const S* __restrict__ U, int64_t ldU, int M, int K, const float4* __restrict__ B4,
+            const float4* __restrict__ X4, const float4* __restrict__ Yt4, float4* __restrict__ Tout,
+            const float4* __restrict__ Yhat4, double* __restrict__ sums, DevState* __restrict__ st, int gate,
+            int trim) {
+  if (trim_skip(st, trim) || (gate && iteration_gated(st))) return;
+  constexpr int L = 16 / (int)sizeof(S);       // elements per 16-byte vector
+  __shared__ float sB[3][kRowsMaxK + 8];
+  __shared__ double sh3[32][3];
+  __shared__ bool last;
+  const int m = blockIdx.x * kRowsThreads + threadIdx.x;
+  const bool row = m < M;
+  // the row's inputs, in flight with the basis row
+  float4 x = make_float4(0.f, 0.f, 0.f, 0.f), to{}, yt{}, yh{};
+  if (row) {
+    if (X4) x = X4[m];
+    if constexpr (EPI) {
+      to = Tout[m];
+      yt = Yt4[m];
+      if (Yhat4) yh = Yhat4[m];
+    }
+  }
+  for (int k = threadIdx.x; k < kRowsMaxK + 8; k += kRowsThreads) {
+    const float4 b = k < K ? B4[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    sB[0][k] = b.x;
+    sB[1][k] = b.y;
+    sB[2][k] = b.z;
+  }
+  __syncthreads();
+  double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
+  if (row) {
+    const int nvec = (K + L - 1) / L;          // 16-byte vectors holding the K columns
+    const S* ur = U + (size_t)m * ldU;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll 8
+    for (int v = 0; v < nvec; ++v) {
+      float u[8];
+      row_load(ur + (size_t)v * L, u);
+#pragma unroll
+      for (int i = 0; i < L; ++i) {
+        const int k = v * L + i;                // sB is zero past K (the padding of U never counts)
+        const float w = k < K ? u[i] : 0.f;
+        a0 = fmaf(w, sB[0][k], a0);
+        a1 = fmaf(w, sB[1][k], a1);
+        a2 = fmaf(w, sB[2][k], a2);
+      }
+    }
+    float4 tn;
+    tn.x = (float)((double)x.x + (double)a0);
+    tn.y = (float)((double)x.y + (double)a1);
+    tn.z = (float)((double)x.z + (double)a2);
+    tn.w = 0.f;
+    if constexpr (EPI) point_terms<float4>(to, tn, yt, Yhat4 ? &yh : nullptr, 0, contrib, dT2, gt2);
+    Tout[m] = tn;
+  }
+  if constexpr (EPI) {
+    block_sum3(contrib, dT2, gt2, sh3, kRowsThreads / 32);
+    if (threadIdx.x == 0) {
+      sums[(size_t)blockIdx.x * 3] = contrib;
+      sums[(size_t)blockIdx.x * 3 + 1] = dT2;
+      sums[(size_t)blockIdx.x * 3 + 2] = gt2;
+      __threadfence();
+      last = atomicAdd(&st->ticket_e, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double s0 = 0, s1 = 0, s2 = 0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += kRowsThreads) {
+        s0 += __ldcg(sums + (size_t)i * 3);
+        s1 += __ldcg(sums + (size_t)i * 3 + 1);
+        s2 += __ldcg(sums + (size_t)i * 3 + 2);
+      }
+      block_sum3(s0, s1, s2, sh3, kRowsThreads / 32);
+      if (threadIdx.x == 0) {
+        finish_iteration(st, s0, s1, s2, M);
+        st->ticket_e = 0;
+        if (trim == 2) st->trim_iters += 1;
+      }
+    }
+  }
+}
+
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Row chunks for a colsum over a rows x ld matrix: enough blocks to fill the
@@ -388,6 +503,23 @@ void launch_colsum(const MstepPlan& pl, bool expansion, const S* A, int64_t ldA,
                                             clear_row_flags, trim);
 }
 
+template <typename F> bool rows_expansion(int64_t K) { return std::is_same<F, float>::value && K <= kRowsMaxK; }
+
+// One thread per model point; the block sums fit the plan's scratch, sized
+// for e_blocks = M / 64 blocks.
+template <typename F, typename S>
+void launch_expand_rows(const S* U, int64_t ldU, int64_t M, int64_t K, const typename Vec<F>::t4* B4,
+                        const typename Vec<F>::t4* X4, const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
+                        const typename Vec<F>::t4* Yhat4, double* sums, int e_blocks, DevState* st, int gate,
+                        int trim, cudaStream_t s) {
+  if constexpr (std::is_same<F, float>::value) {
+    const unsigned grid = (unsigned)cdiv(M, kRowsThreads);   // <= e_blocks (64 rows per block there)
+    (void)e_blocks;
+    expand_rows<S, true><<<grid, kRowsThreads, 0, s>>>(U, ldU, (int)M, (int)K, B4, X4, Yt4, T4, Yhat4, sums, st,
+                                                       gate, trim);
+  }
+}
+
 // diag_update over columns 0 .. k_zero - 1 with as few columns per block as
 // keep each thread's share of the `chunks` partial rows at about 8 (64
 // columns per block for few chunks, down to 8 for hundreds).
@@ -422,15 +554,26 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
   if (tr) launch_diag<F>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4, st, g, 2, s);
   launch_diag<F>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g, mf, s);
   record_after(ev, 1, s);
-  if (tr) launch_colsum<F, S>(*tr, true, Ut, tr->ldM, tr->ldM, tr->K, M, B4, part, st, g, 0, 2, s);
-  launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, B4, part, st, g, 0, mf, s);
+  // narrow bases (FP32 working precision, iterations): the row expansion
+  // with its epilogue replaces colsum (U^T) + expand_finish
+  const bool rows_tr = iteration && tr && rows_expansion<F>(tr->K);
+  const bool rows_pl = iteration && rows_expansion<F>(K);
+  if (tr && !rows_tr) launch_colsum<F, S>(*tr, true, Ut, tr->ldM, tr->ldM, tr->K, M, B4, part, st, g, 0, 2, s);
+  if (!rows_pl) launch_colsum<F, S>(pl, true, Ut, pl.ldM, pl.ldM, K, M, B4, part, st, g, 0, mf, s);
   record_after(ev, 2, s);
   if (iteration) {
-    if (tr)
-      expand_finish<F, true><<<tr->e_blocks, kThreadsD, 0, s>>>(part, tr->e_row_chunks, tr->ldM, (int)M, X4, Yt4,
-                                                                T4, Yhat4, sums, st, g, 2);
-    expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
-                                                             Yhat4, sums, st, g, mf);
+    if (tr) {
+      if (rows_tr)
+        launch_expand_rows<F, S>(U, tr->ldU, M, tr->K, B4, X4, Yt4, T4, Yhat4, sums, tr->e_blocks, st, g, 2, s);
+      else
+        expand_finish<F, true><<<tr->e_blocks, kThreadsD, 0, s>>>(part, tr->e_row_chunks, tr->ldM, (int)M, X4,
+                                                                  Yt4, T4, Yhat4, sums, st, g, 2);
+    }
+    if (rows_pl)
+      launch_expand_rows<F, S>(U, pl.ldU, M, K, B4, X4, Yt4, T4, Yhat4, sums, pl.e_blocks, st, g, mf, s);
+    else
+      expand_finish<F, true><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4, T4,
+                                                               Yhat4, sums, st, g, mf);
   } else {
     expand_finish<F, false><<<pl.e_blocks, kThreadsD, 0, s>>>(part, pl.e_row_chunks, pl.ldM, (int)M, X4, Yt4,
                                                               T4, nullptr, sums, st, 0, 0);
