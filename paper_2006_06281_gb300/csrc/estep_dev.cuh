@@ -289,6 +289,8 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
   if (threadIdx.x == 0) c_sh = sizeof(F) == 4 ? outlier_c_f32(st, M, N) : outlier_c(st, M, N);   // once per block
   const int col = threadIdx.x % kRedCols, sub = threadIdx.x / kRedCols;
   const int n = bx * kRedCols + col;
+  typename Vec<F>::t4 y{};                    // y_n, in flight with the partial loads
+  if (sub == 0 && n < N) y = Y4[n];
   F s = (F)0;   // FP32 partials summed in FP32 (fixed order), FP64 in FP64
   if (n < N) {
 #pragma unroll 8
@@ -304,7 +306,6 @@ __device__ __forceinline__ bool reduceA_body(const F* FCPD_RESTRICT partA, int c
 #pragma unroll
     for (int j = 0; j < kRedSub; ++j) tot += part[j][col];
     const double den = (double)tot + c;
-    const typename Vec<F>::t4 y = Y4[n];
     if constexpr (sizeof(F) == 4) {
       const float q = scale_q(s2);
       if (!(den >= kColFloor) || !isfinite(den)) {
@@ -841,8 +842,7 @@ __device__ __forceinline__ void passB_f64_body(const dvec4* FCPD_RESTRICT T4, in
 // Writes the Eq. 5 outputs of row m from its (possibly rescaled) sums.
 template <typename F>
 __device__ __forceinline__ void write_row(int m, double p1s, double px, double py, double pz, double v,
-                                          double unscale, double unscale2,
-                                          const typename Vec<F>::t4* FCPD_RESTRICT X4,
+                                          double unscale, double unscale2, const typename Vec<F>::t4& x,
                                           typename Vec<F>::t4* FCPD_RESTRICT Yt4,
                                           typename Vec<F>::t4* FCPD_RESTRICT R4, double* vrow_out) {
   const double inv = 1.0 / p1s;                       // one FP64 division per row
@@ -853,7 +853,6 @@ __device__ __forceinline__ void write_row(int m, double p1s, double px, double p
   yt.x = (F)yx; yt.y = (F)yy; yt.z = (F)yz; yt.w = (F)vrow;
   Yt4[m] = yt;
   if (R4) {
-    const V4 x = X4[m];
     V4 r;
     r.x = (F)(yx - (double)x.x); r.y = (F)(yy - (double)x.y); r.z = (F)(yz - (double)x.z); r.w = (F)0;
     R4[m] = r;
@@ -891,6 +890,8 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
   const int row = threadIdx.x % kRedRows, sub = threadIdx.x / kRedRows;
   const int m = bx * kRedRows + row;
   const size_t plane = (size_t)chunks * M;
+  typename Vec<F>::t4 xm{};                   // x_m, in flight with the partial loads
+  if (R4 && sub == 0 && m < M) xm = X4[m];
   F a[5] = {(F)0, (F)0, (F)0, (F)0, (F)0};   // summed in F, fixed order
   if (m < M) {
 #pragma unroll 4
@@ -918,7 +919,7 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
         flag_rows[atomicAdd(&st->n_flag_rows, 1)] = m;
       } else {
         const float qi = 1.0f / scale_q(st->sigma2);
-        write_row<F>(m, p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, X4, Yt4, R4, &vrow);
+        write_row<F>(m, p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, xm, Yt4, R4, &vrow);
         if (P1_out) P1_out[m] = p1;
       }
     } else {
@@ -926,7 +927,7 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
         bad = 1;
         p1 = 1.0;   // keep outputs finite; the status word reports the failure
       }
-      write_row<F>(m, p1, px, py, pz, v, 1.0, 1.0, X4, Yt4, R4, &vrow);
+      write_row<F>(m, p1, px, py, pz, v, 1.0, 1.0, xm, Yt4, R4, &vrow);
       if (P1_out) P1_out[m] = bad ? 0.0 : p1;
     }
   }
@@ -1000,7 +1001,8 @@ __device__ __forceinline__ void fixB_f32_body(const float4* FCPD_RESTRICT T4, in
       } else {
         const float qi = 1.0f / q;
         double vrow = 0.0;
-        write_row<float>(m, (double)p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, X4, Yt4, R4, &vrow);
+        const float4 xf = R4 ? X4[m] : float4{};
+        write_row<float>(m, (double)p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, xf, Yt4, R4, &vrow);
         if (P1_out) P1_out[m] = mass;
         atomicAdd(&st->vsum, vrow);
       }
