@@ -26,19 +26,21 @@
 // Buffers such as T, Yb and the partial sums are written in one phase and
 // read in a later one of the same launch, so no argument of the device bodies
 // is __restrict__ here (only U and U^T, constant for the launch, go through
-// the read-only path).  The E-step bodies are compiled with 4 scene points
-// (pass A) and 4 model points (pass B) per thread: tiles of 1024 points keep
-// the padding of small pairs (a few hundred points) low, where the per-pair
-// launches use 16 and 8 for scenes of tens of thousands of points
-// (FCPD_BATCH_PTS sets the count for full tiles; partial last tiles use
-// fewer).  The
+// the read-only path).  The E-step bodies are compiled with 8 scene points
+// (pass A) and 8 model points (pass B) per thread: 2048-point tiles, whose
+// partial last tile runs with 2, 4 or 6 points per thread (the fewest that
+// cover it) so that small pairs stay lightly padded, where the per-pair
+// launches use 16 and 8 for scenes of tens of thousands of points.  At 256
+// pairs of 500..8000 points 8 per thread took 0.40 s per 100 iterations
+// against 0.42 s with 4 (pass A's shared-memory reads are then shared by
+// twice the Gaussians); FCPD_BATCH_PTS sets the count.  The
 // reduction bodies give each thread a whole column (row) of chunk partials:
 // a pair has only a few chunks here, and a reduction block's fixed latency
 // (dependent loads, block sums, the completion ticket) is paid per 256
 // columns instead of per 32 or 64.
 #define FCPD_RESTRICT
 #ifndef FCPD_BATCH_PTS
-#define FCPD_BATCH_PTS 4
+#define FCPD_BATCH_PTS 8
 #endif
 #define FCPD_EA_COLS FCPD_BATCH_PTS
 #define FCPD_EB_ROWS FCPD_BATCH_PTS
@@ -262,7 +264,7 @@ __device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int
 }
 
 // Pass A (B) of one tile with the fewest points per thread that cover the
-// points left in it: a partial last tile runs with 2 or 4 per thread.
+// points left in it: a partial last tile runs with 2, 4 or 6 per thread.
 __device__ __forceinline__ void passA_tile(const BatchPair& P, int bx, int by) {
   using namespace dev;
   const EstepPlan& e = P.ep;
@@ -275,6 +277,13 @@ __device__ __forceinline__ void passA_tile(const BatchPair& P, int bx, int by) {
   if constexpr (kColsA32 > 4) {
     if (rem <= kThreadsA * 4) {
       passA_f32_body<4>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
+                        e.a_row_chunks);
+      return;
+    }
+  }
+  if constexpr (kColsA32 > 6) {
+    if (rem <= kThreadsA * 6) {
+      passA_f32_body<6>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
                         e.a_row_chunks);
       return;
     }
@@ -296,6 +305,13 @@ __device__ __forceinline__ void passB_tile(const BatchPair& P, int bx, int by) {
   if constexpr (kRowsB32 > 4) {
     if (rem <= kThreadsB * 4) {
       passB_f32_body<4>(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles,
+                        e.b_col_chunks, 0);
+      return;
+    }
+  }
+  if constexpr (kRowsB32 > 6) {
+    if (rem <= kThreadsB * 6) {
+      passB_f32_body<6>(P.T4, P.M, P.Yb, P.N, e.b_cols_per_chunk, P.partB, P.st, 1, bx, by, e.b_row_tiles,
                         e.b_col_chunks, 0);
       return;
     }

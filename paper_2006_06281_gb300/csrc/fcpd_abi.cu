@@ -220,8 +220,10 @@ cpd_status upload_points(cpd_ctx* c, const void* src, int64_t n, void* dst, bool
 }
 
 // Writes 4-vectors `src` to a caller array (n x 3, host or device).  Host
-// destinations synchronise `s`.
-cpd_status download_points(const void* src, int64_t n, void* dst, Buf& stage, bool fp64, cudaStream_t s) {
+// destinations synchronise `s` (unless `sync` is false: the caller then
+// synchronises before it returns).
+cpd_status download_points(const void* src, int64_t n, void* dst, Buf& stage, bool fp64, cudaStream_t s,
+                           bool sync = true) {
   const size_t es = fp64 ? 8 : 4;
   const bool dev = is_device_ptr(dst);
   void* out = dst;
@@ -234,7 +236,7 @@ cpd_status download_points(const void* src, int64_t n, void* dst, Buf& stage, bo
   CUDA_TRY(cudaGetLastError());
   if (!dev) {
     CUDA_TRY(cudaMemcpyAsync(dst, stage.p, (size_t)n * 3 * es, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    if (sync) CUDA_TRY(cudaStreamSynchronize(s));
   }
   return CPD_OK;
 }
@@ -254,8 +256,8 @@ cpd_status upload_model(cpd_ctx* c, const void* src, void* dst4) {
   return CPD_OK;
 }
 
-cpd_status download_model(cpd_ctx* c, const void* src4, void* dst) {
-  if (!c->sorted_model) return download_points(src4, c->M, dst, c->stage, c->fp64, c->stream);
+cpd_status download_model(cpd_ctx* c, const void* src4, void* dst, bool sync = true) {
+  if (!c->sorted_model) return download_points(src4, c->M, dst, c->stage, c->fp64, c->stream, sync);
   const bool dev = is_device_ptr(dst);
   float* out = static_cast<float*>(dst);
   if (!dev) {
@@ -266,7 +268,7 @@ cpd_status download_model(cpd_ctx* c, const void* src4, void* dst) {
   CUDA_TRY(cudaGetLastError());
   if (!dev) {
     CUDA_TRY(cudaMemcpyAsync(dst, out, (size_t)c->M * 3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (sync) CUDA_TRY(cudaStreamSynchronize(c->stream));
   }
   return CPD_OK;
 }
@@ -900,8 +902,11 @@ cpd_status cpd_iterate(cpd_ctx* c, const void* Y, int64_t N, int32_t n_iter, voi
       for (int i = 0; i < n1; ++i) CUDA_TRY(cudaGraphLaunch(c->graph[0], c->stream));
     }
   }
-  if (T_out) STATUS_TRY(download_model(c, c->T4.p, T_out));
-  if (sigma2_out || iters_done || (T_out && !is_device_ptr(T_out))) {
+  // a host T_out is followed by the state read, whose synchronisation
+  // covers the copy of T as well
+  const bool host_T = T_out && !is_device_ptr(T_out);
+  if (T_out) STATUS_TRY(download_model(c, c->T4.p, T_out, !host_T));
+  if (sigma2_out || iters_done || host_T) {
     DevState h;
     STATUS_TRY(read_state(c, &h));
     if (sigma2_out) *sigma2_out = h.sigma2;

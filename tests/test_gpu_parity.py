@@ -181,6 +181,14 @@ def test_register_fp32_m5000():
     assert rel(T, ref["T"]) <= FP32_TOL
     check_sigma2(s2, ref["sigma2"], FP32_TOL, "FP32 M=N=5000 final")
     check_sigma2(hist["sigma2"], ref["sigma2_hist"], FP32_TOL, "FP32 M=N=5000 history")
+    # Eq. 3 per iteration: in the FP32 path each column's ln den_n comes from
+    # the FP32 exponent offset -log2 den_n (formed beside pass B, off the
+    # critical path) and sigma2 enters as -(N D / 2) ln sigma2, so the
+    # absolute error is held to N (1.5 FP32_TOL + 2^-18)
+    ll_err = float(np.abs(hist["loglik"] - ref["loglik_hist"]).max())
+    ll_tol = Y.shape[0] * (1.5 * FP32_TOL + 2.0 ** -18)
+    print(f"[loglik] FP32 M=N=5000 history: largest error {ll_err:.3e} (tolerance {ll_tol:.3e})")
+    assert ll_err <= ll_tol
 
 
 # (M = N = 1 collapses sigma2 to the rounding floor within a few iterations;
