@@ -354,7 +354,7 @@ def run_batch(args, peaks, torch):
                setup_s=setup_s, timed_calls=len(ms),
                autotune=dict(chosen=dict(e_items_per_block=tune_e, proj_kbytes=tune_p), seconds=tune_s,
                              candidates_ms_3_iters=dict(zip(["e2/p256", "e2/p512", "e4/p256", "e4/p512", "e8/p256",
-                                                             "e8/p512"], tune_ms))))
+                                                             "e8/p512", "e16/p256", "e16/p512"], tune_ms))))
     # the same pairs in CPD_MIXED: FP16 bases streamed by the M-step phases
     t0 = time.perf_counter()
     bm = cpd.Batch(Xs, Ys, w=bc["omega"], beta=bc["beta"], lam=bc["lam"], K=bc["K"], precision=cpd.MIXED)

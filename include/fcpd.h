@@ -525,11 +525,11 @@ cpd_status cpd_batch_reset(cpd_batch *b);
 
 /*
  * Autotuner of the persistent kernel's work items: times n_iter (1..64)
- * iterations of the batch under each of six work-item plans -- E-step items
- * per resident block in {2, 4, 8} x projection items of {256, 512} KB of the
- * basis, in that order -- keeps the fastest, and restarts every
+ * iterations of the batch under each of eight work-item plans -- E-step items
+ * per resident block in {2, 4, 8, 16} x projection items of {256, 512} KB of
+ * the basis, in that order -- keeps the fastest, and restarts every
  * registration (as cpd_batch_reset).  Optional outputs (host): the chosen
- * e_items and proj_kb, and ms_out[6], the measured milliseconds of each
+ * e_items and proj_kb, and ms_out[8], the measured milliseconds of each
  * candidate.  Synchronises.  The results of the registrations do not depend
  * on the plan beyond summation order.
  */

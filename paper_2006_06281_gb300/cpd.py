@@ -431,10 +431,10 @@ class Batch:
         _check(load().cpd_batch_reset(self._h))
 
     def autotune(self, n_iter=3):
-        """Times six work-item plans, keeps the fastest (registrations restart).
+        """Times eight work-item plans, keeps the fastest (registrations restart).
         Returns (e_items, proj_kb, ms per candidate)."""
         e, p = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 6)()
+        ms = (C.c_float * 8)()
         _check(load().cpd_batch_autotune(self._h, int(n_iter), C.byref(e), C.byref(p), ms))
         return e.value, p.value, list(ms)
 

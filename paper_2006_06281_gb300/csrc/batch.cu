@@ -33,17 +33,20 @@
 // launches use 16 and 8 for scenes of tens of thousands of points.  At 256
 // pairs of 500..8000 points 8 per thread took 0.40 s per 100 iterations
 // against 0.42 s with 4 (pass A's shared-memory reads are then shared by
-// twice the Gaussians); FCPD_BATCH_PTS sets the count.  The
+// twice the Gaussians); FCPD_BATCH_PTS_A / _B set the counts.  The
 // reduction bodies give each thread a whole column (row) of chunk partials:
 // a pair has only a few chunks here, and a reduction block's fixed latency
 // (dependent loads, block sums, the completion ticket) is paid per 256
 // columns instead of per 32 or 64.
 #define FCPD_RESTRICT
-#ifndef FCPD_BATCH_PTS
-#define FCPD_BATCH_PTS 8
+#ifndef FCPD_BATCH_PTS_A
+#define FCPD_BATCH_PTS_A 8
 #endif
-#define FCPD_EA_COLS FCPD_BATCH_PTS
-#define FCPD_EB_ROWS FCPD_BATCH_PTS
+#ifndef FCPD_BATCH_PTS_B
+#define FCPD_BATCH_PTS_B 8
+#endif
+#define FCPD_EA_COLS FCPD_BATCH_PTS_A
+#define FCPD_EB_ROWS FCPD_BATCH_PTS_B
 #define FCPD_RED_COLS 256
 #define FCPD_RED_ROWS 256
 #define FCPD_MRED_COLS 256
@@ -182,28 +185,47 @@ __device__ __forceinline__ void proj_narrow_body(const B* U, int64_t ldU, int M,
   }
 }
 
-// Expansion for a basis of at most 128 columns, fused with the T update and
-// Eq. 18: one item is a tile of kTileColsE model points over all K rows of
-// U^T (8 points per thread, B staged in shared memory), so T comes out of
-// registers; a per-pair ticket over the tiles lets the block that completes
-// the pair finish the iteration.
+// Expansion of a narrow basis (K <= kNarrowMaxK) fused with T and Eq. 18: one
+// item is a tile of kNarrowTileE = 256 model points; lane l of every warp
+// owns points 8l..8l+7 of the tile (32-byte loads of a row of U^T) and warp w
+// takes the rows k = w, w + 8, .. of U^T, so each thread has K / 8 rows to
+// stream instead of K; the eight warps' partial sums meet in shared memory
+// (added in warp order), after which thread t forms point t's t_m and Eq. 18
+// terms -- the FP64 epilogue of 256 points in parallel.  A per-pair ticket
+// over the tiles lets the block that completes the pair finish the iteration.
+constexpr int kNarrowTileE = 256;
+static_assert(kNarrowTileE == 32 * 8 && kThreadsBatch == kNarrowTileE, "one point per thread in the epilogue");
+// the warps' partial sums: [warp][coordinate][point w of a lane][lane],
+// padded; one array for both basis types
+__shared__ float s_narrow_red[kThreadsBatch / 32][3][8][33];
 template <typename B>
 __device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int K, int M, const float4* B4,
                                                    const float4* X4, const float4* Yt4, float4* T4,
                                                    const float4* Yhat4, double* sums, DevState* st, int bx, int gx) {
   if (iteration_gated(st)) return;
+  constexpr int NW = kThreadsBatch / 32;
   __shared__ float4 sB[kNarrowMaxK];
-  __shared__ double sh[32];
+  float (*red)[3][8][33] = s_narrow_red;
+  __shared__ double sh3[32][3];
   __shared__ bool last;
+  // the epilogue's inputs of point t, in flight with the expansion
+  const int m = bx * kNarrowTileE + threadIdx.x;
+  float4 x{}, to{}, yt{};
+  if (m < M) {
+    x = X4[m];
+    to = T4[m];
+    yt = Yt4[m];
+  }
   for (int i = threadIdx.x; i < K; i += kThreadsBatch) sB[i] = B4[i];
   __syncthreads();
-  const int c0 = (bx * kThreadsBatch + threadIdx.x) * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c0 = bx * kNarrowTileE + lane * 8;
   float acc[8][3];
 #pragma unroll
   for (int w = 0; w < 8; ++w) acc[w][0] = acc[w][1] = acc[w][2] = 0.f;
-  if (c0 < M) {
+  if (c0 < M) {                                 // c0 + 8 <= ldM: rows of U^T are padded to 8
 #pragma unroll 4
-    for (int k = 0; k < K; ++k) {
+    for (int k = warp; k < K; k += NW) {
       float u[8];
       load8(Ut + (size_t)k * ldM + c0, u);
       const float4 b = sB[k];
@@ -215,32 +237,34 @@ __device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int
       }
     }
   }
-  double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const int m = c0 + w;
-    if (m < M) {
-      const float4 x = X4[m];
-      float4 tn;
-      tn.x = (float)((double)x.x + (double)acc[w][0]);
-      tn.y = (float)((double)x.y + (double)acc[w][1]);
-      tn.z = (float)((double)x.z + (double)acc[w][2]);
-      tn.w = 0.f;
-      double c, d, g;
-      dev::point_terms<float4>(T4[m], tn, Yt4[m], Yhat4, m, c, d, g);
-      contrib += c;
-      dT2 += d;
-      gt2 += g;
-      T4[m] = tn;
+  for (int w = 0; w < 8; ++w)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) red[warp][d][w][lane] = acc[w][d];
+  __syncthreads();
+  const int lp = threadIdx.x >> 3, wp = threadIdx.x & 7;   // point t = 8 * lane' + w
+  double contrib = 0.0, dT2 = 0.0, gt2 = 0.0;
+  if (m < M) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      a0 += red[j][0][wp][lp];
+      a1 += red[j][1][wp][lp];
+      a2 += red[j][2][wp][lp];
     }
+    float4 tn;
+    tn.x = (float)((double)x.x + (double)a0);
+    tn.y = (float)((double)x.y + (double)a1);
+    tn.z = (float)((double)x.z + (double)a2);
+    tn.w = 0.f;
+    dev::point_terms<float4>(to, tn, yt, Yhat4, m, contrib, dT2, gt2);
+    T4[m] = tn;
   }
-  const double b0 = block_sum(contrib, sh);
-  const double b1 = block_sum(dT2, sh);
-  const double b2 = block_sum(gt2, sh);
+  block_sum3(contrib, dT2, gt2, sh3, NW);
   if (threadIdx.x == 0) {
-    sums[(size_t)bx * 3] = b0;
-    sums[(size_t)bx * 3 + 1] = b1;
-    sums[(size_t)bx * 3 + 2] = b2;
+    sums[(size_t)bx * 3] = contrib;
+    sums[(size_t)bx * 3 + 1] = dT2;
+    sums[(size_t)bx * 3 + 2] = gt2;
     __threadfence();
     last = atomicAdd(&st->ticket_e, 1u) == (unsigned)gx - 1;
   }
@@ -253,41 +277,35 @@ __device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int
       a1 += __ldcg(sums + (size_t)i * 3 + 1);
       a2 += __ldcg(sums + (size_t)i * 3 + 2);
     }
-    const double t0 = block_sum(a0, sh);
-    const double t1 = block_sum(a1, sh);
-    const double t2 = block_sum(a2, sh);
+    block_sum3(a0, a1, a2, sh3, NW);
     if (threadIdx.x == 0) {
-      dev::finish_iteration(st, t0, t1, t2, M);
+      dev::finish_iteration(st, a0, a1, a2, M);
       st->ticket_e = 0;
     }
   }
 }
 
 // Pass A (B) of one tile with the fewest points per thread that cover the
-// points left in it: a partial last tile runs with 2, 4 or 6 per thread.
+// points left in it: a partial last tile runs with 2, 4, 6 (or, with wider
+// tiles, 8 and 12) per thread.
 __device__ __forceinline__ void passA_tile(const BatchPair& P, int bx, int by) {
   using namespace dev;
   const EstepPlan& e = P.ep;
   const int rem = P.N - bx * kTileColsA;
-  if (rem <= kThreadsA * 2) {
-    passA_f32_body<2>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
-                      e.a_row_chunks);
-    return;
+#define FCPD_PASS_A_PART(C)                                                                                  \
+  if constexpr (kColsA32 > C) {                                                                              \
+    if (rem <= kThreadsA * C) {                                                                              \
+      passA_f32_body<C>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,   \
+                        e.a_row_chunks);                                                                     \
+      return;                                                                                                \
+    }                                                                                                        \
   }
-  if constexpr (kColsA32 > 4) {
-    if (rem <= kThreadsA * 4) {
-      passA_f32_body<4>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
-                        e.a_row_chunks);
-      return;
-    }
-  }
-  if constexpr (kColsA32 > 6) {
-    if (rem <= kThreadsA * 6) {
-      passA_f32_body<6>(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles,
-                        e.a_row_chunks);
-      return;
-    }
-  }
+  FCPD_PASS_A_PART(2)
+  FCPD_PASS_A_PART(4)
+  FCPD_PASS_A_PART(6)
+  FCPD_PASS_A_PART(8)
+  FCPD_PASS_A_PART(12)
+#undef FCPD_PASS_A_PART
   passA_f32_body(P.T4, P.M, e.a_rows_per_chunk, P.Y4, P.N, P.partA, P.st, 1, bx, by, e.a_col_tiles, e.a_row_chunks);
 }
 
@@ -538,7 +556,7 @@ void plan_batch(BatchPair* P, int n_pairs, int resident, int e_items_per_block, 
       m.p_row_chunks = (int)cdiv(M, rows);
     }
     m.p_rows_per_chunk = (int)cdiv(M, m.p_row_chunks);
-    m.e_col_tiles = (int)cdiv(m.ldM, colsC);
+    m.e_col_tiles = (int)cdiv(p.narrow ? M : m.ldM, p.narrow ? (int64_t)kNarrowTileE : colsC);
     if (p.narrow) {
       m.e_row_chunks = 1;                // the fused expansion takes all K rows per tile
       m.e_rows_per_chunk = (int)K;

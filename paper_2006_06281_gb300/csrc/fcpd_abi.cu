@@ -1640,7 +1640,7 @@ cpd_status cpd_batch_autotune(cpd_batch* b, int32_t n_iter, int32_t* e_items_out
   if (!b) return fail(CPD_EINVAL, "batch is NULL");
   if (n_iter < 1 || n_iter > 64) return fail(CPD_EINVAL, "n_iter must be in [1, 64]");
   DeviceGuard guard(b->dev);
-  static const int cand[][2] = {{2, 256}, {2, 512}, {4, 256}, {4, 512}, {8, 256}, {8, 512}};
+  static const int cand[][2] = {{2, 256}, {2, 512}, {4, 256}, {4, 512}, {8, 256}, {8, 512}, {16, 256}, {16, 512}};
   const int nc = (int)(sizeof(cand) / sizeof(cand[0]));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));

@@ -188,9 +188,9 @@ def test_autotuner_keeps_results_and_reports_candidates(scenes):
         Tref = [ref.T(i) for i in range(len(Xs))]
     with cpd.Batch(Xs, Ys, K=128) as b:
         e, p, ms = b.autotune(2)
-        assert e in (2, 4, 8) and p in (256, 512)
-        assert len(ms) == 6 and all(m > 0 for m in ms)
-        assert min(ms) == pytest.approx(ms[[2, 4, 8].index(e) * 2 + [256, 512].index(p)])
+        assert e in (2, 4, 8, 16) and p in (256, 512)
+        assert len(ms) == 8 and all(m > 0 for m in ms)
+        assert min(ms) == pytest.approx(ms[[2, 4, 8, 16].index(e) * 2 + [256, 512].index(p)])
         assert not b.state()[1].any()          # registrations restarted
         b.iterate(12)
         for i in range(len(Xs)):
