@@ -11,6 +11,13 @@ namespace {
 
 using namespace dev;
 
+// Resident blocks per SM that pass B's register budget is fitted to: 2 (96
+// registers); 3 (80 registers, no spills) measured 0.194 against 0.168 ms at
+// M = N = 20000 -- the extra warps do not pay for the tighter schedule.
+#ifndef FCPD_EB_MINB
+#define FCPD_EB_MINB 2
+#endif
+
 // The dense FP32 passes step aside (return at once) in iterations that use
 // the pruned layout, and the pruned ones in all others; both are in every
 // captured iteration.
@@ -90,7 +97,7 @@ fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, in
                      defer);
 }
 
-__global__ void __launch_bounds__(kThreadsB)
+__global__ void __launch_bounds__(kThreadsB, FCPD_EB_MINB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
           int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
   if (prune_active(st) || mma_active(st)) return;
