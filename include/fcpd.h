@@ -44,9 +44,13 @@
  *   - Only D = 3 is implemented (the paper's experiments are 3-D point sets).
  *   - Host-side fault injection for tests: environment variable CPD_FAULT =
  *     "alloc" (first device allocation of cpd_setup fails -> CPD_ENOMEM),
- *     "solver" (the eigensolver reports failure -> CPD_ESOLVER) or
+ *     "solver" (the eigensolver reports failure -> CPD_ESOLVER),
  *     "nan_sigma" (the initial variance is NaN -> CPD_ENUMERIC on the first
- *     iteration).  Nothing is faulted on the GPU.
+ *     iteration), or a device wait made to run out without faulting the
+ *     GPU -> CPD_ETIMEOUT: "barrier" (the batched kernel's grid barrier),
+ *     "bulk_wait" (the M-step's bulk-copy ring), "umma_wait" (the
+ *     shared-model tensor-core products), "gemm_wait" (the BF16 tensor-core
+ *     GEMM of the warm-start network).  Nothing is faulted on the GPU.
  */
 #ifndef FCPD_H
 #define FCPD_H

@@ -455,10 +455,12 @@ cudaError_t launch_mstep_multi_mma(const UmmaPlan& pp, const UmmaPlan& pe, const
 // split-K partials out[chunk][P][ldo] (to be summed in order); else the
 // epilogue + bias, ReLU or the mask (0 where mask[p][n] <= 0) and the FP32
 // result out[P][ldo] with optional BF16 copies (row-major, transposed [N][ld_t]).
+// fault_wait (host fault injection only): every pipeline wait runs out
+// after 50 ms and *status receives CPD_ETIMEOUT.
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int P, int N,
                            int Q, int chunks, const float* bias, bool relu, const float* mask, int64_t ldm,
                            float* out, int64_t ldo, __nv_bfloat16* out_bf, int64_t ld_bf, __nv_bfloat16* out_t,
-                           int64_t ld_t, int* status, cudaStream_t s);
+                           int64_t ld_t, int* status, bool fault_wait, cudaStream_t s);
 int gemm_tc_chunks(int Q, int chunks);
 void launch_to_bf16(const float* X, int64_t R, int C, __nv_bfloat16* row, __nv_bfloat16* tr, int64_t ldt,
                     cudaStream_t s);

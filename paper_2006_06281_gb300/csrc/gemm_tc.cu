@@ -19,7 +19,9 @@
 //                  copies -- the operands of the next GEMMs.
 // Every wait is bounded in wall time; on expiry the CTA records
 // CPD_ETIMEOUT in *status, waits (bounded) for its copies and MMAs, frees
-// its TMEM and returns without writing.
+// its TMEM and returns without writing.  extra_tx > 0 (host fault injection
+// only) makes every full barrier expect more bytes than its copies carry,
+// so the waits run out (after wait_ns) while every copy still lands.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -66,7 +68,7 @@ struct GemmOut {
 template <int NB>
 __global__ void __launch_bounds__(kGThreads, 1)
 gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int P, int Q, int kspc,
-        GemmOut o, int* __restrict__ status) {
+        GemmOut o, int* __restrict__ status, unsigned int extra_tx, unsigned long long wait_ns) {
   constexpr int STAGE = g_stage_bytes<NB>();
   constexpr uint32_t COLS = NB;           // 128 or 256 TMEM columns
   constexpr uint32_t IDESC = g_idesc<NB>();
@@ -106,13 +108,13 @@ gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     for (int i = 0; i < nk; ++i) {
       const int slot = i % kGStages;
-      if (i >= kGStages && !mbar_wait(&empty[slot], (uint32_t)((i / kGStages) - 1) & 1u, kGWaitNs)) {
+      if (i >= kGStages && !mbar_wait(&empty[slot], (uint32_t)((i / kGStages) - 1) & 1u, wait_ns)) {
         s_fail = 1;
         break;
       }
       if (s_fail) break;
       unsigned char* st = smem + (size_t)slot * STAGE;
-      mbar_expect_tx(&full[slot], (uint32_t)STAGE);
+      mbar_expect_tx(&full[slot], (uint32_t)STAGE + extra_tx);
       tma_load_2d(st, &tmA, (k0 + i) * kGK, blockIdx.x * kGM, &full[slot], pol);
       tma_load_2d(st + kGABytes, &tmB, (k0 + i) * kGK, 0, &full[slot], pol);
       issued = i + 1;
@@ -121,7 +123,7 @@ gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     int i = 0;
     for (; i < nk; ++i) {
       const int slot = i % kGStages;
-      if (s_fail || !mbar_wait(&full[slot], (uint32_t)(i / kGStages) & 1u, kGWaitNs)) {
+      if (s_fail || !mbar_wait(&full[slot], (uint32_t)(i / kGStages) & 1u, wait_ns)) {
         s_fail = 1;
         break;
       }
@@ -137,14 +139,14 @@ gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtenso
     s_consumed = i;
     umma_commit(done);
   }
-  const bool ok_done = mbar_wait(done, 0, kGWaitNs);
+  const bool ok_done = mbar_wait(done, 0, wait_ns);
   __syncthreads();
   if (!ok_done) s_fail = 1;
   __syncthreads();
   if (s_fail || nk == 0) {
     if (s_fail && threadIdx.x == 0) {
       atomicExch(status, (int)CPD_ETIMEOUT);
-      for (int j = s_consumed; j < issued; ++j) mbar_wait(&full[j % kGStages], (uint32_t)(j / kGStages) & 1u, kGWaitNs);
+      for (int j = s_consumed; j < issued; ++j) mbar_wait(&full[j % kGStages], (uint32_t)(j / kGStages) & 1u, wait_ns);
     }
   } else {
     fence_after();
@@ -259,8 +261,10 @@ template <int NB> bool gemm_smem_ready() {
 cudaError_t launch_gemm_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int P, int N,
                            int Q, int chunks, const float* bias, bool relu, const float* mask, int64_t ldm,
                            float* out, int64_t ldo, __nv_bfloat16* out_bf, int64_t ld_bf, __nv_bfloat16* out_t,
-                           int64_t ld_t, int* status, cudaStream_t s) {
+                           int64_t ld_t, int* status, bool fault_wait, cudaStream_t s) {
   if (N != 128 && N != 256) return cudaErrorInvalidValue;
+  const unsigned int extra_tx = fault_wait ? 16u : 0u;
+  const unsigned long long wait_ns = fault_wait ? 50000000ull : kGWaitNs;
   CUtensorMap ma, mb;
   if (!make_map_2d(&ma, A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, P, Q, lda, kGM) ||
       !make_map_2d(&mb, B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, N, Q, ldb, N))
@@ -287,10 +291,10 @@ cudaError_t launch_gemm_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloa
   const dim3 grid((unsigned)cdiv(P, kGM), (unsigned)chunks);
   if (N == 128) {
     if (!gemm_smem_ready<128>()) return cudaErrorInvalidValue;
-    gemm_tc<128><<<grid, kGThreads, g_smem_bytes<128>(), s>>>(ma, mb, P, Q, kspc, o, status);
+    gemm_tc<128><<<grid, kGThreads, g_smem_bytes<128>(), s>>>(ma, mb, P, Q, kspc, o, status, extra_tx, wait_ns);
   } else {
     if (!gemm_smem_ready<256>()) return cudaErrorInvalidValue;
-    gemm_tc<256><<<grid, kGThreads, g_smem_bytes<256>(), s>>>(ma, mb, P, Q, kspc, o, status);
+    gemm_tc<256><<<grid, kGThreads, g_smem_bytes<256>(), s>>>(ma, mb, P, Q, kspc, o, status, extra_tx, wait_ns);
   }
   return cudaGetLastError();
 }

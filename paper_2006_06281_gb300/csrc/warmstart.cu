@@ -23,6 +23,7 @@
 // weights, Adam moments, biases, the first layer (3 inputs), the head and all
 // reductions stay FP32.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <random>
@@ -315,11 +316,18 @@ __nv_bfloat16* w2t_bf(cpd_net* n) { return bf(n->wbf) + 128 * 128; }
 __nv_bfloat16* w3_bf(cpd_net* n) { return bf(n->wbf) + 2 * 128 * 128; }
 __nv_bfloat16* w3t_bf(cpd_net* n) { return bf(n->wbf) + 2 * 128 * 128 + 128 * 256; }
 
+// CPD_FAULT=gemm_wait (host fault injection): the tensor-core GEMMs' waits
+// run out, exercising their bounded waits and the CPD_ETIMEOUT report.
+bool gemm_fault() {
+  const char* f = std::getenv("CPD_FAULT");
+  return f && std::strcmp(f, "gemm_wait") == 0;
+}
+
 // out (R x N) = epilogue(A B^T) on the tensor cores, A: R x Q, B: N x Q (BF16).
 void tc(cpd_net* n, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t R, int N, int Q,
         const float* bias, bool relu, const float* mask_by, float* out, __nv_bfloat16* out_bf, __nv_bfloat16* out_t) {
   if (launch_gemm_tc(A, lda, B, ldb, (int)R, N, Q, 1, bias, relu, mask_by, N, out, N, out_bf, N, out_t, n->ldt,
-                     n->gstat.as<int>(), n->stream) != cudaSuccess)
+                     n->gstat.as<int>(), gemm_fault(), n->stream) != cudaSuccess)
     n->launch_failed = true;
 }
 
@@ -328,7 +336,7 @@ void tc(cpd_net* n, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B,
 void tc_splitk(cpd_net* n, const __nv_bfloat16* A, const __nv_bfloat16* B, int P, int N, int64_t Q, float* C) {
   const int S = gemm_tc_chunks((int)Q, kTcChunks);
   if (launch_gemm_tc(A, n->ldt, B, n->ldt, P, N, (int)Q, S, nullptr, false, nullptr, 0, n->part.as<float>(), N,
-                     nullptr, 0, nullptr, 0, n->gstat.as<int>(), n->stream) != cudaSuccess)
+                     nullptr, 0, nullptr, 0, n->gstat.as<int>(), gemm_fault(), n->stream) != cudaSuccess)
     n->launch_failed = true;
   sum_splits<<<(unsigned)cdiv((int64_t)P * N, 256), 256, 0, n->stream>>>(n->part.as<float>(), S, (int64_t)P * N, C);
 }

@@ -191,6 +191,25 @@ def test_bf16_long_contraction_and_many_tiles():
     net.close()
 
 
+def test_bf16_gemm_wait_timeout_is_reported_and_recoverable(monkeypatch):
+    """Host fault injection: every full barrier of the BF16 tensor-core GEMM
+    expects 16 bytes more than its copies carry, so its bounded waits run
+    out (50 ms); the call reports CPD_ETIMEOUT, the GPU stays usable and the
+    next call equals one before the fault."""
+    n_out, B, N = 5, 3, 100
+    rng = np.random.default_rng(41)
+    Yd = torch.tensor(rng.uniform(-1, 1, (B, N, 3)).astype(np.float32), device="cuda")
+    net = warmstart.Net(n_out, N, max_batch=B, seed=2, precision=warmstart.NET_BF16)
+    before = net.forward(Yd)
+    monkeypatch.setenv("CPD_FAULT", "gemm_wait")
+    with pytest.raises(cpd.CpdError) as ei:
+        net.forward(Yd)
+    assert ei.value.status == cpd.ETIMEOUT
+    monkeypatch.delenv("CPD_FAULT")
+    np.testing.assert_array_equal(net.forward(Yd), before)
+    net.close()
+
+
 @pytest.mark.parametrize("precision", [warmstart.NET_FP32, warmstart.NET_BF16])
 def test_training_reduces_the_loss(precision):
     # a target that depends on the point set: its centroid and extent
