@@ -348,9 +348,12 @@ def run_batch(args, peaks, torch):
                grid_blocks=grid, work_items_per_iter=items, launches_per_call=2,
                ms_per_call=t * 1e3, pair_iters_per_s=float(it.sum()) / t, gaussian_pairs_per_s=gauss / t,
                estep_alu_floor_frac=floor / t, all_ok=bool((it == I).all() and not st.any()),
-               phase_ms_per_iter=dict(zip(["estep_a_with_column_reduction", "estep_b_with_row_reduction",
-                                           "projection_with_diag_update", "expansion_with_sigma2"], phase)),
-               phase_busy_fraction=busy,
+               phase_gpu_ms_per_iter=dict(zip(["estep_a_with_column_reduction", "estep_b_with_row_reduction",
+                                               "projection_with_diag_update", "expansion_with_sigma2"], phase)),
+               phase_work_fraction=busy,
+               phase_note="GPU time per iteration inside each phase's work items (phases of different pairs "
+                          "overlap); work fraction = time working / (working + waiting for the pair's "
+                          "previous phase)",
                setup_s=setup_s, timed_calls=len(ms),
                autotune=dict(chosen=dict(e_items_per_block=tune_e, proj_kbytes=tune_p), seconds=tune_s,
                              candidates_ms_3_iters=dict(zip(["e2/p256", "e2/p512", "e4/p256", "e4/p512", "e8/p256",

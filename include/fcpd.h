@@ -47,7 +47,8 @@
  *     "solver" (the eigensolver reports failure -> CPD_ESOLVER),
  *     "nan_sigma" (the initial variance is NaN -> CPD_ENUMERIC on the first
  *     iteration), or a device wait made to run out without faulting the
- *     GPU -> CPD_ETIMEOUT: "barrier" (the batched kernel's grid barrier),
+ *     GPU -> CPD_ETIMEOUT: "barrier" (the batched kernel's waits between
+ *     the phases of a pair),
  *     "bulk_wait" (the M-step's bulk-copy ring), "umma_wait" (the
  *     shared-model tensor-core products), "gemm_wait" (the BF16 tensor-core
  *     GEMM of the warm-start network).  Nothing is faulted on the GPU.
@@ -452,8 +453,8 @@ void cpd_destroy(cpd_ctx *ctx);
  * ONE persistent cooperative kernel launch, replayed from a CUDA graph.  The
  * launch's blocks take the work items of all pairs (tiles of the E-step
  * passes, row chunks of the basis products, reduction blocks) from a shared
- * queue, largest pairs first, and meet at a grid-wide barrier between the
- * phases of an iteration.
+ * queue, phase by phase and largest pairs first; an item waits only for its
+ * own pair's previous phase, so the phases of different pairs overlap.
  * ---------------------------------------------------------------------- */
 typedef struct cpd_batch cpd_batch;   /* opaque; owned by the library */
 
@@ -471,9 +472,10 @@ typedef struct cpd_batch cpd_batch;   /* opaque; owned by the library */
  *                      M-step phases; the E-step phases stay FP32).  The
  *                      basis of pair i keeps min(p->K, M[i]) eigenpairs (all
  *                      with p->K = 0).  p->tol > 0 stops each pair on its own.
- *   barrier_timeout_s  wall-time limit of one wait at a grid barrier inside
- *                      the kernel, in (0, 60]; 0 selects 5 s.  A wait that
- *                      exceeds it ends the launch with CPD_ETIMEOUT.
+ *   barrier_timeout_s  wall-time limit of one wait inside the kernel (for a
+ *                      pair's previous phase), in (0, 60]; 0 selects 5 s.  A
+ *                      wait that exceeds it ends the launch with
+ *                      CPD_ETIMEOUT.
  *   stream             cudaStream_t all later work of the batch runs on.
  * The caller's arrays are only read during the call.  Synchronises.
  * Errors: CPD_EINVAL (arguments, with the pair index), CPD_ENOMEM,
@@ -487,7 +489,7 @@ cpd_status cpd_batch_create(int32_t n_pairs, const void *const *X, const int64_t
 /*
  * Run n_iter (0..2^20) EM iterations of every pair that has not stopped (by
  * p->tol or a device failure) in one launch, then synchronise.  CPD_ETIMEOUT
- * if a grid barrier's wait ran out (the registrations' state is then
+ * if a wait inside the kernel ran out (the registrations' state is then
  * undefined until cpd_batch_reset); per-pair failures are reported by
  * cpd_batch_state, not here.
  */
@@ -511,15 +513,16 @@ cpd_status cpd_batch_launch_shape(const cpd_batch *b, int32_t *n_pairs, int32_t 
 
 /*
  * Where the last cpd_batch_iterate call spent its time: 8 floats (host).
- * [0..3]: milliseconds per iteration of each phase, averaged over the
- * call's iterations, as seen by the launch's first block (from the end of
- * the previous grid barrier to the end of the phase's own barrier, so each
- * includes its barrier): [0] E pass A with the column reduction (Eq. 4) and
- * its fix-up, [1] E pass B with the row reduction (Eq. 5) and its fix-up,
- * [2] projection U^T (Ytil - X) with the diagonal update, [3] expansion
- * with T and Eq. 18.  [4..7]: for the same phases, the fraction of the
- * blocks' time spent inside work items (1 = no block ever waited at the
- * barrier).  CPD_ESTATE before the first completed call.
+ * [0..3]: milliseconds per iteration of the whole GPU's time spent inside
+ * each phase's work items (block-time summed over the blocks, divided by
+ * their number), averaged over the call's iterations: [0] E pass A with the
+ * column reduction (Eq. 4) and its fix-up, [1] E pass B with the row
+ * reduction (Eq. 5) and its fix-up, [2] projection U^T (Ytil - X) with the
+ * diagonal update, [3] expansion with T and Eq. 18.  Phases of different
+ * pairs overlap, so these add up to the call's time less the waits.
+ * [4..7]: for the same phases, the fraction of the blocks' time on that
+ * phase's items spent working rather than waiting for the pair's previous
+ * phase (1 = never waited).  CPD_ESTATE before the first completed call.
  */
 cpd_status cpd_batch_phase_ms(const cpd_batch *b, float *phase_ms);
 

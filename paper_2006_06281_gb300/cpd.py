@@ -415,14 +415,16 @@ class Batch:
         return a.value, b.value, c.value
 
     def phase_ms(self):
-        """Milliseconds per iteration of the 4 phases in the last call: pass A
-        (+ column reduction), pass B (+ row reduction), projection (+ diagonal
-        update), expansion (+ T and Eq. 18)."""
+        """Milliseconds of GPU time per iteration inside the 4 phases' work
+        items in the last call: pass A (+ column reduction), pass B (+ row
+        reduction), projection (+ diagonal update), expansion (+ T and Eq.
+        18).  Phases of different pairs overlap."""
         return self.phase_profile()[0]
 
     def phase_profile(self):
-        """(ms per iteration of the 4 phases, fraction of block time spent in
-        work items per phase) for the last call."""
+        """(GPU ms per iteration inside the 4 phases' items, fraction of the
+        blocks' time on each phase's items spent working rather than waiting
+        for the pair's previous phase) for the last call."""
         out = (C.c_float * 8)()
         _check(load().cpd_batch_phase_ms(self._h, out))
         return list(out[:4]), list(out[4:])

@@ -2,8 +2,7 @@
 // run their EM iterations in ONE persistent cooperative kernel launch.
 //
 // Every iteration of every pair runs the same arithmetic as the per-pair
-// path (estep_dev.cuh / mstep_dev.cuh) in four phases, each closed by a
-// grid-wide barrier:
+// path (estep_dev.cuh / mstep_dev.cuh) in four phases:
 //   A  E pass A tiles; the last row chunk of a column tile to finish reduces
 //      that tile's columns (den, Eq. 4), and the block completing a pair's
 //      columns runs the FP32 log-domain fix-up of its flagged columns;
@@ -17,11 +16,18 @@
 // "Last" is decided by per-tile completion tickets (an atomic counter per
 // tile, reset by the block that completes it).  For each phase the host
 // lists the work items of all pairs -- (pair, block coordinates), largest
-// pairs first -- and the resident blocks take items from an atomic counter,
-// so small and large pairs share the GPU without per-pair launches.  The
-// barrier's wait is bounded in wall time: if it does not complete within the
-// limit the kernel records CPD_ETIMEOUT in the control block and every block
-// returns (no GPU hang); the host reports the status.
+// pairs first -- and the resident blocks take items from one atomic counter
+// running over every iteration's phases in order, so small and large pairs
+// share the GPU without per-pair launches.  Phases are ordered per pair, not
+// by grid barriers: the block that completes a pair's phase (its last
+// reduction, diagonal update or expansion tile) bumps the pair's counter for
+// that phase, and an item of the next phase waits for it -- so pass B items
+// of a pair whose columns are done run while other pairs' pass A items are
+// still in flight.  The items a block waits for were taken from the counter
+// before its own by running blocks, so the wait always ends; it is bounded
+// in wall time all the same: past the limit the kernel records CPD_ETIMEOUT
+// in the control block and every block returns (no GPU hang); the host
+// reports the status.
 //
 // Buffers such as T, Yb and the partial sums are written in one phase and
 // read in a later one of the same launch, so no argument of the device bodies
@@ -87,38 +93,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier over all co-resident blocks.  Returns false (and leaves
-// CPD_ETIMEOUT in ctl->status) if another block failed or the wait exceeded
-// limit_ns of wall time.
-__device__ bool grid_barrier(BatchCtl* ctl, unsigned int nblocks, unsigned long long limit_ns) {
-  __shared__ int ok;
+// Thread 0: waits until pair P's phase `need_ph` has completed `need` times
+// in this launch (or P's iterations are gated: then the item does nothing
+// and needs nothing).  False (CPD_ETIMEOUT recorded unless another failure
+// is) past limit_ns, or at once if another block has failed.
+__device__ bool wait_phase(const BatchPair& P, int need_ph, unsigned int need, BatchCtl* ctl,
+                           unsigned long long limit_ns) {
+  volatile unsigned int* c = P.done + need_ph;
+  if (*c >= need || iteration_gated(P.st)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    __nanosleep(64);
+    if (*c >= need) return true;
+    const volatile DevState* st = P.st;
+    if (st->iter >= st->iter_target || st->done || st->status != 0) return true;
+    if (*(volatile int*)&ctl->status != 0) return false;
+    if (global_ns() - t0 > limit_ns) {
+      atomicCAS(&ctl->status, 0, (int)CPD_ETIMEOUT);
+      return false;
+    }
+  }
+}
+
+// Called by every thread of the block that completed pair P's phase ph.
+__device__ __forceinline__ void phase_done(const BatchPair& P, int ph) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned int* genp = &ctl->barrier_gen;
-    const unsigned int gen = *genp;
     __threadfence();
-    const unsigned int arrived = atomicAdd(&ctl->barrier_count, 1u);
-    if (arrived == nblocks - 1) {
-      ctl->barrier_count = 0;
-      __threadfence();
-      atomicAdd(&ctl->barrier_gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*genp == gen) {
-        if (*(volatile int*)&ctl->status != 0) { ok = 0; break; }
-        __nanosleep(128);
-        if (global_ns() - t0 > limit_ns) {
-          atomicExch(&ctl->status, (int)CPD_ETIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
+    atomicAdd(P.done + ph, 1u);
   }
-  __syncthreads();
-  return ok != 0;
 }
 
 // Eight consecutive basis elements as floats (16-byte aligned): FP32, or the
@@ -199,10 +202,10 @@ static_assert(kNarrowTileE == 32 * 8 && kThreadsBatch == kNarrowTileE, "one poin
 // padded; one array for both basis types
 __shared__ float s_narrow_red[kThreadsBatch / 32][3][8][33];
 template <typename B>
-__device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int K, int M, const float4* B4,
+__device__ __forceinline__ bool expand_narrow_body(const B* Ut, int64_t ldM, int K, int M, const float4* B4,
                                                    const float4* X4, const float4* Yt4, float4* T4,
                                                    const float4* Yhat4, double* sums, DevState* st, int bx, int gx) {
-  if (iteration_gated(st)) return;
+  if (iteration_gated(st)) return false;
   constexpr int NW = kThreadsBatch / 32;
   __shared__ float4 sB[kNarrowMaxK];
   float (*red)[3][8][33] = s_narrow_red;
@@ -283,6 +286,7 @@ __device__ __forceinline__ void expand_narrow_body(const B* Ut, int64_t ldM, int
       st->ticket_e = 0;
     }
   }
+  return last;
 }
 
 // Pass A (B) of one tile with the fewest points per thread that cover the
@@ -378,7 +382,7 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
         if (pair_done) {
           __threadfence();
           fixA_f32_body(P.T4, P.M, P.Y4, P.N, P.Yb, nullptr, P.flags + P.M, P.st, 1, 0, 0, 1, 1);
-          __syncthreads();
+          phase_done(P, PH_A);
         }
       }
       break;
@@ -394,7 +398,7 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
         if (pair_done) {
           __threadfence();
           fixB_f32_body(P.T4, P.M, P.Yb, P.N, P.X4, P.Yt4, P.R4, nullptr, P.flags, P.st, 1, 0, 0, 1, 1);
-          __syncthreads();
+          phase_done(P, PH_B);
         }
       }
       break;
@@ -420,16 +424,18 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
         diag_update_body<float>(P.partP, m.p_row_chunks, m.ldU, P.K, P.lam, P.B4, P.C4, P.st, 1, u, 0, nu, 1);
         __syncthreads();
       }
+      phase_done(P, PH_P);
       break;
     }
     case PH_E: {
       if (P.narrow) {
-        if (P.half_basis)
-          expand_narrow_body(static_cast<const __half*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4,
-                             P.sums, P.st, bx, m.e_col_tiles);
-        else
-          expand_narrow_body(static_cast<const float*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4, P.Yhat4,
-                             P.sums, P.st, bx, m.e_col_tiles);
+        const bool last =
+            P.half_basis
+                ? expand_narrow_body(static_cast<const __half*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4,
+                                     P.Yhat4, P.sums, P.st, bx, m.e_col_tiles)
+                : expand_narrow_body(static_cast<const float*>(P.Ut), m.ldM, P.K, P.M, P.B4, P.X4, P.Yt4, P.T4,
+                                     P.Yhat4, P.sums, P.st, bx, m.e_col_tiles);
+        if (last) phase_done(P, PH_E);
         break;
       }
       if (P.half_basis)
@@ -443,9 +449,10 @@ __device__ void run_item(int ph, const BatchPair& P, int bx, int by) {
       if (!tile_done(tE + bx, (unsigned)m.e_row_chunks)) break;
       const int u1 = min((bx + 1) * (kTileColsE / kMRedCols), m.e_blocks);
       for (int u = bx * (kTileColsE / kMRedCols); u < u1; ++u) {
-        expand_finish_body<float, true>(P.partP, m.e_row_chunks, m.ldM, P.M, P.X4, P.Yt4, P.T4, P.Yhat4, P.sums, P.st,
-                                        1, u, 0, m.e_blocks, 1);
+        const bool last = expand_finish_body<float, true>(P.partP, m.e_row_chunks, m.ldM, P.M, P.X4, P.Yt4, P.T4,
+                                                          P.Yhat4, P.sums, P.st, 1, u, 0, m.e_blocks, 1);
         __syncthreads();
+        if (last) phase_done(P, PH_E);
       }
       break;
     }
@@ -456,34 +463,50 @@ __global__ void __launch_bounds__(kThreadsBatch)
 batch_iterations(const BatchPair* __restrict__ pairs, const BatchItem* __restrict__ items,
                  const int* __restrict__ phase_off, BatchCtl* __restrict__ ctl, int n_iter,
                  unsigned long long limit_ns, int barrier_extra) {
-  __shared__ int s_idx;
-  unsigned long long t_prev = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = t_prev = global_ns();
-  for (int it = 0; it < n_iter; ++it) {
-    for (int ph = 0; ph < kPhases; ++ph) {
-      const int lo = phase_off[ph], hi = phase_off[ph + 1];
-      unsigned long long busy = 0;
-      for (;;) {
-        if (threadIdx.x == 0) s_idx = lo + (int)atomicAdd(&ctl->next_item[ph], 1u);
-        __syncthreads();
-        const int idx = s_idx;
-        if (idx >= hi) break;
-        const unsigned long long t0 = threadIdx.x == 0 ? global_ns() : 0ull;
-        const BatchItem itm = items[idx];
-        run_item(ph, pairs[itm.pair], itm.bx, itm.by);
-        __syncthreads();
-        if (threadIdx.x == 0) busy += global_ns() - t0;
+  __shared__ unsigned long long s_idx;
+  __shared__ int s_ok;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_start = global_ns();
+  const int n_items = phase_off[kPhases];
+  const unsigned long long total = (unsigned long long)n_iter * (unsigned long long)n_items;
+  unsigned long long busy[kPhases] = {}, waited[kPhases] = {};
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = *(volatile int*)&ctl->status != 0 ? total : atomicAdd(&ctl->next, 1ull);
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    if (idx >= total) break;
+    const int it = (int)(idx / (unsigned long long)n_items);
+    const int j = (int)(idx % (unsigned long long)n_items);
+    int ph = 0;
+    while (ph + 1 < kPhases && j >= phase_off[ph + 1]) ++ph;
+    const BatchItem itm = items[j];
+    const BatchPair& P = pairs[itm.pair];
+    // the pair's previous phase: the expansion of the previous iteration
+    // before pass A (none in the launch's first iteration), else the phase
+    // before in this iteration
+    if (threadIdx.x == 0) {
+      const unsigned long long t0 = global_ns();
+      s_ok = 1;
+      if (ph != PH_A || it > 0) {
+        const int need_ph = ph == PH_A ? PH_E : ph - 1;
+        const unsigned int need = (unsigned int)(ph == PH_A ? it : it + 1) + (unsigned int)barrier_extra;
+        s_ok = wait_phase(P, need_ph, need, ctl, limit_ns) ? 1 : 0;
       }
-      if (threadIdx.x == 0 && busy) atomicAdd(&ctl->busy_ns[ph], busy);
-      if (!grid_barrier(ctl, gridDim.x + (unsigned int)barrier_extra, limit_ns)) return;
-      // every block has left phase ph: its item counter can be rewound
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->next_item[ph] = 0;
-        const unsigned long long t = global_ns();
-        ctl->phase_ns[ph] += t - t_prev;
-        t_prev = t;
-      }
+      __threadfence();
+      waited[ph] += global_ns() - t0;
     }
+    __syncthreads();
+    if (!s_ok) break;
+    const unsigned long long t1 = threadIdx.x == 0 ? global_ns() : 0ull;
+    run_item(ph, P, itm.bx, itm.by);
+    __syncthreads();
+    if (threadIdx.x == 0) busy[ph] += global_ns() - t1;
+  }
+  if (threadIdx.x == 0) {
+    for (int ph = 0; ph < kPhases; ++ph) {
+      if (busy[ph]) atomicAdd(&ctl->busy_ns[ph], busy[ph]);
+      if (waited[ph]) atomicAdd(&ctl->wait_ns[ph], waited[ph]);
+    }
+    atomicMax(&ctl->t_end, global_ns());
   }
 }
 
@@ -604,9 +627,11 @@ int batch_tickets(const BatchPair& p) { return p.ep.a_col_tiles + p.ep.b_row_til
 int batch_phases() { return kPhases; }
 
 cudaError_t launch_batch(const BatchPair* pairs_dev, int n_pairs, const BatchItem* items, const int* phase_off,
-                         BatchCtl* ctl, int grid, int n_iter, double wait_limit_s, int barrier_extra,
+                         BatchCtl* ctl, unsigned int* done, int grid, int n_iter, double wait_limit_s, int barrier_extra,
                          cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(BatchCtl), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(done, 0, sizeof(unsigned int) * kPhases * (size_t)n_pairs, s);
   if (e != cudaSuccess) return e;
   batch_begin<<<(n_pairs + 255) / 256, 256, 0, s>>>(pairs_dev, n_pairs, n_iter);
   e = cudaGetLastError();

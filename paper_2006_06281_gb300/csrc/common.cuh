@@ -306,6 +306,7 @@ struct BatchPair {
   int* flags;
   DevState* st;
   unsigned int* tix;          // completion tickets of the pair's tiles (batch_tickets entries, zeroed)
+  unsigned int* done;         // phases completed in the current launch, one counter per phase (zeroed per launch)
   int narrow;                 // projection by the row-split body (K <= 128)
 };
 struct BatchItem {
@@ -313,13 +314,12 @@ struct BatchItem {
 };
 // Control block of one persistent launch (zeroed before each launch).
 struct BatchCtl {
-  unsigned int barrier_count;
-  unsigned int barrier_gen;
-  unsigned int next_item[16];
-  int status;                 // CPD_ETIMEOUT if a grid barrier gave up
+  unsigned long long next;           // next work item of the launch (iteration-major)
+  int status;                 // CPD_ETIMEOUT if a wait for a pair's previous phase gave up
   int pad;
   unsigned long long t_start;        // block 0's clock at the start of the launch
-  unsigned long long phase_ns[16];   // per phase: block 0's time from the previous barrier to the end of this one
+  unsigned long long t_end;          // latest clock at which a block ran out of work items
+  unsigned long long wait_ns[16];    // per phase: time blocks spent waiting for a pair's previous phase
   unsigned long long busy_ns[16];    // per phase: time all blocks spent inside work items
 };
 // Resident blocks of the persistent kernel on `sms` SMs (0 on failure).
@@ -332,12 +332,13 @@ void batch_items(const BatchPair* pairs_host, int n_pairs, std::vector<BatchItem
 // Completion tickets a pair needs (after plan_batch), and the phases per iteration.
 int batch_tickets(const BatchPair& p);
 int batch_phases();
-// Zeroes ctl, then runs n_iter iterations of every pair in one cooperative
-// launch of `grid` blocks.  barrier_extra > 0 makes every grid barrier wait
-// for blocks that do not exist (host-side fault injection for the timeout
-// path).
+// Zeroes ctl and the pairs' phase counters (done: 4 per pair), then runs
+// n_iter iterations of every pair in one cooperative launch of `grid`
+// blocks.  barrier_extra > 0 makes every wait for a pair's previous phase
+// ask for one phase more than will ever complete (host-side fault injection
+// for the timeout path).
 cudaError_t launch_batch(const BatchPair* pairs_dev, int n_pairs, const BatchItem* items, const int* phase_off,
-                         BatchCtl* ctl, int grid, int n_iter, double wait_limit_s, int barrier_extra,
+                         BatchCtl* ctl, unsigned int* done, int grid, int n_iter, double wait_limit_s, int barrier_extra,
                          cudaStream_t s);
 // Copies every pair's device state into out[0..n_pairs).
 void launch_batch_states(const BatchPair* pairs_dev, int n_pairs, DevState* out, cudaStream_t s);

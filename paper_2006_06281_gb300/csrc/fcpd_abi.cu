@@ -1316,7 +1316,7 @@ struct cpd_batch {
   std::vector<cpd_ctx*> ctx;
   std::vector<BatchPair> pairs;
   std::vector<int> phase_off_host;
-  Buf pairs_dev, items, phase_off, ctl, states, tickets;
+  Buf pairs_dev, items, phase_off, ctl, states, tickets, done;
   int n_items = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_iters = -1;
@@ -1329,7 +1329,7 @@ struct cpd_batch {
   ~cpd_batch() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cpd_ctx* c : ctx) delete c;
-    for (Buf* b : {&pairs_dev, &items, &phase_off, &ctl, &states, &tickets}) b->release();
+    for (Buf* b : {&pairs_dev, &items, &phase_off, &ctl, &states, &tickets, &done}) b->release();
     if (cap) cudaStreamDestroy(cap);
   }
 };
@@ -1399,11 +1399,14 @@ cpd_status batch_apply_plan(cpd_batch* b, int e_items, int proj_kb) {
   for (int i = 0; i < n; ++i) n_tickets += (size_t)batch_tickets(b->pairs[i]);
   STATUS_TRY(b->tickets.ensure(n_tickets * sizeof(unsigned int)));
   b->n_tickets = n_tickets;
+  const int np = batch_phases();
+  STATUS_TRY(b->done.ensure((size_t)np * n * sizeof(unsigned int)));
   for (int i = 0, off = 0; i < n; ++i) {
     STATUS_TRY(batch_size_pair(b->ctx[i], b->pairs[i]));
     const int nt = batch_tickets(b->pairs[i]);
     b->pairs[i] = batch_pointers(b->ctx[i], b->pairs[i]);
     b->pairs[i].tix = b->tickets.as<unsigned int>() + off;
+    b->pairs[i].done = b->done.as<unsigned int>() + (size_t)np * i;
     off += nt;
   }
   std::vector<BatchItem> items;
@@ -1434,7 +1437,8 @@ cpd_status batch_capture(cpd_batch* b, int n_iter, int extra) {
   b->graph_iters = -1;
   CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
   cudaError_t le = launch_batch(b->pairs_dev.as<BatchPair>(), b->n, b->items.as<BatchItem>(), b->phase_off.as<int>(),
-                                b->ctl.as<BatchCtl>(), b->grid, n_iter, b->wait_s, extra, b->cap);
+                                b->ctl.as<BatchCtl>(), b->done.as<unsigned int>(), b->grid, n_iter, b->wait_s, extra,
+                                b->cap);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -1573,7 +1577,7 @@ cpd_status cpd_batch_iterate(cpd_batch* b, int32_t n_iter) {
   CUDA_TRY(cudaStreamSynchronize(b->stream));
   b->last_iters = n_iter;
   if (h.status != 0)
-    return fail((cpd_status)h.status, "a grid barrier of the batched kernel timed out (" +
+    return fail((cpd_status)h.status, "a wait of the batched kernel for a pair's previous phase timed out (" +
                                           std::to_string(b->wait_s) + " s); the pairs' state is undefined until "
                                           "cpd_batch_reset" + (extra ? " (injected: CPD_FAULT=barrier)" : ""));
   return CPD_OK;
@@ -1627,9 +1631,9 @@ cpd_status cpd_batch_phase_ms(const cpd_batch* b, float* phase_ms) {
   if (b->last_iters < 1) return fail(CPD_ESTATE, "no batched call has completed yet");
   const int np = batch_phases();
   for (int ph = 0; ph < np; ++ph) {
-    const double span = (double)b->last.phase_ns[ph];
-    phase_ms[ph] = (float)(span / 1e6 / b->last_iters);
-    phase_ms[np + ph] = span > 0 ? (float)((double)b->last.busy_ns[ph] / ((double)b->grid * span)) : 0.f;
+    const double busy = (double)b->last.busy_ns[ph], wait = (double)b->last.wait_ns[ph];
+    phase_ms[ph] = (float)(busy / (double)b->grid / 1e6 / b->last_iters);
+    phase_ms[np + ph] = busy + wait > 0 ? (float)(busy / (busy + wait)) : 0.f;
   }
   return CPD_OK;
 }

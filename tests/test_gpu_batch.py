@@ -121,8 +121,9 @@ def test_batch_barrier_timeout_is_reported_and_recoverable(scenes, monkeypatch):
     Xs = [f32(ps.X) for ps in scenes[:3]]
     Ys = [f32(ps.Y) for ps in scenes[:3]]
     with cpd.Batch(Xs, Ys, K=128, barrier_timeout_s=0.2) as b:
-        # every grid barrier waits for one block that does not exist: each wait
-        # ends after 0.2 s and the launch returns with CPD_ETIMEOUT
+        # every wait for a pair's previous phase asks for one phase more than
+        # will complete: the first ends after 0.2 s and the launch returns
+        # with CPD_ETIMEOUT
         monkeypatch.setenv("CPD_FAULT", "barrier")
         with pytest.raises(cpd.CpdError) as ei:
             b.iterate(2)
