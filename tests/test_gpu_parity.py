@@ -270,6 +270,27 @@ def test_narrow_basis_rmse_history_against_the_oracle(prec):
                      "narrow basis mixed")
 
 
+@pytest.mark.parametrize("M,K", [(129, 1), (300, 7), (1000, 255), (1000, 256), (1000, 257)])
+@pytest.mark.parametrize("prec", [cpd.FP32, cpd.MIXED])
+def test_narrow_basis_edges_against_the_oracle(prec, M, K):
+    """Basis widths around the row expansion's limit (K <= 256 one launch,
+    257 the column-parallel path), a one-column basis, ragged K (not a
+    multiple of the 16-byte vector) and a ragged M: T and sigma2 after 10
+    iterations against the oracle."""
+    ps = pointsets(M, seed=M + K)
+    f = lambda a: a.astype(np.float32).astype(np.float64)
+    X, Y = f(ps.X), f(ps.Y)
+    ref = oracle.register(X, Y, w=0.1, beta=2.0, lam_reg=2.0, n_iter=10, K=K)
+    T, s2, it, _ = run_gpu(X, Y, prec, 10, K=K)
+    assert it == 10
+    tol = FP32_TOL if prec == cpd.FP32 else MIXED_TOL
+    err = rel(T, ref["T"])
+    print(f"[narrow edges] prec={prec} M={M} K={K}: T relative error {err:.2e}")
+    assert err <= tol
+    stol = tol if prec == cpd.FP32 else sigma2_tol(tol, ref["T"], ref["sigma2"])
+    check_sigma2(s2, ref["sigma2"], stol, f"narrow edges prec={prec} M={M} K={K}")
+
+
 @pytest.mark.parametrize("prec,M,K", [(cpd.FP64, 600, 40), (cpd.FP32, 3000, 200)])
 def test_topk_subspace_iteration_basis(prec, M, K):
     """Eq. 19 by subspace iteration: the context reports that method, its
