@@ -968,11 +968,12 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(ps, cfg, M, N, K)
-    # per iteration: pass A, reduce A, fix A, pass B, reduce B, fix B,
-    # projection, diagonal update, expansion, expansion finish (T, Eq. 18);
-    # per registration: scene packing, state init, initial variance, E-step
-    # layout control, iteration target
-    launches = 10 * steps + 5 * R
+    # per iteration: pass A, reduce A, fix A, the log-likelihood total (side
+    # branch), pass B, reduce B, fix B, projection, diagonal update,
+    # expansion, expansion finish (T, Eq. 18); per registration: scene
+    # packing, state init, initial variance, E-step layout control,
+    # iteration target
+    launches = 11 * steps + 5 * R
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=steps, warmup=warm,

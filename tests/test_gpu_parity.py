@@ -270,6 +270,32 @@ def test_narrow_basis_rmse_history_against_the_oracle(prec):
                      "narrow basis mixed")
 
 
+def test_log_domain_fixups_inside_captured_iterations():
+    """A registration whose first E-step has FP32 Gaussian sums that flush to
+    zero: no outlier term (w = 0), scene points beyond the model's +x face
+    and model points beyond the scene's -x face, and a small initial
+    variance (2e-4), so ~50 columns and ~24 rows take the exact log-domain
+    path in the first iteration and none later -- the fix-up launches of
+    the captured iterations run for real once and step aside after: had
+    they not, those columns' offsets would be 0 and those rows stale, far
+    outside the FP32 tolerance against the oracle."""
+    ps = pointsets(600, seed=77)
+    rng = np.random.default_rng(5)
+    yo = np.column_stack([np.full(25, 1.3), rng.uniform(-0.8, 0.8, 25), rng.uniform(-0.8, 0.8, 25)])
+    xo = np.column_stack([np.full(15, -1.3), rng.uniform(-0.8, 0.8, 15), rng.uniform(-0.8, 0.8, 15)])
+    X = np.vstack([ps.X, xo]).astype(np.float32).astype(np.float64)
+    Y = np.vstack([ps.Y, yo]).astype(np.float32).astype(np.float64)
+    ref = oracle.register(X, Y, w=0.0, beta=2.0, lam_reg=2.0, n_iter=10, sigma2_0=2e-4)
+    assert ref["status"] == oracle.OK
+    with cpd.Context(dev(X, cpd.FP32), precision=cpd.FP32, w=0.0, beta=2.0, lam=2.0, sigma2_init=2e-4) as ctx:
+        T, s2, it = ctx.iterate(dev(Y, cpd.FP32), 10)
+    assert it == 10
+    err = rel(host(T), ref["T"])
+    print(f"[fix-ups] T relative error {err:.2e}")
+    assert err <= FP32_TOL
+    check_sigma2(s2, ref["sigma2"], FP32_TOL, "log-domain fix-ups")
+
+
 @pytest.mark.parametrize("M,K", [(129, 1), (300, 7), (1000, 255), (1000, 256), (1000, 257)])
 @pytest.mark.parametrize("prec", [cpd.FP32, cpd.MIXED])
 def test_narrow_basis_edges_against_the_oracle(prec, M, K):
