@@ -79,6 +79,10 @@ def parse():
                     help="skip timing the same pairs through per-pair contexts")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched-registration section (prints its object as the JSON line)")
+    ap.add_argument("--warmstart-sweep", default="",
+                    help="comma-separated training-set sizes (e.g. 512,2048,8192): run only a sweep of the "
+                         "learned warm start over them on the --warmstart workload (prints its object as the "
+                         "JSON line)")
     return ap.parse_args()
 
 
@@ -634,6 +638,75 @@ def run_warmstart(args, torch):
                      "T_end is the FP32 registration's end point after 150 iterations")
 
 
+def run_warmstart_sweep(args, torch, sizes):
+    """Learned warm start against the size of its training set: the largest
+    set is generated once (registrations from W = 0, as in run_warmstart) and
+    each size trains a fresh network on its first n scenes, for
+    max(steps, n / 2) Adam steps of 32 scenes; the held-out scenes (start
+    variance calibration and coefficient error) and the test scenes are the
+    same for every size.  Reported per size: held-out coefficient error and
+    the FP32 iterations from the prediction until RMSE(T, T_end) <= 1e-3, with
+    the same count from W = 0 once."""
+    from paper_2006_06281_gb300 import cpd, datagen, warmstart
+    cfg = datagen.WARMSTART_WORKLOADS[args.warmstart]
+    sizes = sorted(set(sizes))
+    nmax, nva, nte = sizes[-1], cfg["n_val"], cfg["n_test"]
+    X = datagen.gen(cfg["M"], seed=cfg["seed_x"]).X.astype(np.float32)
+
+    def scenes(seeds):
+        return np.stack([datagen.gen_from_template(X, s, amp=cfg["amp"], noise=cfg["noise"]).Y.astype(np.float32)
+                         for s in seeds])
+
+    t0 = time.perf_counter()
+    train = scenes(range(cfg["seed0"], cfg["seed0"] + nmax))
+    held = scenes(range(cfg["seed0"] + 1_000_000, cfg["seed0"] + 1_000_000 + nva + nte))
+    Xd = torch.tensor(X, device="cuda")
+    ctx = cpd.Context(Xd, precision=cpd.FP32, w=cfg["omega"], beta=cfg["beta"], lam=cfg["lam"], K=cfg["K"])
+    t1 = time.perf_counter()
+    targets = warmstart.registration_targets(ctx, np.concatenate([train, held[:nva]]), cfg["K"], cfg["iters"])
+    t2 = time.perf_counter()
+    tr_targets, va_targets = targets[:nmax], targets[nmax:]
+    test = held[nva:]
+    ends = []
+    for j, Y in enumerate(test):
+        Yd = torch.tensor(Y, device="cuda")
+        if j > 0:
+            ctx.set_ground_truth(ends[-1], 0.0)
+        ctx.reset()
+        T, _, _ = ctx.iterate(Yd, 150)
+        ends.append(T)
+
+    def iters_to_target(Y, Tend, start):
+        ctx.set_ground_truth(Tend, 1e-3)
+        ctx.reset()
+        start()
+        _, _, it = ctx.iterate(torch.tensor(Y, device="cuda"), 150, want_T=False)
+        return it
+
+    cold = float(np.mean([iters_to_target(Y, Te, lambda: None) for Y, Te in zip(test, ends)]))
+    rows = []
+    for n in sizes:
+        steps = max(cfg["steps"], n // 2)
+        ws = warmstart.WarmStart(cfg["K"], cfg["M"], max_batch=cfg["batch"], seed=3, precision=warmstart.NET_BF16)
+        ta = time.perf_counter()
+        losses = ws.fit(train[:n], tr_targets[:n], steps, cfg["batch"], cfg["lr"])
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        ws.calibrate(held[:nva], va_targets, cfg["M"])
+        c, _ = ws.predict(held[:nva])
+        ct = va_targets[:, :-1].reshape(c.shape)
+        err = float(np.linalg.norm(c - ct) / np.linalg.norm(ct))
+        warm = float(np.mean([iters_to_target(Y, Te, lambda Y=Y: ws.start(ctx, Y)) for Y, Te in zip(test, ends)]))
+        rows.append(dict(train_scenes=n, steps=steps, train_s=tb - ta, loss_last=float(np.mean(losses[-50:])),
+                         heldout_coef_rel_err=err, start_sigma2=ws.sigma2_floor, warm_iters_to_rmse_1e3=warm))
+        ws.net.close()
+    ctx.close()
+    return dict(workload=args.warmstart, M=cfg["M"], K=cfg["K"], network_precision="bf16", heldout_scenes=nva,
+                test_scenes=nte, data_gen_host_s=t1 - t0, data_s=t2 - t1, cold_iters_to_rmse_1e3=cold, sizes=rows,
+                note="one data set: size n trains on its first n scenes; T_end is each test scene's FP32 "
+                     "end point after 150 iterations")
+
+
 def workload_config(cfg, M, N, K):
     return dict(workload=f"M={M} N={N} D=3 synthetic deformed pair (uniform model points, Gaussian-RBF "
                          f"deformation amp {cfg['amp']}, noise {cfg['noise']}, {cfg['n_out']} outliers), "
@@ -699,6 +772,12 @@ def main():
     if args.batch_only:
         if rank == 0:
             print(json.dumps(dict(impl="ours", batch=run_batch(args, peaks, torch))), flush=True)
+        return 0
+    if args.warmstart_sweep:
+        if rank == 0:
+            sizes = [int(v) for v in args.warmstart_sweep.split(",") if v.strip()]
+            print(json.dumps(dict(impl="ours", warm_start_sweep=run_warmstart_sweep(args, torch, sizes))),
+                  flush=True)
         return 0
 
     M = cfg["M"]
