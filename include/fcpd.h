@@ -374,6 +374,23 @@ cpd_status cpd_iterate_shared(cpd_ctx *ctx, int32_t n_scenes, const void *const 
  */
 cpd_status cpd_get_trim(cpd_ctx *ctx, int64_t *k_cap, int32_t *trimmed_iters);
 
+/*
+ * Launch layout of the iterations (not in the paper; Eq. 4, 5 and 17 are
+ * unchanged): *pieces (host) = the row pieces pass B of the E-step runs in.
+ * With pieces > 1 each piece's model rows go through pass B, their row
+ * reduction and log-domain fix-up, and the M-step's projection U^T R of
+ * those rows (Eq. 17) starts on a side stream while the next piece's pass B
+ * runs, so the HBM-bound projection overlaps the ALU-bound pass B; the
+ * diagonal update then sums every piece's partials.  Chosen at cpd_setup:
+ * CPD_FP32 contexts without flags whose basis has more than 256 columns and
+ * M >= 8192 use 3 pieces; all others 1.  The environment variable
+ * FCPD_SPLIT_B, read at cpd_setup, sets the count (1..4; 1: off).  Each
+ * piece's scene-point partial sums are split for its own grid, so results
+ * differ from one piece in FP32 rounding only.  No device work.  CPD_EINVAL
+ * for a null argument.
+ */
+cpd_status cpd_pass_b_pieces(cpd_ctx *ctx, int32_t *pieces);
+
 /* ------------------------------------------------------------------------
  * Warm start (not in the paper).  In the top-K basis the displacement of
  * every iteration lies in span(U) (Eq. 20), so T - X = U c with c = U^T

@@ -31,7 +31,7 @@ FLAG_PRUNE, FLAG_PRUNE_ALWAYS, FLAG_PRUNE_NOSKIP, FLAG_SPECTRAL_TRIM, FLAG_FULL_
 EXPORTS = ["cpd_abi_version", "cpd_status_string", "cpd_last_error", "cpd_params_default",
            "cpd_setup", "cpd_iterate", "cpd_iterate_profiled", "cpd_reset", "cpd_set_ground_truth", "cpd_get_state",
            "cpd_get_history", "cpd_get_W", "cpd_get_basis", "cpd_basis_rank", "cpd_eig_info", "cpd_mstep",
-           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_iterate_shared", "cpd_destroy",
+           "cpd_estep", "cpd_estep_noalloc", "cpd_register", "cpd_get_work", "cpd_spatial_order", "cpd_get_trim", "cpd_pass_b_pieces", "cpd_iterate_shared", "cpd_destroy",
            "cpd_coefficients", "cpd_coefficients_of", "cpd_warm_start", "cpd_net_create", "cpd_net_create_ex",
            "cpd_net_precision", "cpd_net_num_params", "cpd_net_get_params", "cpd_net_set_params", "cpd_net_forward", "cpd_net_gradients", "cpd_net_train_step", "cpd_net_destroy",
            "cpd_batch_create", "cpd_batch_iterate", "cpd_batch_state", "cpd_batch_get_T", "cpd_batch_info",
@@ -90,6 +90,7 @@ def load():
                 "cpd_destroy": ([vp], None),
                 "cpd_get_work": ([vp, i32, vp], C.c_int),
                 "cpd_get_trim": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
+                "cpd_pass_b_pieces": ([vp, C.POINTER(i32)], C.c_int),
                 "cpd_iterate_shared": ([vp, i32, C.POINTER(vp), C.POINTER(i64), i32, C.POINTER(vp), dp], C.c_int),
                 "cpd_coefficients": ([vp, i32, vp], C.c_int),
                 "cpd_coefficients_of": ([vp, i32, vp, vp], C.c_int),
@@ -291,6 +292,13 @@ class Context:
         n = C.c_int32()
         _check(load().cpd_get_trim(self._h, C.byref(k), C.byref(n)))
         return k.value, n.value
+
+    def pass_b_pieces(self):
+        """Row pieces pass B runs in (1: one launch; > 1: each piece's
+        projection overlaps the next piece's pass B)."""
+        n = C.c_int32()
+        _check(load().cpd_pass_b_pieces(self._h, C.byref(n)))
+        return n.value
 
     def work(self, n):
         """Fraction of the 2 M N Gaussian pairs evaluated by each of the first n iterations."""

@@ -241,9 +241,22 @@ void launch_passB_mma(const MmaPlan& p, const float4* T4, int64_t M, const float
 // sigma2 floor of the tensor-core passes from the largest point norm of X and Y.
 void launch_mma_threshold(const float4* X4, int64_t M, const float4* Y4, int64_t N, DevState* st, cudaStream_t s);
 
+// Pass B of an FP32 iteration split into row pieces, so that the M-step's
+// projection of the rows a piece has finished (on a side stream) runs beside
+// the next piece's pass B: the projection streams U from HBM while pass B
+// keeps the FP32 pipes busy.  Piece i covers model rows [m0, m0 + rows).
+constexpr int kMaxPieces = 4;
+struct BPiece {
+  int m0, rows;                                      // model rows of the piece
+  int row_tiles, col_chunks, cols_per_chunk;         // its pass B grid
+  int red_blocks;                                    // its row-reduction grid
+};
+
 struct EstepPlan {
   int a_col_tiles, a_row_chunks, a_rows_per_chunk;   // pass A grid
   int b_row_tiles, b_col_chunks, b_cols_per_chunk;   // pass B grid
+  int n_pieces;                                      // > 1: pass B in row pieces (see BPiece)
+  BPiece piece[kMaxPieces];
   int64_t partA_elems, partB_elems;                  // scratch sizes (elements of F)
   int64_t redA_blocks, redB_blocks;                  // reduce grids
   int64_t sums_elems;                                // double scratch for block sums
@@ -258,6 +271,13 @@ struct EstepPlan {
 };
 // with_pruned / with_mma: also plan those layouts (partial buffers sized for all).
 EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned = false, bool with_mma = false);
+// Row boundaries of `pieces` pass B pieces over M rows: whole pass B row
+// tiles, as even as they go; returns the number of pieces (fewer when M has
+// fewer tiles).
+int split_rows(int64_t M, int pieces, int* m0, int* rows);
+// Pass B grids of the pieces (FP32 only); enlarges the partial-sum and
+// block-sum sizes where a piece needs more.
+void plan_estep_pieces(EstepPlan& p, int64_t N, int sms, int pieces, const int* m0, const int* rows);
 
 struct MstepPlan {
   int64_t ldU, ldM;                                  // row strides of U (M x ldU) and U^T (K x ldM)
@@ -269,6 +289,11 @@ struct MstepPlan {
   bool bulk;                                         // products by colsum_bulk (bulk-copy ring)
   int64_t K;                                         // basis columns the plan streams
   int64_t ldPp;                                      // row stride of the projection partials
+  // projection in row pieces (with the E-step's pass B pieces): piece i
+  // streams rows [pp_m0, pp_m0 + pp_rows) into partial rows from pp_off on
+  int n_pieces;
+  int pp_m0[kMaxPieces], pp_rows[kMaxPieces], pp_chunks[kMaxPieces], pp_rpc[kMaxPieces], pp_off[kMaxPieces];
+  int pp_chunks_total;
 };
 // `colsum_threads`: block size of the streaming kernel the plan is for (128
 // for the per-pair launches, 256 inside the batched persistent kernel).
@@ -278,6 +303,10 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_thread
 // Plan of the trimmed M-step: the leading K_cap columns of the basis laid
 // out by `full` (same row strides).
 MstepPlan plan_mstep_trim(const MstepPlan& full, int64_t M, int64_t K_cap, bool fp64, int sms, int basis_bytes);
+// Projection grids of row pieces (FP32 basis streamed by colsum_bulk, wide
+// bases only); enlarges part_elems.  False (plan unchanged) where the plan
+// cannot be split.
+bool plan_mstep_pieces(MstepPlan& p, int64_t M, int sms, int pieces, const int* m0, const int* rows);
 
 // ------------------------------------------------------------ batched mode
 // One registration inside the batched persistent kernel: its sizes, plans
@@ -369,12 +398,21 @@ struct EstepSide {
 // optional), per-column den (double, optional).  Gated by `gate` (iteration mode)
 // or always run (standalone).  Without `side`, st->loglik and st->vsum are
 // complete when the last kernel ends.
+// With `pieces` (FP32 iterations with `side`, plan with n_pieces > 1) pass B
+// runs piece by piece and after_piece(user, i) is called once piece i's rows
+// of Yt4 / R4 are enqueued on `s`; the side stream is then left for the
+// caller to join.
+struct EstepPieces {
+  void (*after_piece)(void* user, int piece);
+  void* user;
+};
 template <typename F>
 void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
-                  bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr, const EstepSide* side = nullptr);
+                  bool gate, cudaStream_t s, cudaEvent_t* ev = nullptr, const EstepSide* side = nullptr,
+                  const EstepPieces* pieces = nullptr);
 
 // M-step: projection a = U^T R, diagonal update, expansion T = X + U B and
 // the Eq. 18 variance in the epilogue.  U is M x ldU, Ut = U^T is K x ldM.
@@ -386,13 +424,19 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
 // M-step (plan *trim) or the full one (pl) for this iteration; both are
 // enqueued, step by step, and the other steps aside.  The trimmed M-step sets B and C to 0 for the
 // dropped directions.
+// projected: the projection already ran in the plan's row pieces
+// (launch_projection_piece); the M-step starts at the diagonal update.
 template <typename F, typename S = F>
 void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* lam, int64_t M, int64_t K,
                   const typename Vec<F>::t4* X4, const typename Vec<F>::t4* R4,
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums,
                   typename Vec<F>::t4* B4, typename Vec<F>::t4* C4, DevState* st,
-                  bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr, const MstepPlan* trim = nullptr);
+                  bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr, const MstepPlan* trim = nullptr,
+                  bool projected = false);
+// Projection partials of piece `piece` of an iteration (FP32 basis).
+void launch_projection_piece(const MstepPlan& pl, int piece, const float* U, const float4* R4, float* part,
+                             DevState* st, cudaStream_t s);
 
 // Several registrations against one model (multi.cu): the M-step of S
 // scenes with both products in one pass over U and U^T each (FP32 basis).

@@ -99,9 +99,10 @@ fixA_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Y4, in
 
 __global__ void __launch_bounds__(kThreadsB, FCPD_EB_MINB)
 passB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
-          int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate) {
+          int cols_per_chunk, float* __restrict__ partB, DevState* __restrict__ st, int gate, int clear_rows) {
   if (prune_active(st) || mma_active(st)) return;
-  dev::passB_f32_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  dev::passB_f32_body(T4, M, Yb, N, cols_per_chunk, partB, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
+                      clear_rows);
 }
 
 __global__ void __launch_bounds__(kThreadsB)
@@ -122,21 +123,23 @@ __global__ void __launch_bounds__(kThreadsR)
 reduceB(const F* __restrict__ partB, int chunks, int chunks_pruned, int chunks_mma, int M, const typename Vec<F>::t4* __restrict__ X4,
         typename Vec<F>::t4* __restrict__ Yt4, typename Vec<F>::t4* __restrict__ R4,
         double* __restrict__ P1_out, double* __restrict__ sums, int* __restrict__ flag_rows,
-        DevState* __restrict__ st, int gate, int skip_vsum) {
+        DevState* __restrict__ st, int gate, int skip_vsum, int m_off) {
   const int ch = mma_active(st) ? chunks_mma : prune_active(st) ? chunks_pruned : chunks;
   dev::reduceB_body<F>(partB, ch, M, X4, Yt4, R4, P1_out, sums, flag_rows, st, gate, blockIdx.x, blockIdx.y,
-                       gridDim.x, gridDim.y, skip_vsum);
+                       gridDim.x, gridDim.y, skip_vsum, m_off);
 }
 
 __global__ void __launch_bounds__(kThreadsF)
 fixB_f32(const float4* __restrict__ T4, int M, const float4* __restrict__ Yb, int N,
          const float4* __restrict__ X4, float4* __restrict__ Yt4, float4* __restrict__ R4,
-         double* __restrict__ P1_out, const int* __restrict__ flag_rows, DevState* __restrict__ st, int gate) {
+         double* __restrict__ P1_out, const int* __restrict__ flag_rows, DevState* __restrict__ st, int gate,
+         int m_lo, int m_hi) {
   // the E-step's last launch also takes the iteration's spectral-trim
   // decision for the M-step that follows (sigma2 is the same in both)
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !(gate && iteration_gated(st)))
     st->trim_now = trim_active(st) ? 1 : 0;
-  dev::fixB_f32_body(T4, M, Yb, N, X4, Yt4, R4, P1_out, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+  dev::fixB_f32_body(T4, M, Yb, N, X4, Yt4, R4, P1_out, flag_rows, st, gate, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y,
+                     m_lo, m_hi);
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -215,12 +218,48 @@ EstepPlan plan_estep(int64_t M, int64_t N, bool fp64, int sms, bool with_pruned,
   return p;
 }
 
+int split_rows(int64_t M, int pieces, int* m0, int* rows) {
+  const int64_t tile = (int64_t)kThreadsB * kRowsB32;
+  const int64_t tiles = cdiv(M, tile);
+  const int n = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)pieces, tiles, (int64_t)kMaxPieces}));
+  int64_t start = 0;
+  for (int i = 0; i < n; ++i) {
+    const int64_t t1 = tiles * (i + 1) / n;          // tiles [t0, t1) of piece i
+    const int64_t end = std::min(M, t1 * tile);
+    m0[i] = (int)start;
+    rows[i] = (int)(end - start);
+    start = end;
+  }
+  return n;
+}
+
+// Each piece's pass B fills the GPU on its own (same rule as plan_estep):
+// fewer row tiles per piece, so more scene-point chunks.
+void plan_estep_pieces(EstepPlan& p, int64_t N, int sms, int pieces, const int* m0, const int* rows) {
+  int occB = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, passB_f32, kThreadsB, 0);
+  const int64_t slotsB = (int64_t)sms * std::max(occB, 1);
+  const int64_t rowsB = (int64_t)kThreadsB * kRowsB32;
+  p.n_pieces = pieces;
+  for (int i = 0; i < pieces; ++i) {
+    BPiece& b = p.piece[i];
+    b.m0 = m0[i];
+    b.rows = rows[i];
+    b.row_tiles = (int)cdiv(b.rows, rowsB);
+    const int64_t want = std::max<int64_t>(1, slotsB / b.row_tiles);
+    b.cols_per_chunk = (int)std::max<int64_t>(32, cdiv(N, want));
+    b.col_chunks = (int)cdiv(N, b.cols_per_chunk);
+    b.red_blocks = (int)cdiv(b.rows, kRedRows);
+    p.partB_elems = std::max(p.partB_elems, (int64_t)5 * b.col_chunks * b.rows);
+  }
+}
+
 template <typename F>
 void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
-                  bool gate, cudaStream_t s, cudaEvent_t* ev, const EstepSide* side) {
+                  bool gate, cudaStream_t s, cudaEvent_t* ev, const EstepSide* side, const EstepPieces* pieces) {
   const int g = gate ? 1 : 0;
   const int defer = side ? 1 : 0;
   dim3 ga(pl.a_col_tiles, pl.a_row_chunks);
@@ -251,7 +290,23 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   }
   record_after(ev, 1, s);
   if constexpr (sizeof(F) == 4) {
-    passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g);
+    if (pieces && side && pl.n_pieces > 1 && !pl.pruned && !pl.mma) {
+      // pass B in row pieces; the caller enqueues each piece's projection
+      // and joins the side stream
+      for (int i = 0; i < pl.n_pieces; ++i) {
+        const BPiece& b = pl.piece[i];
+        passB_f32<<<dim3(b.row_tiles, b.col_chunks), kThreadsB, 0, s>>>(T4 + b.m0, b.rows, Yb, (int)N,
+                                                                        b.cols_per_chunk, partB, st, g, i == 0);
+        reduceB<F><<<(unsigned)b.red_blocks, kThreadsR, 0, s>>>(
+            partB, b.col_chunks, b.col_chunks, b.col_chunks, b.rows, X4 + b.m0, Yt4 + b.m0, R4 + b.m0,
+            P1_out ? P1_out + b.m0 : nullptr, sums, flag_rows, st, g, 1, b.m0);
+        fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g, b.m0,
+                                           b.m0 + b.rows);
+        pieces->after_piece(pieces->user, i);
+      }
+      return;
+    }
+    passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g, 1);
     if (pl.pruned)
       passB_f32_pruned<<<dim3(pl.pb_row_tiles, pl.pb_col_chunks), kThreadsB, 0, s>>>(
           T4, (int)M, Yb, (int)N, pl.pb_cols_per_chunk, partB, st, g);
@@ -261,9 +316,10 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   }
   record_after(ev, 2, s);
   reduceB<F><<<(unsigned)pl.redB_blocks, kThreadsR, 0, s>>>(partB, pl.b_col_chunks, pl.pb_col_chunks, pl.mm.b_chunks, (int)M, X4,
-                                                            Yt4, R4, P1_out, sums, flag_rows, st, g, defer);
+                                                            Yt4, R4, P1_out, sums, flag_rows, st, g, defer, 0);
   if constexpr (sizeof(F) == 4) {
-    fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g);
+    fixB_f32<<<304, kThreadsF, 0, s>>>(T4, (int)M, Yb, (int)N, X4, Yt4, R4, P1_out, flag_rows, st, g, 0,
+                                       0x7fffffff);
   }
   if (side) cudaStreamWaitEvent(s, side->join, 0);
   record_after(ev, 3, s);
@@ -271,9 +327,11 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
 
 template void launch_estep<float>(const EstepPlan&, const float4*, const float4*, int64_t, const float4*,
                                   float4*, int64_t, float*, float*, double*, int*, float4*, float4*, double*,
-                                  double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*);
+                                  double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*,
+                                  const EstepPieces*);
 template void launch_estep<double>(const EstepPlan&, const dvec4*, const dvec4*, int64_t, const dvec4*,
                                    dvec4*, int64_t, double*, double*, double*, int*, dvec4*, dvec4*, double*,
-                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*);
+                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*,
+                                   const EstepPieces*);
 
 }  // namespace fcpd

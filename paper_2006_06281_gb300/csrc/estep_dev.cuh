@@ -879,10 +879,13 @@ template <typename F>
 // Returns true in the block that completed the reduction over all gx blocks.
 // skip_vsum: the EM iterations, which do not use the Eq. 18 sum of V_m / P1_m
 // as such (each row carries its share to the M-step), skip its reduction.
+// m_off: row of the first model point this launch reduces (pass B in row
+// pieces: X4, Yt4, R4 and P1_out start at that row); the flagged-row list
+// holds rows of the whole model.
 __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int chunks, int M, const typename Vec<F>::t4* FCPD_RESTRICT X4,
         typename Vec<F>::t4* FCPD_RESTRICT Yt4, typename Vec<F>::t4* FCPD_RESTRICT R4,
         double* FCPD_RESTRICT P1_out, double* FCPD_RESTRICT sums, int* FCPD_RESTRICT flag_rows,
-        DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy, int skip_vsum = 0) {
+        DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy, int skip_vsum = 0, int m_off = 0) {
   if (gate && iteration_gated(st)) return false;
   __shared__ double sh[32];
   __shared__ F part[kRedRowSub][5][kRedRows];
@@ -916,7 +919,7 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
     double p1 = f1, px = fx, py = fy, pz = fz, v = fv;
     if constexpr (sizeof(F) == 4) {
       if (!(p1 >= kRowFloor) || !isfinite(p1)) {
-        flag_rows[atomicAdd(&st->n_flag_rows, 1)] = m;
+        flag_rows[atomicAdd(&st->n_flag_rows, 1)] = m + m_off;
       } else {
         const float qi = 1.0f / scale_q(st->sigma2);
         write_row<F>(m, p1, px, py, pz, v, (double)qi, (double)qi * (double)qi, xm, Yt4, R4, &vrow);
@@ -956,9 +959,12 @@ __device__ __forceinline__ bool reduceB_body(const F* FCPD_RESTRICT partB, int c
 // Exact FP32 rows in the log domain for the listed rows: with
 // a = max_n (lid_n - d'^2_mn), every sum is taken over 2^(lid_n - d'^2 - a);
 // the Eq. 5 ratios do not depend on the shift, and P1_m = 2^a * sum.
+// Only listed rows in [m_lo, m_hi) are taken (pass B in row pieces: each
+// piece's fix-up leaves the rows of the other pieces alone).
 __device__ __forceinline__ void fixB_f32_body(const float4* FCPD_RESTRICT T4, int M, const float4* FCPD_RESTRICT Yb, int N,
          const float4* FCPD_RESTRICT X4, float4* FCPD_RESTRICT Yt4, float4* FCPD_RESTRICT R4,
-         double* FCPD_RESTRICT P1_out, const int* FCPD_RESTRICT flag_rows, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy) {
+         double* FCPD_RESTRICT P1_out, const int* FCPD_RESTRICT flag_rows, DevState* FCPD_RESTRICT st, int gate, int bx, int by, int gx, int gy,
+         int m_lo = 0, int m_hi = 0x7fffffff) {
   if (gate && iteration_gated(st)) return;
   const int count = st->n_flag_rows;
   if (count == 0) return;
@@ -967,6 +973,7 @@ __device__ __forceinline__ void fixB_f32_body(const float4* FCPD_RESTRICT T4, in
   const int nwarps = gx * (kThreadsF / 32);
   for (int j = bx * (kThreadsF / 32) + (threadIdx.x >> 5); j < count; j += nwarps) {
     const int m = flag_rows[j];
+    if (m < m_lo || m >= m_hi) continue;     // another piece's row (same for the whole warp)
     const float4 t = T4[m];
     const float tx = q * t.x, ty = q * t.y, tz = q * t.z;
     float amax = -INFINITY;

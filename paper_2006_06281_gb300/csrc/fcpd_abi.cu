@@ -144,6 +144,7 @@ struct cpd_ctx {
   cudaStream_t stream = nullptr; // caller's stream
   cudaStream_t cap = nullptr;    // internal stream used only for graph capture
   EstepSide side{};              // captured side branch of each iteration's E-step
+  cudaEvent_t piece_ev[kMaxPieces] = {};   // pass B piece i done: its projection may start (side stream)
   Buf X4, T4, U, Ut, lam, Yt4, R4, B4, C4, Yhat4, W4, hist;
   Buf st, st_aux;
   Buf Y4, Yb, partA, partB, partP, sums, flags, stage;
@@ -181,6 +182,8 @@ struct cpd_ctx {
     if (side.s) cudaStreamDestroy(side.s);
     if (side.fork) cudaEventDestroy(side.fork);
     if (side.join) cudaEventDestroy(side.join);
+    for (cudaEvent_t e : piece_ev)
+      if (e) cudaEventDestroy(e);
   }
   void drop_graphs() {
     for (auto& g : graph)
@@ -287,6 +290,28 @@ cpd_status sort_points(cpd_ctx* c, void* pts4, int64_t n, int* perm) {
 // E-step layout control of the context for the current scene: pruning
 // (spatially ordered points) and, in the mixed-precision mode, the
 // tensor-core passes with their sigma2 floor from the current points.
+// Pass B in row pieces beside the projection (see after_piece): FP32 with a
+// wide FP32 basis, no spatial order and no spectral trim; 3 pieces from
+// kSplitMinM model points (measured at M = N = 20000, full basis: 1291 EM
+// it/s in one piece, 1334 in 2, 1352 in 3).  FCPD_SPLIT_B sets the number
+// of pieces (1: off).
+constexpr int kSplitPieces = 3;
+constexpr int64_t kSplitMinM = 8192;
+int pieces_wanted(int64_t M) {
+  const char* v = std::getenv("FCPD_SPLIT_B");
+  if (v && *v) return std::atoi(v);
+  return M >= kSplitMinM ? kSplitPieces : 1;
+}
+void plan_pieces(cpd_ctx* c) {
+  c->mp.n_pieces = 0;
+  if (c->fp64 || c->half_basis || c->sorted_model || c->k_cap > 0) return;
+  const int want = pieces_wanted(c->M);
+  if (want < 2) return;
+  int m0[kMaxPieces], rows[kMaxPieces];
+  const int n = split_rows(c->M, want, m0, rows);
+  if (n >= 2) plan_mstep_pieces(c->mp, c->M, c->sms, n, m0, rows);
+}
+
 void apply_prune(cpd_ctx* c) {
   int ctl = 0;
   if (c->sorted_model && c->scene_sorted) {
@@ -484,7 +509,8 @@ cpd_status read_state(cpd_ctx* c, DevState* h) {
 
 // M-step launches of an FP32-point context, for either basis storage.
 void mstep_f32(cpd_ctx* c, const float4* R4, const float4* Yt4, float4* T4, const float4* Yhat4, float4* B4,
-               float4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+               float4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev = nullptr,
+               bool projected = false) {
   const MstepPlan* trim = iteration && c->k_cap > 0 ? &c->mp_trim : nullptr;
   if (c->half_basis)
     launch_mstep<float, __half>(c->mp, c->U.as<__half>(), c->Ut.as<__half>(), c->lam.as<double>(), c->M, c->K,
@@ -493,7 +519,27 @@ void mstep_f32(cpd_ctx* c, const float4* R4, const float4* Yt4, float4* T4, cons
   else
     launch_mstep<float>(c->mp, c->U.as<float>(), c->Ut.as<float>(), c->lam.as<double>(), c->M, c->K,
                         c->X4.as<float4>(), R4, Yt4, T4, Yhat4, c->partP.as<float>(), c->sums.as<double>(), B4, C4,
-                        st, iteration, s, ev, trim);
+                        st, iteration, s, ev, trim, projected);
+}
+
+// Pass B in row pieces: once piece i's rows of R are enqueued, their share
+// of the projection U^T R follows -- on the side stream for every piece but
+// the last, so that it streams U while the next piece's pass B computes.
+struct PieceLaunch {
+  cpd_ctx* c;
+  cudaStream_t s;
+  DevState* st;
+};
+void after_piece(void* user, int i) {
+  const PieceLaunch* pl = static_cast<const PieceLaunch*>(user);
+  cpd_ctx* c = pl->c;
+  cudaStream_t ps = pl->s;
+  if (i + 1 < c->mp.n_pieces) {
+    cudaEventRecord(c->piece_ev[i], pl->s);
+    cudaStreamWaitEvent(c->side.s, c->piece_ev[i], 0);
+    ps = c->side.s;
+  }
+  launch_projection_piece(c->mp, i, c->U.as<float>(), c->R4.as<float4>(), c->partP.as<float>(), pl->st, ps);
 }
 
 void w_f32(cpd_ctx* c, const float4* C4, float4* W4, cudaStream_t s) {
@@ -521,6 +567,18 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
                          c->X4.as<dvec4>(), c->R4.as<dvec4>(), c->Yt4.as<dvec4>(), c->T4.as<dvec4>(),
                          c->has_gt ? c->Yhat4.as<dvec4>() : nullptr, c->partP.as<double>(), c->sums.as<double>(),
                          c->B4.as<dvec4>(), c->C4.as<dvec4>(), st, true, s, em);
+  } else if (!ev && c->ep.n_pieces > 1 && c->ep.n_pieces == c->mp.n_pieces) {
+    PieceLaunch pl{c, s, st};
+    const EstepPieces hook{&after_piece, &pl};
+    launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
+                        c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
+                        c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, nullptr, &c->side,
+                        &hook);
+    cudaEventRecord(c->side.join, c->side.s);       // log-likelihood and the side projections
+    cudaStreamWaitEvent(s, c->side.join, 0);
+    mstep_f32(c, c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
+              c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->B4.as<float4>(), c->C4.as<float4>(), st, true, s,
+              nullptr, true);
   } else {
     launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
                         c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
@@ -586,6 +644,8 @@ cpd_status ensure_scene(cpd_ctx* c, int64_t N) {
   if (N == c->N) return CPD_OK;
   c->drop_graphs();
   c->ep = plan_estep(c->M, N, c->fp64, c->sms, c->sorted_model, c->half_basis);
+  if (c->mp.n_pieces > 1 && !c->ep.pruned && !c->ep.mma)
+    plan_estep_pieces(c->ep, N, c->sms, c->mp.n_pieces, c->mp.pp_m0, c->mp.pp_rows);
   STATUS_TRY(c->Y4.ensure((size_t)N * c->v4));
   STATUS_TRY(c->Yb.ensure((size_t)N * c->v4));
   STATUS_TRY(c->partA.ensure((size_t)c->ep.partA_elems * c->es));
@@ -738,6 +798,9 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
       cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(CPD_ECUDA, "cannot create the capture streams"));
+  for (cudaEvent_t& e : c->piece_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(CPD_ECUDA, "cannot create the capture events"));
 
   cpd_status s;
   if ((s = c->X4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
@@ -853,6 +916,7 @@ cpd_status cpd_setup(const void* X, int64_t M, const cpd_params* p, void* stream
   free_top();
   free_setup();
   if ((p->flags & CPD_FLAG_SPECTRAL_TRIM) && (s = plan_trim(c)) != CPD_OK) return bail(s);
+  plan_pieces(c);
 
   if ((s = c->Yt4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
   if ((s = c->R4.ensure((size_t)M * c->v4)) != CPD_OK) return bail(s);
@@ -1085,6 +1149,13 @@ cpd_status cpd_iterate_shared(cpd_ctx* c, int32_t n_scenes, const void* const* Y
     const int S = std::min(per_pass, n_scenes - g0);
     STATUS_TRY(shared_group(c, S, Y + g0, N + g0, n_iter, T_out + g0, sigma2_out + g0));
   }
+  return CPD_OK;
+}
+
+cpd_status cpd_pass_b_pieces(cpd_ctx* c, int32_t* pieces) {
+  g_err.clear();
+  if (!c || !pieces) return fail(CPD_EINVAL, "ctx and pieces are required");
+  *pieces = c->mp.n_pieces > 1 ? c->mp.n_pieces : 1;
   return CPD_OK;
 }
 

@@ -479,12 +479,53 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_thread
 
 MstepPlan plan_mstep_trim(const MstepPlan& full, int64_t M, int64_t K_cap, bool fp64, int sms, int basis_bytes) {
   MstepPlan p = full;
+  p.n_pieces = 0;
   const int64_t es = basis_bytes > 0 ? basis_bytes : (fp64 ? 8 : 4);
   const int W = colsum_width(es);
   p.K = K_cap;
   p.ldPp = std::min(full.ldU, cdiv(K_cap, W) * W);
   plan_products(p, M, K_cap, K_cap, es, sms, W, kThreadsP);
   return p;
+}
+
+// Each piece's projection is planned like a whole one over its rows (one
+// resident wave when it runs alone); its partial rows follow the previous
+// pieces', so the diagonal update sums them all in one launch.
+bool plan_mstep_pieces(MstepPlan& p, int64_t M, int sms, int pieces, const int* m0, const int* rows) {
+  if (!p.bulk || pieces < 2 || pieces > kMaxPieces || p.K <= kRowsMaxK) return false;
+  const int64_t slots = bulk_slots<float, float>(sms);
+  // the pieces that run beside pass B: one block per SM, which fits beside
+  // two pass B blocks (registers exactly, shared memory with room); planned
+  // for two per SM, a side projection that reached the SMs first left room
+  // for one pass B block and the split was slower than one piece
+  const int64_t side_slots = std::min<int64_t>(slots, (int64_t)sms);
+  int off = 0, tiles = 0;
+  for (int i = 0; i < pieces; ++i) {
+    if (rows[i] < 1 || m0[i] < 0 || (int64_t)m0[i] + rows[i] > M) return false;
+    int ch = 0, rpc = 0;
+    plan_colsum_bulk(rows[i], p.ldPp, i + 1 < pieces ? side_slots : slots, BulkGeom<float>::COLS,
+                     BulkGeom<float>::ROWS, tiles, ch, rpc);
+    p.pp_m0[i] = m0[i];
+    p.pp_rows[i] = rows[i];
+    p.pp_chunks[i] = ch;
+    p.pp_rpc[i] = rpc;
+    p.pp_off[i] = off;
+    off += ch;
+  }
+  if (tiles != p.p_col_tiles) return false;
+  p.n_pieces = pieces;
+  p.pp_chunks_total = off;
+  p.part_elems = std::max(p.part_elems, (int64_t)off * 3 * p.ldPp);
+  return true;
+}
+
+void launch_projection_piece(const MstepPlan& pl, int piece, const float* U, const float4* R4, float* part,
+                             DevState* st, cudaStream_t s) {
+  const int64_t m0 = pl.pp_m0[piece];
+  colsum_bulk<float, float><<<dim3(pl.p_col_tiles, pl.pp_chunks[piece]), BulkGeom<float>::THREADS,
+                              bulk_smem_bytes<float, float>(), s>>>(
+      U + m0 * pl.ldU, pl.ldU, pl.pp_rows[piece], (int)pl.K, R4 + m0, pl.pp_rpc[piece],
+      part + (size_t)pl.pp_off[piece] * 3 * pl.ldPp, pl.ldPp, st, 1, 0, 0);
 }
 
 // Partials of A^T V over the plan's grid (colsum or colsum_bulk); ldP: row
@@ -544,15 +585,19 @@ void launch_mstep(const MstepPlan& pl, const S* U, const S* Ut, const double* la
                   const typename Vec<F>::t4* Yt4, typename Vec<F>::t4* T4,
                   const typename Vec<F>::t4* Yhat4, F* part, double* sums, typename Vec<F>::t4* B4,
                   typename Vec<F>::t4* C4, DevState* st, bool iteration, cudaStream_t s, cudaEvent_t* ev,
-                  const MstepPlan* trim) {
+                  const MstepPlan* trim, bool projected) {
   const int g = iteration ? 1 : 0;
   const MstepPlan* tr = iteration ? trim : nullptr;
   const int mf = tr ? 1 : 0;      // the full M-step's trim mode
-  if (tr) launch_colsum<F, S>(*tr, false, U, tr->ldU, tr->ldPp, M, tr->K, R4, part, st, g, g, 2, s);
-  launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
+  projected = projected && iteration && !tr && pl.n_pieces > 1;
+  if (!projected) {
+    if (tr) launch_colsum<F, S>(*tr, false, U, tr->ldU, tr->ldPp, M, tr->K, R4, part, st, g, g, 2, s);
+    launch_colsum<F, S>(pl, false, U, pl.ldU, pl.ldPp, M, K, R4, part, st, g, g, mf, s);
+  }
   record_after(ev, 0, s);
   if (tr) launch_diag<F>(part, tr->p_row_chunks, tr->ldPp, (int)tr->K, (int)K, lam, B4, C4, st, g, 2, s);
-  launch_diag<F>(part, pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st, g, mf, s);
+  launch_diag<F>(part, projected ? pl.pp_chunks_total : pl.p_row_chunks, pl.ldPp, (int)K, (int)K, lam, B4, C4, st,
+                 g, mf, s);
   record_after(ev, 1, s);
   // narrow bases (FP32 working precision, iterations): the row expansion
   // with its epilogue replaces colsum (U^T) + expand_finish
@@ -592,15 +637,15 @@ void launch_w(const MstepPlan& pl, const S* Ut, int64_t M, int64_t K, const type
 template void launch_mstep<float, float>(const MstepPlan&, const float*, const float*, const double*, int64_t,
                                          int64_t, const float4*, const float4*, const float4*, float4*,
                                          const float4*, float*, double*, float4*, float4*, DevState*, bool,
-                                         cudaStream_t, cudaEvent_t*, const MstepPlan*);
+                                         cudaStream_t, cudaEvent_t*, const MstepPlan*, bool);
 template void launch_mstep<double, double>(const MstepPlan&, const double*, const double*, const double*, int64_t,
                                            int64_t, const dvec4*, const dvec4*, const dvec4*, dvec4*, const dvec4*,
                                            double*, double*, dvec4*, dvec4*, DevState*, bool, cudaStream_t,
-                                           cudaEvent_t*, const MstepPlan*);
+                                           cudaEvent_t*, const MstepPlan*, bool);
 template void launch_mstep<float, __half>(const MstepPlan&, const __half*, const __half*, const double*, int64_t,
                                           int64_t, const float4*, const float4*, const float4*, float4*,
                                           const float4*, float*, double*, float4*, float4*, DevState*, bool,
-                                          cudaStream_t, cudaEvent_t*, const MstepPlan*);
+                                          cudaStream_t, cudaEvent_t*, const MstepPlan*, bool);
 template void launch_w<float, float>(const MstepPlan&, const float*, int64_t, int64_t, const float4*, float*,
                                      float4*, DevState*, cudaStream_t);
 template void launch_w<double, double>(const MstepPlan&, const double*, int64_t, int64_t, const dvec4*, double*,

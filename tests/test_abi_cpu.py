@@ -89,6 +89,7 @@ def test_get_trim_rejects_null_arguments(lib):
     k = C.c_int64()
     n = C.c_int32()
     assert lib.cpd_get_trim(None, C.byref(k), C.byref(n)) == cpd.EINVAL
+    assert lib.cpd_pass_b_pieces(None, C.byref(n)) == cpd.EINVAL
 
 
 def test_setup_rejects_bad_shapes(lib):
