@@ -1051,9 +1051,12 @@ def main():
     # per iteration: pass A, reduce A, fix A, the log-likelihood total (side
     # branch), then per pass B piece pass B, reduce B, fix B and its share of
     # the projection, then the diagonal update, expansion, expansion finish
-    # (T, Eq. 18); per registration: scene packing, state init, initial
-    # variance, E-step layout control, iteration target
-    launches = (7 + 4 * pieces) * steps + 5 * R
+    # (T, Eq. 18).  The iterations that carry timing events (every 10th and
+    # the last of a registration) run pass B and the projection whole: 11.
+    # Per registration: scene packing, state init, initial variance, E-step
+    # layout control, iteration target.
+    timed_iters = sum(1 for i in range(I) if i % 10 == 0 or i == I - 1)
+    launches = R * (11 * timed_iters + (7 + 4 * pieces) * (I - timed_iters)) + 5 * R
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=steps, warmup=warm,
