@@ -401,13 +401,13 @@ struct EstepSide {
 // With `pieces` (FP32 iterations with `side`, plan with n_pieces > 1) pass B
 // runs piece by piece and after_piece(user, i) is called once piece i's rows
 // of Yt4 / R4 are enqueued on `s`; the side stream is then left for the
-// caller to join.
+// caller to join.  Returns true when pass B ran in pieces.
 struct EstepPieces {
   void (*after_piece)(void* user, int piece);
   void* user;
 };
 template <typename F>
-void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
+bool launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,

@@ -255,7 +255,7 @@ void plan_estep_pieces(EstepPlan& p, int64_t N, int sms, int pieces, const int* 
 }
 
 template <typename F>
-void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
+bool launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const typename Vec<F>::t4* X4,
                   int64_t M, const typename Vec<F>::t4* Y4, typename Vec<F>::t4* Yb, int64_t N,
                   F* partA, F* partB, double* sums, int* flags, typename Vec<F>::t4* Yt4,
                   typename Vec<F>::t4* R4, double* P1_out, double* den_out, DevState* st,
@@ -304,7 +304,7 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
                                            b.m0 + b.rows);
         pieces->after_piece(pieces->user, i);
       }
-      return;
+      return true;
     }
     passB_f32<<<gb, kThreadsB, 0, s>>>(T4, (int)M, Yb, (int)N, pl.b_cols_per_chunk, partB, st, g, 1);
     if (pl.pruned)
@@ -323,13 +323,14 @@ void launch_estep(const EstepPlan& pl, const typename Vec<F>::t4* T4, const type
   }
   if (side) cudaStreamWaitEvent(s, side->join, 0);
   record_after(ev, 3, s);
+  return false;
 }
 
-template void launch_estep<float>(const EstepPlan&, const float4*, const float4*, int64_t, const float4*,
+template bool launch_estep<float>(const EstepPlan&, const float4*, const float4*, int64_t, const float4*,
                                   float4*, int64_t, float*, float*, double*, int*, float4*, float4*, double*,
                                   double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*,
                                   const EstepPieces*);
-template void launch_estep<double>(const EstepPlan&, const dvec4*, const dvec4*, int64_t, const dvec4*,
+template bool launch_estep<double>(const EstepPlan&, const dvec4*, const dvec4*, int64_t, const dvec4*,
                                    dvec4*, int64_t, double*, double*, double*, int*, dvec4*, dvec4*, double*,
                                    double*, DevState*, bool, cudaStream_t, cudaEvent_t*, const EstepSide*,
                                    const EstepPieces*);

@@ -570,15 +570,18 @@ void enqueue_iteration(cpd_ctx* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   } else if (!ev && c->ep.n_pieces > 1 && c->ep.n_pieces == c->mp.n_pieces) {
     PieceLaunch pl{c, s, st};
     const EstepPieces hook{&after_piece, &pl};
-    launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
-                        c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
-                        c->Yt4.as<float4>(), c->R4.as<float4>(), nullptr, nullptr, st, true, s, nullptr, &c->side,
-                        &hook);
-    cudaEventRecord(c->side.join, c->side.s);       // log-likelihood and the side projections
-    cudaStreamWaitEvent(s, c->side.join, 0);
+    const bool split = launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(),
+                                           c->Yb.as<float4>(), c->N, c->partA.as<float>(), c->partB.as<float>(),
+                                           c->sums.as<double>(), c->flags.as<int>(), c->Yt4.as<float4>(),
+                                           c->R4.as<float4>(), nullptr, nullptr, st, true, s, nullptr, &c->side,
+                                           &hook);
+    if (split) {
+      cudaEventRecord(c->side.join, c->side.s);     // log-likelihood and the side projections
+      cudaStreamWaitEvent(s, c->side.join, 0);
+    }
     mstep_f32(c, c->R4.as<float4>(), c->Yt4.as<float4>(), c->T4.as<float4>(),
               c->has_gt ? c->Yhat4.as<float4>() : nullptr, c->B4.as<float4>(), c->C4.as<float4>(), st, true, s,
-              nullptr, true);
+              nullptr, split);
   } else {
     launch_estep<float>(c->ep, c->T4.as<float4>(), c->X4.as<float4>(), c->M, c->Y4.as<float4>(), c->Yb.as<float4>(),
                         c->N, c->partA.as<float>(), c->partB.as<float>(), c->sums.as<double>(), c->flags.as<int>(),
