@@ -737,6 +737,20 @@ def timing_helpers(world, device):
     return barrier, allmax
 
 
+def timed_launches(iters, registrations, pieces):
+    """This library's kernel launches in the timed region: R registrations of
+    `iters` iterations, replayed from the graph with timing events.  Per
+    iteration: pass A, reduce A, fix A, the log-likelihood total (side
+    branch), then per pass B piece pass B, reduce B, fix B and its share of
+    the projection, then the diagonal update, expansion and expansion finish
+    (T, Eq. 18).  The iterations that carry the events (every 10th and the
+    last of a registration) run pass B and the projection whole: 11.  Per
+    registration: scene packing, state init, initial variance, E-step layout
+    control, iteration target."""
+    evented = sum(1 for i in range(iters) if i % 10 == 0 or i == iters - 1)
+    return registrations * (11 * evented + (7 + 4 * pieces) * (iters - evented) + 5)
+
+
 def rank_seed(cfg, rank):
     """Each rank registers its own pair: the workload's seed offset by the rank."""
     return cfg["seed"] + rank
@@ -1048,15 +1062,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle(ps, cfg, M, N, K)
-    # per iteration: pass A, reduce A, fix A, the log-likelihood total (side
-    # branch), then per pass B piece pass B, reduce B, fix B and its share of
-    # the projection, then the diagonal update, expansion, expansion finish
-    # (T, Eq. 18).  The iterations that carry timing events (every 10th and
-    # the last of a registration) run pass B and the projection whole: 11.
-    # Per registration: scene packing, state init, initial variance, E-step
-    # layout control, iteration target.
-    timed_iters = sum(1 for i in range(I) if i % 10 == 0 or i == I - 1)
-    launches = R * (11 * timed_iters + (7 + 4 * pieces) * (I - timed_iters)) + 5 * R
+    launches = timed_launches(I, R, pieces)
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=steps, warmup=warm,

@@ -67,3 +67,12 @@ def test_traffic_is_reported_only_for_the_recorded_workload_and_source():
 def test_job_rate_is_all_ranks_steps_over_the_slowest_rank():
     assert bench.job_rate(100, 1, 50.0) == pytest.approx(2000.0)
     assert bench.job_rate(100, 4, 200.0) == pytest.approx(2000.0)
+
+
+def test_timed_launch_count():
+    # one piece: 11 launches per iteration + 5 per registration
+    assert bench.timed_launches(100, 30, 1) == 30 * (100 * 11 + 5)
+    # 3 pieces: 19 per iteration except the 11 evented ones (0, 10, .., 90, 99)
+    assert bench.timed_launches(100, 30, 3) == 30 * (11 * 11 + 19 * 89 + 5) == 54510
+    # a registration of 1 iteration: that iteration carries the events
+    assert bench.timed_launches(1, 4, 3) == 4 * (11 + 5)
