@@ -287,9 +287,6 @@ cpd_status sort_points(cpd_ctx* c, void* pts4, int64_t n, int* perm) {
   return CPD_OK;
 }
 
-// E-step layout control of the context for the current scene: pruning
-// (spatially ordered points) and, in the mixed-precision mode, the
-// tensor-core passes with their sigma2 floor from the current points.
 // Pass B in row pieces beside the projection (see after_piece): FP32 with a
 // wide FP32 basis, no spatial order and no spectral trim; 3 pieces from
 // kSplitMinM model points (measured at M = N = 20000, full basis: 1291 EM
@@ -312,6 +309,9 @@ void plan_pieces(cpd_ctx* c) {
   if (n >= 2) plan_mstep_pieces(c->mp, c->M, c->sms, n, m0, rows);
 }
 
+// E-step layout control of the context for the current scene: pruning
+// (spatially ordered points) and, in the mixed-precision mode, the
+// tensor-core passes with their sigma2 floor from the current points.
 void apply_prune(cpd_ctx* c) {
   int ctl = 0;
   if (c->sorted_model && c->scene_sorted) {
