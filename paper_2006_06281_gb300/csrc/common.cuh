@@ -304,8 +304,9 @@ MstepPlan plan_mstep(int64_t M, int64_t K, bool fp64, int sms, int colsum_thread
 // out by `full` (same row strides).
 MstepPlan plan_mstep_trim(const MstepPlan& full, int64_t M, int64_t K_cap, bool fp64, int sms, int basis_bytes);
 // Projection grids of row pieces (FP32 basis streamed by colsum_bulk, wide
-// bases only); enlarges part_elems.  False (plan unchanged) where the plan
-// cannot be split.
+// bases only): the last piece, which runs alone, gets one resident wave; the
+// others one block per SM, the room left beside two pass B blocks.
+// Enlarges part_elems.  False (no pieces) where the plan cannot be split.
 bool plan_mstep_pieces(MstepPlan& p, int64_t M, int sms, int pieces, const int* m0, const int* rows);
 
 // ------------------------------------------------------------ batched mode
